@@ -1,0 +1,47 @@
+"""The seeded generators are deterministic and produce the stated shapes."""
+import numpy as np
+
+from oracle import hugin
+from paper_1202_3777_gb300 import synth
+
+
+def test_deterministic_by_seed():
+    a, b = synth.batched_tree(), synth.batched_tree()
+    assert np.array_equal(a.pot, b.pot) and np.array_equal(a.parent, b.parent)
+    assert all(np.array_equal(x, y) for x, y in zip(a.cliques, b.cliques))
+    c = synth.batched_tree(seed=7)
+    assert not np.array_equal(a.parent, c.parent)
+    e1 = synth.evidence_matrix(a, 8, 0.1, 55)
+    e2 = synth.evidence_matrix(a, 8, 0.1, 55)
+    assert np.array_equal(e1, e2)
+    # case i depends only on base_seed + i
+    assert np.array_equal(synth.evidence_matrix(a, 3, 0.1, 56)[0], e1[1])
+
+
+def test_shapes_of_the_workloads():
+    t = synth.small_tree()
+    assert t.n_cliques == 32 and all(len(c) == 5 for c in t.cliques)
+    assert set(t.card.tolist()) == {3} and t.n_vars == 5 + 31 * 3
+    for c in range(1, 32):
+        assert len(hugin.separator(t.cliques[c], t.cliques[t.parent[c]])) == 2
+    t = synth.batched_tree()
+    sizes = t.table_sizes()
+    assert t.n_cliques == 256 and sizes.min() >= 64 and sizes.max() <= 4 ** 9
+    for c in range(1, t.n_cliques):
+        s = len(hugin.separator(t.cliques[c], t.cliques[t.parent[c]]))
+        assert 1 <= s <= 5 and s <= len(t.cliques[c]) - 1
+    t = synth.binary_serving_tree()
+    assert t.n_cliques == 1024 and set(t.card.tolist()) == {2}
+    assert all(3 <= len(c) <= 6 for c in t.cliques)
+    ev = synth.evidence_matrix(t, 16, (0.01, 0.2), 3)
+    frac = (ev >= 0).mean(axis=1)
+    assert frac.min() >= 0.005 and frac.max() <= 0.205
+
+
+def test_large_clique_structure_small_variant():
+    t = synth.large_clique_tree(n_cliques=16, n_vars_per=6, card=4, max_depth=3)
+    assert t.depth().max() <= 3
+    for c in range(1, t.n_cliques):
+        s = len(hugin.separator(t.cliques[c], t.cliques[t.parent[c]]))
+        assert 4 <= s <= 6
+    hugin.validate(t.card, t.cliques, t.parent)
