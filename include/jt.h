@@ -1,0 +1,200 @@
+/*
+ * jt.h -- C ABI of the GB300 junction-tree belief-propagation library (libjt).
+ *
+ * The library computes every Hugin message of a full collect-then-distribute
+ * propagation on the GPU: marginalise a clique onto its separator (Eq. 2),
+ * form the new/old separator ratio with 0/0 := 0 (Eq. 3 and the rule stated
+ * after it), and scatter-multiply that ratio into the neighbouring clique
+ * (Eq. 1, Sec. 3).  The schedule is Algorithm 4: collect towards the root
+ * (Algorithm 2), then distribute from it (Algorithm 3); independent cliques
+ * of one tree depth run concurrently (the breadth-first traversal the paper
+ * allows in Sec. 3.3).  Many evidence cases of one resident tree are
+ * propagated together.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a jt_status; nothing aborts or throws across
+ *     the ABI.  jt_last_error() gives a human-readable reason for the last
+ *     failure on the calling thread.
+ *   - The caller owns every pointer it passes; the library copies what it
+ *     needs before returning (except where an entry point says it enqueues
+ *     an asynchronous copy).
+ *   - A stream is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  It may be a stream owned by another framework
+ *     (for example torch.cuda.current_stream().cuda_stream).
+ *   - Table layout: a clique's table lists its variables in the order given
+ *     in clique_vars; the first-listed variable is the most significant
+ *     digit of the flat index and the last-listed varies fastest (the layout
+ *     of Fig. 2: for {A,B,D}, B = 0 selects entries {0,1,4,5}).
+ *   - A tree is used by one host thread at a time; different trees are
+ *     independent.
+ */
+#ifndef JT_H_
+#define JT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jt_tree_s* jt_tree; /* opaque; owned by the library until jt_free */
+
+typedef enum {
+  JT_OK = 0,
+  JT_ERR_INVALID_ARG = 1,         /* bad pointer, size, id, or non-finite/negative potential */
+  JT_ERR_NOT_A_JUNCTION_TREE = 2, /* not a tree rooted at 0, or running intersection fails */
+  JT_ERR_OOM = 3,                 /* device (or pinned host) allocation failed */
+  JT_ERR_ZERO_EVIDENCE = 4,       /* P(e) = 0 for the queried case: no posterior exists */
+  JT_ERR_TIMEOUT = 5,             /* a bounded device-side wait gave up */
+  JT_ERR_CUDA = 6,                /* any other CUDA runtime error (see jt_last_error) */
+  JT_ERR_STATE = 7,               /* result queried before a propagation covered the case */
+  JT_ERR_UNSUPPORTED = 8          /* valid input outside the library's limits (see jt_last_error) */
+} jt_status;
+
+typedef enum { JT_F32 = 0, JT_F64 = 1 } jt_dtype;
+
+/* jt_tree_desc.flags */
+#define JT_MATERIALIZE_CLIQUES 0x1u /* also write every calibrated clique table per case */
+
+/* Limits (checked by jt_load_tree; JT_ERR_UNSUPPORTED beyond them). */
+#define JT_MAX_CLIQUE_VARS 32       /* variables per clique */
+#define JT_MAX_TABLE_ENTRIES 0x7FFFFFF0LL /* entries of one clique table */
+#define JT_MAX_CARD 32767           /* states of one variable */
+
+/*
+ * A junction tree J = (T, Phi) (Sec. 2.1): cliques C_i with variable sets
+ * X_i and potential tables phi_{X_i}; the separator of the edge between a
+ * clique and its parent is the intersection of their variable sets.
+ */
+typedef struct {
+  int32_t n_vars;               /* variables 0 .. n_vars-1; each must appear in some clique */
+  const int32_t* card;          /* [n_vars] states per variable, 2 <= card <= JT_MAX_CARD */
+  int32_t n_cliques;            /* >= 1 */
+  const int64_t* clique_off;    /* [n_cliques+1] CSR offsets into clique_vars */
+  const int32_t* clique_vars;   /* listed order = table order (first most significant) */
+  const int32_t* parent;        /* [n_cliques] parent[0] = -1 (root = clique 0) */
+  const void* potentials;       /* host; tables concatenated in clique order, >= 0, finite */
+  jt_dtype potentials_dtype;    /* element type of `potentials` */
+  jt_dtype compute;             /* arithmetic type on the device (JT_F32 or JT_F64) */
+  int32_t max_cases;            /* evidence-case slots kept resident, >= 1 */
+  uint32_t flags;               /* JT_MATERIALIZE_CLIQUES, ... */
+} jt_tree_desc;
+
+/*
+ * Validate the tree (Sec. 2.1 structure; running intersection), plan the
+ * device layout, and upload the potentials.  Each clique table is stored
+ * with its variables re-ordered so that its parent-separator variables are
+ * the most significant digits, in `compute` precision.  `stream` orders the
+ * uploads; the call returns after they complete.  All inputs are copied.
+ * On failure *out is set to NULL and nothing is leaked.
+ */
+jt_status jt_load_tree(const jt_tree_desc* desc, void* stream, jt_tree* out);
+
+/*
+ * Replace the evidence of case `case_id` (0 <= case_id < max_cases):
+ * n_obs (variable, state) pairs from host arrays; n_obs = 0 clears it.
+ * A repeated variable, an out-of-range id or state is JT_ERR_INVALID_ARG.
+ * Evidence enters every clique that holds the variable by zeroing the
+ * disagreeing entries (applied on the fly inside the message kernels).
+ */
+jt_status jt_set_evidence(jt_tree t, int32_t case_id, int32_t n_obs,
+                          const int32_t* vars, const int32_t* states);
+
+/*
+ * Dense evidence for cases first_case .. first_case+n_cases-1: `states` is
+ * int16 [n_cases][n_vars], -1 = unobserved.  `on_device` = 0: host memory
+ * (copied before return); 1: device memory (copied asynchronously on
+ * `stream`; the caller keeps it alive until the stream reaches that point).
+ * States are range-checked on the device during propagation; a bad state
+ * marks that case JT_ERR_INVALID_ARG.
+ */
+jt_status jt_set_evidence_dense(jt_tree t, int32_t first_case, int32_t n_cases,
+                                const int16_t* states, int32_t on_device, void* stream);
+
+/*
+ * Belief_Propagation (Algorithm 4) for cases first_case .. first_case+n_cases-1:
+ * collect (Algorithm 2) then distribute (Algorithm 3), every message by
+ * Eq. 1-3, all cases in one CUDA-graph launch.  Asynchronous: only enqueues
+ * work on `stream`.  Per-message rescaling keeps FP32 in range; log Z(e) is
+ * accumulated in FP64.
+ */
+jt_status jt_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* stream);
+
+/*
+ * The propagation of jt_propagate, issued as individual kernel launches
+ * (no graph) with a CUDA event before each launch and after the last one,
+ * for measurement.  Waits for completion and writes the duration of each
+ * launch, in milliseconds, to launch_ms[0 .. *n_launches-1] in issue order:
+ * depth+1 collect levels (deepest first), depth+1 distribute levels (root
+ * first), then the finalisation.  max_launches must be >= 2*(depth+1)+1;
+ * *n_launches is always set.  Results are the same as jt_propagate's.
+ */
+jt_status jt_profile_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* stream,
+                               float* launch_ms, int32_t max_launches, int32_t* n_launches);
+
+/*
+ * P(X = x | e) for variable `var` of case `case_id`: writes card[var]
+ * doubles to host `out`.  Synchronises the stream of the last propagation.
+ * JT_ERR_ZERO_EVIDENCE if P(e) = 0 (out is then filled with NaN),
+ * JT_ERR_STATE if no propagation covered the case since its evidence changed.
+ */
+jt_status jt_get_marginal(jt_tree t, int32_t case_id, int32_t var, double* out);
+
+/*
+ * log Z(e) = log sum_x prod_C phi_C(x_C) prod_{v in E} [x_v = e_v], the log
+ * of P(e) when the potentials are a normalised Bayesian-network
+ * factorisation.  Synchronises like jt_get_marginal; -INFINITY and
+ * JT_ERR_ZERO_EVIDENCE when P(e) = 0.
+ */
+jt_status jt_log_evidence(jt_tree t, int32_t case_id, double* out);
+
+/*
+ * Bulk read-out for cases first_case .. first_case+n_cases-1.
+ * jt_get_marginals: double [n_cases][sum_v card[v]], variable v at offset
+ * sum_{u<v} card[u].  jt_get_log_evidence: double [n_cases].
+ * jt_get_status: int32 [n_cases] per-case jt_status.
+ * `on_device` = 0: `out` is host memory and the call synchronises `stream`;
+ * 1: `out` is device memory and the copy is only enqueued on `stream`.
+ */
+jt_status jt_get_marginals(jt_tree t, int32_t first_case, int32_t n_cases, double* out,
+                           int32_t on_device, void* stream);
+jt_status jt_get_log_evidence(jt_tree t, int32_t first_case, int32_t n_cases, double* out,
+                              int32_t on_device, void* stream);
+jt_status jt_get_status(jt_tree t, int32_t first_case, int32_t n_cases, int32_t* out);
+
+/*
+ * Calibrated table of clique `clique` for case `case_id`, normalised to sum
+ * to one (= P(x_C | e)), in the caller's listed variable order: writes the
+ * clique's table size of doubles to host `out`.  Needs
+ * JT_MATERIALIZE_CLIQUES at load (else JT_ERR_STATE).
+ */
+jt_status jt_get_clique(jt_tree t, int32_t case_id, int32_t clique, double* out);
+
+/* Sizes and schedule facts of a loaded tree. */
+typedef struct {
+  int32_t n_vars, n_cliques, depth;  /* depth = largest clique depth (root 0) */
+  int64_t entries;                   /* sum of clique table sizes */
+  int64_t work_per_case;             /* sum over the 2(n-1) messages of |phi_src| + |phi_dst| (Eq. 4 numerator) */
+  int64_t marginal_len;              /* sum_v card[v] */
+  int64_t device_bytes;              /* device memory held by the tree */
+  int32_t max_cases;
+  jt_dtype compute;
+  uint32_t flags;
+} jt_tree_info;
+
+jt_status jt_get_info(jt_tree t, jt_tree_info* out);
+
+/* Release every resource of the tree (waits for its pending work). NULL is a no-op. */
+void jt_free(jt_tree t);
+
+/* Static string for a status code. */
+const char* jt_strerror(jt_status s);
+
+/* Reason for the last failing call on this thread ("" if none). */
+const char* jt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JT_H_ */

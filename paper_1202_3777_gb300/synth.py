@@ -283,7 +283,7 @@ def binary_serving_tree(seed: int = 1005, n_cliques: int = 1024) -> Tree:
     return _finish(rng, card, cl, par, fr, f"binary-{n_cliques}")
 
 
-def random_small_tree(seed: int, n_cliques: int = 5, max_states: int = 1 << 14,
+def random_small_tree(seed: int, n_cliques: int = 5, max_states: float = 1 << 14,
                       card_range=(2, 5), k_range=(2, 4), allow_empty_sep: bool = False) -> Tree:
     """A random small tree (random cardinalities, separator sizes including
     empty ones if allowed) whose joint has at most ``max_states`` states."""
