@@ -122,13 +122,12 @@ jt_status jt_set_evidence_dense(jt_tree t, int32_t first_case, int32_t n_cases,
 jt_status jt_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* stream);
 
 /*
- * The propagation of jt_propagate, issued as individual kernel launches
- * (no graph) with a CUDA event before each launch and after the last one,
- * for measurement.  Waits for completion and writes the duration of each
- * launch, in milliseconds, to launch_ms[0 .. *n_launches-1] in issue order:
- * depth+1 collect levels (deepest first), depth+1 distribute levels (root
- * first), then the finalisation.  max_launches must be >= 2*(depth+1)+1;
- * *n_launches is always set.  Results are the same as jt_propagate's.
+ * The propagation of jt_propagate, issued without a graph with CUDA events
+ * around its kernels, for measurement.  Waits for completion and writes, in
+ * milliseconds, launch_ms[0] = the propagation kernel (every collect and
+ * distribute message) and launch_ms[1] = the finalisation (marginals and
+ * log Z).  max_launches must be >= 2; *n_launches is always set.  Results are
+ * the same as jt_propagate's.
  */
 jt_status jt_profile_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* stream,
                                float* launch_ms, int32_t max_launches, int32_t* n_launches);

@@ -37,19 +37,26 @@ jt_status cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 constexpr int kCbMax = 8;
+constexpr int kMinStages = 2, kMaxStages = 6;   // bulk-copy ring depth (chunks of 8 KB)
+constexpr int kRowMax = 4096;                   // rows of one slice held in shared memory
+constexpr int kChunkVecs = 2 * kLevelThreads;   // 16-byte vectors per bulk-copy chunk
+constexpr int kTwoPerSm = 112 * 1024;           // dynamic shared memory that leaves room for two CTAs
 constexpr int kWinMax = 4096;     // max parent-separator entries one collect CTA accumulates
 constexpr int kStatusZero = 1, kStatusBadState = 2;
 
-struct LevelSched {
-  LaunchLevel col, dis;
-  std::vector<DevWork> work;
+// The schedule of one case range: shared-memory plan, work items, grid.
+struct Schedule {
+  SmemPlan sp{};
+  int32_t grid = 0;
+  int32_t n_items = 0;
+  DevWork* items = nullptr;       // device
 };
 
 struct GraphEntry {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<void*> dev_bufs;    // work lists owned by this graph
-  std::vector<LevelSched> sched;
+  Schedule sched;
 };
 
 }  // namespace
@@ -70,6 +77,12 @@ struct jt_tree_s {
   DevChild* d_ch = nullptr;
   DevHome* d_hm = nullptr;
   DevSrc* d_src = nullptr;
+  DevSrc* d_jh = nullptr;
+  int32_t* d_cnt = nullptr;
+  VarSrc* d_vs = nullptr;
+  int32_t* d_done = nullptr;      // [2][n_cliques][max_cases] dependency flags + the work-queue counter
+  int32_t* d_parent = nullptr;
+  int32_t* d_err = nullptr;       // set by a kernel whose bounded wait gave up
   DevField* d_fld = nullptr;
   int32_t* d_card = nullptr;
   int32_t* d_moff = nullptr;
@@ -120,7 +133,7 @@ void destroy(jt_tree t) {
   cudaSetDevice(t->device);
   cudaDeviceSynchronize();
   free_graphs(t);
-  void* ptrs[] = {t->base, t->d_cl, t->d_pos, t->d_ch, t->d_hm, t->d_src, t->d_fld, t->d_card, t->d_moff,
+  void* ptrs[] = {t->base, t->d_cl, t->d_pos, t->d_ch, t->d_hm, t->d_src, t->d_jh, t->d_cnt, t->d_vs, t->d_done, t->d_parent, t->d_err, t->d_fld, t->d_card, t->d_moff,
                   t->d_ev, t->d_acc, t->d_ls, t->d_status, t->d_marg, t->d_logz, t->d_calib, t->d_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -134,83 +147,117 @@ void destroy(jt_tree t) {
 // Schedule for a case range: per level, the CTA slices and shared-memory plan.
 // ---------------------------------------------------------------------------
 
-jt_status plan_level(jt_tree t, int d, int n_cases, LevelSched* ls) {
+// Work items and the (uniform) shared-memory plan of one propagation over
+// n_cases cases: every clique table is cut into slices (multiples of the
+// bulk-copy chunk, at most `rowcap` rows, a collect window of at most kWinMax
+// parent-separator entries, about two slices per SM per level); cases are
+// grouped into blocks of cb.  Shared-memory residency, most valuable first:
+// per-slice row sums / row factors and the column joint (touched per entry),
+// then factors and outputs (touched per row), which otherwise stay in global
+// memory.
+jt_status plan_schedule(jt_tree t, int n_cases, Schedule* S, std::vector<DevWork>* items) {
   const Plan& p = t->plan;
-  const auto& cl = p.levels[d];
   const int VEC = (int)(16 / t->elem);
-  int n_child = 0, n_field = 0, n_home = 0, n_src = 0, k = 0, facm = 0, rho = 0, outd = 0, srcacc = 0;
-  int64_t E = 0;
-  bool pow2 = true, vec = true;
-  for (int c : cl) {
+  const int chunk = kChunkVecs * VEC;       // two vectors per consumer thread per chunk
+  int n_child = 0, n_field = 0, n_home = 0, k = 0, facm = 0, rho = 0, outd = 0, jnt = 0;
+  for (int c = 0; c < p.n_cliques; ++c) {
     const DevClique& dc = p.dcl[c];
     n_child = std::max(n_child, dc.n_child);
-    int nf = 0;
-    for (int i = 0; i < dc.n_child; ++i) nf += p.dch[dc.child_first + i].n_field;
-    n_field = std::max(n_field, nf);
+    n_field = std::max(n_field, dc.n_field);
     n_home = std::max(n_home, dc.n_home);
-    n_src = std::max(n_src, dc.n_src);
     k = std::max(k, dc.k);
     facm = std::max(facm, p.fac_collect[c]);
     if (c != 0) rho = std::max(rho, dc.sep_size);
     outd = std::max(outd, p.out_dist[c]);
-    int sa = 0;
-    for (int i = 0; i < dc.n_src; ++i) sa += p.dsrc[dc.src_first + i].card;
-    srcacc = std::max(srcacc, sa);
-    E += dc.n;
-    pow2 = pow2 && dc.pow2;
-    vec = vec && (dc.card_last % VEC == 0);
+    if (dc.joint_off >= 0) jnt = std::max(jnt, dc.P);
   }
-  // case block: as many cases as fit (<= 8); fall back to global factors/outputs
-  auto smem_bytes = [&](int cb, int fac, int out, int rh, int sa) {
-    SmemPlan s{cb, n_child, n_field, n_home, n_src, k, fac, rh, out, sa, 0, 0, (int32_t)t->elem};
-    return SmemLayout(s).bytes;
-  };
   const int budget = t->smem_max;
-  int cb = std::min(kCbMax, std::max(1, n_cases));
-  // tile size: enough CTAs to fill the GPU a few times over
-  const int nb_guess = (n_cases + cb - 1) / cb;
-  const int64_t target = 4ll * t->n_sm;
-  int64_t tiles_wanted = std::max<int64_t>(1, target / std::max(1, nb_guess));
-  int64_t tile = (E + tiles_wanted - 1) / tiles_wanted;
-  tile = std::max<int64_t>(tile, 2048);
-  tile = std::min<int64_t>(tile, 1 << 18);
-  tile = (tile + 255) / 256 * 256;
-  // per-clique tiles (bounded so a collect window stays <= kWinMax)
-  std::vector<int64_t> ctile(cl.size());
-  int win = 1;
-  for (size_t i = 0; i < cl.size(); ++i) {
-    const DevClique& dc = p.dcl[cl[i]];
-    int64_t tc = std::min<int64_t>(tile, (int64_t)(kWinMax - 2) * dc.L);
-    tc = std::max<int64_t>(VEC, tc / VEC * VEC);
-    ctile[i] = tc;
-    int64_t wn = std::min<int64_t>(tc, dc.n) / dc.L + 2;
-    win = (int)std::max<int64_t>(win, std::min<int64_t>(wn, dc.sep_size));
-  }
-  int fac_global = 0, out_global = 0;
-  auto fits_col = [&](int cbv, int fg) { return smem_bytes(cbv, fg ? 0 : facm, win, 0, 0) <= budget; };
-  auto fits_dis = [&](int cbv, int fg, int og) {
-    return smem_bytes(cbv, fg ? 0 : facm, og ? 0 : outd, rho, srcacc) <= budget;
+  std::vector<int64_t> ctile(p.n_cliques);
+  int win = 1, rowmax = 1, cb = 1;
+  auto make_tiles = [&](int cbv, int rowcap) {
+    win = 1;
+    rowmax = 1;
+    const int nb = (n_cases + cbv - 1) / cbv;
+    for (int d = 0; d <= p.max_depth; ++d) {
+      int64_t E = 0;
+      for (int c : p.levels[d]) E += p.dcl[c].n;
+      const int64_t tiles_wanted = std::max<int64_t>(1, (2ll * t->n_sm) / std::max(1, nb));
+      int64_t tile = (E + tiles_wanted - 1) / tiles_wanted;
+      tile = std::max<int64_t>(tile, chunk);
+      tile = std::min<int64_t>(tile, 1 << 20);
+      for (int c : p.levels[d]) {
+        const DevClique& dc = p.dcl[c];
+        const int64_t L = (int64_t)dc.LR * dc.P;
+        // without private variables (and a vector-aligned fastest digit) the
+        // slice streams straight from the ring: no per-row buffers
+        const bool p1vec = dc.P == 1 && dc.pow2 && dc.card_last % VEC == 0;
+        int64_t tc = std::min<int64_t>(tile, (int64_t)(kWinMax - 2) * L);
+        if (!p1vec) tc = std::min<int64_t>(tc, (int64_t)(rowcap - 2) * dc.P);
+        tc = std::max<int64_t>(chunk, tc / chunk * chunk);
+        ctile[c] = tc;
+        const int64_t wn = std::min<int64_t>(tc, dc.n) / L + 2;
+        win = (int)std::max<int64_t>(win, std::min<int64_t>(wn, dc.sep_size));
+        if (!p1vec) rowmax = (int)std::max<int64_t>(rowmax, std::min<int64_t>(tc, dc.n) / dc.P + 2);
+      }
+    }
   };
-  while (cb > 1 && !(fits_col(cb, 0) && fits_dis(cb, 0, 0))) --cb;
-  if (!fits_dis(cb, 0, 0)) out_global = 1;
-  if (!fits_dis(cb, 0, out_global) || !fits_col(cb, 0)) fac_global = 1;
-  if (!fits_dis(cb, fac_global, out_global) || !fits_col(cb, fac_global))
-    return fail(JT_ERR_UNSUPPORTED, "a clique's parent separator (" + std::to_string(rho) +
-                                        " entries) does not fit in shared memory");
-  const int nb = (n_cases + cb - 1) / cb;
-  ls->work.clear();
-  for (size_t i = 0; i < cl.size(); ++i) {
-    const DevClique& dc = p.dcl[cl[i]];
-    int ti = 0;
-    for (int64_t t0 = 0; t0 < dc.n; t0 += ctile[i], ++ti)
-      ls->work.push_back(DevWork{cl[i], (int32_t)t0, (int32_t)std::min<int64_t>(dc.n, t0 + ctile[i]), ti});
+  int fac_s = 0, rho_s = 0, out_s = 0, jnt_s = 0;
+  auto plan_of = [&](int stages) {
+    return SmemPlan{cb, n_child, n_field, n_home, k, fac_s, rho_s, out_s, win, jnt_s, (int32_t)t->elem, stages,
+                    chunk, rowmax, 0};
+  };
+  auto fits = [&]() { return SmemLayout(plan_of(kMinStages)).bytes <= budget; };
+  bool ok = false;
+  for (int cbv = std::min(kCbMax, std::max(1, n_cases)); cbv >= 1 && !ok; cbv = cbv > 1 ? cbv / 2 : 0) {
+    cb = cbv;
+    for (int rowcap = kRowMax; rowcap >= 64 && !ok; rowcap /= 2) {
+      make_tiles(cbv, rowcap);
+      fac_s = facm; rho_s = rho; out_s = outd; jnt_s = jnt;
+      if (fits()) { ok = true; break; }
+      fac_s = 0; rho_s = 0;
+      if (fits()) { ok = true; break; }
+      out_s = 0;
+      if (fits()) { ok = true; break; }
+      jnt_s = 0;
+      if (fits()) { ok = true; break; }
+    }
   }
-  SmemPlan sc{cb, n_child, n_field, n_home, n_src, k, fac_global ? 0 : facm, 0, win, 0, fac_global, 0,
-              (int32_t)t->elem};
-  SmemPlan sd{cb, n_child, n_field, n_home, n_src, k, fac_global ? 0 : facm, rho, out_global ? 0 : outd, srcacc,
-              fac_global, out_global, (int32_t)t->elem};
-  ls->col = LaunchLevel{true, (int32_t)ls->work.size(), nb, nullptr, sc, pow2 ? 1 : 0, vec ? 1 : 0};
-  ls->dis = LaunchLevel{false, (int32_t)ls->work.size(), nb, nullptr, sd, pow2 ? 1 : 0, vec ? 1 : 0};
+  if (!ok) return fail(JT_ERR_UNSUPPORTED, "the tree's per-clique tables do not fit in shared memory");
+  // deepen the bulk-copy ring while two CTAs still fit on an SM
+  SmemPlan sp = plan_of(kMinStages);
+  const int cap = std::max(SmemLayout(sp).bytes, std::min(budget, kTwoPerSm));
+  while (sp.stages < kMaxStages) {
+    SmemPlan q = sp;
+    q.stages++;
+    if (SmemLayout(q).bytes > cap) break;
+    sp = q;
+  }
+  const int nb = (n_cases + cb - 1) / cb;
+  items->clear();
+  auto add_level = [&](int d, int collect) {
+    for (int c : p.levels[d]) {
+      const DevClique& dc = p.dcl[c];
+      const int nt = (int)((dc.n + ctile[c] - 1) / ctile[c]);
+      for (int ti = 0; ti < nt; ++ti)
+        for (int b = 0; b < nb; ++b) {
+          DevWork wk{};
+          wk.base_off = dc.base_off;
+          wk.clique = c;
+          wk.t0 = (int32_t)(ti * ctile[c]);
+          wk.t1 = (int32_t)std::min<int64_t>(dc.n, (ti + 1) * ctile[c]);
+          wk.ntiles = nt;
+          wk.cbk = b;
+          wk.collect = collect;
+          items->push_back(wk);
+        }
+    }
+  };
+  for (int d = p.max_depth; d >= 0; --d) add_level(d, 1);  // collect: deepest level first
+  for (int d = 0; d <= p.max_depth; ++d) add_level(d, 0);  // distribute: root first
+  const int occ = std::max(1, propagate_occupancy((int)t->elem, cb, SmemLayout(sp).bytes));
+  S->sp = sp;
+  S->n_items = (int32_t)items->size();
+  S->grid = (int32_t)std::min<int64_t>(S->n_items, (int64_t)t->n_sm * occ);
   return JT_OK;
 }
 
@@ -222,6 +269,7 @@ LevelArgs<T> level_args(jt_tree t, int case0, int n_cases) {
   a.ch = t->d_ch;
   a.hm = t->d_hm;
   a.src = t->d_src;
+  a.jh = t->d_jh;
   a.fld = t->d_fld;
   a.base = (const T*)t->base;
   a.case0 = case0;
@@ -232,49 +280,47 @@ LevelArgs<T> level_args(jt_tree t, int case0, int n_cases) {
   a.acc_stride = t->acc_stride;
   a.msg_total = t->plan.msg_total;
   a.marg_total = t->plan.marg_total;
+  a.joint_total = t->plan.joint_total;
   a.ls = t->d_ls;
   a.n_cliques = t->plan.n_cliques;
   a.status = t->d_status;
+  a.cnt = t->d_cnt;
+  a.done = t->d_done;
+  a.queue = t->d_done + 2ll * t->plan.n_cliques * t->max_cases;
+  a.parent_of = t->d_parent;
+  a.err = t->d_err;
+  a.max_cases = t->max_cases;
   a.calib = (T*)t->d_calib;
   a.calib_stride = t->plan.base_len;
   return a;
 }
 
 // Launch the whole propagation for a case range on `s`: zero the per-case
-// accumulators, collect levels deepest first, distribute levels root first,
-// finalise.  With `ev` non-null an event is recorded before every launch and
-// after the last one (used by jt_profile_propagate).
+// accumulators, dependency flags and the work queue, run the persistent
+// propagation kernel, finalise.  With `ev` non-null an event is recorded
+// before the propagation kernel, between it and the finalisation, and after.
 template <typename T>
-cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const std::vector<LevelSched>& sched,
-                             cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const Schedule& sc, cudaStream_t s,
+                             cudaEvent_t* ev) {
   const Plan& p = t->plan;
   cudaError_t err = cudaSuccess;
-  int ne = 0;
   auto chk = [&](cudaError_t e) {
     if (err == cudaSuccess && e != cudaSuccess) err = e;
-  };
-  auto mark = [&]() {
-    if (ev) chk(cudaEventRecord(ev[ne++], s));
   };
   chk(cudaMemsetAsync((T*)t->d_acc + (int64_t)case0 * t->acc_stride, 0,
                       (size_t)n_cases * t->acc_stride * sizeof(T), s));
   chk(cudaMemsetAsync(t->d_status + case0, 0, (size_t)n_cases * sizeof(int32_t), s));
+  chk(cudaMemsetAsync(t->d_done, 0, (2ull * p.n_cliques * t->max_cases + 1) * sizeof(int32_t), s));
+  chk(cudaMemsetAsync(t->d_cnt, 0, 2ull * p.n_cliques * t->max_cases * sizeof(int32_t), s));
   LevelArgs<T> a = level_args<T>(t, case0, n_cases);
-  for (int d = p.max_depth; d >= 0; --d) {   // collect: deepest level first
-    mark();
-    a.work = sched[d].col.work;
-    a.cb = sched[d].col.sp.cb;
-    chk(launch_level<T>(a, sched[d].col, s));
-  }
-  for (int d = 0; d <= p.max_depth; ++d) {   // distribute: root first
-    mark();
-    a.work = sched[d].dis.work;
-    a.cb = sched[d].dis.sp.cb;
-    chk(launch_level<T>(a, sched[d].dis, s));
-  }
+  a.work = sc.items;
+  a.n_items = sc.n_items;
+  a.cb = sc.sp.cb;
+  if (ev) chk(cudaEventRecord(ev[0], s));
+  chk(launch_propagate<T>(a, sc.sp, sc.grid, s));
+  if (ev) chk(cudaEventRecord(ev[1], s));
   FinalArgs<T> f{};
-  f.card_of = t->d_card;
-  f.moff = t->d_moff;
+  f.vs = t->d_vs;
   f.n_vars = p.n_vars;
   f.n_cliques = p.n_cliques;
   f.case0 = case0;
@@ -283,34 +329,28 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const std::vecto
   f.acc_stride = t->acc_stride;
   f.msg_total = p.msg_total;
   f.marg_total = p.marg_total;
-  f.root_sep_off = p.sep_off[0];
   f.ls = t->d_ls;
   f.status = t->d_status;
   f.marg_out = t->d_marg;
   f.logz_out = t->d_logz;
-  mark();
   chk(launch_finalize<T>(f, s));
-  mark();
+  if (ev) chk(cudaEventRecord(ev[2], s));
   return err;
 }
 
-// Build the schedule of a case range (work lists on the device) and record
-// it into a CUDA graph.
+// Plan the schedule of a case range (work items on the device) and record it
+// into a CUDA graph.
 template <typename T>
 jt_status record_schedule(jt_tree t, int case0, int n_cases, cudaStream_t s, GraphEntry* ge) {
-  const Plan& p = t->plan;
-  ge->sched.assign(p.max_depth + 1, LevelSched{});
-  for (int d = 0; d <= p.max_depth; ++d) {
-    jt_status st = plan_level(t, d, n_cases, &ge->sched[d]);
-    if (st != JT_OK) return st;
-    DevWork* dw = nullptr;
-    size_t bytes = ge->sched[d].work.size() * sizeof(DevWork);
-    CU(cudaMalloc((void**)&dw, bytes), "work list");
-    ge->dev_bufs.push_back(dw);
-    CU(cudaMemcpy(dw, ge->sched[d].work.data(), bytes, cudaMemcpyHostToDevice), "work list upload");
-    ge->sched[d].col.work = dw;
-    ge->sched[d].dis.work = dw;
-  }
+  std::vector<DevWork> items;
+  jt_status st = plan_schedule(t, n_cases, &ge->sched, &items);
+  if (st != JT_OK) return st;
+  DevWork* dw = nullptr;
+  const size_t bytes = std::max<size_t>(1, items.size()) * sizeof(DevWork);
+  CU(cudaMalloc((void**)&dw, bytes), "work list");
+  ge->dev_bufs.push_back(dw);
+  CU(cudaMemcpy(dw, items.data(), items.size() * sizeof(DevWork), cudaMemcpyHostToDevice), "work list upload");
+  ge->sched.items = dw;
   CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t err = enqueue_schedule<T>(t, case0, n_cases, ge->sched, s, nullptr);
   cudaGraph_t g = nullptr;
@@ -371,7 +411,17 @@ jt_status sync_last(jt_tree t) {
   return JT_OK;
 }
 
+// A kernel gave up a bounded wait: every result since is invalid.
+jt_status check_err(jt_tree t) {
+  int32_t e = 0;
+  CU(cudaMemcpy(&e, t->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost), "error word read");
+  if (e) return fail(JT_ERR_TIMEOUT, "a device-side wait timed out; results are invalid");
+  return JT_OK;
+}
+
 jt_status case_status(jt_tree t, int32_t cs, int32_t* code) {
+  jt_status es = check_err(t);
+  if (es != JT_OK) return es;
   int32_t st = 0;
   CU(cudaMemcpy(&st, t->d_status + cs, sizeof(int32_t), cudaMemcpyDeviceToHost), "status read");
   if (st & kStatusBadState) *code = JT_ERR_INVALID_ARG;
@@ -388,7 +438,7 @@ jt_status load_typed(jt_tree t, const jt_tree_desc* d, cudaStream_t s) {
   jt_status st;
   if ((st = alloc(t, (T**)&t->base, p.base_len, "clique tables")) != JT_OK) return st;
   CU(cudaMemcpyAsync(t->base, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s), "table upload");
-  t->acc_stride = ((int64_t)2 * p.msg_total + p.marg_total + 31) / 32 * 32;
+  t->acc_stride = ((int64_t)3 * p.msg_total + p.marg_total + p.joint_total + 31) / 32 * 32;
   if ((st = alloc(t, (T**)&t->d_acc, t->acc_stride * t->max_cases, "per-case messages")) != JT_OK) return st;
   if (t->flags & JT_MATERIALIZE_CLIQUES) {
     if ((st = alloc(t, (T**)&t->d_calib, p.base_len * t->max_cases, "calibrated tables")) != JT_OK) return st;
@@ -479,6 +529,18 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   if ((st = upload_vec(raw, &raw->d_ch, p.dch, "descriptors")) != JT_OK) return bail(st);
   if ((st = upload_vec(raw, &raw->d_hm, p.dhm, "descriptors")) != JT_OK) return bail(st);
   if ((st = upload_vec(raw, &raw->d_src, p.dsrc, "descriptors")) != JT_OK) return bail(st);
+  if ((st = upload_vec(raw, &raw->d_jh, p.djh, "descriptors")) != JT_OK) return bail(st);
+  if ((st = upload_vec(raw, &raw->d_vs, p.vsrc, "descriptors")) != JT_OK) return bail(st);
+  if ((st = alloc(raw, &raw->d_err, 1, "error word")) != JT_OK) return bail(st);
+  if ((st = alloc(raw, &raw->d_done, 2ll * p.n_cliques * raw->max_cases + 1, "dependency flags")) != JT_OK)
+    return bail(st);
+  if ((st = upload_vec(raw, &raw->d_parent, p.parent, "descriptors")) != JT_OK) return bail(st);
+  if (cudaMemset(raw->d_err, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
+  {
+    const int64_t ncnt = 2ll * p.n_cliques * raw->max_cases;
+    if ((st = alloc(raw, &raw->d_cnt, ncnt, "tile counters")) != JT_OK) return bail(st);
+    if (cudaMemset(raw->d_cnt, 0, ncnt * sizeof(int32_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
+  }
   if ((st = upload_vec(raw, &raw->d_fld, p.dfld, "descriptors")) != JT_OK) return bail(st);
   if ((st = upload_vec(raw, &raw->d_card, p.card, "descriptors")) != JT_OK) return bail(st);
   if ((st = upload_vec(raw, &raw->d_moff, p.moff, "descriptors")) != JT_OK) return bail(st);
@@ -583,10 +645,10 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
   jt_status st = check_tree(t);
   if (st != JT_OK) return st;
   if ((st = check_range(t, first, n)) != JT_OK) return st;
-  const int nl = 2 * (t->plan.max_depth + 1) + 1;
+  const int nl = 2;
   if (n_launches) *n_launches = nl;
   if (n == 0) return JT_OK;
-  if (!launch_ms || max_launches < nl) return fail(JT_ERR_INVALID_ARG, "launch_ms needs 2*(depth+1)+1 slots");
+  if (!launch_ms || max_launches < nl) return fail(JT_ERR_INVALID_ARG, "launch_ms needs 2 slots");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
@@ -678,6 +740,7 @@ jt_status jt_get_status(jt_tree t, int32_t first, int32_t n, int32_t* out) {
   if (n == 0) return JT_OK;
   if (!out) return fail(JT_ERR_INVALID_ARG, "null output");
   if ((st = sync_last(t)) != JT_OK) return st;
+  if ((st = check_err(t)) != JT_OK) return st;
   std::vector<int32_t> raw(n);
   CU(cudaMemcpy(raw.data(), t->d_status + first, n * sizeof(int32_t), cudaMemcpyDeviceToHost), "status read");
   for (int i = 0; i < n; ++i) {

@@ -12,18 +12,23 @@ namespace jt {
 struct SmemPlan {
   int32_t cb;                    // evidence cases handled by one CTA
   int32_t n_child, n_field;      // maxima over the level's cliques
-  int32_t n_home, n_src, k;
-  int32_t fac;                   // per case: smem entries for child factors (0: read from global)
-  int32_t rho;                   // per case: smem entries for the parent ratio (distribute)
-  int32_t out;                   // per case: smem entries for outputs (0: accumulate in global)
-  int32_t srcacc;                // per case: smem entries for separator-read marginals
-  int32_t fac_global, out_global;
+  int32_t n_home, k;
+  int32_t fac;                   // per case: entries for child factors (0: read from global)
+  int32_t rho;                   // per case: entries for the parent ratio (0: read from global)
+  int32_t out;                   // per case: child-separator + row-home accumulators (0: global)
+  int32_t win;                   // per case: collect window of parent-separator entries
+  int32_t jnt;                   // per case: column-joint accumulators (0: global or none)
   int32_t elem;                  // sizeof(T)
+  int32_t stages;                // bulk-copy ring: number of chunk buffers
+  int32_t chunk;                 // entries per chunk (= threads x vector width)
+  int32_t rowmax;                // per case: rows of one slice (row sums, row factors)
+  int32_t pad;
 };
 
 struct SmemLayout {
-  int32_t off_ch, off_fld, off_hm, off_src, off_pos, off_obs, off_nobs;
-  int32_t off_facp, off_outp, off_scale, off_houtp, off_rho, off_fac, off_out, off_srcacc, off_red;
+  int32_t off_ch, off_fld, off_hm, off_pos, off_obs, off_nobs;
+  int32_t off_facp, off_outp, off_rhop, off_houtp, off_jntp;
+  int32_t off_fac, off_rho, off_out, off_win, off_jnt, off_red, off_bar, off_rsum, off_gsm, off_buf;
   int32_t bytes;
 
   __host__ __device__ static int32_t a16(int32_t x) { return (x + 15) & ~15; }
@@ -33,36 +38,36 @@ struct SmemLayout {
     off_ch = o;    o = a16(o + s.n_child * (int32_t)sizeof(DevChild));
     off_fld = o;   o = a16(o + s.n_field * (int32_t)sizeof(DevField));
     off_hm = o;    o = a16(o + s.n_home * (int32_t)sizeof(DevHome));
-    off_src = o;   o = a16(o + s.n_src * (int32_t)sizeof(DevSrc));
     off_pos = o;   o = a16(o + s.k * (int32_t)sizeof(DevPos));
-    off_obs = o;   o = a16(o + s.cb * s.k * 8);
-    off_nobs = o;  o = a16(o + s.cb * 4);
+    off_obs = o;   o = a16(o + 2 * s.cb * s.k * 8);      // row and column observations
+    off_nobs = o;  o = a16(o + 2 * s.cb * 4);
     off_facp = o;  o = a16(o + s.cb * s.n_child * 8);
     off_outp = o;  o = a16(o + s.cb * s.n_child * 8);
-    off_scale = o; o = a16(o + s.cb * s.n_child * s.elem);
+    off_rhop = o;  o = a16(o + s.cb * 8);
     off_houtp = o; o = a16(o + s.cb * 8);
-    off_rho = o;   o = a16(o + s.cb * s.rho * s.elem);
+    off_jntp = o;  o = a16(o + s.cb * 8);
     off_fac = o;   o = a16(o + s.cb * s.fac * s.elem);
+    off_rho = o;   o = a16(o + s.cb * s.rho * s.elem);
     off_out = o;   o = a16(o + s.cb * s.out * s.elem);
-    off_srcacc = o; o = a16(o + s.cb * s.srcacc * s.elem);
-    off_red = o;   o = a16(o + 64 * 8);
+    off_win = o;   o = a16(o + s.cb * s.win * s.elem);
+    off_jnt = o;   o = a16(o + s.cb * s.jnt * s.elem);
+    off_red = o;   o = a16(o + 80 * 8);
+    off_bar = o;   o = a16(o + 2 * s.stages * 8);   // full and empty barriers
+    off_rsum = o;  o = a16(o + s.cb * s.rowmax * s.elem);
+    off_gsm = o;   o = a16(o + s.cb * s.rowmax * s.elem);
+    o = (o + 127) & ~127;
+    off_buf = o;   o += s.stages * s.chunk * s.elem;
     bytes = o;
   }
 };
 
-struct LaunchLevel {
-  bool collect;
-  int32_t n_work;                // CTAs along x
-  int32_t n_caseblk;             // CTAs along y
-  const DevWork* work;           // device
-  SmemPlan sp;
-  int32_t pow2_mode;             // 1: every clique of the level is all powers of two
-  int32_t vec_mode;              // 1: every clique's fastest cardinality is a multiple of the vector width
-};
-
-// Enqueue one level pass (collect or distribute) on `s`.
+// Enqueue a whole propagation (collect and distribute of every clique for
+// the case range of `a`) as one persistent launch of `grid` CTAs on `s`.
 template <typename T>
-cudaError_t launch_level(const LevelArgs<T>& a, const LaunchLevel& L, cudaStream_t s);
+cudaError_t launch_propagate(const LevelArgs<T>& a, const SmemPlan& sp, int grid, cudaStream_t s);
+
+// Resident CTAs per SM of the propagation kernel for a shared-memory plan.
+int32_t propagate_occupancy(int elem, int cb, int bytes);
 
 // Enqueue the finalisation (log Z and normalised marginals) for a case range.
 template <typename T>
@@ -80,5 +85,8 @@ cudaError_t launch_get_clique(const T* calib_clique, const CliqueOut& co, double
 
 // Maximum dynamic shared memory per CTA the kernels may use on this device.
 int32_t smem_budget(int device);
+
+// Consumer threads per CTA of the propagation kernel (plus one producer warp).
+constexpr int kLevelThreads = 512;
 
 }  // namespace jt

@@ -22,6 +22,9 @@ uint32_t magic_for(uint32_t d) {
   return (uint32_t)(((1ull << 32) + d - 1) / d);
 }
 
+// Columns kept per row (product of the trailing private cardinalities).
+constexpr int64_t kMaxCols = 4096;
+
 static bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 static int32_t ilog2(int64_t x) {
   int32_t r = 0;
@@ -174,10 +177,11 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     }
 
   // permuted order: parent separator (ascending), variables of child
-  // separators (ascending), then the rest (ascending) -- with a variable whose
-  // cardinality is a multiple of 4 moved last when one exists in that group,
-  // so a 4-wide vector of entries shares all slower digits.
+  // separators (ascending), then the private variables (ascending) -- with a
+  // private variable whose cardinality is a multiple of 4 moved last when one
+  // exists, so a 4-wide vector of entries stays inside one row.
   p->pvars.assign(nc, {});
+  std::vector<int32_t> n_private(nc, 0);
   for (int c = 0; c < nc; ++c) {
     std::vector<int32_t> a = p->sep[c], b, r;
     for (int v : a) mark[v] = 1;
@@ -202,6 +206,7 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
           break;
         }
     }
+    n_private[c] = (int32_t)r.size();
     std::vector<int32_t>& pv = p->pvars[c];
     pv.insert(pv.end(), a.begin(), a.end());
     pv.insert(pv.end(), b.begin(), b.end());
@@ -223,17 +228,25 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
   p->dch.clear();
   p->dhm.clear();
   p->dsrc.clear();
+  p->djh.clear();
   p->dfld.clear();
   p->fac_collect.assign(nc, 0);
-  p->fac_dist.assign(nc, 0);
   p->out_dist.assign(nc, 0);
+  p->joint_total = 0;
   std::vector<int64_t> st(JT_MAX_CLIQUE_VARS);
   std::vector<int32_t> posof(nv, -1);
   for (int c = 0; c < nc; ++c) {
     const auto& pv = p->pvars[c];
-    int k = (int)pv.size();
+    const int k = (int)pv.size();
     bool pow2 = true;
     for (int v : pv) pow2 = pow2 && is_pow2(p->card[v]);
+    // column suffix: trailing private variables while the product stays <= kMaxCols
+    int kr = k;
+    int64_t P = 1;
+    while (kr > k - n_private[c] && P * p->card[pv[kr - 1]] <= kMaxCols) {
+      P *= p->card[pv[kr - 1]];
+      --kr;
+    }
     int64_t s = 1;
     for (int i = k - 1; i >= 0; --i) {
       st[i] = s;
@@ -244,30 +257,39 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     dc.base_off = p->base_off[c];
     dc.n = (int32_t)p->n_entries[c];
     dc.k = k;
+    dc.kr = kr;
+    dc.P = (int32_t)P;
+    dc.P_magic = magic_for((uint32_t)P);
+    dc.logP = pow2 ? ilog2(P) : 0;
     dc.sep_size = p->sep_size[c];
     dc.sep_off = p->sep_off[c];
-    dc.L = (int32_t)(p->n_entries[c] / p->sep_size[c]);
-    dc.L_magic = magic_for((uint32_t)dc.L);
+    const int64_t L = p->n_entries[c] / p->sep_size[c];
+    dc.LR = (int32_t)(L / P);
+    dc.LR_magic = magic_for((uint32_t)dc.LR);
+    dc.logLR = pow2 ? ilog2(dc.LR) : 0;
     dc.pow2 = pow2 ? 1 : 0;
-    dc.card_last = p->card[pv[k - 1]];
     dc.depth = p->depth[c];
+    dc.card_last = p->card[pv[k - 1]];
     dc.pos_first = (int32_t)p->dpos.size();
     for (int i = 0; i < k; ++i) {
       DevPos q{};
       q.var = pv[i];
       q.card = p->card[pv[i]];
-      q.st = (int32_t)st[i];
-      q.st_magic = magic_for((uint32_t)st[i]);
+      q.is_col = i >= kr ? 1 : 0;
+      const int64_t sti = i >= kr ? st[i] : st[i] / P;   // column stride or row stride
+      q.st = (int32_t)sti;
+      q.st_magic = magic_for((uint32_t)sti);
       q.card_magic = magic_for((uint32_t)q.card);
-      q.sh = pow2 ? ilog2(st[i]) : 0;
+      q.sh = pow2 ? ilog2(sti) : 0;
       q.cbits = pow2 ? ilog2(q.card) : 0;
       p->dpos.push_back(q);
       posof[pv[i]] = i;
     }
-    // children: digit-run fields of each child separator in this clique
+    // children: digit-run fields of each child separator over the row index
     dc.child_first = (int32_t)p->dch.size();
     dc.n_child = (int32_t)p->children[c].size();
     int32_t fac = 0;
+    const int32_t field0 = (int32_t)p->dfld.size();
     for (int g : p->children[c]) {
       const auto& sv = p->sep[g];  // ascending = table order, first most significant
       std::vector<int64_t> ts(sv.size());
@@ -276,7 +298,6 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
         ts[i] = t;
         t *= p->card[sv[i]];
       }
-      // (clique position -> table stride) for separator vars, walk fastest to slowest
       std::vector<int64_t> tstride_at(k, 0);
       std::vector<char> in(k, 0);
       for (size_t i = 0; i < sv.size(); ++i) {
@@ -288,8 +309,10 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
       ch.sep_size = p->sep_size[g];
       ch.sep_off = p->sep_off[g];
       ch.field_first = (int32_t)p->dfld.size();
-      ch.w_last = in[k - 1] ? (int32_t)tstride_at[k - 1] : 0;
-      int i = k - 1;
+      ch.field_rel = ch.field_first - field0;
+      ch.fac_off = fac;
+      ch.w_last = (kr == k && in[k - 1]) ? (int32_t)tstride_at[k - 1] : 0;
+      int i = kr - 1;
       while (i >= 0) {
         if (!in[i]) {
           --i;
@@ -302,12 +325,13 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
           len *= p->card[pv[j]];
         }
         DevField f{};
-        f.st = (int32_t)st[i];
+        const int64_t rs = st[i] / P;
+        f.st = (int32_t)rs;
         f.len = (int32_t)len;
-        f.st_magic = magic_for((uint32_t)st[i]);
+        f.st_magic = magic_for((uint32_t)rs);
         f.len_magic = magic_for((uint32_t)len);
         f.w = (int32_t)tstride_at[i];
-        f.sh = pow2 ? ilog2(st[i]) : 0;
+        f.sh = pow2 ? ilog2(rs) : 0;
         f.lbits = pow2 ? ilog2(len) : 0;
         p->dfld.push_back(f);
         i = j - 1;
@@ -316,19 +340,29 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
       p->dch.push_back(ch);
       fac += ch.sep_size;
     }
+    dc.field_first = field0;
+    dc.n_field = (int32_t)p->dfld.size() - field0;
     for (int v : pv) posof[v] = -1;
-    // home variables (marginal accumulated in this clique)
+    // private variables at row positions: marginal accumulated per row
     dc.home_first = (int32_t)p->dhm.size();
     int32_t homes = 0;
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < kr; ++i) {
       int v = pv[i];
       if (p->home[v] == c) {
-        DevHome h{v, i, p->card[v], p->moff[v]};
-        p->dhm.push_back(h);
+        p->dhm.push_back(DevHome{i, p->card[v], p->moff[v], fac + homes});
         homes += p->card[v];
       }
     }
     dc.n_home = (int32_t)p->dhm.size() - dc.home_first;
+    // private variables in the columns: marginal binned from the column joint
+    dc.jh_first = (int32_t)p->djh.size();
+    for (int i = kr; i < k; ++i) p->djh.push_back(DevSrc{pv[i], p->card[pv[i]], (int32_t)st[i], p->moff[pv[i]]});
+    dc.n_jh = (int32_t)p->djh.size() - dc.jh_first;
+    dc.joint_off = -1;
+    if (P > 1) {
+      dc.joint_off = p->joint_total;
+      p->joint_total += (int32_t)P;
+    }
     // variables read from this clique's parent separator
     dc.src_first = (int32_t)p->dsrc.size();
     if (c > 0) {
@@ -344,8 +378,41 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     }
     dc.n_src = (int32_t)p->dsrc.size() - dc.src_first;
     p->fac_collect[c] = fac;
-    p->fac_dist[c] = fac + (c == 0 ? 0 : p->sep_size[c]);
     p->out_dist[c] = fac + homes;
+  }
+  // marginal sources, as offsets in the per-case array
+  // [up | down | rho | marg | joint] (see LevelArgs)
+  p->vsrc.assign(nv, VarSrc{});
+  for (int v = 0; v < nv; ++v) {
+    VarSrc& q = p->vsrc[v];
+    q.card = p->card[v];
+    q.moff = p->moff[v];
+    const int e = p->src_edge[v];
+    if (e >= 0) {           // separator-held: bin the distribute message of edge e
+      q.kind = 1;
+      q.off = (int64_t)p->msg_total + p->sep_off[e];
+      q.size = p->sep_size[e];
+      int64_t t = 1;
+      for (int i = (int)p->sep[e].size() - 1; i >= 0; --i) {
+        if (p->sep[e][i] == v) q.st = (int32_t)t;
+        t *= p->card[p->sep[e][i]];
+      }
+      continue;
+    }
+    const int c = p->home[v];
+    const DevClique& dc = p->dcl[c];
+    int pos = -1;
+    for (int i = 0; i < dc.k; ++i)
+      if (p->pvars[c][i] == v) pos = i;
+    if (pos >= dc.kr) {     // in the column joint of its clique
+      q.kind = 1;
+      q.off = 3ll * p->msg_total + p->marg_total + dc.joint_off;
+      q.size = dc.P;
+      q.st = p->dpos[dc.pos_first + pos].st;
+    } else {                // accumulated per row
+      q.kind = 0;
+      q.off = 3ll * p->msg_total + p->moff[v];
+    }
   }
   return JT_OK;
 }

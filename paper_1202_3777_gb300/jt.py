@@ -200,10 +200,10 @@ def jt_propagate(t: Tree, first_case: int = 0, n_cases: int = 1, stream=None):
 
 
 def jt_profile_propagate(t: Tree, first_case: int = 0, n_cases: int = 1, stream=None) -> np.ndarray:
-    """Per-launch device times (ms) of one propagation issued launch by
-    launch: collect levels (deepest first), distribute levels, finalise."""
+    """Device times (ms) of one propagation: [propagation kernel,
+    finalisation]."""
     n = C.c_int32(0)
-    buf = np.zeros(2 * (t.info.depth + 1) + 1, dtype=np.float32)
+    buf = np.zeros(2, dtype=np.float32)
     _check(_lib.jt_profile_propagate(t.handle, first_case, n_cases, _stream(stream), _ptr(buf), len(buf),
                                      C.byref(n)), "jt_profile_propagate")
     return buf[:n.value]
