@@ -108,6 +108,16 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def msg_total(tree):
+    """Entries of all separator tables (the per-case message arrays)."""
+    from math import prod
+    n = 1
+    for c in range(1, tree.n_cliques):
+        sv = set(tree.cliques[c].tolist()) & set(tree.cliques[tree.parent[c]].tolist())
+        n += prod(int(tree.card[v]) for v in sv)
+    return n
+
+
 def oracle_rate(tree, cases, budget_s=20.0):
     """The FP64 oracle, as it stands, on a bounded sample of the cases."""
     from oracle import hugin
@@ -230,18 +240,22 @@ def main():
     st = jt.jt_get_status(h, 0, B)
     assert np.all(st == jt.JT_OK), st
 
-    # per-launch times of the same schedule (dominant kernel = level kernels)
-    nl_per_step = 2 * (tree.depth().max() + 1) + 1
+    # device time of the dominant kernel (the persistent propagation kernel),
+    # CUDA events on the launching stream, same schedule as the timed steps
     prof_b = np.mean([jt.jt_profile_propagate(h, 0, B, stream) for _ in range(3)], axis=0)
     prof_1 = np.mean([jt.jt_profile_propagate(h, 0, 1, stream) for _ in range(3)], axis=0)
-    level_ms_b = float(prof_b[:-1].sum())
-    level_ms_1 = float(prof_1[:-1].sum())
     hbm, src = peaks()
     w = 4
     entries = tree.entries()
-    bytes_plain = 2 * w * entries                    # each table read once per pass
-    ach_plain = bytes_plain / (level_ms_1 * 1e-3) / 1e9
-    ach_batched = bytes_plain * B / (level_ms_b * 1e-3) / 1e9
+    info = h.info
+
+    def alg_bytes(cases):
+        # every clique table read once per pass, plus per case: messages
+        # written and read in each pass and the marginal sums
+        return 2 * w * entries + cases * w * (4 * msg_total(tree) + info.marginal_len)
+
+    ach_b = alg_bytes(B) / (prof_b[0] * 1e-3) / 1e9
+    ach_1 = alg_bytes(1) / (prof_1[0] * 1e-3) / 1e9
 
     # end to end through the public API with host buffers
     md = np.empty((B, h.marginal_len))
@@ -280,16 +294,16 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "plain": {"value": plain_value, "unit": UNIT, "ms_per_case": plain_ms},
         "batched_over_plain": value / plain_value,
-        "roofline": {"bound": "hbm", "achieved": ach_plain, "peak": hbm, "unit": "GB/s",
-                     "frac": ach_plain / hbm, "traffic": None,
-                     "kernel": "k_level (plain, one case: every clique table read once per pass)",
-                     "peak_source": src},
-        "roofline_batched": {"achieved_effective": ach_batched, "unit": "GB/s",
-                             "note": "cases x per-case bytes / level-kernel time; base reads are shared by cases"},
-        "level_ms": {"batched": level_ms_b, "plain": level_ms_1},
+        "roofline": {"bound": "hbm", "achieved": ach_b, "peak": hbm, "unit": "GB/s",
+                     "frac": ach_b / hbm, "traffic": None, "kernel": "k_propagate",
+                     "kernel_ms": float(prof_b[0]), "alg_bytes": int(alg_bytes(B)),
+                     "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"},
+        "roofline_plain": {"bound": "hbm", "achieved": ach_1, "peak": hbm, "unit": "GB/s", "frac": ach_1 / hbm,
+                           "kernel_ms": float(prof_1[0]), "alg_bytes": int(alg_bytes(1))},
+        "finalize_ms": {"batched": float(prof_b[1]), "plain": float(prof_1[1])},
         "e2e": {"value": W * total_cases / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(ev.nbytes), "d2h_bytes_per_step": int(md.nbytes + lzh.nbytes)},
-        "gpu_launches": int(nl_per_step * args.steps),
+        "gpu_launches": int(2 * args.steps),   # k_propagate + k_finalize per step
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -37,7 +39,7 @@ jt_status cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 constexpr int kCbMax = 8;
-constexpr int kMinStages = 2, kMaxStages = 6;   // bulk-copy ring depth (chunks of 8 KB)
+constexpr int kMinStages = 3, kMaxStages = 6;   // bulk-copy ring depth (chunks of 16 KB)
 constexpr int kRowMax = 4096;                   // rows of one slice held in shared memory
 constexpr int kChunkVecs = 2 * kLevelThreads;   // 16-byte vectors per bulk-copy chunk
 constexpr int kTwoPerSm = 112 * 1024;           // dynamic shared memory that leaves room for two CTAs
@@ -50,6 +52,7 @@ struct Schedule {
   int32_t grid = 0;
   int32_t n_items = 0;
   DevWork* items = nullptr;       // device
+  DevClique* cliques = nullptr;   // device: the tree's descriptors with this schedule's residency
 };
 
 struct GraphEntry {
@@ -155,7 +158,8 @@ void destroy(jt_tree t) {
 // per-slice row sums / row factors and the column joint (touched per entry),
 // then factors and outputs (touched per row), which otherwise stay in global
 // memory.
-jt_status plan_schedule(jt_tree t, int n_cases, Schedule* S, std::vector<DevWork>* items) {
+jt_status plan_schedule(jt_tree t, int n_cases, Schedule* S, std::vector<DevWork>* items,
+                        std::vector<DevClique>* cliques) {
   const Plan& p = t->plan;
   const int VEC = (int)(16 / t->elem);
   const int chunk = kChunkVecs * VEC;       // two vectors per consumer thread per chunk
@@ -188,49 +192,70 @@ jt_status plan_schedule(jt_tree t, int n_cases, Schedule* S, std::vector<DevWork
       for (int c : p.levels[d]) {
         const DevClique& dc = p.dcl[c];
         const int64_t L = (int64_t)dc.LR * dc.P;
-        // without private variables (and a vector-aligned fastest digit) the
-        // slice streams straight from the ring: no per-row buffers
-        const bool p1vec = dc.P == 1 && dc.pow2 && dc.card_last % VEC == 0;
+        // short rows are processed inline while streaming (no per-row buffers)
+        const bool inl = inline_rows(dc, VEC);
         int64_t tc = std::min<int64_t>(tile, (int64_t)(kWinMax - 2) * L);
-        if (!p1vec) tc = std::min<int64_t>(tc, (int64_t)(rowcap - 2) * dc.P);
+        if (!inl) tc = std::min<int64_t>(tc, (int64_t)(rowcap - 2) * dc.P);
         tc = std::max<int64_t>(chunk, tc / chunk * chunk);
         ctile[c] = tc;
         const int64_t wn = std::min<int64_t>(tc, dc.n) / L + 2;
         win = (int)std::max<int64_t>(win, std::min<int64_t>(wn, dc.sep_size));
-        if (!p1vec) rowmax = (int)std::max<int64_t>(rowmax, std::min<int64_t>(tc, dc.n) / dc.P + 2);
+        if (!inl) rowmax = (int)std::max<int64_t>(rowmax, std::min<int64_t>(tc, dc.n) / dc.P + 2);
       }
     }
   };
-  int fac_s = 0, rho_s = 0, out_s = 0, jnt_s = 0;
-  auto plan_of = [&](int stages) {
-    return SmemPlan{cb, n_child, n_field, n_home, k, fac_s, rho_s, out_s, win, jnt_s, (int32_t)t->elem, stages,
-                    chunk, rowmax, 0};
+  // fixed part of the layout; what is left of the shared memory becomes the
+  // per-case table region, packed clique by clique
+  int maxneed = 0;
+  for (int c = 0; c < p.n_cliques; ++c) {
+    const DevClique& dc = p.dcl[c];
+    const int need = p.fac_collect[c] + (c ? dc.sep_size : 0) + p.out_dist[c] + (dc.joint_off >= 0 ? dc.P : 0);
+    maxneed = std::max(maxneed, need);
+  }
+  auto plan_of = [&](int stages, int tabs) {
+    return SmemPlan{cb, n_child, n_field, n_home, k, tabs, win, (int32_t)t->elem, stages, chunk, rowmax, 0};
   };
-  auto fits = [&]() { return SmemLayout(plan_of(kMinStages)).bytes <= budget; };
   bool ok = false;
+  int tabs = 0;
   for (int cbv = std::min(kCbMax, std::max(1, n_cases)); cbv >= 1 && !ok; cbv = cbv > 1 ? cbv / 2 : 0) {
     cb = cbv;
     for (int rowcap = kRowMax; rowcap >= 64 && !ok; rowcap /= 2) {
       make_tiles(cbv, rowcap);
-      fac_s = facm; rho_s = rho; out_s = outd; jnt_s = jnt;
-      if (fits()) { ok = true; break; }
-      fac_s = 0; rho_s = 0;
-      if (fits()) { ok = true; break; }
-      out_s = 0;
-      if (fits()) { ok = true; break; }
-      jnt_s = 0;
-      if (fits()) { ok = true; break; }
+      const int fixed = SmemLayout(plan_of(kMinStages, 0)).bytes;
+      if (fixed > budget) continue;
+      const int cap = fixed <= kTwoPerSm ? kTwoPerSm : budget;
+      tabs = std::max(0, (cap - fixed - 64) / (cb * (int)t->elem));
+      tabs = std::min(tabs, maxneed);
+      ok = true;
     }
   }
   if (!ok) return fail(JT_ERR_UNSUPPORTED, "the tree's per-clique tables do not fit in shared memory");
-  // deepen the bulk-copy ring while two CTAs still fit on an SM
-  SmemPlan sp = plan_of(kMinStages);
+  // deepen the bulk-copy ring with what is left while two CTAs still fit on an SM
+  SmemPlan sp = plan_of(kMinStages, tabs);
   const int cap = std::max(SmemLayout(sp).bytes, std::min(budget, kTwoPerSm));
   while (sp.stages < kMaxStages) {
     SmemPlan q = sp;
     q.stages++;
     if (SmemLayout(q).bytes > cap) break;
     sp = q;
+  }
+  // per-clique residency in the table region: child factors, parent ratio,
+  // accumulators, column joint -- in that order while they fit
+  cliques->assign(p.dcl.begin(), p.dcl.end());
+  for (int c = 0; c < p.n_cliques; ++c) {
+    DevClique& dc = (*cliques)[c];
+    int off = 0;
+    auto place = [&](int n) {
+      if (n <= 0 || off + n > tabs) return -1;
+      const int o = off;
+      off += n;
+      return o;
+    };
+    dc.sm_fac = dc.n_child ? place(p.fac_collect[c]) : -1;
+    dc.sm_rho = c ? place(dc.sep_size) : -1;
+    dc.sm_out_len = p.out_dist[c];
+    dc.sm_out = place(p.out_dist[c]);
+    dc.sm_jnt = dc.joint_off >= 0 ? place(dc.P) : -1;
   }
   const int nb = (n_cases + cb - 1) / cb;
   items->clear();
@@ -255,6 +280,21 @@ jt_status plan_schedule(jt_tree t, int n_cases, Schedule* S, std::vector<DevWork
   for (int d = p.max_depth; d >= 0; --d) add_level(d, 1);  // collect: deepest level first
   for (int d = 0; d <= p.max_depth; ++d) add_level(d, 0);  // distribute: root first
   const int occ = std::max(1, propagate_occupancy((int)t->elem, cb, SmemLayout(sp).bytes));
+  if (const char* dbg = std::getenv("JT_DEBUG_PLAN"); dbg && *dbg == '1') {
+    int nf = 0, nr = 0, no = 0, nj = 0;
+    for (const DevClique& dc : *cliques) {
+      nf += dc.sm_fac >= 0;
+      nr += dc.sm_rho >= 0;
+      no += dc.sm_out >= 0;
+      nj += dc.sm_jnt >= 0;
+    }
+    std::fprintf(stderr,
+                 "[jt plan] cases=%d cb=%d items=%zu grid=%d occ=%d smem=%d stages=%d chunk=%d rowmax=%d win=%d "
+                 "tabs=%d resident fac/rho/out/jnt=%d/%d/%d/%d of %d cliques\n",
+                 n_cases, cb, items->size(), (int)std::min<int64_t>((int64_t)items->size(), (int64_t)t->n_sm * occ), occ,
+                 SmemLayout(sp).bytes, sp.stages, sp.chunk, sp.rowmax, sp.win, sp.tabs, nf, nr, no, nj,
+                 p.n_cliques);
+  }
   S->sp = sp;
   S->n_items = (int32_t)items->size();
   S->grid = (int32_t)std::min<int64_t>(S->n_items, (int64_t)t->n_sm * occ);
@@ -313,6 +353,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const Schedule& 
   chk(cudaMemsetAsync(t->d_done, 0, (2ull * p.n_cliques * t->max_cases + 1) * sizeof(int32_t), s));
   chk(cudaMemsetAsync(t->d_cnt, 0, 2ull * p.n_cliques * t->max_cases * sizeof(int32_t), s));
   LevelArgs<T> a = level_args<T>(t, case0, n_cases);
+  a.cl = sc.cliques;
   a.work = sc.items;
   a.n_items = sc.n_items;
   a.cb = sc.sp.cb;
@@ -343,8 +384,15 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const Schedule& 
 template <typename T>
 jt_status record_schedule(jt_tree t, int case0, int n_cases, cudaStream_t s, GraphEntry* ge) {
   std::vector<DevWork> items;
-  jt_status st = plan_schedule(t, n_cases, &ge->sched, &items);
+  std::vector<DevClique> cliques;
+  jt_status st = plan_schedule(t, n_cases, &ge->sched, &items, &cliques);
   if (st != JT_OK) return st;
+  DevClique* dcl = nullptr;
+  CU(cudaMalloc((void**)&dcl, cliques.size() * sizeof(DevClique)), "clique descriptors");
+  ge->dev_bufs.push_back(dcl);
+  CU(cudaMemcpy(dcl, cliques.data(), cliques.size() * sizeof(DevClique), cudaMemcpyHostToDevice),
+     "clique descriptors");
+  ge->sched.cliques = dcl;
   DevWork* dw = nullptr;
   const size_t bytes = std::max<size_t>(1, items.size()) * sizeof(DevWork);
   CU(cudaMalloc((void**)&dw, bytes), "work list");

@@ -105,7 +105,13 @@ struct DevClique {
   int32_t depth;
   int32_t field_first, n_field; // fields of all child separators (contiguous)
   int32_t card_last;            // cardinality of the fastest position
-  int32_t pad;
+  // offsets (entries) of this clique's tables inside the per-case shared-memory
+  // table region of a propagation, or -1 when the table stays in global memory
+  int32_t sm_fac;               // child factors (collect messages of the children)
+  int32_t sm_rho;               // parent ratio
+  int32_t sm_out;               // child-separator and row-home accumulators
+  int32_t sm_jnt;               // column joint
+  int32_t sm_out_len;           // entries of the accumulators (child separators + row homes)
 };
 
 // One work item of a propagation: a slice of one clique's table for one

@@ -305,198 +305,19 @@ __device__ __forceinline__ void rows_factor(const SmemPlan& sp, const DevClique&
   }
 }
 
-// Stream the slice through the bulk-copy ring: per entry v = phi E_col
-// (times G for distribute); row sums R(r) = sum_col v; distribute also
-// accumulates the column joint and writes the calibrated entry.  Chunks carry
-// a per-CTA sequence number `seq0 + ci`, so ring stages and mbarrier phases
-// continue across the CTA's items.  The producer warp refills a stage once
-// every consumer warp released it; consumer warps never wait for each other.
-// Returns false (after letting issued copies land) if a wait timed out.
-template <typename T, bool COLLECT, bool POW2, bool ROWVEC, int CBMAX>
-__device__ __forceinline__ bool stream(const LevelArgs<T>& a, const SmemPlan& sp, const DevClique& c,
-                                       const CtaView<T>& v, const SliceGeo& g, const T* tab, int cb0, int ncb,
-                                       uint32_t seq0, int n_pre) {
+// The bulk-copy ring over [t0, t1): the producer warp refills a stage once
+// every consumer warp released it; consumer warps call fn(ce, cend, sb) for
+// each chunk (entries [ce, cend) staged at sb) and never wait for each other.
+// Chunks carry a per-CTA sequence number seq0 + ci, so stages and mbarrier
+// phases continue across the CTA's items; the item prologue issued the first
+// n_pre chunks.  Returns false (after letting issued copies land) if a wait
+// timed out or another CTA reported an error.
+template <typename T, typename Fn>
+__device__ __forceinline__ bool ring_stream(const LevelArgs<T>& a, const SmemPlan& sp, const CtaView<T>& v,
+                                            const T* tab, uint32_t t0, uint32_t t1, uint32_t seq0, int n_pre,
+                                            Fn&& fn) {
   constexpr int VEC = VecT<T>::N;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t P = g.P, t0 = g.t0, t1 = g.t1;
-  const bool has_joint = c.joint_off >= 0;
-  const bool regjoint = !COLLECT && has_joint && ((uint32_t)sp.chunk % P == 0u);
-  const bool row_in_warp = POW2 && ROWVEC && P <= 32u * VEC;
-  const bool p1 = (P == 1u);
-  // column-joint accumulators per vector slot: the columns a thread sees in
-  // slot `it` repeat every chunk when P divides the chunk
-  T jacc[CBMAX][kVpt][VEC];
-#pragma unroll
-  for (int cl = 0; cl < CBMAX; ++cl)
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it)
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) jacc[cl][it][j] = T(0);
-  const uint32_t S = (uint32_t)sp.stages;
-  const uint32_t chunk = (uint32_t)sp.chunk;
-  const int n_chunks = (int)((t1 - t0 + chunk - 1) / chunk);
-  bool failed = false;
-  int issued = n_pre;  // chunks of this slice already issued (by the item prologue)
-  if (warp == kWarps) {
-    if (lane == 0) {
-      for (int cn = n_pre; cn < n_chunks && !failed; ++cn) {
-        const uint32_t q = seq0 + (uint32_t)cn, st = q % S;
-        if (!mbar_wait(v.ebar + st, ((q / S) - 1) & 1u, a.err)) {
-          failed = true;
-          break;
-        }
-        fence_proxy_async();
-        const uint32_t e = t0 + (uint32_t)cn * chunk;
-        const uint32_t ne = (min(chunk, t1 - e) + VEC - 1) / VEC * VEC;
-        mbar_expect_tx(v.bar + st, ne * (uint32_t)sizeof(T));
-        bulk_g2s(v.buf + (size_t)st * chunk, tab + e, ne * (uint32_t)sizeof(T), v.bar + st);
-        issued = cn + 1;
-      }
-    }
-  } else {
-    for (int ci = 0; ci < n_chunks; ++ci) {
-      const uint32_t q = seq0 + (uint32_t)ci, st = q % S;
-      if (!mbar_wait(v.bar + st, (q / S) & 1u, a.err)) {
-        failed = true;
-        break;
-      }
-      const uint32_t ce = t0 + (uint32_t)ci * chunk;
-      const uint32_t cend = min(t1, ce + chunk);
-      const int nvec = (int)((cend - ce + VEC - 1) / VEC);
-      const T* sb = v.buf + (size_t)st * chunk;
-      T xs[kVpt][VEC];
-#pragma unroll
-      for (int it = 0; it < kVpt; ++it) {
-        const int i = it * kThreads + tid;
-        if (i < nvec) {
-          VecT<T>::lds(sb + (size_t)i * VEC, xs[it]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) xs[it][j] = T(0);
-        }
-      }
-#pragma unroll
-      for (int it = 0; it < kVpt; ++it) {
-        const int i = it * kThreads + tid;
-        if (it * kThreads + warp * 32 >= nvec) break;  // warp-uniform
-        const bool act = i < nvec;
-        const uint32_t e0 = ce + (uint32_t)i * VEC;
-        T x[VEC];
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) x[j] = (act && e0 + j < cend) ? xs[it][j] : T(0);
-        if (ROWVEC) {
-          const uint32_t ea = act ? e0 : t0;
-          const uint32_t rr = row_of<POW2>(c, ea);
-          const uint32_t pr = rr - g.r_lo, col0 = ea - rr * P;
-          T outv[CBMAX][VEC];
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl) {
-            T sum = T(0);
-            if (cl < ncb) {
-              const T G = COLLECT ? T(1) : v.gsm[(size_t)cl * sp.rowmax + pr];
-              const bool cm = v.nobs[sp.cb + cl] != 0;
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) {
-                T o = x[j];
-                if (cm) o *= colmask<T, POW2>(v, sp, cl, col0 + j);
-                if (!COLLECT) {
-                  o *= G;
-                  if (regjoint) jacc[cl][it][j] += o;
-                  else if (has_joint && o != T(0)) atomicAdd(v.jntp[cl] + col0 + j, o);
-                }
-                outv[cl][j] = o;
-                sum += o;
-              }
-              T* rs = v.rsum + (size_t)cl * sp.rowmax;
-              if (POW2) {
-                const uint32_t w = min(P / VEC, 32u);  // lanes sharing the row
-                for (uint32_t o = 1; o < w; o <<= 1) sum += __shfl_xor_sync(kFull, sum, o);
-                if (act && (lane & (w - 1)) == 0) {
-                  if (row_in_warp) rs[pr] = sum;
-                  else atomicAdd(rs + pr, sum);
-                }
-              } else if (act) {
-                atomicAdd(rs + pr, sum);
-              }
-            }
-          }
-          if (!COLLECT && a.calib != nullptr && act) {
-#pragma unroll
-            for (int cl = 0; cl < CBMAX; ++cl)
-              if (cl < ncb)
-                VecT<T>::store(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e0, outv[cl]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) {
-            if (act && e0 + j < cend) {
-              const uint32_t e = e0 + j;
-              const uint32_t rr = row_of<POW2>(c, e);
-              const uint32_t pr = rr - g.r_lo, col = e - rr * P;
-#pragma unroll
-              for (int cl = 0; cl < CBMAX; ++cl) {
-                if (cl < ncb) {
-                  T o = x[j];
-                  if (v.nobs[sp.cb + cl]) o *= colmask<T, POW2>(v, sp, cl, col);
-                  if (!COLLECT) {
-                    o *= v.gsm[(size_t)cl * sp.rowmax + pr];
-                    if (has_joint && o != T(0)) atomicAdd(v.jntp[cl] + col, o);
-                    if (a.calib != nullptr) a.calib[(int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e] = o;
-                  }
-                  T* rs = v.rsum + (size_t)cl * sp.rowmax + pr;
-                  if (p1) *rs = o;
-                  else atomicAdd(rs, o);
-                }
-              }
-            }
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(v.ebar + st);  // this warp is done with the stage
-    }
-  }
-  if (__syncthreads_or(failed)) {
-    if (warp == kWarps && lane == 0) {
-      atomicExch(a.err, 1);
-      // the producer runs at most S chunks ahead of the slowest consumer: let
-      // those copies land before the CTA exits (bounded)
-      for (int cj = max(0, issued - (int)S); cj < issued; ++cj) {
-        const uint32_t q = seq0 + (uint32_t)cj;
-        mbar_wait(v.bar + q % S, (q / S) & 1u, nullptr);
-      }
-    }
-    return false;
-  }
-  if (regjoint && tid < kThreads) {
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it) {
-      const uint32_t colt = (t0 + (uint32_t)(it * kThreads + tid) * VEC) % P;
-#pragma unroll
-      for (int cl = 0; cl < CBMAX; ++cl)
-        if (cl < ncb)
-#pragma unroll
-          for (int j = 0; j < VEC; ++j)
-            if (jacc[cl][it][j] != T(0)) atomicAdd(v.jntp[cl] + (colt + j) % P, jacc[cl][it][j]);
-    }
-  }
-  return true;
-}
-
-// Stream a slice of a clique without private variables (P == 1: every entry
-// is a row) whose fastest digit has a cardinality that is a multiple of the
-// vector width: the entries of a vector differ only in that digit, so every
-// child key is computed once per vector and stepped by the child's w_last.
-// All factors are applied and all outputs formed while streaming.
-template <typename T, bool COLLECT, int CBMAX>
-__device__ __forceinline__ bool stream_p1(const LevelArgs<T>& a, const SmemPlan& sp, const DevClique& c,
-                                          const CtaView<T>& v, const SliceGeo& g, const T* tab, int cb0, int ncb,
-                                          uint32_t seq0, int n_pre, bool is_root, bool out_smem) {
-  constexpr int VEC = VecT<T>::N;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t t0 = g.t0, t1 = g.t1;
-  const int nch = c.n_child, klast = c.k - 1;
-  const bool seg_vec = (c.LR % VEC) == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t S = (uint32_t)sp.stages;
   const uint32_t chunk = (uint32_t)sp.chunk;
   const int n_chunks = (int)((t1 - t0 + chunk - 1) / chunk);
@@ -526,102 +347,7 @@ __device__ __forceinline__ bool stream_p1(const LevelArgs<T>& a, const SmemPlan&
         break;
       }
       const uint32_t ce = t0 + (uint32_t)ci * chunk;
-      const uint32_t cend = min(t1, ce + chunk);
-      const int nvec = (int)((cend - ce + VEC - 1) / VEC);
-      const T* sb = v.buf + (size_t)st * chunk;
-      T xs[kVpt][VEC];
-#pragma unroll
-      for (int it = 0; it < kVpt; ++it) {
-        const int i = it * kThreads + tid;
-        if (i < nvec) {
-          VecT<T>::lds(sb + (size_t)i * VEC, xs[it]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) xs[it][j] = T(0);
-        }
-      }
-#pragma unroll
-      for (int it = 0; it < kVpt; ++it) {
-        if (it * kThreads + warp * 32 >= nvec) break;  // warp-uniform
-        const int i = it * kThreads + tid;
-        const bool act = i < nvec;
-        const uint32_t e0 = act ? ce + (uint32_t)i * VEC : t0;
-        T F[CBMAX][VEC];
-#pragma unroll
-        for (int cl = 0; cl < CBMAX; ++cl) {
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) F[cl][j] = (act && e0 + j < cend) ? xs[it][j] : T(0);
-          if (cl < ncb) {
-            for (int o = 0; o < v.nobs[cl]; ++o) {
-              const int2 ob = v.obs[cl * sp.k + o];
-              const uint32_t d0 = digit<true>(e0, v.pos[ob.x]);
-#pragma unroll
-              for (int j = 0; j < VEC; ++j)
-                if ((ob.x == klast ? d0 + j : d0) != (uint32_t)ob.y) F[cl][j] = T(0);
-            }
-          }
-        }
-        for (int t = 0; t < nch; ++t) {
-          const uint32_t k0 = eval_key<true>(e0, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
-          const uint32_t wl = (uint32_t)v.ch[t].w_last;
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-            if (cl < ncb) {
-              const T* fp = v.facp[cl * sp.n_child + t];
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) F[cl][j] *= fp[k0 + j * wl];
-            }
-        }
-        const uint32_t s0 = e0 >> c.logLR;
-        if (COLLECT) {
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-            if (cl < ncb) {
-              if (seg_vec) {
-                T sum = T(0);
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) sum += F[cl][j];
-                add_combined(v.win + (int64_t)cl * sp.win, s0 - g.seg_lo, sum, lane);
-              } else {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j)
-                  add_combined(v.win + (int64_t)cl * sp.win, ((e0 + j) >> c.logLR) - g.seg_lo, F[cl][j], lane);
-              }
-            }
-        } else {
-          if (!is_root) {
-#pragma unroll
-            for (int cl = 0; cl < CBMAX; ++cl)
-              if (cl < ncb) {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) F[cl][j] *= v.rhop[cl][seg_vec ? s0 : (e0 + j) >> c.logLR];
-              }
-          }
-          for (int t = 0; t < nch; ++t) {
-            const uint32_t k0 = eval_key<true>(e0, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
-            const uint32_t wl = (uint32_t)v.ch[t].w_last;
-#pragma unroll
-            for (int cl = 0; cl < CBMAX; ++cl)
-              if (cl < ncb) {
-                T* op = v.outp[cl * sp.n_child + t];
-                if (wl == 0u) {
-                  T sum = T(0);
-#pragma unroll
-                  for (int j = 0; j < VEC; ++j) sum += F[cl][j];
-                  add_combined(op, k0, sum, lane);
-                } else {
-#pragma unroll
-                  for (int j = 0; j < VEC; ++j) add_combined(op, k0 + j * wl, F[cl][j], lane);
-                }
-              }
-          }
-          if (a.calib != nullptr && act) {
-#pragma unroll
-            for (int cl = 0; cl < CBMAX; ++cl)
-              if (cl < ncb) VecT<T>::store(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e0, F[cl]);
-          }
-        }
-      }
+      fn(ce, min(t1, ce + chunk), v.buf + (size_t)st * chunk);
       __syncwarp();
       if (lane == 0) mbar_arrive(v.ebar + st);  // this warp is done with the stage
     }
@@ -629,12 +355,327 @@ __device__ __forceinline__ bool stream_p1(const LevelArgs<T>& a, const SmemPlan&
   if (__syncthreads_or(failed)) {
     if (warp == kWarps && lane == 0) {
       atomicExch(a.err, 1);
+      // the producer runs at most S chunks ahead of the slowest consumer
       for (int cj = max(0, issued - (int)S); cj < issued; ++cj) {
         const uint32_t q = seq0 + (uint32_t)cj;
         mbar_wait(v.bar + q % S, (q / S) & 1u, nullptr);
       }
     }
     return false;
+  }
+  return true;
+}
+
+// Load the consumer thread's kVpt vectors of a staged chunk (zeros past the end).
+template <typename T>
+__device__ __forceinline__ void load_chunk(const T* sb, uint32_t ce, uint32_t cend, T (&xs)[kVpt][VecT<T>::N]) {
+  constexpr int VEC = VecT<T>::N;
+  const int nvec = (int)((cend - ce + VEC - 1) / VEC);
+#pragma unroll
+  for (int it = 0; it < kVpt; ++it) {
+    const int i = it * kThreads + (int)threadIdx.x;
+    if (i < nvec) {
+      VecT<T>::lds(sb + (size_t)i * VEC, xs[it]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) xs[it][j] = T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j)
+      if (ce + (uint32_t)i * VEC + j >= cend) xs[it][j] = T(0);
+  }
+}
+
+// Stream the slice through the bulk-copy ring: per entry v = phi E_col
+// (times G for distribute); row sums R(r) = sum_col v; distribute also
+// accumulates the column joint and writes the calibrated entry.  Chunks carry
+// a per-CTA sequence number `seq0 + ci`, so ring stages and mbarrier phases
+// continue across the CTA's items.  The producer warp refills a stage once
+// every consumer warp released it; consumer warps never wait for each other.
+// Returns false (after letting issued copies land) if a wait timed out.
+template <typename T, bool COLLECT, bool POW2, bool ROWVEC, int CBMAX>
+__device__ __forceinline__ bool stream(const LevelArgs<T>& a, const SmemPlan& sp, const DevClique& c,
+                                       const CtaView<T>& v, const SliceGeo& g, const T* tab, int cb0, int ncb,
+                                       uint32_t seq0, int n_pre) {
+  constexpr int VEC = VecT<T>::N;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t P = g.P, t0 = g.t0;
+  const bool has_joint = c.joint_off >= 0;
+  const bool regjoint = !COLLECT && has_joint && ((uint32_t)sp.chunk % P == 0u);
+  const bool row_in_warp = POW2 && ROWVEC && P <= 32u * VEC;
+  const bool p1 = (P == 1u);
+  // column-joint accumulators per vector slot: the columns a thread sees in
+  // slot `it` repeat every chunk when P divides the chunk
+  T jacc[CBMAX][kVpt][VEC];
+#pragma unroll
+  for (int cl = 0; cl < CBMAX; ++cl)
+#pragma unroll
+    for (int it = 0; it < kVpt; ++it)
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) jacc[cl][it][j] = T(0);
+  const bool ok = ring_stream<T>(a, sp, v, tab, g.t0, g.t1, seq0, n_pre, [&](uint32_t ce, uint32_t cend, const T* sb) {
+    T xs[kVpt][VEC];
+    load_chunk<T>(sb, ce, cend, xs);
+    const int nvec = (int)((cend - ce + VEC - 1) / VEC);
+#pragma unroll
+    for (int it = 0; it < kVpt; ++it) {
+      if (it * kThreads + (tid & ~31) >= nvec) break;  // warp-uniform
+      const int i = it * kThreads + tid;
+      const bool act = i < nvec;
+      const uint32_t e0 = ce + (uint32_t)i * VEC;
+      const T (&x)[VEC] = xs[it];
+      if (ROWVEC) {
+        const uint32_t ea = act ? e0 : t0;
+        const uint32_t rr = row_of<POW2>(c, ea);
+        const uint32_t pr = rr - g.r_lo, col0 = ea - rr * P;
+        T outv[CBMAX][VEC];
+#pragma unroll
+        for (int cl = 0; cl < CBMAX; ++cl) {
+          T sum = T(0);
+          if (cl < ncb) {
+            const T G = COLLECT ? T(1) : v.gsm[(size_t)cl * sp.rowmax + pr];
+            const bool cm = v.nobs[sp.cb + cl] != 0;
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+              T o = x[j];
+              if (cm) o *= colmask<T, POW2>(v, sp, cl, col0 + j);
+              if (!COLLECT) {
+                o *= G;
+                if (regjoint) jacc[cl][it][j] += o;
+                else if (has_joint && o != T(0)) atomicAdd(v.jntp[cl] + col0 + j, o);
+              }
+              outv[cl][j] = o;
+              sum += o;
+            }
+            T* rs = v.rsum + (size_t)cl * sp.rowmax;
+            if (POW2) {
+              const uint32_t w = min(P / VEC, 32u);  // lanes sharing the row
+              for (uint32_t o = 1; o < w; o <<= 1) sum += __shfl_xor_sync(kFull, sum, o);
+              if (act && (lane & (w - 1)) == 0) {
+                if (row_in_warp) rs[pr] = sum;
+                else atomicAdd(rs + pr, sum);
+              }
+            } else if (act) {
+              atomicAdd(rs + pr, sum);
+            }
+          }
+        }
+        if (!COLLECT && a.calib != nullptr && act) {
+#pragma unroll
+          for (int cl = 0; cl < CBMAX; ++cl)
+            if (cl < ncb) VecT<T>::store(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e0, outv[cl]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          if (act && e0 + j < cend) {
+            const uint32_t e = e0 + j;
+            const uint32_t rr = row_of<POW2>(c, e);
+            const uint32_t pr = rr - g.r_lo, col = e - rr * P;
+#pragma unroll
+            for (int cl = 0; cl < CBMAX; ++cl) {
+              if (cl < ncb) {
+                T o = x[j];
+                if (v.nobs[sp.cb + cl]) o *= colmask<T, POW2>(v, sp, cl, col);
+                if (!COLLECT) {
+                  o *= v.gsm[(size_t)cl * sp.rowmax + pr];
+                  if (has_joint && o != T(0)) atomicAdd(v.jntp[cl] + col, o);
+                  if (a.calib != nullptr) a.calib[(int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e] = o;
+                }
+                T* rs = v.rsum + (size_t)cl * sp.rowmax + pr;
+                if (p1) *rs = o;
+                else atomicAdd(rs, o);
+              }
+            }
+          }
+        }
+      }
+    }
+  });
+  if (!ok) return false;
+  if (regjoint && tid < kThreads) {
+#pragma unroll
+    for (int it = 0; it < kVpt; ++it) {
+      const uint32_t colt = (t0 + (uint32_t)(it * kThreads + tid) * VEC) % P;
+#pragma unroll
+      for (int cl = 0; cl < CBMAX; ++cl)
+        if (cl < ncb)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j)
+            if (jacc[cl][it][j] != T(0)) atomicAdd(v.jntp[cl] + (colt + j) % P, jacc[cl][it][j]);
+    }
+  }
+  return true;
+}
+
+// Stream a slice of a power-of-two clique whose rows are short, doing all row
+// work inline (no per-slice row buffers):
+//   P == 1 (no private variables; the fastest cardinality a multiple of the
+//          vector width): the entries of a vector differ only in the fastest
+//          digit, so every child key is computed once per vector and stepped
+//          by the child's w_last;
+//   VEC <= P <= 32 VEC: a vector lies in one row and a row in one warp
+//          iteration; each lane computes its row factor (lanes of one row read
+//          the same shared-memory words), a segmented shuffle forms the row
+//          sum, and the row's first lane adds the row outputs.
+template <typename T, bool COLLECT, int CBMAX>
+__device__ __forceinline__ bool stream_inline(const LevelArgs<T>& a, const SmemPlan& sp, const DevClique& c,
+                                              const CtaView<T>& v, const SliceGeo& g, const T* tab, int cb0,
+                                              int ncb, uint32_t seq0, int n_pre, bool is_root, bool out_smem) {
+  constexpr int VEC = VecT<T>::N;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t P = g.P;
+  const bool p1 = (P == 1u);
+  const int nch = c.n_child, klast = c.k - 1;
+  const uint32_t w = p1 ? 1u : P / VEC;           // lanes sharing a row
+  const bool seg_vec = !p1 || (c.LR % VEC) == 0;  // the vector's entries share the parent entry
+  const bool has_joint = c.joint_off >= 0;
+  // P divides the chunk (P <= 32 VEC), so each slot's columns repeat every chunk
+  T jacc[CBMAX][kVpt][VEC];
+#pragma unroll
+  for (int cl = 0; cl < CBMAX; ++cl)
+#pragma unroll
+    for (int it = 0; it < kVpt; ++it)
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) jacc[cl][it][j] = T(0);
+  const bool ok = ring_stream<T>(a, sp, v, tab, g.t0, g.t1, seq0, n_pre, [&](uint32_t ce, uint32_t cend, const T* sb) {
+    T xs[kVpt][VEC];
+    load_chunk<T>(sb, ce, cend, xs);
+    const int nvec = (int)((cend - ce + VEC - 1) / VEC);
+#pragma unroll
+    for (int it = 0; it < kVpt; ++it) {
+      if (it * kThreads + (tid & ~31) >= nvec) break;  // warp-uniform
+      const int i = it * kThreads + tid;
+      const bool act = i < nvec;
+      const uint32_t e0 = act ? ce + (uint32_t)i * VEC : g.t0;
+      const uint32_t r = p1 ? e0 : (e0 >> c.logP);    // row (P == 1: of the vector's first entry)
+      const uint32_t col0 = e0 - r * P;
+      // factor per entry: E_row x prod_g mu_g (x rho for distribute), times phi E_col
+      T f[CBMAX][VEC];
+#pragma unroll
+      for (int cl = 0; cl < CBMAX; ++cl) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) f[cl][j] = act ? xs[it][j] : T(0);
+        if (cl < ncb) {
+          for (int o = 0; o < v.nobs[cl]; ++o) {
+            const int2 ob = v.obs[cl * sp.k + o];
+            const uint32_t d0 = digit<true>(r, v.pos[ob.x]);
+#pragma unroll
+            for (int j = 0; j < VEC; ++j)
+              if (((p1 && ob.x == klast) ? d0 + j : d0) != (uint32_t)ob.y) f[cl][j] = T(0);
+          }
+          if (!p1 && v.nobs[sp.cb + cl]) {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) f[cl][j] *= colmask<T, true>(v, sp, cl, col0 + j);
+          }
+        }
+      }
+      for (int t = 0; t < nch; ++t) {
+        const uint32_t k0 = eval_key<true>(r, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
+        const uint32_t wl = p1 ? (uint32_t)v.ch[t].w_last : 0u;
+#pragma unroll
+        for (int cl = 0; cl < CBMAX; ++cl)
+          if (cl < ncb) {
+            const T* fp = v.facp[cl * sp.n_child + t];
+            if (wl == 0u) {
+              const T fv = fp[k0];
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) f[cl][j] *= fv;
+            } else {
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) f[cl][j] *= fp[k0 + j * wl];
+            }
+          }
+      }
+      const uint32_t s0 = r >> c.logLR;
+      if (COLLECT) {
+#pragma unroll
+        for (int cl = 0; cl < CBMAX; ++cl)
+          if (cl < ncb) {
+            if (seg_vec) {
+              T sum = T(0);
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) sum += f[cl][j];
+              add_combined(v.win + (int64_t)cl * sp.win, s0 - g.seg_lo, sum, lane);
+            } else {
+#pragma unroll
+              for (int j = 0; j < VEC; ++j)
+                add_combined(v.win + (int64_t)cl * sp.win, ((r + j) >> c.logLR) - g.seg_lo, f[cl][j], lane);
+            }
+          }
+      } else {
+        if (!is_root) {
+#pragma unroll
+          for (int cl = 0; cl < CBMAX; ++cl)
+            if (cl < ncb) {
+              if (seg_vec) {
+                const T rh = v.rhop[cl][s0];
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) f[cl][j] *= rh;
+              } else {
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) f[cl][j] *= v.rhop[cl][(r + j) >> c.logLR];
+              }
+            }
+        }
+        // row sums over the lanes of a row (P > 1) and the row outputs
+        T rs[CBMAX];
+#pragma unroll
+        for (int cl = 0; cl < CBMAX; ++cl) {
+          rs[cl] = T(0);
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) rs[cl] += f[cl][j];
+          for (uint32_t o = 1; o < w; o <<= 1) rs[cl] += __shfl_xor_sync(kFull, rs[cl], o);
+          if ((lane & (w - 1)) != 0) rs[cl] = T(0);  // the row's first lane adds it
+        }
+        for (int t = 0; t < nch; ++t) {
+          const uint32_t k0 = eval_key<true>(r, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
+          const uint32_t wl = p1 ? (uint32_t)v.ch[t].w_last : 0u;
+#pragma unroll
+          for (int cl = 0; cl < CBMAX; ++cl)
+            if (cl < ncb) {
+              T* op = v.outp[cl * sp.n_child + t];
+              if (wl == 0u) {
+                add_combined(op, k0, rs[cl], lane);
+              } else {
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) add_combined(op, k0 + j * wl, f[cl][j], lane);
+              }
+            }
+        }
+        for (int h = 0; h < c.n_home; ++h) {
+          const DevHome hm = v.hm[h];
+          const uint32_t d = digit<true>(r, v.pos[hm.pos]);
+#pragma unroll
+          for (int cl = 0; cl < CBMAX; ++cl)
+            if (cl < ncb) add_combined(v.houtp[cl] + (out_smem ? hm.out_off : hm.moff), d, rs[cl], lane);
+        }
+        if (has_joint) {
+#pragma unroll
+          for (int cl = 0; cl < CBMAX; ++cl)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) jacc[cl][it][j] += f[cl][j];
+        }
+        if (a.calib != nullptr && act) {
+#pragma unroll
+          for (int cl = 0; cl < CBMAX; ++cl)
+            if (cl < ncb) VecT<T>::store(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e0, f[cl]);
+        }
+      }
+    }
+  });
+  if (!ok) return false;
+  if (!COLLECT && has_joint && tid < kThreads) {
+#pragma unroll
+    for (int it = 0; it < kVpt; ++it) {
+      const uint32_t colt = (g.t0 + (uint32_t)(it * kThreads + tid) * VEC) % P;
+#pragma unroll
+      for (int cl = 0; cl < CBMAX; ++cl)
+        if (cl < ncb)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j)
+            if (jacc[cl][it][j] != T(0)) atomicAdd(v.jntp[cl] + colt + j, jacc[cl][it][j]);
+    }
   }
   return true;
 }
@@ -724,11 +765,8 @@ __device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const De
   const T** s_rhop = reinterpret_cast<const T**>(smem + lay.off_rhop);  // [cb]
   T** s_houtp = reinterpret_cast<T**>(smem + lay.off_houtp);            // [cb]
   T** s_jntp = reinterpret_cast<T**>(smem + lay.off_jntp);              // [cb]
-  T* s_fac = reinterpret_cast<T*>(smem + lay.off_fac);
-  T* s_rho = reinterpret_cast<T*>(smem + lay.off_rho);
-  T* s_out = reinterpret_cast<T*>(smem + lay.off_out);
+  T* s_tabs = reinterpret_cast<T*>(smem + lay.off_tabs);
   T* s_win = reinterpret_cast<T*>(smem + lay.off_win);
-  T* s_jnt = reinterpret_cast<T*>(smem + lay.off_jnt);
   double* s_red = reinterpret_cast<double*>(smem + lay.off_red);
   int* s_flag = reinterpret_cast<int*>(s_red + 72);
   const int32_t** s_deps = reinterpret_cast<const int32_t**>(s_red + 40);  // up to 32 dependency flags per batch
@@ -767,7 +805,10 @@ __device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const De
   const int64_t msg = a.msg_total;
   const int64_t off_down = msg, off_rho = 2 * msg, off_marg = 3 * msg, off_joint = 3 * msg + a.marg_total;
   const bool has_joint = c.joint_off >= 0;
-  const bool fac_smem = sp.fac > 0, rho_smem = sp.rho > 0, out_smem = sp.out > 0, jnt_smem = sp.jnt > 0;
+  // per-clique residency in the per-case table region (offsets from the plan)
+  const bool fac_smem = c.sm_fac >= 0, rho_smem = c.sm_rho >= 0, out_smem = c.sm_out >= 0;
+  const bool jnt_smem = c.sm_jnt >= 0;
+  auto region = [&](int cl) { return s_tabs + (int64_t)cl * sp.tabs; };
   auto case_acc = [&](int cl) { return a.acc + (int64_t)(cb0 + cl) * a.acc_stride; };
   auto flag_of = [&](int phase, int clique) { return a.done + ((int64_t)phase * a.n_cliques + clique) * a.max_cases + cbk; };
 
@@ -781,18 +822,20 @@ __device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const De
   if (tid < ncb) {
     T* acc = case_acc(tid);
     s_rhop[tid] = (is_root || COLLECT) ? nullptr
-                  : (rho_smem ? (const T*)(s_rho + (int64_t)tid * sp.rho) : (const T*)(acc + off_rho + c.sep_off));
-    s_houtp[tid] = out_smem ? s_out + (int64_t)tid * sp.out : acc + off_marg;
-    s_jntp[tid] = !has_joint ? nullptr : (jnt_smem ? s_jnt + (int64_t)tid * sp.jnt : acc + off_joint + c.joint_off);
+                  : (rho_smem ? (const T*)(region(tid) + c.sm_rho) : (const T*)(acc + off_rho + c.sep_off));
+    s_houtp[tid] = out_smem ? region(tid) + c.sm_out : acc + off_marg;
+    s_jntp[tid] = !has_joint ? nullptr : (jnt_smem ? region(tid) + c.sm_jnt : acc + off_joint + c.joint_off);
   }
   for (int i = tid; i < sp.cb * sp.rowmax; i += kBlock) s_rsum[i] = T(0);
   if (COLLECT) {
     for (int i = tid; i < ncb * sp.win; i += kBlock) s_win[i] = T(0);
   } else {
-    if (out_smem)
-      for (int i = tid; i < ncb * sp.out; i += kBlock) s_out[i] = T(0);
+    if (out_smem) {
+      const int n_out = c.sm_out_len;
+      for (int i = tid; i < ncb * n_out; i += kBlock) region(i / n_out)[c.sm_out + i % n_out] = T(0);
+    }
     if (jnt_smem && has_joint)
-      for (int i = tid; i < ncb * sp.jnt; i += kBlock) s_jnt[i] = T(0);
+      for (int i = tid; i < ncb * c.P; i += kBlock) region(i / c.P)[c.sm_jnt + i % c.P] = T(0);
   }
   __syncthreads();
   for (int idx = tid; idx < ncb * k; idx += kBlock) {
@@ -815,10 +858,10 @@ __device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const De
     const int cl = idx / nch, t = idx - cl * nch;
     const DevChild ch = s_ch[t];
     T* acc = case_acc(cl);
-    s_facp[cl * sp.n_child + t] = fac_smem ? (const T*)(s_fac + (int64_t)cl * sp.fac + ch.fac_off)
+    s_facp[cl * sp.n_child + t] = fac_smem ? (const T*)(region(cl) + c.sm_fac + ch.fac_off)
                                            : (const T*)(acc + ch.sep_off);
     if (!COLLECT)
-      s_outp[cl * sp.n_child + t] = out_smem ? s_out + (int64_t)cl * sp.out + ch.fac_off : acc + off_down + ch.sep_off;
+      s_outp[cl * sp.n_child + t] = out_smem ? region(cl) + c.sm_out + ch.fac_off : acc + off_down + ch.sep_off;
   }
   __syncthreads();
 
@@ -840,12 +883,12 @@ __device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const De
       if (fac_smem) {
         for (int t = 0; t < nch; ++t) {
           const DevChild ch = s_ch[t];
-          T* dst = s_fac + (int64_t)cl * sp.fac + ch.fac_off;
+          T* dst = region(cl) + c.sm_fac + ch.fac_off;
           for (int j = tid; j < ch.sep_size; j += kBlock) dst[j] = __ldcg(acc + ch.sep_off + j);
         }
       }
       if (rho_smem && !COLLECT && !is_root) {
-        T* dst = s_rho + (int64_t)cl * sp.rho;
+        T* dst = region(cl) + c.sm_rho;
         for (int j = tid; j < c.sep_size; j += kBlock) dst[j] = __ldcg(acc + off_rho + c.sep_off + j);
       }
     }
@@ -858,12 +901,12 @@ __device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const De
     const CtaView<T> v{s_ch,   s_fld,   s_hm,   s_pos, s_obs, s_cobs, s_nobs,  s_facp, s_outp,
                  s_rhop, s_houtp, s_jntp, s_win, s_buf, s_bar,  s_ebar, s_rsum, s_gsm};
     const bool rowvec = (c.P % VEC) == 0;
-    const bool p1vec = c.P == 1 && c.pow2 && (c.card_last % VEC) == 0;
+    const bool inl = inline_rows(c, VEC);
     bool ok = true;
-    if (!COLLECT || p1vec) ok = await_inputs();
-    if (ok && p1vec) {
+    if (!COLLECT || inl) ok = await_inputs();
+    if (ok && inl) {
       const SliceGeo g = slice_geo<true>(c, t0, t1);
-      ok = stream_p1<T, COLLECT, CBMAX>(a, sp, c, v, g, tab, cb0, ncb, seq0, n_pre, is_root, out_smem);
+      ok = stream_inline<T, COLLECT, CBMAX>(a, sp, c, v, g, tab, cb0, ncb, seq0, n_pre, is_root, out_smem);
     } else if (ok) {
       if (c.pow2) {
         const SliceGeo g = slice_geo<true>(c, t0, t1);
@@ -915,21 +958,21 @@ __device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const De
         for (int t = 0; t < nch; ++t) {
           const DevChild ch = s_ch[t];
           for (int j = tid; j < ch.sep_size; j += kBlock) {
-            const T val = s_out[(int64_t)cl * sp.out + ch.fac_off + j];
+            const T val = region(cl)[c.sm_out + ch.fac_off + j];
             if (val != T(0)) atomicAdd(acc + off_down + ch.sep_off + j, val);
           }
         }
         for (int h = 0; h < c.n_home; ++h) {
           const DevHome hm = s_hm[h];
           for (int st = tid; st < hm.card; st += kBlock) {
-            const T val = s_out[(int64_t)cl * sp.out + hm.out_off + st];
+            const T val = region(cl)[c.sm_out + hm.out_off + st];
             if (val != T(0)) atomicAdd(acc + off_marg + hm.moff + st, val);
           }
         }
       }
       if (jnt_smem && has_joint) {
         for (int j = tid; j < c.P; j += kBlock) {
-          const T val = s_jnt[(int64_t)cl * sp.jnt + j];
+          const T val = region(cl)[c.sm_jnt + j];
           if (val != T(0)) atomicAdd(acc + off_joint + c.joint_off + j, val);
         }
       }
@@ -1131,15 +1174,22 @@ int32_t smem_budget(int device) {
   return v;
 }
 
+// Kernel attributes (maximum dynamic shared memory, carveout) are set once per
+// process, before the first occupancy query or launch.
 template <typename T>
-cudaError_t launch_propagate(const LevelArgs<T>& a, const SmemPlan& sp, int grid, cudaStream_t s) {
-  static bool attr_done = false;  // once per dtype instantiation
-  if (!attr_done) {
+void ensure_attrs() {
+  static bool done = false;
+  if (!done) {
     int dev = 0;
     cudaGetDevice(&dev);
     attr_all<T>(smem_budget(dev));
-    attr_done = true;
+    done = true;
   }
+}
+
+template <typename T>
+cudaError_t launch_propagate(const LevelArgs<T>& a, const SmemPlan& sp, int grid, cudaStream_t s) {
+  ensure_attrs<T>();
   const int bytes = SmemLayout(sp).bytes;
   if (sp.cb <= 1) {
     k_propagate<T, 1><<<grid, kBlock, bytes, s>>>(a, sp);
@@ -1152,6 +1202,8 @@ cudaError_t launch_propagate(const LevelArgs<T>& a, const SmemPlan& sp, int grid
 int32_t propagate_occupancy(int elem, int cb, int bytes) {
   int n = 0;
   cudaError_t e;
+  if (elem == 8) ensure_attrs<double>();
+  else ensure_attrs<float>();
   if (elem == 8) {
     e = cb <= 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<double, 1>, kBlock, bytes)
                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<double, 8>, kBlock, bytes);

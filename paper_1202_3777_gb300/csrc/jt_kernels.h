@@ -13,11 +13,9 @@ struct SmemPlan {
   int32_t cb;                    // evidence cases handled by one CTA
   int32_t n_child, n_field;      // maxima over the level's cliques
   int32_t n_home, k;
-  int32_t fac;                   // per case: entries for child factors (0: read from global)
-  int32_t rho;                   // per case: entries for the parent ratio (0: read from global)
-  int32_t out;                   // per case: child-separator + row-home accumulators (0: global)
+  int32_t tabs;                  // per case: entries of the table region (per-clique residency,
+                                 // see DevClique.sm_*)
   int32_t win;                   // per case: collect window of parent-separator entries
-  int32_t jnt;                   // per case: column-joint accumulators (0: global or none)
   int32_t elem;                  // sizeof(T)
   int32_t stages;                // bulk-copy ring: number of chunk buffers
   int32_t chunk;                 // entries per chunk (= threads x vector width)
@@ -28,7 +26,7 @@ struct SmemPlan {
 struct SmemLayout {
   int32_t off_ch, off_fld, off_hm, off_pos, off_obs, off_nobs;
   int32_t off_facp, off_outp, off_rhop, off_houtp, off_jntp;
-  int32_t off_fac, off_rho, off_out, off_win, off_jnt, off_red, off_bar, off_rsum, off_gsm, off_buf;
+  int32_t off_tabs, off_win, off_red, off_bar, off_rsum, off_gsm, off_buf;
   int32_t bytes;
 
   __host__ __device__ static int32_t a16(int32_t x) { return (x + 15) & ~15; }
@@ -46,11 +44,8 @@ struct SmemLayout {
     off_rhop = o;  o = a16(o + s.cb * 8);
     off_houtp = o; o = a16(o + s.cb * 8);
     off_jntp = o;  o = a16(o + s.cb * 8);
-    off_fac = o;   o = a16(o + s.cb * s.fac * s.elem);
-    off_rho = o;   o = a16(o + s.cb * s.rho * s.elem);
-    off_out = o;   o = a16(o + s.cb * s.out * s.elem);
+    off_tabs = o;  o = a16(o + s.cb * s.tabs * s.elem);
     off_win = o;   o = a16(o + s.cb * s.win * s.elem);
-    off_jnt = o;   o = a16(o + s.cb * s.jnt * s.elem);
     off_red = o;   o = a16(o + 80 * 8);
     off_bar = o;   o = a16(o + 2 * s.stages * 8);   // full and empty barriers
     off_rsum = o;  o = a16(o + s.cb * s.rowmax * s.elem);
@@ -60,6 +55,16 @@ struct SmemLayout {
     bytes = o;
   }
 };
+
+// Cliques whose rows are short enough to be processed inline while streaming
+// (the kernel's stream_inline): power-of-two cardinalities, and either no
+// private variables with a vector-aligned fastest digit, or vector-aligned
+// rows of at most 32 vectors.
+__host__ __device__ inline bool inline_rows(const DevClique& c, int vec) {
+  if (!c.pow2) return false;
+  if (c.P == 1) return c.card_last % vec == 0;
+  return c.P % vec == 0 && c.P <= 32 * vec;
+}
 
 // Enqueue a whole propagation (collect and distribute of every clique for
 // the case range of `a`) as one persistent launch of `grid` CTAs on `s`.
