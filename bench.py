@@ -36,6 +36,13 @@ METRIC = "propagation clique-entries/s (batched FP32 vs plain); p50/p99 query la
 UNIT = "clique-entries/s"
 
 
+def _json_default(o):
+    """numpy scalars in the JSON line."""
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(type(o))
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -307,7 +314,7 @@ def main():
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(out), flush=True)
+    print(json.dumps(out, default=_json_default), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
