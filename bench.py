@@ -256,10 +256,14 @@ def main():
     entries = tree.entries()
     info = h.info
 
+    root_entries = int(tree.table_sizes()[0])
+    streamed = 2 * entries - root_entries   # collect reads every non-root table, distribute every table
+
     def alg_bytes(cases):
-        # every clique table read once per pass, plus per case: messages
-        # written and read in each pass and the marginal sums
-        return 2 * w * entries + cases * w * (4 * msg_total(tree) + info.marginal_len)
+        # every clique table read once per pass and per block of 8 cases,
+        # plus per case: messages written and read in each pass
+        n_cb = (cases + 7) // 8
+        return w * streamed * n_cb + cases * w * (4 * msg_total(tree) + info.marginal_len)
 
     ach_b = alg_bytes(B) / (prof_b[0] * 1e-3) / 1e9
     ach_1 = alg_bytes(1) / (prof_1[0] * 1e-3) / 1e9

@@ -1,15 +1,15 @@
-// C ABI of libjt: tree lifetime, evidence, propagation schedule (CUDA graphs
-// of level launches), and read-out.  See include/jt.h for the contract.
+// C ABI of libjt: tree lifetime, evidence, propagation (one CUDA graph per
+// case range: zeroing, the persistent propagation kernel, finalisation) and
+// read-out.  See include/jt.h for the contract.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
-#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -38,28 +38,22 @@ jt_status cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, where); \
   } while (0)
 
-constexpr int kCbMax = 8;
-constexpr int kMinStages = 3, kMaxStages = 6;   // bulk-copy ring depth (chunks of 16 KB)
-constexpr int kRowMax = 4096;                   // rows of one slice held in shared memory
-constexpr int kChunkVecs = 2 * kLevelThreads;   // 16-byte vectors per bulk-copy chunk
-constexpr int kTwoPerSm = 112 * 1024;           // dynamic shared memory that leaves room for two CTAs
-constexpr int kWinMax = 4096;     // max parent-separator entries one collect CTA accumulates
-constexpr int kStatusZero = 1, kStatusBadState = 2;
+constexpr int kCaseBlock = 8;   // evidence cases per work item when a propagation covers several cases
 
-// The schedule of one case range: shared-memory plan, work items, grid.
-struct Schedule {
-  SmemPlan sp{};
-  int32_t grid = 0;
-  int32_t n_items = 0;
-  DevWork* items = nullptr;       // device
-  DevClique* cliques = nullptr;   // device: the tree's descriptors with this schedule's residency
-};
-
+// A propagation shape (case range) recorded as a CUDA graph, with the device
+// copy of its schedule.
 struct GraphEntry {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<void*> dev_bufs;    // work lists owned by this graph
   Schedule sched;
+  std::vector<void*> dev_bufs;
+  const DevStage* stages = nullptr;
+  const DevPort* ports = nullptr;
+  const DevField* fields = nullptr;
+  const DevPos* pos = nullptr;
+  const int32_t* deps = nullptr;
+  const DevItem* items = nullptr;
+  int32_t grid = 0, smem = 0;
 };
 
 }  // namespace
@@ -74,31 +68,20 @@ struct jt_tree_s {
   int32_t max_cases = 1;
   size_t elem = 4;
   // device memory
-  void* base = nullptr;
-  DevClique* d_cl = nullptr;
-  DevPos* d_pos = nullptr;
-  DevChild* d_ch = nullptr;
-  DevHome* d_hm = nullptr;
-  DevSrc* d_src = nullptr;
-  DevSrc* d_jh = nullptr;
-  int32_t* d_cnt = nullptr;
-  VarSrc* d_vs = nullptr;
-  int32_t* d_done = nullptr;      // [2][n_cliques][max_cases] dependency flags + the work-queue counter
-  int32_t* d_parent = nullptr;
+  void* base = nullptr;           // permuted clique tables
+  void* d_msg = nullptr;          // [max_cases][msg_stride] u | delta | joint
+  double* d_sums = nullptr;       // [max_cases][2 n_cliques] stage totals
+  int32_t* d_done = nullptr;      // [0] work queue, then [2 n_cliques][case blocks] finished blocks
   int32_t* d_err = nullptr;       // set by a kernel whose bounded wait gave up
-  DevField* d_fld = nullptr;
-  int32_t* d_card = nullptr;
-  int32_t* d_moff = nullptr;
-  int16_t* d_ev = nullptr;
-  void* d_acc = nullptr;
-  int64_t acc_stride = 0;
-  double* d_ls = nullptr;
-  int32_t* d_status = nullptr;
-  double* d_marg = nullptr;
-  double* d_logz = nullptr;
-  void* d_calib = nullptr;
+  int32_t* d_status = nullptr;    // [max_cases]
+  double* d_marg = nullptr;       // [max_cases][marg_total]
+  double* d_logz = nullptr;       // [max_cases]
+  int16_t* d_ev = nullptr;        // [max_cases][n_vars]
+  void* d_calib = nullptr;        // [max_cases][base_len] (JT_MATERIALIZE_CLIQUES)
   double* d_scratch = nullptr;    // read-out scratch (sum + clique table)
   int64_t scratch_len = 0;
+  VarSrc* d_vs = nullptr;
+  int32_t* d_sep_size = nullptr;
   int64_t device_bytes = 0;
   // host state
   int16_t* h_ev = nullptr;        // pinned mirror [max_cases][n_vars]
@@ -136,8 +119,8 @@ void destroy(jt_tree t) {
   cudaSetDevice(t->device);
   cudaDeviceSynchronize();
   free_graphs(t);
-  void* ptrs[] = {t->base, t->d_cl, t->d_pos, t->d_ch, t->d_hm, t->d_src, t->d_jh, t->d_cnt, t->d_vs, t->d_done, t->d_parent, t->d_err, t->d_fld, t->d_card, t->d_moff,
-                  t->d_ev, t->d_acc, t->d_ls, t->d_status, t->d_marg, t->d_logz, t->d_calib, t->d_scratch};
+  void* ptrs[] = {t->base,   t->d_msg,  t->d_sums,  t->d_done,    t->d_err, t->d_status, t->d_marg,
+                  t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_sep_size};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->h_ev) cudaFreeHost(t->h_ev);
@@ -146,219 +129,73 @@ void destroy(jt_tree t) {
   delete t;
 }
 
-// ---------------------------------------------------------------------------
-// Schedule for a case range: per level, the CTA slices and shared-memory plan.
-// ---------------------------------------------------------------------------
-
-// Work items and the (uniform) shared-memory plan of one propagation over
-// n_cases cases: every clique table is cut into slices (multiples of the
-// bulk-copy chunk, at most `rowcap` rows, a collect window of at most kWinMax
-// parent-separator entries, about two slices per SM per level); cases are
-// grouped into blocks of cb.  Shared-memory residency, most valuable first:
-// per-slice row sums / row factors and the column joint (touched per entry),
-// then factors and outputs (touched per row), which otherwise stay in global
-// memory.
-jt_status plan_schedule(jt_tree t, int n_cases, Schedule* S, std::vector<DevWork>* items,
-                        std::vector<DevClique>* cliques) {
-  const Plan& p = t->plan;
-  const int VEC = (int)(16 / t->elem);
-  const int chunk = kChunkVecs * VEC;       // two vectors per consumer thread per chunk
-  int n_child = 0, n_field = 0, n_home = 0, k = 0, facm = 0, rho = 0, outd = 0, jnt = 0;
-  for (int c = 0; c < p.n_cliques; ++c) {
-    const DevClique& dc = p.dcl[c];
-    n_child = std::max(n_child, dc.n_child);
-    n_field = std::max(n_field, dc.n_field);
-    n_home = std::max(n_home, dc.n_home);
-    k = std::max(k, dc.k);
-    facm = std::max(facm, p.fac_collect[c]);
-    if (c != 0) rho = std::max(rho, dc.sep_size);
-    outd = std::max(outd, p.out_dist[c]);
-    if (dc.joint_off >= 0) jnt = std::max(jnt, dc.P);
-  }
-  const int budget = t->smem_max;
-  std::vector<int64_t> ctile(p.n_cliques);
-  int win = 1, rowmax = 1, cb = 1;
-  auto make_tiles = [&](int cbv, int rowcap) {
-    win = 1;
-    rowmax = 1;
-    const int nb = (n_cases + cbv - 1) / cbv;
-    for (int d = 0; d <= p.max_depth; ++d) {
-      int64_t E = 0;
-      for (int c : p.levels[d]) E += p.dcl[c].n;
-      const int64_t tiles_wanted = std::max<int64_t>(1, (2ll * t->n_sm) / std::max(1, nb));
-      int64_t tile = (E + tiles_wanted - 1) / tiles_wanted;
-      tile = std::max<int64_t>(tile, chunk);
-      tile = std::min<int64_t>(tile, 1 << 20);
-      for (int c : p.levels[d]) {
-        const DevClique& dc = p.dcl[c];
-        const int64_t L = (int64_t)dc.LR * dc.P;
-        // short rows are processed inline while streaming (no per-row buffers)
-        const bool inl = inline_rows(dc, VEC);
-        int64_t tc = std::min<int64_t>(tile, (int64_t)(kWinMax - 2) * L);
-        if (!inl) tc = std::min<int64_t>(tc, (int64_t)(rowcap - 2) * dc.P);
-        tc = std::max<int64_t>(chunk, tc / chunk * chunk);
-        ctile[c] = tc;
-        const int64_t wn = std::min<int64_t>(tc, dc.n) / L + 2;
-        win = (int)std::max<int64_t>(win, std::min<int64_t>(wn, dc.sep_size));
-        if (!inl) rowmax = (int)std::max<int64_t>(rowmax, std::min<int64_t>(tc, dc.n) / dc.P + 2);
-      }
-    }
-  };
-  // fixed part of the layout; what is left of the shared memory becomes the
-  // per-case table region, packed clique by clique
-  int maxneed = 0;
-  for (int c = 0; c < p.n_cliques; ++c) {
-    const DevClique& dc = p.dcl[c];
-    const int need = p.fac_collect[c] + (c ? dc.sep_size : 0) + p.out_dist[c] + (dc.joint_off >= 0 ? dc.P : 0);
-    maxneed = std::max(maxneed, need);
-  }
-  auto plan_of = [&](int stages, int tabs) {
-    return SmemPlan{cb, n_child, n_field, n_home, k, tabs, win, (int32_t)t->elem, stages, chunk, rowmax, 0};
-  };
-  bool ok = false;
-  int tabs = 0;
-  for (int cbv = std::min(kCbMax, std::max(1, n_cases)); cbv >= 1 && !ok; cbv = cbv > 1 ? cbv / 2 : 0) {
-    cb = cbv;
-    for (int rowcap = kRowMax; rowcap >= 64 && !ok; rowcap /= 2) {
-      make_tiles(cbv, rowcap);
-      const int fixed = SmemLayout(plan_of(kMinStages, 0)).bytes;
-      if (fixed > budget) continue;
-      const int cap = fixed <= kTwoPerSm ? kTwoPerSm : budget;
-      tabs = std::max(0, (cap - fixed - 64) / (cb * (int)t->elem));
-      tabs = std::min(tabs, maxneed);
-      ok = true;
-    }
-  }
-  if (!ok) return fail(JT_ERR_UNSUPPORTED, "the tree's per-clique tables do not fit in shared memory");
-  // deepen the bulk-copy ring with what is left while two CTAs still fit on an SM
-  SmemPlan sp = plan_of(kMinStages, tabs);
-  const int cap = std::max(SmemLayout(sp).bytes, std::min(budget, kTwoPerSm));
-  while (sp.stages < kMaxStages) {
-    SmemPlan q = sp;
-    q.stages++;
-    if (SmemLayout(q).bytes > cap) break;
-    sp = q;
-  }
-  // per-clique residency in the table region: child factors, parent ratio,
-  // accumulators, column joint -- in that order while they fit
-  cliques->assign(p.dcl.begin(), p.dcl.end());
-  for (int c = 0; c < p.n_cliques; ++c) {
-    DevClique& dc = (*cliques)[c];
-    int off = 0;
-    auto place = [&](int n) {
-      if (n <= 0 || off + n > tabs) return -1;
-      const int o = off;
-      off += n;
-      return o;
-    };
-    dc.sm_fac = dc.n_child ? place(p.fac_collect[c]) : -1;
-    dc.sm_rho = c ? place(dc.sep_size) : -1;
-    dc.sm_out_len = p.out_dist[c];
-    dc.sm_out = place(p.out_dist[c]);
-    dc.sm_jnt = dc.joint_off >= 0 ? place(dc.P) : -1;
-  }
-  const int nb = (n_cases + cb - 1) / cb;
-  items->clear();
-  auto add_level = [&](int d, int collect) {
-    for (int c : p.levels[d]) {
-      const DevClique& dc = p.dcl[c];
-      const int nt = (int)((dc.n + ctile[c] - 1) / ctile[c]);
-      for (int ti = 0; ti < nt; ++ti)
-        for (int b = 0; b < nb; ++b) {
-          DevWork wk{};
-          wk.base_off = dc.base_off;
-          wk.clique = c;
-          wk.t0 = (int32_t)(ti * ctile[c]);
-          wk.t1 = (int32_t)std::min<int64_t>(dc.n, (ti + 1) * ctile[c]);
-          wk.ntiles = nt;
-          wk.cbk = b;
-          wk.collect = collect;
-          items->push_back(wk);
-        }
-    }
-  };
-  for (int d = p.max_depth; d >= 0; --d) add_level(d, 1);  // collect: deepest level first
-  for (int d = 0; d <= p.max_depth; ++d) add_level(d, 0);  // distribute: root first
-  const int occ = std::max(1, propagate_occupancy((int)t->elem, cb, SmemLayout(sp).bytes));
-  if (const char* dbg = std::getenv("JT_DEBUG_PLAN"); dbg && *dbg == '1') {
-    int nf = 0, nr = 0, no = 0, nj = 0;
-    for (const DevClique& dc : *cliques) {
-      nf += dc.sm_fac >= 0;
-      nr += dc.sm_rho >= 0;
-      no += dc.sm_out >= 0;
-      nj += dc.sm_jnt >= 0;
-    }
-    std::fprintf(stderr,
-                 "[jt plan] cases=%d cb=%d items=%zu grid=%d occ=%d smem=%d stages=%d chunk=%d rowmax=%d win=%d "
-                 "tabs=%d resident fac/rho/out/jnt=%d/%d/%d/%d of %d cliques\n",
-                 n_cases, cb, items->size(), (int)std::min<int64_t>((int64_t)items->size(), (int64_t)t->n_sm * occ), occ,
-                 SmemLayout(sp).bytes, sp.stages, sp.chunk, sp.rowmax, sp.win, sp.tabs, nf, nr, no, nj,
-                 p.n_cliques);
-  }
-  S->sp = sp;
-  S->n_items = (int32_t)items->size();
-  S->grid = (int32_t)std::min<int64_t>(S->n_items, (int64_t)t->n_sm * occ);
+template <typename V>
+jt_status upload_vec(jt_tree t, std::vector<void*>* owner, const V** dst, const std::vector<V>& src,
+                     const char* what) {
+  V* p = nullptr;
+  const size_t n = std::max<size_t>(1, src.size());
+  cudaError_t e = cudaMalloc((void**)&p, n * sizeof(V));
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  owner->push_back(p);
+  if (!src.empty()) CU(cudaMemcpy(p, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice), what);
+  *dst = p;
+  (void)t;
   return JT_OK;
 }
 
+// Enqueue a whole propagation of a case range on `s`: zero the per-case
+// accumulators, counters and the work queue, run the persistent propagation
+// kernel, finalise.  With `ev` non-null an event is recorded before the
+// propagation kernel, between it and the finalisation, and after.
 template <typename T>
-LevelArgs<T> level_args(jt_tree t, int case0, int n_cases) {
-  LevelArgs<T> a{};
-  a.cl = t->d_cl;
-  a.pos = t->d_pos;
-  a.ch = t->d_ch;
-  a.hm = t->d_hm;
-  a.src = t->d_src;
-  a.jh = t->d_jh;
-  a.fld = t->d_fld;
-  a.base = (const T*)t->base;
-  a.case0 = case0;
-  a.n_cases = n_cases;
-  a.ev = t->d_ev;
-  a.n_vars = t->plan.n_vars;
-  a.acc = (T*)t->d_acc;
-  a.acc_stride = t->acc_stride;
-  a.msg_total = t->plan.msg_total;
-  a.marg_total = t->plan.marg_total;
-  a.joint_total = t->plan.joint_total;
-  a.ls = t->d_ls;
-  a.n_cliques = t->plan.n_cliques;
-  a.status = t->d_status;
-  a.cnt = t->d_cnt;
-  a.done = t->d_done;
-  a.queue = t->d_done + 2ll * t->plan.n_cliques * t->max_cases;
-  a.parent_of = t->d_parent;
-  a.err = t->d_err;
-  a.max_cases = t->max_cases;
-  a.calib = (T*)t->d_calib;
-  a.calib_stride = t->plan.base_len;
-  return a;
-}
-
-// Launch the whole propagation for a case range on `s`: zero the per-case
-// accumulators, dependency flags and the work queue, run the persistent
-// propagation kernel, finalise.  With `ev` non-null an event is recorded
-// before the propagation kernel, between it and the finalisation, and after.
-template <typename T>
-cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const Schedule& sc, cudaStream_t s,
-                             cudaEvent_t* ev) {
+cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry& ge, cudaStream_t s,
+                             cudaEvent_t* ev, uint64_t* trace = nullptr) {
   const Plan& p = t->plan;
+  const Schedule& sc = ge.sched;
   cudaError_t err = cudaSuccess;
   auto chk = [&](cudaError_t e) {
     if (err == cudaSuccess && e != cudaSuccess) err = e;
   };
-  chk(cudaMemsetAsync((T*)t->d_acc + (int64_t)case0 * t->acc_stride, 0,
-                      (size_t)n_cases * t->acc_stride * sizeof(T), s));
+  chk(cudaMemsetAsync((T*)t->d_msg + (int64_t)case0 * p.msg_stride, 0,
+                      (size_t)n_cases * p.msg_stride * sizeof(T), s));
+  chk(cudaMemsetAsync(t->d_sums + (int64_t)case0 * 2 * p.n_cliques, 0,
+                      (size_t)n_cases * 2 * p.n_cliques * sizeof(double), s));
   chk(cudaMemsetAsync(t->d_status + case0, 0, (size_t)n_cases * sizeof(int32_t), s));
-  chk(cudaMemsetAsync(t->d_done, 0, (2ull * p.n_cliques * t->max_cases + 1) * sizeof(int32_t), s));
-  chk(cudaMemsetAsync(t->d_cnt, 0, 2ull * p.n_cliques * t->max_cases * sizeof(int32_t), s));
-  LevelArgs<T> a = level_args<T>(t, case0, n_cases);
-  a.cl = sc.cliques;
-  a.work = sc.items;
-  a.n_items = sc.n_items;
-  a.cb = sc.sp.cb;
+  chk(cudaMemsetAsync(t->d_done, 0, (1 + 2ull * p.n_cliques * sc.n_cb) * sizeof(int32_t), s));
+  PropArgs<T> a{};
+  a.base = (const T*)t->base;
+  a.stages = ge.stages;
+  a.ports = ge.ports;
+  a.fields = ge.fields;
+  a.pos = ge.pos;
+  a.deps = ge.deps;
+  a.items = ge.items;
+  a.n_items = (int32_t)sc.items.size();
+  a.case0 = case0;
+  a.n_cases = n_cases;
+  a.n_cb = sc.n_cb;
+  a.ev = t->d_ev;
+  a.n_vars = p.n_vars;
+  a.msg = (T*)t->d_msg;
+  a.msg_stride = p.msg_stride;
+  a.delta_off = p.msg_total;
+  a.sums = t->d_sums;
+  a.n_cliques = p.n_cliques;
+  a.status = t->d_status;
+  a.queue = t->d_done;
+  a.done = t->d_done + 1;
+  a.err = t->d_err;
+  a.calib = (T*)t->d_calib;
+  a.calib_stride = p.base_len;
+  a.trace = trace;
+  a.ring = sc.ring;
+  a.chunk = sc.chunk;
+  a.max_k = sc.max_k;
+  a.max_ports = sc.max_ports;
+  a.max_fields = sc.max_fields;
+  a.win_max = sc.win_max;
   if (ev) chk(cudaEventRecord(ev[0], s));
-  chk(launch_propagate<T>(a, sc.sp, sc.grid, s));
+  chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
   if (ev) chk(cudaEventRecord(ev[1], s));
   FinalArgs<T> f{};
   f.vs = t->d_vs;
@@ -366,12 +203,12 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const Schedule& 
   f.n_cliques = p.n_cliques;
   f.case0 = case0;
   f.n_cases = n_cases;
-  f.acc = (const T*)t->d_acc;
-  f.acc_stride = t->acc_stride;
-  f.msg_total = p.msg_total;
-  f.marg_total = p.marg_total;
-  f.ls = t->d_ls;
+  f.msg = (const T*)t->d_msg;
+  f.msg_stride = p.msg_stride;
+  f.sums = t->d_sums;
+  f.sep_size = t->d_sep_size;
   f.status = t->d_status;
+  f.marg_total = p.marg_total;
   f.marg_out = t->d_marg;
   f.logz_out = t->d_logz;
   chk(launch_finalize<T>(f, s));
@@ -379,33 +216,40 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const Schedule& 
   return err;
 }
 
-// Plan the schedule of a case range (work items on the device) and record it
+// Plan the schedule of a case range, upload it, and record the propagation
 // into a CUDA graph.
 template <typename T>
 jt_status record_schedule(jt_tree t, int case0, int n_cases, cudaStream_t s, GraphEntry* ge) {
-  std::vector<DevWork> items;
-  std::vector<DevClique> cliques;
-  jt_status st = plan_schedule(t, n_cases, &ge->sched, &items, &cliques);
-  if (st != JT_OK) return st;
-  DevClique* dcl = nullptr;
-  CU(cudaMalloc((void**)&dcl, cliques.size() * sizeof(DevClique)), "clique descriptors");
-  ge->dev_bufs.push_back(dcl);
-  CU(cudaMemcpy(dcl, cliques.data(), cliques.size() * sizeof(DevClique), cudaMemcpyHostToDevice),
-     "clique descriptors");
-  ge->sched.cliques = dcl;
-  DevWork* dw = nullptr;
-  const size_t bytes = std::max<size_t>(1, items.size()) * sizeof(DevWork);
-  CU(cudaMalloc((void**)&dw, bytes), "work list");
-  ge->dev_bufs.push_back(dw);
-  CU(cudaMemcpy(dw, items.data(), items.size() * sizeof(DevWork), cudaMemcpyHostToDevice), "work list upload");
-  ge->sched.items = dw;
+  const int cb = n_cases > 1 ? kCaseBlock : 1;
+  std::string err;
+  const int smem_cap = smem_budget(t->device, ctas_per_sm_for(cb)) - 256;
+  jt_status st = build_schedule(t->plan, (int)t->elem, cb, n_cases, t->n_sm, smem_cap, &ge->sched, &err);
+  if (st != JT_OK) return fail(st, err);
+  const Schedule& sc = ge->sched;
+  if ((st = upload_vec(t, &ge->dev_bufs, &ge->stages, sc.stages, "schedule upload")) != JT_OK) return st;
+  if ((st = upload_vec(t, &ge->dev_bufs, &ge->ports, sc.ports, "schedule upload")) != JT_OK) return st;
+  if ((st = upload_vec(t, &ge->dev_bufs, &ge->fields, sc.fields, "schedule upload")) != JT_OK) return st;
+  if ((st = upload_vec(t, &ge->dev_bufs, &ge->pos, sc.pos, "schedule upload")) != JT_OK) return st;
+  if ((st = upload_vec(t, &ge->dev_bufs, &ge->deps, sc.deps, "schedule upload")) != JT_OK) return st;
+  if ((st = upload_vec(t, &ge->dev_bufs, &ge->items, sc.items, "schedule upload")) != JT_OK) return st;
+  ge->smem = prop_smem_bytes(sc, (int)t->elem);
+  ge->grid = (int32_t)std::min<int64_t>((int64_t)sc.items.size(), (int64_t)t->n_sm * ctas_per_sm_for(cb));
+  if (const char* dbg = std::getenv("JT_DEBUG_PLAN"); dbg && *dbg == '1') {
+    std::fprintf(stderr, "[jt plan] cases=%d cb=%d n_cb=%d items=%zu grid=%d smem=%d ring=%d win_max=%d\n", n_cases,
+                 sc.cb, sc.n_cb, sc.items.size(), ge->grid, ge->smem, sc.ring, sc.win_max);
+    for (const DevStage& S : sc.stages) {
+      if (S.n_blocks == 0) continue;
+      std::fprintf(stderr, "  stage c=%d pass=%d n=%d B=%d blocks=%d bits=%d kin=%d ports=%d(in %d) win=%d deps=%d\n",
+                   S.clique, S.pass, S.n, S.B, S.n_blocks, S.bits, S.kin, S.np, S.nin, S.win_len, S.ndep);
+    }
+  }
   CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
-  cudaError_t err = enqueue_schedule<T>(t, case0, n_cases, ge->sched, s, nullptr);
+  cudaError_t e = enqueue_schedule<T>(t, case0, n_cases, *ge, s, nullptr);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s, &g);
-  if (err != cudaSuccess) {
+  if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return cuda_fail(err, "recording the propagation");
+    return cuda_fail(e, "recording the propagation");
   }
   if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
   ge->graph = g;
@@ -486,20 +330,11 @@ jt_status load_typed(jt_tree t, const jt_tree_desc* d, cudaStream_t s) {
   jt_status st;
   if ((st = alloc(t, (T**)&t->base, p.base_len, "clique tables")) != JT_OK) return st;
   CU(cudaMemcpyAsync(t->base, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s), "table upload");
-  t->acc_stride = ((int64_t)3 * p.msg_total + p.marg_total + p.joint_total + 31) / 32 * 32;
-  if ((st = alloc(t, (T**)&t->d_acc, t->acc_stride * t->max_cases, "per-case messages")) != JT_OK) return st;
+  if ((st = alloc(t, (T**)&t->d_msg, p.msg_stride * t->max_cases, "per-case messages")) != JT_OK) return st;
   if (t->flags & JT_MATERIALIZE_CLIQUES) {
     if ((st = alloc(t, (T**)&t->d_calib, p.base_len * t->max_cases, "calibrated tables")) != JT_OK) return st;
   }
   CU(cudaStreamSynchronize(s), "table upload");
-  return JT_OK;
-}
-
-template <typename V>
-jt_status upload_vec(jt_tree t, V** dst, const std::vector<V>& src, const char* what) {
-  jt_status st = alloc(t, dst, (int64_t)src.size(), what);
-  if (st != JT_OK) return st;
-  if (!src.empty()) CU(cudaMemcpy(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice), what);
   return JT_OK;
 }
 
@@ -561,7 +396,7 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   CU(cudaGetDevice(&dev), "cudaGetDevice");
   t->device = dev;
   CU(cudaDeviceGetAttribute(&t->n_sm, cudaDevAttrMultiProcessorCount, dev), "device query");
-  t->smem_max = smem_budget(dev) - 1024;
+  t->smem_max = smem_budget(dev, 1);
   cudaStream_t s = (cudaStream_t)stream;
   jt_tree raw = t.release();
   auto bail = [&](jt_status code) {
@@ -572,35 +407,25 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   };
   if ((st = (raw->compute == JT_F64 ? load_typed<double>(raw, d, s) : load_typed<float>(raw, d, s))) != JT_OK)
     return bail(st);
-  if ((st = upload_vec(raw, &raw->d_cl, p.dcl, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_pos, p.dpos, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_ch, p.dch, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_hm, p.dhm, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_src, p.dsrc, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_jh, p.djh, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_vs, p.vsrc, "descriptors")) != JT_OK) return bail(st);
+  const int nc = p.n_cliques;
+  if ((st = alloc(raw, &raw->d_sums, 2ll * nc * raw->max_cases, "stage totals")) != JT_OK) return bail(st);
+  if ((st = alloc(raw, &raw->d_done, 1 + 2ll * nc * raw->max_cases, "block counters")) != JT_OK) return bail(st);
   if ((st = alloc(raw, &raw->d_err, 1, "error word")) != JT_OK) return bail(st);
-  if ((st = alloc(raw, &raw->d_done, 2ll * p.n_cliques * raw->max_cases + 1, "dependency flags")) != JT_OK)
-    return bail(st);
-  if ((st = upload_vec(raw, &raw->d_parent, p.parent, "descriptors")) != JT_OK) return bail(st);
   if (cudaMemset(raw->d_err, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
-  {
-    const int64_t ncnt = 2ll * p.n_cliques * raw->max_cases;
-    if ((st = alloc(raw, &raw->d_cnt, ncnt, "tile counters")) != JT_OK) return bail(st);
-    if (cudaMemset(raw->d_cnt, 0, ncnt * sizeof(int32_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
-  }
-  if ((st = upload_vec(raw, &raw->d_fld, p.dfld, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_card, p.card, "descriptors")) != JT_OK) return bail(st);
-  if ((st = upload_vec(raw, &raw->d_moff, p.moff, "descriptors")) != JT_OK) return bail(st);
+  if ((st = alloc(raw, &raw->d_status, raw->max_cases, "status")) != JT_OK) return bail(st);
+  if (cudaMemset(raw->d_status, 0, raw->max_cases * sizeof(int32_t)) != cudaSuccess)
+    return bail(fail(JT_ERR_CUDA, "memset"));
+  if ((st = alloc(raw, &raw->d_marg, (int64_t)raw->max_cases * p.marg_total, "marginals")) != JT_OK) return bail(st);
+  if ((st = alloc(raw, &raw->d_logz, raw->max_cases, "log evidence")) != JT_OK) return bail(st);
   const int64_t nev = (int64_t)raw->max_cases * p.n_vars;
   if ((st = alloc(raw, &raw->d_ev, nev, "evidence")) != JT_OK) return bail(st);
   if (cudaMemset(raw->d_ev, 0xFF, nev * sizeof(int16_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
-  if ((st = alloc(raw, &raw->d_ls, (int64_t)raw->max_cases * p.n_cliques, "log scales")) != JT_OK) return bail(st);
-  if (cudaMemset(raw->d_ls, 0, (size_t)raw->max_cases * p.n_cliques * sizeof(double)) != cudaSuccess)
-    return bail(fail(JT_ERR_CUDA, "memset"));
-  if ((st = alloc(raw, &raw->d_status, raw->max_cases, "status")) != JT_OK) return bail(st);
-  if ((st = alloc(raw, &raw->d_marg, (int64_t)raw->max_cases * p.marg_total, "marginals")) != JT_OK) return bail(st);
-  if ((st = alloc(raw, &raw->d_logz, raw->max_cases, "log evidence")) != JT_OK) return bail(st);
+  if ((st = alloc(raw, &raw->d_vs, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
+  if (cudaMemcpy(raw->d_vs, p.vsrc.data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(JT_ERR_CUDA, "descriptor upload"));
+  if ((st = alloc(raw, &raw->d_sep_size, nc, "separator sizes")) != JT_OK) return bail(st);
+  if (cudaMemcpy(raw->d_sep_size, p.sep_size.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(JT_ERR_CUDA, "descriptor upload"));
   int64_t maxn = 0;
   for (int64_t n : p.n_entries) maxn = std::max(maxn, n);
   raw->scratch_len = maxn + 2;
@@ -701,13 +526,44 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
   if ((st = get_graph(t, first, n, &ge)) != JT_OK) return st;
+  // JT_TRACE=<file>: also record every work item's SM and timeline
+  // (global timer, ns) and write them to <file> as CSV
+  const char* trace_path = std::getenv("JT_TRACE");
+  uint64_t* trace = nullptr;
+  const size_t n_items = ge->sched.items.size();
+  if (trace_path && *trace_path) {
+    CU(cudaMalloc((void**)&trace, n_items * kTraceSlots * sizeof(uint64_t)), "trace buffer");
+    CU(cudaMemset(trace, 0, n_items * kTraceSlots * sizeof(uint64_t)), "trace buffer");
+  }
   std::vector<cudaEvent_t> ev(nl + 1, nullptr);
   for (auto& e : ev) CU(cudaEventCreate(&e), "event");
-  cudaError_t err = t->compute == JT_F64 ? enqueue_schedule<double>(t, first, n, ge->sched, s, ev.data())
-                                         : enqueue_schedule<float>(t, first, n, ge->sched, s, ev.data());
+  cudaError_t err = t->compute == JT_F64 ? enqueue_schedule<double>(t, first, n, *ge, s, ev.data(), trace)
+                                         : enqueue_schedule<float>(t, first, n, *ge, s, ev.data(), trace);
   if (err == cudaSuccess) err = cudaEventSynchronize(ev[nl]);
   for (int i = 0; i < nl && err == cudaSuccess; ++i) err = cudaEventElapsedTime(&launch_ms[i], ev[i], ev[i + 1]);
   for (auto& e : ev) cudaEventDestroy(e);
+  if (trace) {
+    std::vector<uint64_t> h(n_items * kTraceSlots);
+    if (err == cudaSuccess) err = cudaMemcpy(h.data(), trace, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    cudaFree(trace);
+    if (FILE* f = err == cudaSuccess ? std::fopen(trace_path, "w") : nullptr) {
+      uint64_t t0 = ~0ull;
+      for (size_t i = 0; i < n_items; ++i)
+        if (h[i * kTraceSlots + 1]) t0 = std::min(t0, h[i * kTraceSlots + 1]);
+      std::fprintf(f, "item,stage,clique,pass,block,cbk,n,sm,start_ns,deps_ns,ready_ns,streamed_ns,end_ns,"
+                      "chunk_wait_ns,handover_ns,issued_ns\n");
+      for (size_t i = 0; i < n_items; ++i) {
+        const DevItem& w = ge->sched.items[i];
+        const DevStage& S = ge->sched.stages[w.stage];
+        const uint64_t* r = &h[i * kTraceSlots];
+        std::fprintf(f, "%zu,%d,%d,%d,%d,%d,%d,%llu,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld\n", i, w.stage, S.clique,
+                     S.pass, w.block, w.cbk, w.n, (unsigned long long)r[0], (long long)(r[1] - t0),
+                     (long long)(r[2] - t0), (long long)(r[3] - t0), (long long)(r[4] - t0), (long long)(r[5] - t0),
+                     (long long)r[6], (long long)(r[7] - t0), (long long)(r[8] - t0));
+      }
+      std::fclose(f);
+    }
+  }
   if (err != cudaSuccess) return cuda_fail(err, "profiled propagation");
   for (int i = first; i < first + n; ++i) t->ready[i] = 1;
   t->last_stream = s;

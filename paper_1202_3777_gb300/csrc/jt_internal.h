@@ -11,170 +11,155 @@
 namespace jt {
 
 // ---------------------------------------------------------------------------
-// Device-side descriptors (plain structs, copied to device memory once).
+// Layout (planned once per tree, see build_plan).
 //
-// Every clique table is stored with its variables permuted:
-//   [parent-separator variables, ascending id]   (most significant digits)
-//   [variables of child separators, ascending]
-//   [private variables]                           (fastest digits)
-// A private variable belongs to no separator, so it appears in this clique
-// only.  The trailing private variables (product of cardinalities P, the
-// "columns") never enter a separator index, a factor or the parent segment:
-// viewed as a matrix of rows x P columns, every per-row quantity (factors,
-// keys, ratio) is computed once per row, and each entry only costs a
-// multiply-add.  Because the parent-separator variables are the slowest
-// digits, the rows of one parent-separator entry j form the contiguous run
-// [j*LR, (j+1)*LR): marginalisation towards the parent (Eq. 2) is a
-// segmented reduction.
-//
-// Other tables over a subset of the row variables (a child separator) are
-// indexed by a key computed from the row index r with digit-run "fields":
-// a field is a maximal run of consecutive row positions that is also
-// consecutive (in the same order) in the small table's layout:
-//     key(r) = sum_f ((r / f.st) % f.len) * f.w
-// When every cardinality is a power of two the fields use shifts and masks.
+// Every clique table is stored with its variables permuted ("positions",
+// position 0 most significant):
+//   [parent-separator variables, in the order they have in the parent]
+//   [variables shared with child separators, most-shared first]
+//   [private variables (in no separator)]                   (fastest digits)
+// and every separator table is laid out in the order its variables have in
+// the parent clique (first most significant).  So for any small table over a
+// subset V of a clique's variables (a separator, or the joint of the private
+// variables) the table key of an entry is the clique index with the digits
+// outside V dropped:
+//     key(x) = sum_f ((x / f.st) % f.len) * f.w
+// over "fields" = maximal runs of consecutive positions inside V.  The key is
+// additive over disjoint digit sets, so for a block of the table that fixes
+// every digit above some position, key(block_start + o) = key(block_start)
+// + key(o): the block touches the contiguous key window
+// [key(block_start), key(block_start) + K), K = product of the cardinalities
+// of V's positions inside the block.  When every cardinality is a power of
+// two the digits are bit fields and blocks may cut a digit.
 // ---------------------------------------------------------------------------
 
+// Port kinds: the small tables one clique touches in one pass.
+constexpr int32_t kPortMu = 0;     // in : collect message of a child, normalised to mean one
+constexpr int32_t kPortRho = 1;    // in : ratio new/old of the clique's own parent separator (0/0 := 0)
+constexpr int32_t kPortU = 2;      // out: collect message to the parent (raw sums)
+constexpr int32_t kPortDelta = 3;  // out: distribute message to a child (raw sums)
+constexpr int32_t kPortJoint = 4;  // out: joint of the private variables (raw sums)
+
+// Optional per-item trace (global timer, ns): SM, start, dependencies met,
+// windows ready, streamed, end, time thread 0 waited for chunks, producer
+// hand-over, producer's last chunk issued.
+constexpr int kTraceSlots = 9;
+
+constexpr int kStatusZero = 1;      // P(e) = 0
+constexpr int kStatusBadState = 2;  // an evidence state >= card
+
 struct DevField {
-  int32_t st;         // row stride of the run's fastest position
+  int32_t st;         // entry stride of the run's fastest position
   int32_t len;        // product of the run's cardinalities
-  uint32_t st_magic;  // ceil(2^32 / st) (st > 1)
+  uint32_t st_magic;  // ceil(2^32 / st)
   uint32_t len_magic; // ceil(2^32 / len)
   int32_t w;          // stride of the run's fastest variable in the small table
-  int32_t sh;         // log2(st) (power-of-two cliques)
-  int32_t lbits;      // log2(len) (power-of-two cliques)
+  int32_t sh;         // power-of-two cliques: log2(st)
+  int32_t lb;         // power-of-two cliques: log2(len)
   int32_t pad;
 };
 
-struct DevPos {       // one position (digit) of a clique's permuted layout
+struct DevPos {       // one digit (position) of a clique's permuted layout
   int32_t var;
   int32_t card;
-  int32_t st;         // row positions: row stride; column positions: column stride
+  int32_t st;         // entry stride
   uint32_t st_magic;
   uint32_t card_magic;
-  int32_t sh;         // log2(st) (power-of-two cliques)
-  int32_t cbits;      // log2(card) (power-of-two cliques)
-  int32_t is_col;     // 1 for a column (private suffix) position
+  int32_t sh;         // power-of-two cliques: log2(st)
+  int32_t cb;         // power-of-two cliques: log2(card)
+  int32_t pad;
 };
 
-struct DevChild {     // a child separator seen from the parent clique
-  int32_t child;      // child clique id
-  int32_t sep_size;   // entries of the separator table
-  int32_t sep_off;    // offset of the separator in per-case message arrays
-  int32_t n_field;
-  int32_t field_first;
-  int32_t field_rel;  // field_first relative to the clique's first child field
-  int32_t fac_off;    // offset of this table in the clique's per-case factor/output block
-  int32_t w_last;     // key step of the clique's fastest digit (0 if that variable is not in the separator)
+struct DevPort {
+  int32_t kind;       // kPort*
+  int32_t tab;        // offset of the table in the per-case message array
+  int32_t size;       // entries of the table
+  int32_t K;          // entries of the window a block touches
+  int32_t win;        // offset of the window in the per-case window region
+  int32_t other;      // kPortMu: the child clique; kPortRho: this clique
+  int32_t other2;     // kPortRho: the parent clique
+  int32_t nf;         // fields
+  int32_t f0;         // first field (index relative to the stage's first field)
+  uint32_t lane_free; // fast path: lane bits the key does not depend on
+  int32_t vmode;      // fast path: a vector's entries have keys key0 + dvec[j]: 0 = all dvec 0,
+                      // 1 = dvec[j] = j, 2 = other
+  int32_t dvec[4];    // fast path: key offsets of the entries of a vector
+  int32_t iter_dep;   // fast path: bit 0: the key depends on the iteration bits (entry bits above
+                      // the thread's vector index); bit 1: on the chunk bits (above one chunk)
 };
 
-struct DevHome {      // a private variable at a row position: its marginal is
-  int32_t pos;        // accumulated per row in this clique's distribute pass
-  int32_t card;
-  int32_t moff;       // offset of its marginal in per-case marginal arrays
-  int32_t out_off;    // offset of its accumulator in the clique's per-case output block
-};
-
-struct DevSrc {       // a variable whose marginal is binned from a small table:
-  int32_t var;        // a separator (DevClique.src_*) or the column joint
-  int32_t card;       // (DevClique.jh_*)
-  int32_t st;         // stride of the variable in that table
-  int32_t moff;
-};
-
-struct DevClique {
-  int64_t base_off;   // element offset of the (permuted, padded) table
+// One clique in one pass.
+struct DevStage {
+  int64_t base_off;   // element offset of the permuted table
+  int32_t clique, pass;   // pass 0 = collect (Algorithm 2), 1 = distribute (Algorithm 3)
   int32_t n;          // entries
-  int32_t k;          // variables
-  int32_t kr;         // row positions 0..kr-1; column positions kr..k-1
-  int32_t P;          // columns (product of the column cardinalities), >= 1
-  uint32_t P_magic;
-  int32_t logP;
-  int32_t LR;         // rows per parent-separator entry
-  uint32_t LR_magic;
-  int32_t logLR;
-  int32_t sep_size;   // parent-separator entries (1 for the root)
-  int32_t sep_off;    // offset of that separator in per-case message arrays
-  int32_t n_child, child_first;
-  int32_t n_home, home_first;   // private variables at row positions
-  int32_t n_jh, jh_first;       // private variables in the columns (DevSrc, stride in the joint)
-  int32_t joint_off;            // offset of the column joint in per-case arrays (-1: none)
-  int32_t n_src, src_first;     // variables read from the parent separator
-  int32_t pos_first;            // k DevPos entries
-  int32_t pow2;                 // all cardinalities are powers of two
-  int32_t depth;
-  int32_t field_first, n_field; // fields of all child separators (contiguous)
-  int32_t card_last;            // cardinality of the fastest position
-  // offsets (entries) of this clique's tables inside the per-case shared-memory
-  // table region of a propagation, or -1 when the table stays in global memory
-  int32_t sm_fac;               // child factors (collect messages of the children)
-  int32_t sm_rho;               // parent ratio
-  int32_t sm_out;               // child-separator and row-home accumulators
-  int32_t sm_jnt;               // column joint
-  int32_t sm_out_len;           // entries of the accumulators (child separators + row homes)
+  int32_t B;          // entries of one block (one work item)
+  int32_t n_blocks;
+  int32_t k;          // positions
+  int32_t kin;        // generic path: positions [k - kin, k) lie inside a block
+  int32_t bits;       // fast path: log2(B); -1 selects the generic path
+  int32_t pos0;       // first DevPos
+  int32_t np, nin;    // ports, of which [0, nin) are inputs
+  int32_t port0;      // first DevPort
+  int32_t nf, field0; // fields of all ports
+  int32_t win_len;    // per-case window entries
+  int32_t ndep, dep0; // dependencies: pairs (stage, blocks) in the dependency list
+  int32_t sum_slot;   // index of this stage's total in the per-case sums (pass * n_cliques + clique)
+  int32_t pad[3];
 };
 
-// One work item of a propagation: a slice of one clique's table for one
-// block of evidence cases, in one pass.
-struct DevWork {
-  int64_t base_off;   // element offset of the clique's table (copied from DevClique)
-  int32_t clique;
-  int32_t t0, t1;     // entry range [t0, t1), t0 a multiple of the chunk
-  int32_t ntiles;     // slices of this clique (per case block and pass)
+// One work item: one block of one stage for one block of evidence cases.
+struct DevItem {
+  int64_t off;        // element offset of the block's first entry in the table array
+  int32_t n;          // entries of the block
+  int32_t stage;
+  int32_t block;
   int32_t cbk;        // case block
-  int32_t collect;    // 1: collect pass, 0: distribute pass
+  int32_t pad[2];
 };
 
-// Kernel arguments for one level launch.
-//
-// Per-case array (stride acc_stride elements):
-//   [up: msg_total]    collect messages; raw sums, normalised to mean one in
-//                      place by the last CTA of the sending clique
-//   [down: msg_total]  distribute messages (raw sums)
-//   [rho: msg_total]   parent ratios new/old (0/0 := 0), written by the last
-//                      CTA of the parent clique
-//   [marg: marg_total] raw marginal sums
-//   [joint: joint_total] column joints of cliques with private variables
+// Where the finalisation reads a variable's marginal: a separator's
+// distribute message or a clique's private joint (per-case offsets).
+struct VarSrc {
+  int32_t off;        // start of the table in the per-case message array
+  int32_t size;       // table entries
+  int32_t st;         // stride of the variable in the table
+  int32_t card;
+  int32_t moff;       // offset of the marginal in the output row
+  int32_t pad[3];
+};
+
+// Arguments of the persistent propagation kernel.
 template <typename T>
-struct LevelArgs {
-  const DevClique* cl;
+struct PropArgs {
+  const T* base;                // permuted clique tables
+  const DevStage* stages;
+  const DevPort* ports;
+  const DevField* fields;
   const DevPos* pos;
-  const DevChild* ch;
-  const DevHome* hm;
-  const DevSrc* src;
-  const DevSrc* jh;
-  const DevField* fld;
-  const T* base;
-  const DevWork* work;
-  int32_t case0, n_cases, cb;   // case range and case-block size
-  const int16_t* ev;            // [max_cases][n_vars]
+  const int32_t* deps;          // pairs (stage, blocks)
+  const DevItem* items;
+  int32_t n_items;
+  int32_t case0, n_cases;       // case range of this propagation
+  int32_t n_cb;                 // case blocks
+  const int16_t* ev;            // [max_cases][n_vars], -1 = unobserved
   int32_t n_vars;
-  T* acc;
-  int64_t acc_stride;
-  int32_t msg_total, marg_total, joint_total;
-  double* ls;                   // [max_cases][n_cliques] log scale of each collect message
+  T* msg;                       // [max_cases][msg_stride]: u | delta | joint
+  int64_t msg_stride;
+  int32_t delta_off;            // start of the distribute messages in a message row
+  double* sums;                 // [max_cases][2 * n_cliques]: collect totals (sigma), distribute totals (Delta)
   int32_t n_cliques;
   int32_t* status;              // [max_cases]
-  int32_t* cnt;                 // [2][n_cliques][max_cases] tile tickets (self-resetting)
-  int32_t* done;                // [2][n_cliques][max_cases] messages final (zeroed per propagation)
-  int32_t* queue;               // next work item (zeroed per propagation)
-  int32_t n_items;
-  const int32_t* parent_of;     // [n_cliques]
-  int32_t* err;                 // device error word (set on a timed-out wait)
-  int32_t max_cases;
-  T* calib;                     // [max_cases][base_len] or null
+  int32_t* done;                // [n_stages][n_cb] finished blocks
+  int32_t* queue;               // next work item
+  int32_t* err;                 // set when a bounded wait gives up
+  T* calib;                     // [max_cases][calib_stride] calibrated tables, or null
   int64_t calib_stride;
-};
-
-// Where the finalisation reads a variable's marginal from (per-case offsets).
-struct VarSrc {
-  int64_t off;        // kind 1: start of the table; kind 0: start of the raw marginal
-  int32_t kind;       // 1: bin a separator table or a column joint; 0: raw sums per state
-  int32_t card;
-  int32_t st;         // stride of the variable in the table (kind 1)
-  int32_t size;       // table entries (kind 1)
-  int32_t moff;       // offset of the marginal in the output
-  int32_t pad;
+  uint64_t* trace;              // [n_items][kTraceSlots] item timeline, or null
+  // shared-memory plan
+  int32_t ring;                 // bulk-copy stages
+  int32_t chunk;                // entries per stage
+  int32_t max_k, max_ports, max_fields, win_max;
 };
 
 template <typename T>
@@ -182,19 +167,19 @@ struct FinalArgs {
   const VarSrc* vs;             // [n_vars]
   int32_t n_vars, n_cliques;
   int32_t case0, n_cases;
-  const T* acc;
-  int64_t acc_stride;
-  int32_t msg_total, marg_total;
-  const double* ls;
+  const T* msg;
+  int64_t msg_stride;
+  const double* sums;
+  const int32_t* sep_size;      // [n_cliques]
   int32_t* status;
+  int32_t marg_total;
   double* marg_out;             // [max_cases][marg_total]
   double* logz_out;             // [max_cases]
 };
 
 // ---------------------------------------------------------------------------
-// Host-side plan.
+// Host-side plan of a tree (independent of the case-block size).
 // ---------------------------------------------------------------------------
-
 struct Plan {
   int32_t n_vars = 0, n_cliques = 0, max_depth = 0;
   std::vector<int32_t> card;
@@ -204,36 +189,51 @@ struct Plan {
   std::vector<std::vector<int32_t>> children;
   std::vector<std::vector<int32_t>> levels; // cliques per depth
   std::vector<int64_t> n_entries, base_off;
-  int64_t base_len = 0;                     // padded element count
-  std::vector<std::vector<int32_t>> sep;    // separator vars of edge (c, parent c), ascending
-  std::vector<int32_t> sep_size, sep_off;
-  int32_t msg_total = 0;
-  std::vector<int32_t> home, moff;          // per variable
-  std::vector<int32_t> src_edge;            // per variable: separator it is read from, or -1
-  int32_t marg_total = 0;
-  int64_t entries = 0, work_per_case = 0;
-
-  std::vector<DevClique> dcl;
-  std::vector<DevPos> dpos;
-  std::vector<DevChild> dch;
-  std::vector<DevHome> dhm;
-  std::vector<DevSrc> dsrc, djh;
-  std::vector<DevField> dfld;
+  std::vector<uint8_t> pow2;                // every cardinality of the clique is a power of two
+  int64_t base_len = 0;                     // padded element count of all tables
+  std::vector<std::vector<int32_t>> sep;    // separator of (c, parent c), in the parent's permuted order
+  std::vector<int32_t> sep_size, sep_off;   // root: a 1-entry slot
+  int32_t msg_total = 0;                    // entries of all separator tables
+  std::vector<int32_t> n_private, joint_off, joint_size;
   int32_t joint_total = 0;
-  std::vector<VarSrc> vsrc;                 // per variable
-  // per clique: per-case shared-memory entries of the child factors and of
-  // the distribute outputs (child separators + row-home marginals)
-  std::vector<int32_t> fac_collect, out_dist;
+  std::vector<int32_t> moff;                // per variable: offset of its marginal
+  int32_t marg_total = 0;
+  std::vector<VarSrc> vsrc;                 // per variable (offsets in a message row)
+  int64_t entries = 0, work_per_case = 0;
+  int64_t msg_stride = 0;                   // u | delta | joint, padded
 };
 
-// Validation + planning from a descriptor.  Returns JT_OK or an error status
-// with `err` filled.  Touches no CUDA API.
+// Validation + layout.  Returns JT_OK or an error status with `err` filled.
+// Touches no CUDA API.
 jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err);
 
 // Copy the caller's tables (listed order, any dtype) into the permuted,
 // padded device layout (host buffer of base_len elements of T).
 template <typename T>
 void permute_tables(const Plan& p, const void* pot, jt_dtype pot_dtype, T* out);
+
+// Schedule of one propagation shape (case-block size): stages, ports,
+// fields, dependencies and the ordered work items.
+struct Schedule {
+  int32_t cb = 1, n_cb = 1;
+  std::vector<DevStage> stages;             // [2 * n_cliques]; the root's collect stage is empty
+  std::vector<DevPort> ports;
+  std::vector<DevField> fields;
+  std::vector<DevPos> pos;
+  std::vector<int32_t> deps;
+  std::vector<DevItem> items;
+  int32_t ring = 0, chunk = 0;
+  int32_t max_k = 1, max_ports = 1, max_fields = 1, win_max = 1;
+  int64_t streamed_entries = 0;             // entries streamed per case block (all stages)
+};
+
+// Plan the schedule for `n_cases` cases in blocks of `cb` on a device with
+// `n_sm` SMs and `smem_bytes` of dynamic shared memory per CTA.
+jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm, int smem_bytes,
+                         Schedule* s, std::string* err);
+
+// Dynamic shared memory of the propagation kernel for a schedule.
+int32_t prop_smem_bytes(const Schedule& s, int elem);
 
 uint32_t magic_for(uint32_t d);
 

@@ -1,26 +1,34 @@
-// Message kernels for Hugin propagation on sm_103a.
+// Propagation kernels for Hugin belief propagation on sm_103a.
 //
-// One launch processes one tree depth ("level") of one pass for a block of
-// evidence cases.  Each CTA owns a contiguous slice [t0, t1) of one clique's
-// table and a block of cases, and streams the slice once with 16-byte vector
-// loads.  The clique table is a matrix of rows x P columns (the columns are
-// the private variables, see jt_internal.h), so per row:
+// One persistent launch runs a whole propagation (Algorithm 4): collect
+// (Algorithm 2) then distribute (Algorithm 3) for a range of evidence cases.
+// Work items are blocks of clique tables; every item belongs to a "stage"
+// (one clique in one pass) and reads or writes a handful of small tables
+// ("ports", see jt_internal.h) through contiguous windows held in shared
+// memory:
 //
-//   collect (Algorithm 2, Eq. 2):
-//       F(r)   = E_row(r) * prod_g mu_g[key_g(r)]
-//       u_c[seg(r)] += F(r) * sum_col phi(r, col) * E_col(col)
-//   distribute (Algorithm 3, Eq. 3):
-//       G(r)   = F(r) * rho_c[seg(r)]            rho = new/old separator, 0/0 := 0
-//       psi*(r, col) = G(r) * phi(r, col) * E_col(col)       (calibrated entry)
-//       delta_g[key_g(r)] += sum_col psi*(r, col)             (child messages, Eq. 2)
-//       joint[col] += psi*(r, col)                            (private marginals)
+//   collect, clique c (Eq. 2):
+//       f(x)  = phi_c(x) E(x) prod_g mu_g[key_g(x)]
+//       u_c[key_p(x)] += f(x),   sigma_c += f(x)
+//   distribute, clique c (Eq. 3, then Eq. 2 towards every child):
+//       f(x)  = phi_c(x) E(x) prod_g mu_g[key_g(x)] rho_c[key_p(x)]
+//       delta_g[key_g(x)] += f(x),  joint_c[key_priv(x)] += f(x),  Delta_c += f(x)
 //
-// mu_g are child collect messages normalised to mean one; E_row / E_col are
-// the evidence indicators evaluated on the row / column digits.  The last CTA
-// to finish a clique (ticket counter after a fence; no CTA ever waits on
-// another) finalises its outgoing messages once: collect normalises u_c and
-// records log(sigma); distribute turns each child message into the ratio
-// rho_g and bins the separator- and joint-held marginals.
+// mu_g = u_g |S_g| / sigma_g is the child's collect message normalised to
+// mean one, rho_c = (delta_c / Delta_parent) / (u_c / sigma_c) the new/old
+// ratio of c's own separator with 0/0 := 0, E the evidence indicator.  Each
+// stage's total (sigma or Delta) accumulates in FP64; log Z(e) =
+// sum_c (log sigma_c - log |S_c|) + log Delta_root.  The root has no collect
+// stage: its distribute pass computes the same total.
+//
+// A CTA has 16 consumer warps and one producer warp.  The producer takes
+// items from a global queue (ordered so that every dependency of an item
+// comes earlier), hands them to the consumers through a small shared-memory
+// FIFO, and streams each block's table into a ring of 16 KB stages with
+// cp.async.bulk, running ahead of the consumers across items.  Consumers wait
+// (bounded) only for the stages an item reads, i.e. on per-stage counters of
+// finished blocks.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -30,141 +38,92 @@ namespace jt {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = kLevelThreads;        // consumer threads of a level CTA
-constexpr int kWarps = kThreads / 32;
-constexpr int kBlock = kThreads + 32;            // + one producer warp (bulk copies)
-constexpr int kVpt = 2;                          // vectors per consumer thread per chunk
-constexpr int kStatusZero = 1;      // some message or the root summed to zero: P(e) = 0
-constexpr int kStatusBadState = 2;  // an evidence state >= card
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s bound on every device-side wait
 
 template <typename T>
 struct VecT;
 template <>
 struct VecT<float> {
   static constexpr int N = 4;
-  __device__ static void load(const float* p, float (&x)[4]) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-  }
   __device__ static void lds(const float* p, float (&x)[4]) {
     const float4 v = *reinterpret_cast<const float4*>(p);
     x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
   }
-  __device__ static void store(float* p, const float (&x)[4]) {
+  __device__ static void stg(float* p, const float (&x)[4]) {
     __stcs(reinterpret_cast<float4*>(p), make_float4(x[0], x[1], x[2], x[3]));
   }
 };
 template <>
 struct VecT<double> {
   static constexpr int N = 2;
-  __device__ static void load(const double* p, double (&x)[2]) {
-    double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    x[0] = v.x; x[1] = v.y;
-  }
   __device__ static void lds(const double* p, double (&x)[2]) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     x[0] = v.x; x[1] = v.y;
   }
-  __device__ static void store(double* p, const double (&x)[2]) {
+  __device__ static void stg(double* p, const double (&x)[2]) {
     __stcs(reinterpret_cast<double2*>(p), make_double2(x[0], x[1]));
   }
 };
 
-// n / d for n < 2^31 with m = ceil(2^32 / d): umulhi gives the quotient or
-// one more; one compare corrects it.
-__device__ __forceinline__ uint32_t udiv(uint32_t n, uint32_t d, uint32_t m) {
-  if (d == 1u) return n;
-  uint32_t q = __umulhi(n, m);
-  if (q * d > n) --q;
-  return q;
-}
-
-// digit of position p in an index x (row index for row positions, column
-// index for column positions)
-template <bool POW2>
-__device__ __forceinline__ uint32_t digit(uint32_t x, const DevPos& p) {
-  if (POW2) return (x >> p.sh) & ((1u << p.cbits) - 1u);
-  const uint32_t q = udiv(x, (uint32_t)p.st, p.st_magic);
-  return q - udiv(q, (uint32_t)p.card, p.card_magic) * (uint32_t)p.card;
-}
-
-template <bool POW2>
-__device__ __forceinline__ uint32_t eval_key(uint32_t r, const DevField* f, int nf) {
-  uint32_t key = 0;
-  for (int i = 0; i < nf; ++i) {
-    uint32_t x;
-    if (POW2) {
-      x = (r >> f[i].sh) & ((1u << f[i].lbits) - 1u);
-    } else {
-      const uint32_t q = udiv(r, (uint32_t)f[i].st, f[i].st_magic);
-      x = q - udiv(q, (uint32_t)f[i].len, f[i].len_magic) * (uint32_t)f[i].len;
-    }
-    key += x * (uint32_t)f[i].w;
-  }
-  return key;
-}
-
+// ---- PTX helpers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// Explicit shared-memory accesses by 32-bit shared address, so the hot
+// loops never fall back to generic addressing.
 template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+__device__ __forceinline__ T sld(uint32_t a);
+template <>
+__device__ __forceinline__ float sld<float>(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
   return v;
 }
-
-// Add v at tab[key] for every lane of a full warp; when all lanes share the
-// key the warp reduces first and issues one atomic.
+template <>
+__device__ __forceinline__ double sld<double>(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int32_t sld_s32(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sld_vec(uint32_t a, float (&x)[4]) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(a));
+}
+__device__ __forceinline__ void sld_vec(uint32_t a, double (&x)[2]) {
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x[0]), "=d"(x[1]) : "r"(a));
+}
 template <typename T>
-__device__ __forceinline__ void add_combined(T* tab, uint32_t key, T v, int lane) {
-  const uint32_t k0 = __shfl_sync(kFull, key, 0);
-  if (__all_sync(kFull, key == k0)) {
-    v = warp_sum(v);
-    if (lane == 0 && v != T(0)) atomicAdd(tab + k0, v);
-  } else if (v != T(0)) {
-    atomicAdd(tab + key, v);
-  }
+__device__ __forceinline__ void sst(uint32_t a, T v);
+template <>
+__device__ __forceinline__ void sst<float>(uint32_t a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v));
 }
-
-// Sum over a level CTA in double (all kBlock threads call; red holds >= 17 doubles).
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int i = 0; i < kBlock / 32; ++i) t += red[i];
-  return t;
+template <>
+__device__ __forceinline__ void sst<double>(uint32_t a, double v) {
+  asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v));
 }
-
-// Shared-memory view of one CTA's tables (set up by the kernel prologue).
-// ---- bulk-copy (TMA) staging: cp.async.bulk global -> shared, completed on
-// an mbarrier by transaction count.  Waits are bounded by %globaltimer.
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
+__device__ __forceinline__ void sred_add(uint32_t a, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void sred_add(uint32_t a, double v) {
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
@@ -187,938 +146,954 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release(int32_t* p, int32_t v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
-// Wait for phase `parity` of `bar`; false if it did not complete in time (or,
-// with `err`, once another CTA reported an error).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int32_t* err) {
+// Named barrier of the NT consumer threads (the producer warp never joins it).
+template <int NT>
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
+// Consumer barrier that also ANDs a predicate over every consumer thread.
+template <int NT>
+__device__ __forceinline__ bool consumer_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(NT)
+      : "memory");
+  return r != 0;
+}
+
+// Wait for phase `parity` of `bar`.  False once the wait limit passed, or
+// (when given) once the error word or the CTA's abort flag is set.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int32_t* err,
+                                          const volatile int* abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
+  uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > kWaitLimitNs) return false;
-    if (err != nullptr && ld_acquire(err) != 0) return false;
+    if ((++spins & 63u) == 0) {
+      if (global_ns() - t0 > kWaitLimitNs) return false;
+      if (abort != nullptr && *abort) return false;
+      if (err != nullptr && ld_relaxed(err) != 0) return false;
+    }
   }
   return true;
 }
 
+// n / d for n < 2^31 with m = ceil(2^32 / d): umulhi gives the quotient or
+// one more; one compare corrects it.
+__device__ __forceinline__ uint32_t udiv(uint32_t n, uint32_t d, uint32_t m) {
+  if (d == 1u) return n;
+  uint32_t q = __umulhi(n, m);
+  if (q * d > n) --q;
+  return q;
+}
+
+// Key of entry offset x in a small table (fields in shared memory).
+template <bool POW2>
+__device__ __forceinline__ uint32_t key_of(uint32_t x, const DevField* f, int nf) {
+  uint32_t key = 0;
+  for (int i = 0; i < nf; ++i) {
+    const DevField q = f[i];
+    uint32_t d;
+    if (POW2) {
+      d = (x >> q.sh) & ((1u << q.lb) - 1u);
+    } else {
+      const uint32_t t = udiv(x, (uint32_t)q.st, q.st_magic);
+      d = t - udiv(t, (uint32_t)q.len, q.len_magic) * (uint32_t)q.len;
+    }
+    key += d * (uint32_t)q.w;
+  }
+  return key;
+}
+
+__device__ __forceinline__ uint32_t digit_of(uint32_t x, const DevPos& p) {
+  const uint32_t t = udiv(x, (uint32_t)p.st, p.st_magic);
+  return t - udiv(t, (uint32_t)p.card, p.card_magic) * (uint32_t)p.card;
+}
+
 template <typename T>
-struct CtaView {
-  const DevChild* ch;
-  const DevField* fld;
-  const DevHome* hm;
-  const DevPos* pos;
-  const int2* obs;     // [cb][k] row observations
-  const int2* cobs;    // [cb][k] column observations
-  const int* nobs;     // [cb] row, then [cb] column counts
-  const T* const* facp;
-  T* const* outp;
-  const T* const* rhop;
-  T* const* houtp;
-  T* const* jntp;
-  T* win;
-  T* buf;              // [stages][chunk] staging ring
-  uint64_t* bar;       // [stages] "full" mbarriers (bulk-copy bytes landed)
-  uint64_t* ebar;      // [stages] "empty" mbarriers (every consumer warp done)
-  T* rsum;             // [cb][rowmax] row sums of the slice
-  T* gsm;              // [cb][rowmax] row factors of the slice (distribute)
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Sum over the lanes that differ from this one only in the bits of `mask`.
+template <typename T>
+__device__ __forceinline__ T lane_reduce(T v, uint32_t mask) {
+#pragma unroll
+  for (int b = 1; b < 32; b <<= 1)
+    if (mask & (uint32_t)b) v += __shfl_xor_sync(kFull, v, b);
+  return v;
+}
+
+// Add v at tab[key] for every lane of a full warp; when every lane has the
+// same key the warp reduces first and issues one atomic.
+template <typename T>
+__device__ __forceinline__ void add_combined(uint32_t tab, uint32_t key, T v, int lane) {
+  const uint32_t k0 = __shfl_sync(kFull, key, 0);
+  if (__all_sync(kFull, key == k0)) {
+    v = warp_sum(v);
+    if (lane == 0 && v != T(0)) sred_add(tab + k0 * (uint32_t)sizeof(T), v);
+  } else if (v != T(0)) {
+    sred_add(tab + key * (uint32_t)sizeof(T), v);
+  }
+}
+
+struct Smem {
+  uint64_t *full, *empty, *ifull, *iempty, *sfull, *sempty;
+  DevItem* fifo;
+  int2* sig;
+  DevStage* stage;
+  DevPort* port;
+  DevField* fld;
+  DevPos* pos;
+  int4* obs;
+  int* nobs;
+  double* pval;
+  double* bf;
+  double* red;
+  int* misc;          // [0] abort flag, [1] dependencies met
+  int* kiter;         // [kMaxFastPorts][kMaxIter] per-iteration key parts of the live ports
+  unsigned char* live;// [kMaxFastPorts] LivePort
+  int* kt;            // [kMaxFastPorts][consumers] per-thread key parts of the live ports
+  unsigned char* win;
+  unsigned char* ring;
 };
 
-// Column evidence factor (0 or 1) of column `col` for case cl.
-template <typename T, bool POW2>
-__device__ __forceinline__ T colmask(const CtaView<T>& v, const SmemPlan& sp, int cl, uint32_t col) {
-  const int nco = v.nobs[sp.cb + cl];
-  for (int o = 0; o < nco; ++o) {
-    const int2 ob = v.cobs[cl * sp.k + o];
-    if (digit<POW2>(col, v.pos[ob.x]) != (uint32_t)ob.y) return T(0);
-  }
-  return T(1);
+__device__ __forceinline__ Smem carve(unsigned char* smem, const SmemLayout& L, int ring_n) {
+  Smem s;
+  s.full = reinterpret_cast<uint64_t*>(smem + L.bar);
+  s.empty = s.full + ring_n;
+  s.ifull = s.empty + ring_n;
+  s.iempty = s.ifull + kFifo;
+  s.sfull = s.iempty + kFifo;
+  s.sempty = s.sfull + kSig;
+  s.fifo = reinterpret_cast<DevItem*>(smem + L.fifo);
+  s.sig = reinterpret_cast<int2*>(smem + L.sig);
+  s.stage = reinterpret_cast<DevStage*>(smem + L.stage);
+  s.port = reinterpret_cast<DevPort*>(smem + L.ports);
+  s.fld = reinterpret_cast<DevField*>(smem + L.fields);
+  s.pos = reinterpret_cast<DevPos*>(smem + L.pos);
+  s.obs = reinterpret_cast<int4*>(smem + L.obs);
+  s.nobs = reinterpret_cast<int*>(smem + L.nobs);
+  s.pval = reinterpret_cast<double*>(smem + L.pval);
+  s.bf = reinterpret_cast<double*>(smem + L.bf);
+  s.red = reinterpret_cast<double*>(smem + L.red);
+  s.misc = reinterpret_cast<int*>(smem + L.misc);
+  s.kiter = reinterpret_cast<int*>(smem + L.kiter);
+  s.live = smem + L.live;
+  s.kt = reinterpret_cast<int*>(smem + L.kt);
+  s.win = smem + L.win;
+  s.ring = smem + L.ring;
+  return s;
 }
 
-// Row factor without the parent ratio: E_row(r) prod_g mu_g[key_g(r)].
-template <typename T, bool POW2, int CBMAX>
-__device__ __forceinline__ void row_factor(const CtaView<T>& v, const SmemPlan& sp, int nch, int ncb, uint32_t r,
-                                           T (&F)[CBMAX]) {
-#pragma unroll
-  for (int cl = 0; cl < CBMAX; ++cl) {
-    F[cl] = T(1);
-    if (cl < ncb) {
-      for (int o = 0; o < v.nobs[cl]; ++o) {
-        const int2 ob = v.obs[cl * sp.k + o];
-        if (digit<POW2>(r, v.pos[ob.x]) != (uint32_t)ob.y) F[cl] = T(0);
-      }
-    }
-  }
-  for (int t = 0; t < nch; ++t) {
-    const uint32_t key = eval_key<POW2>(r, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
-#pragma unroll
-    for (int cl = 0; cl < CBMAX; ++cl)
-      if (cl < ncb) F[cl] *= v.facp[cl * sp.n_child + t][key];
-  }
-}
-
-// Geometry of one slice [t0, t1) of a clique: the table is a matrix of
-// rows x P columns (jt_internal.h); the slice covers rows r_lo .. r_lo+nrow-1
-// (a row cut by a slice boundary is shared through atomics).
-struct SliceGeo {
-  uint32_t t0, t1, P, LR, r_lo, seg_lo;
-  int nrow;
-};
-
-template <bool POW2>
-__device__ __forceinline__ uint32_t row_of(const DevClique& c, uint32_t e) {
-  return POW2 ? (e >> c.logP) : udiv(e, (uint32_t)c.P, c.P_magic);
-}
-template <bool POW2>
-__device__ __forceinline__ uint32_t seg_of(const DevClique& c, uint32_t r) {
-  return POW2 ? (r >> c.logLR) : udiv(r, (uint32_t)c.LR, c.LR_magic);
-}
-
-template <bool POW2>
-__device__ __forceinline__ SliceGeo slice_geo(const DevClique& c, uint32_t t0, uint32_t t1) {
-  SliceGeo g;
-  g.t0 = t0;
-  g.t1 = t1;
-  g.P = (uint32_t)c.P;
-  g.LR = (uint32_t)c.LR;
-  g.r_lo = row_of<POW2>(c, t0);
-  g.nrow = (int)(row_of<POW2>(c, t1 - 1) - g.r_lo + 1);
-  g.seg_lo = seg_of<POW2>(c, g.r_lo);
-  return g;
-}
-
-// Rows phase before streaming (distribute): G(r) = E_row(r) prod_g mu_g[key_g(r)] rho[seg(r)].
-template <typename T, bool POW2, int CBMAX>
-__device__ __forceinline__ void rows_factor(const SmemPlan& sp, const DevClique& c, const CtaView<T>& v,
-                                            const SliceGeo& g, int ncb, bool is_root) {
-  const int tid = threadIdx.x;
-  if (tid >= kThreads) return;
-#pragma unroll 2
-  for (int pr = tid; pr < g.nrow; pr += kThreads) {
-    const uint32_t r = g.r_lo + (uint32_t)pr;
-    T F[CBMAX];
-    row_factor<T, POW2, CBMAX>(v, sp, c.n_child, ncb, r, F);
-    const uint32_t sg = seg_of<POW2>(c, r);
-#pragma unroll
-    for (int cl = 0; cl < CBMAX; ++cl)
-      if (cl < ncb) v.gsm[(size_t)cl * sp.rowmax + pr] = is_root ? F[cl] : F[cl] * v.rhop[cl][sg];
-  }
-}
-
-// The bulk-copy ring over [t0, t1): the producer warp refills a stage once
-// every consumer warp released it; consumer warps call fn(ce, cend, sb) for
-// each chunk (entries [ce, cend) staged at sb) and never wait for each other.
-// Chunks carry a per-CTA sequence number seq0 + ci, so stages and mbarrier
-// phases continue across the CTA's items; the item prologue issued the first
-// n_pre chunks.  Returns false (after letting issued copies land) if a wait
-// timed out or another CTA reported an error.
-template <typename T, typename Fn>
-__device__ __forceinline__ bool ring_stream(const LevelArgs<T>& a, const SmemPlan& sp, const CtaView<T>& v,
-                                            const T* tab, uint32_t t0, uint32_t t1, uint32_t seq0, int n_pre,
-                                            Fn&& fn) {
+// ---- producer: one thread streams the items' blocks into the ring --------
+template <typename T>
+__device__ __forceinline__ void producer(const PropArgs<T>& a, const Smem& s) {
   constexpr int VEC = VecT<T>::N;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t S = (uint32_t)sp.stages;
-  const uint32_t chunk = (uint32_t)sp.chunk;
-  const int n_chunks = (int)((t1 - t0 + chunk - 1) / chunk);
-  bool failed = false;
-  int issued = n_pre;
-  if (warp == kWarps) {
-    if (lane == 0) {
-      for (int cn = n_pre; cn < n_chunks && !failed; ++cn) {
-        const uint32_t q = seq0 + (uint32_t)cn, st = q % S;
-        if (!mbar_wait(v.ebar + st, ((q / S) - 1) & 1u, a.err)) {
-          failed = true;
-          break;
-        }
-        fence_proxy_async();
-        const uint32_t e = t0 + (uint32_t)cn * chunk;
-        const uint32_t ne = (min(chunk, t1 - e) + VEC - 1) / VEC * VEC;
-        mbar_expect_tx(v.bar + st, ne * (uint32_t)sizeof(T));
-        bulk_g2s(v.buf + (size_t)st * chunk, tab + e, ne * (uint32_t)sizeof(T), v.bar + st);
-        issued = cn + 1;
-      }
+  volatile int* abort = s.misc;
+  T* ring = reinterpret_cast<T*>(s.ring);
+  const uint32_t S = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
+  uint32_t q = 0;  // chunks issued
+  bool ok = true;
+  for (uint32_t slot = 0;; ++slot) {
+    int it = a.n_items;
+    if (!*abort && ld_relaxed(a.err) == 0) it = atomicAdd(a.queue, 1);
+    const uint32_t fs = slot % kFifo;
+    if (slot >= (uint32_t)kFifo && !mbar_wait(s.iempty + fs, ((slot / kFifo) - 1) & 1u, a.err, abort)) {
+      ok = false;
+      break;
     }
-  } else {
-    for (int ci = 0; ci < n_chunks; ++ci) {
-      const uint32_t q = seq0 + (uint32_t)ci, st = q % S;
-      if (!mbar_wait(v.bar + st, (q / S) & 1u, a.err)) {
-        failed = true;
+    DevItem w{};
+    w.stage = -1;
+    if (it < a.n_items) {
+      w = a.items[it];
+      w.pad[0] = it;  // item index, for the optional trace
+      if (a.trace != nullptr) a.trace[(int64_t)it * kTraceSlots + 7] = global_ns();
+    }
+    s.fifo[fs] = w;
+    mbar_arrive(s.ifull + fs);
+    if (w.stage < 0) break;
+    const int64_t a0 = w.off / VEC * VEC, a1 = (w.off + w.n + VEC - 1) / VEC * VEC;
+    for (int64_t e = a0; e < a1; e += CH, ++q) {
+      const uint32_t st = q % S;
+      if (q >= S && !mbar_wait(s.empty + st, ((q / S) - 1) & 1u, a.err, abort)) {
+        ok = false;
         break;
       }
-      const uint32_t ce = t0 + (uint32_t)ci * chunk;
-      fn(ce, min(t1, ce + chunk), v.buf + (size_t)st * chunk);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(v.ebar + st);  // this warp is done with the stage
+      fence_proxy_async();
+      const uint32_t ne = (uint32_t)min((int64_t)CH, a1 - e);
+      mbar_expect_tx(s.full + st, ne * (uint32_t)sizeof(T));
+      bulk_g2s(ring + (size_t)st * CH, a.base + e, ne * (uint32_t)sizeof(T), s.full + st);
+    }
+    if (a.trace != nullptr) a.trace[(int64_t)it * kTraceSlots + 8] = global_ns();
+    if (!ok) break;
+  }
+  if (!ok) {
+    atomicExch(a.err, 1);
+    *abort = 1;
+  }
+  // every issued copy lands before the CTA may exit (the last chunk of each stage)
+  for (uint32_t j = q > S ? q - S : 0; j < q; ++j) mbar_wait(s.full + j % S, (j / S) & 1u, nullptr, nullptr);
+}
+
+// ---- signalling lane: publishes finished blocks ---------------------------
+// The consumers hand each finished item's (stage, case block) over once every
+// consumer thread has issued the item's output reductions; this lane makes
+// them visible GPU-wide (fence) and counts the block as done, so the fence's
+// latency stays off the consumers' path.
+__device__ __forceinline__ void signaller(const int32_t* err, int32_t* done, int n_cb, const Smem& s) {
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t sl = k % kSig;
+    if (!mbar_wait(s.sfull + sl, (k / kSig) & 1u, err, s.misc)) break;
+    const int2 w = s.sig[sl];
+    mbar_arrive(s.sempty + sl);
+    if (w.x < 0) break;
+    __threadfence();
+    atomicAdd(done + (int64_t)w.x * n_cb + w.y, 1);
+  }
+}
+
+// Consumer thread 0: hand (stage, case block) to the signalling lane
+// (stage < 0 ends it).  False if the lane did not free the slot in time.
+__device__ __forceinline__ bool hand_over(const Smem& s, uint32_t& k, int stage, int cbk, const int32_t* err) {
+  const uint32_t sl = k % kSig;
+  if (k >= (uint32_t)kSig && !mbar_wait(s.sempty + sl, ((k / kSig) - 1) & 1u, err, s.misc)) return false;
+  s.sig[sl] = make_int2(stage, cbk);
+  mbar_arrive(s.sfull + sl);
+  ++k;
+  return true;
+}
+
+// ---- consumers ------------------------------------------------------------
+
+// A port with a window, as the fast path reads it (shared memory).
+struct LivePort {
+  int32_t mode;       // bits 0-1 vmode, bit 2 key depends on the iteration, bits 3-7 lane_free,
+                      // bit 8 key depends on the chunk
+  int32_t port;
+  int32_t pad[2];
+  int4 dvec;
+};
+constexpr int32_t kModeIter = 4;
+constexpr int32_t kModeChunk = 256;
+
+// Stream the chunks of one item (fast path: power-of-two clique, the block
+// starts on a vector boundary, at most kMaxFastPorts ports).  An entry's
+// offset in the block splits into disjoint bit sets
+//     o = io + tid * VEC + j,   io = m * (consumers * VEC)  (iteration m),
+// so every port key is kt[i][tid] (fixed per item) + kiter[i][m] (uniform,
+// tabulated per item) + dvec[j].  Per vector: evidence, input gathers, the
+// block total, and output scatters reduced over the lanes that share a key;
+// the key work is shared by every case of the case block.  Two outputs
+// accumulate in registers instead: the first output whose vector entries
+// share a key (flushed when its key changes, which happens uniformly across
+// the CTA), and, for one case, a joint whose key ignores the chunk bits
+// (flushed at the end of the item).
+template <typename T, int CB>
+__device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s, const DevItem& w, int ncb, int cb0,
+                                            int n_in, int n_live, bool any_obs, const T (&bfv)[CB], T (&tot)[CB],
+                                            uint32_t& q) {
+  constexpr int NT = consumers_for(CB);
+  constexpr int VEC = VecT<T>::N;
+  constexpr int VPT = kChunkBytes / (16 * NT);  // vectors per thread per chunk
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t RS = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
+  const uint32_t ring32 = smem_u32(s.ring), win32 = smem_u32(s.win);
+  const uint32_t kt32 = smem_u32(s.kt) + 4u * (uint32_t)tid, ki32 = smem_u32(s.kiter);
+  const uint32_t wstride = (uint32_t)a.win_max * (uint32_t)sizeof(T);  // bytes between cases' windows
+  const LivePort* lp = reinterpret_cast<const LivePort*>(s.live);
+  const int nchunks = (int)((w.n + CH - 1) / CH);
+  // register-accumulated outputs
+  int ra = -1, ja = -1;
+  for (int i = n_in; i < n_live; ++i) {
+    const int32_t md = lp[i].mode;
+    if (ra < 0 && (md & 3) == 0) ra = i;
+    else if (CB == 1 && ja < 0 && (md & 3) != 0 && !(md & kModeChunk)) ja = i;
+  }
+  T racc[CB];
+#pragma unroll
+  for (int cl = 0; cl < CB; ++cl) racc[cl] = T(0);
+  uint32_t rkt = 0, rlf = 0, rcur = 0;
+  if (ra >= 0) {
+    rkt = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(ra * NT));
+    rlf = (uint32_t)(lp[ra].mode >> 3) & 31u;
+    rcur = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter));
+  }
+  T jacc[VPT][VEC];
+#pragma unroll
+  for (int it = 0; it < VPT; ++it)
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) jacc[it][j] = T(0);
+  bool ok = true;
+  uint64_t waited = 0;
+  for (int ci = 0; ci < nchunks; ++ci, ++q) {
+    const uint32_t st = q % RS;
+    const uint64_t tw = (a.trace != nullptr && tid == 0) ? global_ns() : 0;
+    // the warp leaves together (its lanes reduce with shuffles below)
+    if (!__all_sync(kFull, mbar_wait(s.full + st, (q / RS) & 1u, a.err, s.misc))) {
+      ok = false;
+      break;
+    }
+    if (a.trace != nullptr && tid == 0) waited += global_ns() - tw;
+    const uint32_t sb = ring32 + st * CH * (uint32_t)sizeof(T);
+    const uint32_t cbase = (uint32_t)ci * CH;
+    const int nvec = (int)(min((uint32_t)w.n - cbase, CH) / VEC);
+#pragma unroll
+    for (int it = 0; it < VPT; ++it) {
+      if (it * NT + warp * 32 >= nvec) break;  // warp-uniform
+      const int vi = it * NT + tid;
+      const bool act = vi < nvec;
+      const int m = ci * VPT + it;             // iteration index within the block
+      T x[VEC];
+      if (act) {
+        sld_vec(sb + (uint32_t)vi * (VEC * (uint32_t)sizeof(T)), x);
+      } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) x[j] = T(0);
+      }
+      const uint32_t o0 = cbase + (uint32_t)vi * VEC;
+      T f[CB][VEC];
+#pragma unroll
+      for (int cl = 0; cl < CB; ++cl) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) f[cl][j] = x[j] * bfv[cl];
+        if (any_obs && cl < ncb && bfv[cl] != T(0)) {
+          const int no = s.nobs[cl];
+          for (int e = 0; e < no; ++e) {
+            const int4 ob = s.obs[cl * a.max_k + e];
+            const uint32_t d = (o0 >> ob.x) & (uint32_t)ob.y;
+#pragma unroll
+            for (int j = 0; j < VEC; ++j)
+              if (d + (((uint32_t)j >> ob.x) & (uint32_t)ob.y) != (uint32_t)ob.z) f[cl][j] = T(0);
+          }
+        }
+      }
+      // input gathers
+      for (int i = 0; i < n_in; ++i) {
+        const int32_t md = lp[i].mode;
+        uint32_t k = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + m));
+        const uint32_t ka = win32 + k * (uint32_t)sizeof(T);
+        const int vm = md & 3;
+        if (vm == 1) {
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl) {
+            if (cl < ncb && bfv[cl] != T(0)) {
+              T g[VEC];
+              sld_vec(ka + (uint32_t)cl * wstride, g);
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) f[cl][j] *= g[j];
+            }
+          }
+        } else if (vm == 0) {
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl) {
+            if (cl < ncb && bfv[cl] != T(0)) {
+              const T g = sld<T>(ka + (uint32_t)cl * wstride);
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) f[cl][j] *= g;
+            }
+          }
+        } else {
+          const int4 dv = lp[i].dvec;
+          const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl) {
+            if (cl < ncb && bfv[cl] != T(0)) {
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) f[cl][j] *= sld<T>(ka + (uint32_t)cl * wstride + (uint32_t)dva[j] * (uint32_t)sizeof(T));
+            }
+          }
+        }
+      }
+      T sum[CB];
+#pragma unroll
+      for (int cl = 0; cl < CB; ++cl) {
+        sum[cl] = T(0);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) sum[cl] += f[cl][j];
+        tot[cl] += sum[cl];
+      }
+      // the register-accumulated output: flush when its key changes
+      if (ra >= 0) {
+        const uint32_t kc = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter + m));
+        if (kc != rcur) {
+          const bool lead = (lane & rlf) == 0u;
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl) {
+            if (cl < ncb) {
+              const T v = lane_reduce(racc[cl], rlf);
+              if (lead && v != T(0)) sred_add(win32 + (uint32_t)cl * wstride + (rkt + rcur) * (uint32_t)sizeof(T), v);
+              racc[cl] = T(0);
+            }
+          }
+          rcur = kc;
+        }
+#pragma unroll
+        for (int cl = 0; cl < CB; ++cl) racc[cl] += sum[cl];
+      }
+      if (ja >= 0) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) jacc[it][j] += f[0][j];
+      }
+      // output scatters, reduced over the lanes that share the key
+      for (int i = n_in; i < n_live; ++i) {
+        if (i == ra || i == ja) continue;
+        const int32_t md = lp[i].mode;
+        uint32_t k = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + m));
+        const uint32_t ka = win32 + k * (uint32_t)sizeof(T);
+        const uint32_t lf = (uint32_t)(md >> 3) & 31u;
+        const bool lead = act && (lane & lf) == 0u;
+        if ((md & 3) == 0) {
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl) {
+            if (cl < ncb && bfv[cl] != T(0)) {
+              const T v = lane_reduce(sum[cl], lf);
+              if (lead && v != T(0)) sred_add(ka + (uint32_t)cl * wstride, v);
+            }
+          }
+        } else {
+          const int4 dv = lp[i].dvec;
+          const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl) {
+            if (cl < ncb && bfv[cl] != T(0)) {
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) {
+                const T v = lane_reduce(f[cl][j], lf);
+                if (lead && v != T(0)) sred_add(ka + (uint32_t)cl * wstride + (uint32_t)dva[j] * (uint32_t)sizeof(T), v);
+              }
+            }
+          }
+        }
+      }
+      if (a.calib != nullptr && act) {
+#pragma unroll
+        for (int cl = 0; cl < CB; ++cl)
+          if (cl < ncb) VecT<T>::stg(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + w.off + o0, f[cl]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(s.empty + st);
+  }
+  if (a.trace != nullptr && tid == 0) a.trace[(int64_t)w.pad[0] * kTraceSlots + 6] = waited;
+  if (!__all_sync(kFull, ok)) return false;
+  // flush the register accumulators (inactive lanes hold zeros)
+  if (ra >= 0) {
+    const bool lead = (lane & rlf) == 0u;
+#pragma unroll
+    for (int cl = 0; cl < CB; ++cl) {
+      if (cl < ncb) {
+        const T v = lane_reduce(racc[cl], rlf);
+        if (lead && v != T(0)) sred_add(win32 + (uint32_t)cl * wstride + (rkt + rcur) * (uint32_t)sizeof(T), v);
+      }
     }
   }
-  if (__syncthreads_or(failed)) {
-    if (warp == kWarps && lane == 0) {
-      atomicExch(a.err, 1);
-      // the producer runs at most S chunks ahead of the slowest consumer
-      for (int cj = max(0, issued - (int)S); cj < issued; ++cj) {
-        const uint32_t q = seq0 + (uint32_t)cj;
-        mbar_wait(v.bar + q % S, (q / S) & 1u, nullptr);
+  if (ja >= 0) {
+    const uint32_t kt = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(ja * NT));
+    const uint32_t lf = (uint32_t)(lp[ja].mode >> 3) & 31u;
+    const int4 dv = lp[ja].dvec;
+    const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
+    const bool lead = (lane & lf) == 0u;
+#pragma unroll
+    for (int it = 0; it < VPT; ++it) {
+      if (it >= (w.n + NT * VEC - 1) / (NT * VEC)) break;  // iteration never reached
+      const uint32_t k = kt + (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ja * kMaxIter + it));
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        const T v = lane_reduce(jacc[it][j], lf);
+        if (lead && v != T(0)) sred_add(win32 + (k + (uint32_t)dva[j]) * (uint32_t)sizeof(T), v);
       }
+    }
+  }
+  return ok;
+}
+
+// Stream the chunks of one item entry by entry (any cardinalities; the block
+// may start inside a vector).
+template <typename T, int CB>
+__device__ __forceinline__ bool stream_generic(const PropArgs<T>& a, const Smem& s, const DevStage& S,
+                                               const DevItem& w, int ncb, int cb0, const T (&bfv)[CB],
+                                               T (&tot)[CB], uint32_t& q) {
+  constexpr int NT = consumers_for(CB);
+  constexpr int VEC = VecT<T>::N;
+  constexpr int VPT = kChunkBytes / (16 * NT);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t RS = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
+  const uint32_t ring32 = smem_u32(s.ring), win32 = smem_u32(s.win);
+  const int64_t a0 = w.off / VEC * VEC, a1 = (w.off + w.n + VEC - 1) / VEC * VEC;
+  const int nchunks = (int)((a1 - a0 + CH - 1) / CH);
+  const int np = S.np, nin = S.nin;
+  bool ok = true;
+  for (int ci = 0; ci < nchunks; ++ci, ++q) {
+    const uint32_t st = q % RS;
+    // the warp leaves together (its lanes reduce with shuffles below)
+    if (!__all_sync(kFull, mbar_wait(s.full + st, (q / RS) & 1u, a.err, s.misc))) {
+      ok = false;
+      break;
+    }
+    {
+      const uint32_t sb = ring32 + st * CH * (uint32_t)sizeof(T);
+      const int64_t cstart = a0 + (int64_t)ci * CH;
+      const int nvec = (int)(min((int64_t)CH, a1 - cstart) / VEC);
+#pragma unroll
+      for (int it = 0; it < VPT; ++it) {
+        if (it * NT + warp * 32 >= nvec) break;  // warp-uniform
+        const int vi = it * NT + tid;
+        const bool act = vi < nvec;
+        T x[VEC];
+        if (act) {
+          sld_vec(sb + (uint32_t)vi * (VEC * (uint32_t)sizeof(T)), x);
+        } else {
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) x[j] = T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          const int64_t e = cstart + (int64_t)vi * VEC + j;
+          const bool valid = act && e >= w.off && e < w.off + w.n;
+          const uint32_t o = valid ? (uint32_t)(e - w.off) : 0u;
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl) {
+            if (cl >= ncb) break;
+            if (bfv[cl] == T(0)) continue;
+            T f = valid ? x[j] * bfv[cl] : T(0);
+            const int no = s.nobs[cl];
+            for (int ei = 0; ei < no; ++ei) {
+              const int4 ob = s.obs[cl * a.max_k + ei];
+              if (digit_of(o, s.pos[ob.x]) != (uint32_t)ob.z) f = T(0);
+            }
+            const uint32_t W = win32 + (uint32_t)(cl * a.win_max) * (uint32_t)sizeof(T);
+            for (int pi = 0; pi < nin; ++pi) {
+              const DevPort& P = s.port[pi];
+              if (P.K <= 1) continue;
+              f *= sld<T>(W + (uint32_t)(P.win + key_of<false>(o, s.fld + P.f0, P.nf)) * (uint32_t)sizeof(T));
+            }
+            tot[cl] += f;
+            for (int pi = nin; pi < np; ++pi) {
+              const DevPort& P = s.port[pi];
+              if (P.K <= 1) continue;
+              add_combined<T>(W + (uint32_t)P.win * (uint32_t)sizeof(T), key_of<false>(o, s.fld + P.f0, P.nf), f, lane);
+            }
+            if (a.calib != nullptr && valid) a.calib[(int64_t)(cb0 + cl) * a.calib_stride + e] = f;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(s.empty + st);
+  }
+  return ok;
+}
+
+// Wait until every dependency of the item has all its blocks finished (warp 0,
+// one dependency per lane).  False if the wait limit passed or an error was
+// reported.
+__device__ __forceinline__ bool await_deps(const int32_t* deps, int ndep, const int32_t* done, int n_cb, int cbk,
+                                           const int32_t* err, const volatile int* abort) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int d = lane; d < ndep; d += 32) {
+    const int32_t stg = deps[2 * d], need = deps[2 * d + 1];
+    const int32_t* ctr = done + (int64_t)stg * n_cb + cbk;
+    if (ld_acquire(ctr) >= need) continue;
+    const uint64_t t0 = global_ns();
+    while (ld_acquire(ctr) < need) {
+      if (*abort || ld_relaxed(err) != 0 || global_ns() - t0 > kWaitLimitNs) {
+        ok = false;
+        break;
+      }
+      __nanosleep(100);
+    }
+    if (!ok) break;
+  }
+  return __all_sync(kFull, ok);
+}
+
+// One work item.  Every consumer thread runs every barrier; the result is
+// uniform over the consumers.
+template <typename T, int CB>
+__device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s, const DevItem& w, uint32_t& q,
+                                             uint32_t& sigk) {
+  constexpr int NT = consumers_for(CB);
+  constexpr int VEC = VecT<T>::N;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const DevStage S = a.stages[w.stage];
+  const int cb0 = a.case0 + w.cbk * CB;
+  const int ncb = min(CB, a.case0 + a.n_cases - cb0);
+  const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;  // block start inside the clique
+  const bool fast = S.bits >= 0;
+  T* win = reinterpret_cast<T*>(s.win);
+  uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)w.pad[0] * kTraceSlots : nullptr;
+  if (tr != nullptr && tid == 0) {
+    uint32_t smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    tr[0] = smid;
+    tr[1] = global_ns();
+  }
+
+  // descriptors into shared memory (warps 1..); dependencies (warp 0)
+  if (tid == 0) s.misc[1] = 1;
+  if (tid < CB) {
+    s.nobs[tid] = 0;
+    s.bf[tid] = 1.0;
+  }
+  if (warp == 0) {
+    if (S.ndep > 0) {
+      const bool dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc);
+      if (lane == 0 && !dok) s.misc[1] = 0;
+    }
+    if (tr != nullptr && lane == 0) tr[2] = global_ns();
+  } else {
+    for (int i = tid - 32; i < S.np; i += NT - 32) s.port[i] = a.ports[S.port0 + i];
+    for (int i = tid - 32; i < S.nf; i += NT - 32) s.fld[i] = a.fields[S.field0 + i];
+    for (int i = tid - 32; i < S.k; i += NT - 32) s.pos[i] = a.pos[S.pos0 + i];
+  }
+  consumer_sync<NT>();
+  const bool ok = s.misc[1] != 0;
+
+  // evidence (block-level digits into the block factor, in-block digits
+  // into per-case lists), windows (inputs gathered and normalised, outputs
+  // zeroed), block-constant inputs, and the fast path's key parts
+  for (int idx = tid; idx < ncb * S.k; idx += NT) {
+    const int cl = idx / S.k, i = idx - cl * S.k;
+    const DevPos P = s.pos[i];
+    const int st = a.ev[(int64_t)(cb0 + cl) * a.n_vars + P.var];
+    if (st < 0) continue;
+    if (st >= P.card) {
+      atomicOr(&a.status[cb0 + cl], kStatusBadState);
+      continue;
+    }
+    if (fast) {
+      const int inside = max(0, min(P.cb, S.bits - P.sh));
+      const uint32_t lo_m = (1u << inside) - 1u;
+      const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
+      if (hi_d != ((uint32_t)st & ~lo_m)) {
+        s.bf[cl] = 0.0;
+      } else if (lo_m != 0u) {
+        const int slot = atomicAdd(&s.nobs[cl], 1);
+        s.obs[cl * a.max_k + slot] = make_int4(P.sh, (int)lo_m, st & (int)lo_m, i);
+      }
+    } else if (i < S.k - S.kin) {
+      if (digit_of(eb, P) != (uint32_t)st) s.bf[cl] = 0.0;
+    } else {
+      const int slot = atomicAdd(&s.nobs[cl], 1);
+      s.obs[cl * a.max_k + slot] = make_int4(i, 0, st, i);
+    }
+  }
+  if (ok) {
+    // per (case, port): a child message's normalisation |S|/sigma (applied
+    // through the block factor), or the value of a block-constant input
+    for (int idx = tid; idx < ncb * S.np; idx += NT) {
+      const int cl = idx / S.np, pi = idx - cl * S.np;
+      const DevPort& P = s.port[pi];
+      const int cs = cb0 + cl;
+      const T* row = a.msg + (int64_t)cs * a.msg_stride;
+      const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
+      double v = 1.0;
+      if (P.kind == kPortMu) {
+        const double sg = __ldcg(sums + P.other);
+        v = sg > 0.0 ? (double)P.size / sg : 0.0;
+        if (P.K <= 1) {
+          const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+          v *= (double)__ldcg(row + P.tab + key);
+        }
+      } else if (P.kind == kPortRho && P.K <= 1) {
+        const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+        const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
+        const double u = (double)__ldcg(row + P.tab + key);
+        const double d = (double)__ldcg(row + a.delta_off + P.tab + key);
+        v = (dp > 0.0 && u > 0.0) ? d * (sgc / dp) / u : 0.0;
+      }
+      s.pval[cl * a.max_ports + pi] = v;
+    }
+    // windows: raw child messages, ratios of the own separator, zeroed outputs
+    const uint32_t win32 = smem_u32(s.win);
+    for (int pi = 0; pi < S.np; ++pi) {
+      const DevPort& P = s.port[pi];
+      if (P.K <= 1) continue;
+      const uint32_t kb = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+      const int K = P.K, total = ncb * K;
+      const uint32_t w0 = win32 + (uint32_t)P.win * (uint32_t)sizeof(T);
+      if (P.kind == kPortMu) {
+        // eight loads in flight per thread
+        for (int base = 0; base < total; base += 8 * NT) {
+          T u[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int idx = base + r * NT + tid;
+            u[r] = T(0);
+            if (idx < total) {
+              const int cl = idx / K, ii = idx - cl * K;
+              u[r] = __ldcg(a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb + ii);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int idx = base + r * NT + tid;
+            if (idx < total) {
+              const int cl = idx / K, ii = idx - cl * K;
+              sst<T>(w0 + (uint32_t)(cl * a.win_max + ii) * (uint32_t)sizeof(T), u[r]);
+            }
+          }
+        }
+      } else if (P.kind == kPortRho) {
+        for (int base = 0; base < total; base += 4 * NT) {
+          double u[4], d[4], sc[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int idx = base + r * NT + tid;
+            u[r] = 0.0;
+            d[r] = 0.0;
+            sc[r] = 0.0;
+            if (idx < total) {
+              const int cl = idx / K, ii = idx - cl * K;
+              const int cs = cb0 + cl;
+              const T* row = a.msg + (int64_t)cs * a.msg_stride;
+              const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
+              u[r] = (double)__ldcg(row + P.tab + kb + ii);
+              d[r] = (double)__ldcg(row + a.delta_off + P.tab + kb + ii);
+              const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
+              sc[r] = dp > 0.0 ? sgc / dp : 0.0;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int idx = base + r * NT + tid;
+            if (idx < total) {
+              const int cl = idx / K, ii = idx - cl * K;
+              const double v = u[r] > 0.0 ? d[r] * sc[r] / u[r] : 0.0;
+              sst<T>(w0 + (uint32_t)(cl * a.win_max + ii) * (uint32_t)sizeof(T), (T)v);
+            }
+          }
+        }
+      } else {
+        for (int idx = tid; idx < total; idx += NT) {
+          const int cl = idx / K, ii = idx - cl * K;
+          sst<T>(w0 + (uint32_t)(cl * a.win_max + ii) * (uint32_t)sizeof(T), T(0));
+        }
+      }
+    }
+  }
+  int n_in = 0, n_live = 0;
+  if (fast) {
+    for (int pi = 0; pi < S.np; ++pi) {
+      if (s.port[pi].K <= 1) continue;
+      if (pi < S.nin) ++n_in;
+      ++n_live;
+    }
+    if (ok) {
+      LivePort* lp = reinterpret_cast<LivePort*>(s.live);
+      const int mi = (w.n + NT * VEC - 1) / (NT * VEC);
+      int li = 0;
+      for (int pi = 0; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1) continue;
+        if (tid == li) {
+          LivePort L;
+          L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
+                   (int32_t)((P.lane_free & 31u) << 3);
+          L.port = pi;
+          L.pad[0] = L.pad[1] = 0;
+          L.dvec = make_int4(P.dvec[0], P.dvec[1], P.dvec[2], P.dvec[3]);
+          lp[li] = L;
+        }
+        s.kt[li * NT + tid] = (int)(key_of<true>((uint32_t)tid * VEC, s.fld + P.f0, P.nf) + (uint32_t)P.win);
+        for (int m = tid; m < mi; m += NT)
+          s.kiter[li * kMaxIter + m] = (int)key_of<true>((uint32_t)m * NT * VEC, s.fld + P.f0, P.nf);
+        ++li;
+      }
+    }
+  }
+  consumer_sync<NT>();
+  if (ok && tid < ncb) {
+    double b = s.bf[tid];
+    for (int pi = 0; pi < S.nin; ++pi) b *= s.pval[tid * a.max_ports + pi];
+    s.bf[tid] = b;
+  }
+  consumer_sync<NT>();
+
+  // stream the block
+  if (tr != nullptr && tid == 0) tr[3] = global_ns();
+  T bfv[CB], tot[CB];
+  bool any_obs = false;
+#pragma unroll
+  for (int cl = 0; cl < CB; ++cl) {
+    bfv[cl] = (ok && cl < ncb) ? (T)s.bf[cl] : T(0);
+    tot[cl] = T(0);
+    if (cl < ncb && s.nobs[cl] > 0) any_obs = true;
+  }
+  bool sok = true;
+  if (ok) {
+    sok = fast ? stream_fast<T, CB>(a, s, w, ncb, cb0, n_in, n_live, any_obs, bfv, tot, q)
+               : stream_generic<T, CB>(a, s, S, w, ncb, cb0, bfv, tot, q);
+  }
+  const bool all_ok = consumer_all<NT>(ok && sok);
+  if (!all_ok) {
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      s.misc[0] = 1;
     }
     return false;
   }
-  return true;
-}
+  if (tr != nullptr && tid == 0) tr[4] = global_ns();
 
-// Load the consumer thread's kVpt vectors of a staged chunk (zeros past the end).
-template <typename T>
-__device__ __forceinline__ void load_chunk(const T* sb, uint32_t ce, uint32_t cend, T (&xs)[kVpt][VecT<T>::N]) {
-  constexpr int VEC = VecT<T>::N;
-  const int nvec = (int)((cend - ce + VEC - 1) / VEC);
+  // flush: block totals (stage total, block-constant outputs), then windows
 #pragma unroll
-  for (int it = 0; it < kVpt; ++it) {
-    const int i = it * kThreads + (int)threadIdx.x;
-    if (i < nvec) {
-      VecT<T>::lds(sb + (size_t)i * VEC, xs[it]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) xs[it][j] = T(0);
-    }
-#pragma unroll
-    for (int j = 0; j < VEC; ++j)
-      if (ce + (uint32_t)i * VEC + j >= cend) xs[it][j] = T(0);
+  for (int cl = 0; cl < CB; ++cl) {
+    const double v = warp_sum((double)tot[cl]);
+    if (lane == 0) s.red[cl * (NT / 32) + warp] = v;
   }
-}
-
-// Stream the slice through the bulk-copy ring: per entry v = phi E_col
-// (times G for distribute); row sums R(r) = sum_col v; distribute also
-// accumulates the column joint and writes the calibrated entry.  Chunks carry
-// a per-CTA sequence number `seq0 + ci`, so ring stages and mbarrier phases
-// continue across the CTA's items.  The producer warp refills a stage once
-// every consumer warp released it; consumer warps never wait for each other.
-// Returns false (after letting issued copies land) if a wait timed out.
-template <typename T, bool COLLECT, bool POW2, bool ROWVEC, int CBMAX>
-__device__ __forceinline__ bool stream(const LevelArgs<T>& a, const SmemPlan& sp, const DevClique& c,
-                                       const CtaView<T>& v, const SliceGeo& g, const T* tab, int cb0, int ncb,
-                                       uint32_t seq0, int n_pre) {
-  constexpr int VEC = VecT<T>::N;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t P = g.P, t0 = g.t0;
-  const bool has_joint = c.joint_off >= 0;
-  const bool regjoint = !COLLECT && has_joint && ((uint32_t)sp.chunk % P == 0u);
-  const bool row_in_warp = POW2 && ROWVEC && P <= 32u * VEC;
-  const bool p1 = (P == 1u);
-  // column-joint accumulators per vector slot: the columns a thread sees in
-  // slot `it` repeat every chunk when P divides the chunk
-  T jacc[CBMAX][kVpt][VEC];
-#pragma unroll
-  for (int cl = 0; cl < CBMAX; ++cl)
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it)
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) jacc[cl][it][j] = T(0);
-  const bool ok = ring_stream<T>(a, sp, v, tab, g.t0, g.t1, seq0, n_pre, [&](uint32_t ce, uint32_t cend, const T* sb) {
-    T xs[kVpt][VEC];
-    load_chunk<T>(sb, ce, cend, xs);
-    const int nvec = (int)((cend - ce + VEC - 1) / VEC);
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it) {
-      if (it * kThreads + (tid & ~31) >= nvec) break;  // warp-uniform
-      const int i = it * kThreads + tid;
-      const bool act = i < nvec;
-      const uint32_t e0 = ce + (uint32_t)i * VEC;
-      const T (&x)[VEC] = xs[it];
-      if (ROWVEC) {
-        const uint32_t ea = act ? e0 : t0;
-        const uint32_t rr = row_of<POW2>(c, ea);
-        const uint32_t pr = rr - g.r_lo, col0 = ea - rr * P;
-        T outv[CBMAX][VEC];
-#pragma unroll
-        for (int cl = 0; cl < CBMAX; ++cl) {
-          T sum = T(0);
-          if (cl < ncb) {
-            const T G = COLLECT ? T(1) : v.gsm[(size_t)cl * sp.rowmax + pr];
-            const bool cm = v.nobs[sp.cb + cl] != 0;
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-              T o = x[j];
-              if (cm) o *= colmask<T, POW2>(v, sp, cl, col0 + j);
-              if (!COLLECT) {
-                o *= G;
-                if (regjoint) jacc[cl][it][j] += o;
-                else if (has_joint && o != T(0)) atomicAdd(v.jntp[cl] + col0 + j, o);
-              }
-              outv[cl][j] = o;
-              sum += o;
-            }
-            T* rs = v.rsum + (size_t)cl * sp.rowmax;
-            if (POW2) {
-              const uint32_t w = min(P / VEC, 32u);  // lanes sharing the row
-              for (uint32_t o = 1; o < w; o <<= 1) sum += __shfl_xor_sync(kFull, sum, o);
-              if (act && (lane & (w - 1)) == 0) {
-                if (row_in_warp) rs[pr] = sum;
-                else atomicAdd(rs + pr, sum);
-              }
-            } else if (act) {
-              atomicAdd(rs + pr, sum);
-            }
-          }
-        }
-        if (!COLLECT && a.calib != nullptr && act) {
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-            if (cl < ncb) VecT<T>::store(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e0, outv[cl]);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-          if (act && e0 + j < cend) {
-            const uint32_t e = e0 + j;
-            const uint32_t rr = row_of<POW2>(c, e);
-            const uint32_t pr = rr - g.r_lo, col = e - rr * P;
-#pragma unroll
-            for (int cl = 0; cl < CBMAX; ++cl) {
-              if (cl < ncb) {
-                T o = x[j];
-                if (v.nobs[sp.cb + cl]) o *= colmask<T, POW2>(v, sp, cl, col);
-                if (!COLLECT) {
-                  o *= v.gsm[(size_t)cl * sp.rowmax + pr];
-                  if (has_joint && o != T(0)) atomicAdd(v.jntp[cl] + col, o);
-                  if (a.calib != nullptr) a.calib[(int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e] = o;
-                }
-                T* rs = v.rsum + (size_t)cl * sp.rowmax + pr;
-                if (p1) *rs = o;
-                else atomicAdd(rs, o);
-              }
-            }
-          }
-        }
-      }
-    }
-  });
-  if (!ok) return false;
-  if (regjoint && tid < kThreads) {
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it) {
-      const uint32_t colt = (t0 + (uint32_t)(it * kThreads + tid) * VEC) % P;
-#pragma unroll
-      for (int cl = 0; cl < CBMAX; ++cl)
-        if (cl < ncb)
-#pragma unroll
-          for (int j = 0; j < VEC; ++j)
-            if (jacc[cl][it][j] != T(0)) atomicAdd(v.jntp[cl] + (colt + j) % P, jacc[cl][it][j]);
-    }
-  }
-  return true;
-}
-
-// Stream a slice of a power-of-two clique whose rows are short, doing all row
-// work inline (no per-slice row buffers):
-//   P == 1 (no private variables; the fastest cardinality a multiple of the
-//          vector width): the entries of a vector differ only in the fastest
-//          digit, so every child key is computed once per vector and stepped
-//          by the child's w_last;
-//   VEC <= P <= 32 VEC: a vector lies in one row and a row in one warp
-//          iteration; each lane computes its row factor (lanes of one row read
-//          the same shared-memory words), a segmented shuffle forms the row
-//          sum, and the row's first lane adds the row outputs.
-template <typename T, bool COLLECT, int CBMAX>
-__device__ __forceinline__ bool stream_inline(const LevelArgs<T>& a, const SmemPlan& sp, const DevClique& c,
-                                              const CtaView<T>& v, const SliceGeo& g, const T* tab, int cb0,
-                                              int ncb, uint32_t seq0, int n_pre, bool is_root, bool out_smem) {
-  constexpr int VEC = VecT<T>::N;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t P = g.P;
-  const bool p1 = (P == 1u);
-  const int nch = c.n_child, klast = c.k - 1;
-  const uint32_t w = p1 ? 1u : P / VEC;           // lanes sharing a row
-  const bool seg_vec = !p1 || (c.LR % VEC) == 0;  // the vector's entries share the parent entry
-  const bool has_joint = c.joint_off >= 0;
-  // P divides the chunk (P <= 32 VEC), so each slot's columns repeat every chunk
-  T jacc[CBMAX][kVpt][VEC];
-#pragma unroll
-  for (int cl = 0; cl < CBMAX; ++cl)
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it)
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) jacc[cl][it][j] = T(0);
-  const bool ok = ring_stream<T>(a, sp, v, tab, g.t0, g.t1, seq0, n_pre, [&](uint32_t ce, uint32_t cend, const T* sb) {
-    T xs[kVpt][VEC];
-    load_chunk<T>(sb, ce, cend, xs);
-    const int nvec = (int)((cend - ce + VEC - 1) / VEC);
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it) {
-      if (it * kThreads + (tid & ~31) >= nvec) break;  // warp-uniform
-      const int i = it * kThreads + tid;
-      const bool act = i < nvec;
-      const uint32_t e0 = act ? ce + (uint32_t)i * VEC : g.t0;
-      const uint32_t r = p1 ? e0 : (e0 >> c.logP);    // row (P == 1: of the vector's first entry)
-      const uint32_t col0 = e0 - r * P;
-      // factor per entry: E_row x prod_g mu_g (x rho for distribute), times phi E_col
-      T f[CBMAX][VEC];
-#pragma unroll
-      for (int cl = 0; cl < CBMAX; ++cl) {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) f[cl][j] = act ? xs[it][j] : T(0);
-        if (cl < ncb) {
-          for (int o = 0; o < v.nobs[cl]; ++o) {
-            const int2 ob = v.obs[cl * sp.k + o];
-            const uint32_t d0 = digit<true>(r, v.pos[ob.x]);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j)
-              if (((p1 && ob.x == klast) ? d0 + j : d0) != (uint32_t)ob.y) f[cl][j] = T(0);
-          }
-          if (!p1 && v.nobs[sp.cb + cl]) {
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) f[cl][j] *= colmask<T, true>(v, sp, cl, col0 + j);
-          }
-        }
-      }
-      for (int t = 0; t < nch; ++t) {
-        const uint32_t k0 = eval_key<true>(r, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
-        const uint32_t wl = p1 ? (uint32_t)v.ch[t].w_last : 0u;
-#pragma unroll
-        for (int cl = 0; cl < CBMAX; ++cl)
-          if (cl < ncb) {
-            const T* fp = v.facp[cl * sp.n_child + t];
-            if (wl == 0u) {
-              const T fv = fp[k0];
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) f[cl][j] *= fv;
-            } else {
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) f[cl][j] *= fp[k0 + j * wl];
-            }
-          }
-      }
-      const uint32_t s0 = r >> c.logLR;
-      if (COLLECT) {
-#pragma unroll
-        for (int cl = 0; cl < CBMAX; ++cl)
-          if (cl < ncb) {
-            if (seg_vec) {
-              T sum = T(0);
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) sum += f[cl][j];
-              add_combined(v.win + (int64_t)cl * sp.win, s0 - g.seg_lo, sum, lane);
-            } else {
-#pragma unroll
-              for (int j = 0; j < VEC; ++j)
-                add_combined(v.win + (int64_t)cl * sp.win, ((r + j) >> c.logLR) - g.seg_lo, f[cl][j], lane);
-            }
-          }
-      } else {
-        if (!is_root) {
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-            if (cl < ncb) {
-              if (seg_vec) {
-                const T rh = v.rhop[cl][s0];
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) f[cl][j] *= rh;
-              } else {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) f[cl][j] *= v.rhop[cl][(r + j) >> c.logLR];
-              }
-            }
-        }
-        // row sums over the lanes of a row (P > 1) and the row outputs
-        T rs[CBMAX];
-#pragma unroll
-        for (int cl = 0; cl < CBMAX; ++cl) {
-          rs[cl] = T(0);
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) rs[cl] += f[cl][j];
-          for (uint32_t o = 1; o < w; o <<= 1) rs[cl] += __shfl_xor_sync(kFull, rs[cl], o);
-          if ((lane & (w - 1)) != 0) rs[cl] = T(0);  // the row's first lane adds it
-        }
-        for (int t = 0; t < nch; ++t) {
-          const uint32_t k0 = eval_key<true>(r, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
-          const uint32_t wl = p1 ? (uint32_t)v.ch[t].w_last : 0u;
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-            if (cl < ncb) {
-              T* op = v.outp[cl * sp.n_child + t];
-              if (wl == 0u) {
-                add_combined(op, k0, rs[cl], lane);
-              } else {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) add_combined(op, k0 + j * wl, f[cl][j], lane);
-              }
-            }
-        }
-        for (int h = 0; h < c.n_home; ++h) {
-          const DevHome hm = v.hm[h];
-          const uint32_t d = digit<true>(r, v.pos[hm.pos]);
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-            if (cl < ncb) add_combined(v.houtp[cl] + (out_smem ? hm.out_off : hm.moff), d, rs[cl], lane);
-        }
-        if (has_joint) {
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) jacc[cl][it][j] += f[cl][j];
-        }
-        if (a.calib != nullptr && act) {
-#pragma unroll
-          for (int cl = 0; cl < CBMAX; ++cl)
-            if (cl < ncb) VecT<T>::store(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + c.base_off + e0, f[cl]);
-        }
-      }
-    }
-  });
-  if (!ok) return false;
-  if (!COLLECT && has_joint && tid < kThreads) {
-#pragma unroll
-    for (int it = 0; it < kVpt; ++it) {
-      const uint32_t colt = (g.t0 + (uint32_t)(it * kThreads + tid) * VEC) % P;
-#pragma unroll
-      for (int cl = 0; cl < CBMAX; ++cl)
-        if (cl < ncb)
-#pragma unroll
-          for (int j = 0; j < VEC; ++j)
-            if (jacc[cl][it][j] != T(0)) atomicAdd(v.jntp[cl] + colt + j, jacc[cl][it][j]);
-    }
-  }
-  return true;
-}
-
-// Rows phase after streaming: collect adds R(r) E_row(r) prod_g mu_g[key_g(r)]
-// to the parent window; distribute adds R(r) (already x G) to every child
-// separator and row-home marginal.
-template <typename T, bool COLLECT, bool POW2, int CBMAX>
-__device__ __forceinline__ void rows_out(const SmemPlan& sp, const DevClique& c, const CtaView<T>& v,
-                                         const SliceGeo& g, int ncb, bool out_smem) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (warp >= kWarps) return;
-  const int nch = c.n_child;
-  for (int pb = warp * 32; pb < g.nrow; pb += kThreads) {
-    const int pr = pb + lane;
-    const bool act = pr < g.nrow;
-    const uint32_t r = g.r_lo + (act ? (uint32_t)pr : 0u);
-    T val[CBMAX];
-#pragma unroll
-    for (int cl = 0; cl < CBMAX; ++cl) val[cl] = (cl < ncb && act) ? v.rsum[(size_t)cl * sp.rowmax + pr] : T(0);
-    if (COLLECT) {
-      T F[CBMAX];
-      row_factor<T, POW2, CBMAX>(v, sp, nch, ncb, r, F);
-      const uint32_t sg = seg_of<POW2>(c, r);
-#pragma unroll
-      for (int cl = 0; cl < CBMAX; ++cl)
-        if (cl < ncb) add_combined(v.win + (int64_t)cl * sp.win, sg - g.seg_lo, F[cl] * val[cl], lane);
-    } else {
-      for (int t = 0; t < nch; ++t) {
-        const uint32_t key = eval_key<POW2>(r, v.fld + v.ch[t].field_rel, v.ch[t].n_field);
-#pragma unroll
-        for (int cl = 0; cl < CBMAX; ++cl)
-          if (cl < ncb) add_combined(v.outp[cl * sp.n_child + t], key, val[cl], lane);
-      }
-      for (int h = 0; h < c.n_home; ++h) {
-        const DevHome hm = v.hm[h];
-        const uint32_t d = digit<POW2>(r, v.pos[hm.pos]);
-#pragma unroll
-        for (int cl = 0; cl < CBMAX; ++cl)
-          if (cl < ncb) add_combined(v.houtp[cl] + (out_smem ? hm.out_off : hm.moff), d, val[cl], lane);
-      }
-    }
-  }
-}
-
-// Wait until flags[i] != 0 for every i in the list (thread 0 polls, with the
-// CTA-uniform result).  Gives up after the wait limit or once another CTA set
-// the error word.
-__device__ __forceinline__ bool wait_flags(const int32_t* const* flags, int n, int32_t* err, int* s_flag) {
-  if (threadIdx.x == 0) {
-    bool ok = true;
-    const uint64_t t0 = global_ns();
-    for (int i = 0; i < n && ok; ++i) {
-      while (ld_acquire(flags[i]) == 0) {
-        if (ld_acquire(err) != 0 || global_ns() - t0 > kWaitLimitNs) {
-          ok = false;
-          break;
-        }
-        __nanosleep(200);
-      }
-    }
-    if (!ok) atomicExch(err, 1);
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
-
-// One work item: a slice of one clique for one block of cases, either pass.
-// The dependencies of the item (children's collect messages; for distribute
-// also the parent's ratio) are awaited as late as possible: a collect slice
-// streams its table before it needs its children.
-template <typename T, bool COLLECT, int CBMAX>
-__device__ bool process_item(const LevelArgs<T>& a, const SmemPlan& sp, const DevWork& w, int cbk,
-                             unsigned char* smem, uint32_t& seq) {
-  constexpr int VEC = VecT<T>::N;
-  const SmemLayout lay(sp);
-  DevChild* s_ch = reinterpret_cast<DevChild*>(smem + lay.off_ch);
-  DevField* s_fld = reinterpret_cast<DevField*>(smem + lay.off_fld);
-  DevHome* s_hm = reinterpret_cast<DevHome*>(smem + lay.off_hm);
-  DevPos* s_pos = reinterpret_cast<DevPos*>(smem + lay.off_pos);
-  int2* s_obs = reinterpret_cast<int2*>(smem + lay.off_obs);            // [cb][k] row observations
-  int2* s_cobs = s_obs + sp.cb * sp.k;                                  // [cb][k] column observations
-  int* s_nobs = reinterpret_cast<int*>(smem + lay.off_nobs);            // [cb] row, then [cb] column counts
-  const T** s_facp = reinterpret_cast<const T**>(smem + lay.off_facp);  // [cb][n_child]
-  T** s_outp = reinterpret_cast<T**>(smem + lay.off_outp);              // [cb][n_child]
-  const T** s_rhop = reinterpret_cast<const T**>(smem + lay.off_rhop);  // [cb]
-  T** s_houtp = reinterpret_cast<T**>(smem + lay.off_houtp);            // [cb]
-  T** s_jntp = reinterpret_cast<T**>(smem + lay.off_jntp);              // [cb]
-  T* s_tabs = reinterpret_cast<T*>(smem + lay.off_tabs);
-  T* s_win = reinterpret_cast<T*>(smem + lay.off_win);
-  double* s_red = reinterpret_cast<double*>(smem + lay.off_red);
-  int* s_flag = reinterpret_cast<int*>(s_red + 72);
-  const int32_t** s_deps = reinterpret_cast<const int32_t**>(s_red + 40);  // up to 32 dependency flags per batch
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + lay.off_bar);
-  uint64_t* s_ebar = s_bar + sp.stages;
-  T* s_rsum = reinterpret_cast<T*>(smem + lay.off_rsum);
-  T* s_gsm = reinterpret_cast<T*>(smem + lay.off_gsm);
-  T* s_buf = reinterpret_cast<T*>(smem + lay.off_buf);
-
-  const int tid = threadIdx.x;
-  const uint32_t t0 = (uint32_t)w.t0, t1 = (uint32_t)w.t1;
-  const T* tab = a.base + w.base_off;
-  const uint32_t S = (uint32_t)sp.stages, chunk = (uint32_t)sp.chunk;
-  const int n_chunks = (int)((t1 - t0 + chunk - 1) / chunk);
-  const int n_pre = min((int)S, n_chunks);
-  const uint32_t seq0 = seq;
-  seq += (uint32_t)n_chunks;
-  // start streaming the slice at once: descriptors and dependencies overlap it
-  if (tid == 0) {
-    for (int ci = 0; ci < n_pre; ++ci) {
-      const uint32_t q = seq0 + (uint32_t)ci, st = q % S;
-      if (q >= S && !mbar_wait(s_ebar + st, ((q / S) - 1) & 1u, a.err)) break;  // stage of an earlier item
-      fence_proxy_async();
-      const uint32_t e = t0 + (uint32_t)ci * chunk;
-      const uint32_t ne = (min(chunk, t1 - e) + VEC - 1) / VEC * VEC;
-      mbar_expect_tx(s_bar + st, ne * (uint32_t)sizeof(T));
-      bulk_g2s(s_buf + (size_t)st * chunk, tab + e, ne * (uint32_t)sizeof(T), s_bar + st);
-    }
-  }
-  const int cid = w.clique;
-  const DevClique c = a.cl[cid];
-  const int cb0 = a.case0 + cbk * sp.cb;
-  const int ncb = min(sp.cb, a.case0 + a.n_cases - cb0);
-  const int nch = c.n_child, k = c.k;
-  const bool is_root = (c.depth == 0);
-  const int64_t msg = a.msg_total;
-  const int64_t off_down = msg, off_rho = 2 * msg, off_marg = 3 * msg, off_joint = 3 * msg + a.marg_total;
-  const bool has_joint = c.joint_off >= 0;
-  // per-clique residency in the per-case table region (offsets from the plan)
-  const bool fac_smem = c.sm_fac >= 0, rho_smem = c.sm_rho >= 0, out_smem = c.sm_out >= 0;
-  const bool jnt_smem = c.sm_jnt >= 0;
-  auto region = [&](int cl) { return s_tabs + (int64_t)cl * sp.tabs; };
-  auto case_acc = [&](int cl) { return a.acc + (int64_t)(cb0 + cl) * a.acc_stride; };
-  auto flag_of = [&](int phase, int clique) { return a.done + ((int64_t)phase * a.n_cliques + clique) * a.max_cases + cbk; };
-
-  // ---- prologue: descriptors, evidence, pointers, zeroed accumulators
-  for (int i = tid; i < nch; i += kBlock) s_ch[i] = a.ch[c.child_first + i];
-  for (int i = tid; i < c.n_field; i += kBlock) s_fld[i] = a.fld[c.field_first + i];
-  for (int i = tid; i < k; i += kBlock) s_pos[i] = a.pos[c.pos_first + i];
-  if (!COLLECT)
-    for (int i = tid; i < c.n_home; i += kBlock) s_hm[i] = a.hm[c.home_first + i];
-  if (tid < 2 * sp.cb) s_nobs[tid] = 0;
+  consumer_sync<NT>();
   if (tid < ncb) {
-    T* acc = case_acc(tid);
-    s_rhop[tid] = (is_root || COLLECT) ? nullptr
-                  : (rho_smem ? (const T*)(region(tid) + c.sm_rho) : (const T*)(acc + off_rho + c.sep_off));
-    s_houtp[tid] = out_smem ? region(tid) + c.sm_out : acc + off_marg;
-    s_jntp[tid] = !has_joint ? nullptr : (jnt_smem ? region(tid) + c.sm_jnt : acc + off_joint + c.joint_off);
-  }
-  for (int i = tid; i < sp.cb * sp.rowmax; i += kBlock) s_rsum[i] = T(0);
-  if (COLLECT) {
-    for (int i = tid; i < ncb * sp.win; i += kBlock) s_win[i] = T(0);
-  } else {
-    if (out_smem) {
-      const int n_out = c.sm_out_len;
-      for (int i = tid; i < ncb * n_out; i += kBlock) region(i / n_out)[c.sm_out + i % n_out] = T(0);
-    }
-    if (jnt_smem && has_joint)
-      for (int i = tid; i < ncb * c.P; i += kBlock) region(i / c.P)[c.sm_jnt + i % c.P] = T(0);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < ncb * k; idx += kBlock) {
-    const int cl = idx / k, i = idx - cl * k;
-    const DevPos P = s_pos[i];
-    const int s = a.ev[(int64_t)(cb0 + cl) * a.n_vars + P.var];
-    if (s >= 0) {
-      if (s >= P.card) {
-        atomicOr(&a.status[cb0 + cl], kStatusBadState);
-      } else if (!P.is_col) {
-        const int slot = atomicAdd(&s_nobs[cl], 1);
-        s_obs[cl * sp.k + slot] = make_int2(i, s);
-      } else {
-        const int slot = atomicAdd(&s_nobs[sp.cb + cl], 1);
-        s_cobs[cl * sp.k + slot] = make_int2(i, s);
+    double t = 0.0;
+    for (int i = 0; i < (NT / 32); ++i) t += s.red[tid * (NT / 32) + i];
+    const int cs = cb0 + tid;
+    T* row = a.msg + (int64_t)cs * a.msg_stride;
+    if (t != 0.0) {
+      for (int pi = S.nin; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K > 1) continue;
+        const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+        atomicAdd(row + P.tab + key, (T)t);
       }
+      atomicAdd(a.sums + (int64_t)cs * 2 * a.n_cliques + S.sum_slot, t);
     }
   }
-  for (int idx = tid; idx < ncb * nch; idx += kBlock) {
-    const int cl = idx / nch, t = idx - cl * nch;
-    const DevChild ch = s_ch[t];
-    T* acc = case_acc(cl);
-    s_facp[cl * sp.n_child + t] = fac_smem ? (const T*)(region(cl) + c.sm_fac + ch.fac_off)
-                                           : (const T*)(acc + ch.sep_off);
-    if (!COLLECT)
-      s_outp[cl * sp.n_child + t] = out_smem ? region(cl) + c.sm_out + ch.fac_off : acc + off_down + ch.sep_off;
-  }
-  __syncthreads();
-
-  // dependencies: the children's collect messages (and, for distribute, the
-  // parent's ratio), then the factor tables they finalised
-  auto await_inputs = [&]() -> bool {
-    for (int b = 0; b < nch + 1; b += 32) {
-      int nd = 0;
-      if (tid == 0) {
-        for (int t = b; t < min(nch, b + 32); ++t) s_deps[nd++] = flag_of(0, s_ch[t].child);
-        if (!COLLECT && !is_root && b == 0 && nd < 32) s_deps[nd++] = flag_of(1, a.parent_of[cid]);
-        s_flag[1] = nd;
-      }
-      __syncthreads();
-      if (!wait_flags(s_deps, s_flag[1], a.err, s_flag)) return false;
-    }
-    for (int cl = 0; cl < ncb; ++cl) {
-      const T* acc = case_acc(cl);
-      if (fac_smem) {
-        for (int t = 0; t < nch; ++t) {
-          const DevChild ch = s_ch[t];
-          T* dst = region(cl) + c.sm_fac + ch.fac_off;
-          for (int j = tid; j < ch.sep_size; j += kBlock) dst[j] = __ldcg(acc + ch.sep_off + j);
-        }
-      }
-      if (rho_smem && !COLLECT && !is_root) {
-        T* dst = region(cl) + c.sm_rho;
-        for (int j = tid; j < c.sep_size; j += kBlock) dst[j] = __ldcg(acc + off_rho + c.sep_off + j);
-      }
-    }
-    __syncthreads();
-    return true;
-  };
-
-  // ---- the slice
-  {
-    const CtaView<T> v{s_ch,   s_fld,   s_hm,   s_pos, s_obs, s_cobs, s_nobs,  s_facp, s_outp,
-                 s_rhop, s_houtp, s_jntp, s_win, s_buf, s_bar,  s_ebar, s_rsum, s_gsm};
-    const bool rowvec = (c.P % VEC) == 0;
-    const bool inl = inline_rows(c, VEC);
-    bool ok = true;
-    if (!COLLECT || inl) ok = await_inputs();
-    if (ok && inl) {
-      const SliceGeo g = slice_geo<true>(c, t0, t1);
-      ok = stream_inline<T, COLLECT, CBMAX>(a, sp, c, v, g, tab, cb0, ncb, seq0, n_pre, is_root, out_smem);
-    } else if (ok) {
-      if (c.pow2) {
-        const SliceGeo g = slice_geo<true>(c, t0, t1);
-        if (!COLLECT) {
-          rows_factor<T, true, CBMAX>(sp, c, v, g, ncb, is_root);
-          __syncthreads();
-        }
-        ok = rowvec ? stream<T, COLLECT, true, true, CBMAX>(a, sp, c, v, g, tab, cb0, ncb, seq0, n_pre)
-                    : stream<T, COLLECT, true, false, CBMAX>(a, sp, c, v, g, tab, cb0, ncb, seq0, n_pre);
-        if (ok && COLLECT) ok = await_inputs();
-        if (ok) rows_out<T, COLLECT, true, CBMAX>(sp, c, v, g, ncb, out_smem);
-      } else {
-        const SliceGeo g = slice_geo<false>(c, t0, t1);
-        if (!COLLECT) {
-          rows_factor<T, false, CBMAX>(sp, c, v, g, ncb, is_root);
-          __syncthreads();
-        }
-        ok = rowvec ? stream<T, COLLECT, false, true, CBMAX>(a, sp, c, v, g, tab, cb0, ncb, seq0, n_pre)
-                    : stream<T, COLLECT, false, false, CBMAX>(a, sp, c, v, g, tab, cb0, ncb, seq0, n_pre);
-        if (ok && COLLECT) ok = await_inputs();
-        if (ok) rows_out<T, COLLECT, false, CBMAX>(sp, c, v, g, ncb, out_smem);
-      }
-    } else if (tid == 0) {
-      // the prefetched chunks of this slice must land before the CTA leaves
-      for (int ci = 0; ci < n_pre; ++ci) {
-        const uint32_t q = seq0 + (uint32_t)ci;
-        mbar_wait(s_bar + q % S, (q / S) & 1u, nullptr);
-      }
-    }
-    if (!ok) return false;  // a wait gave up: the error word is set, results are invalid
-  }
-
-  // ---- flush the CTA's partial sums
-  __syncthreads();
-  if (COLLECT) {
-    const uint32_t seg_lo = c.pow2 ? seg_of<true>(c, row_of<true>(c, t0)) : seg_of<false>(c, row_of<false>(c, t0));
-    const uint32_t seg_hi =
-        c.pow2 ? seg_of<true>(c, row_of<true>(c, t1 - 1)) : seg_of<false>(c, row_of<false>(c, t1 - 1));
-    const int nwin = (int)(seg_hi - seg_lo + 1);
-    for (int idx = tid; idx < ncb * nwin; idx += kBlock) {
-      const int cl = idx / nwin, j = idx - cl * nwin;
-      const T val = s_win[(int64_t)cl * sp.win + j];
-      if (val != T(0)) atomicAdd(case_acc(cl) + c.sep_off + seg_lo + j, val);
-    }
-  } else {
-    for (int cl = 0; cl < ncb; ++cl) {
-      T* acc = case_acc(cl);
-      if (out_smem) {
-        for (int t = 0; t < nch; ++t) {
-          const DevChild ch = s_ch[t];
-          for (int j = tid; j < ch.sep_size; j += kBlock) {
-            const T val = region(cl)[c.sm_out + ch.fac_off + j];
-            if (val != T(0)) atomicAdd(acc + off_down + ch.sep_off + j, val);
-          }
-        }
-        for (int h = 0; h < c.n_home; ++h) {
-          const DevHome hm = s_hm[h];
-          for (int st = tid; st < hm.card; st += kBlock) {
-            const T val = region(cl)[c.sm_out + hm.out_off + st];
-            if (val != T(0)) atomicAdd(acc + off_marg + hm.moff + st, val);
-          }
-        }
-      }
-      if (jnt_smem && has_joint) {
-        for (int j = tid; j < c.P; j += kBlock) {
-          const T val = region(cl)[c.sm_jnt + j];
-          if (val != T(0)) atomicAdd(acc + off_joint + c.joint_off + j, val);
-        }
-      }
+  for (int pi = S.nin; pi < S.np; ++pi) {
+    const DevPort P = s.port[pi];
+    if (P.K <= 1) continue;
+    const uint32_t kb = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+    const uint32_t win32 = smem_u32(s.win);
+    for (int idx = tid; idx < ncb * P.K; idx += NT) {
+      const int cl = idx / P.K, i = idx - cl * P.K;
+      const T v = sld<T>(win32 + (uint32_t)(cl * a.win_max + P.win + i) * (uint32_t)sizeof(T));
+      if (v != T(0)) atomicAdd(a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb + i, v);
     }
   }
-
-  // ---- the last CTA of this clique (and case block) finalises its messages
-  __threadfence();
-  __syncthreads();
+  consumer_sync<NT>();
   if (tid == 0) {
-    int32_t* ctr = a.cnt + ((int64_t)(COLLECT ? 0 : 1) * a.n_cliques + cid) * a.max_cases + cbk;
-    const int ticket = atomicAdd(ctr, 1);
-    const int last = (ticket == w.ntiles - 1);
-    if (last) *ctr = 0;  // ready for the next propagation
-    *s_flag = last;
-  }
-  __syncthreads();
-  if (!*s_flag) return true;
-  __threadfence();
-
-  if (COLLECT) {
-    if (!is_root) {  // the root keeps its raw total for log Z
-      for (int cl = 0; cl < ncb; ++cl) {
-        T* u = case_acc(cl) + c.sep_off;
-        double sm = 0.0;
-        for (int j = tid; j < c.sep_size; j += kBlock) sm += (double)__ldcg(u + j);
-        const double sigma = block_sum(sm, s_red);
-        const T scale = sigma > 0.0 ? (T)((double)c.sep_size / sigma) : T(0);
-        for (int j = tid; j < c.sep_size; j += kBlock) u[j] = __ldcg(u + j) * scale;
-        if (tid == 0) {
-          a.ls[(int64_t)(cb0 + cl) * a.n_cliques + cid] =
-              sigma > 0.0 ? log(sigma) - log((double)c.sep_size) : -INFINITY;
-          if (!(sigma > 0.0)) atomicOr(&a.status[cb0 + cl], kStatusZero);
-        }
-      }
+    if (!hand_over(s, sigk, w.stage, w.cbk, a.err)) {
+      atomicExch(a.err, 1);
+      s.misc[0] = 1;
     }
-  } else {
-    // child ratios rho_g = new/old (0/0 := 0)
-    for (int cl = 0; cl < ncb; ++cl) {
-      T* acc = case_acc(cl);
-      for (int t = 0; t < nch; ++t) {
-        const DevChild ch = s_ch[t];
-        const T* d = acc + off_down + ch.sep_off;
-        const T* mu = acc + ch.sep_off;
-        double sm = 0.0;
-        for (int j = tid; j < ch.sep_size; j += kBlock) sm += (double)__ldcg(d + j);
-        const double del = block_sum(sm, s_red);
-        const T r0 = del > 0.0 ? (T)((double)ch.sep_size / del) : T(0);
-        for (int j = tid; j < ch.sep_size; j += kBlock) {
-          const T m = __ldcg(mu + j), dv = __ldcg(d + j);
-          acc[off_rho + ch.sep_off + j] = m > T(0) ? dv * r0 / m : T(0);
-        }
-      }
-    }
+    if (tr != nullptr) tr[5] = global_ns();
   }
-  // publish: the messages of this clique (this case block) are final
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) st_release(flag_of(COLLECT ? 0 : 1, cid), 1);
   return true;
 }
 
-// The whole propagation of a case range in one launch: CTAs take work items
-// (clique slices x case blocks, collect items deepest level first, then
-// distribute items root first) from a queue.  An item's dependencies are
-// always earlier in the queue and held by running CTAs, so the schedule
-// always progresses; every wait is bounded.
-template <typename T, int CBMAX>
-__global__ void __launch_bounds__(kBlock, CBMAX == 1 ? 2 : 1) k_propagate(LevelArgs<T> a, SmemPlan sp) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const SmemLayout lay(sp);
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + lay.off_bar);
-  int* s_item = reinterpret_cast<int*>(reinterpret_cast<double*>(smem + lay.off_red) + 76);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < sp.stages; ++i) {
-      mbar_init(s_bar + i, 1);                   // full: bulk-copy bytes landed
-      mbar_init(s_bar + sp.stages + i, kWarps);  // empty: every consumer warp done
+template <typename T, int CB>
+__device__ __forceinline__ void consumer(const PropArgs<T>& a, const Smem& s) {
+  constexpr int NT = consumers_for(CB);
+  uint32_t q = 0;     // chunks consumed (the producer's numbering)
+  uint32_t sigk = 0;  // items handed to the signalling lane (thread 0)
+  for (uint32_t slot = 0;; ++slot) {
+    const uint32_t fs = slot % kFifo;
+    bool ok = mbar_wait(s.ifull + fs, (slot / kFifo) & 1u, a.err, s.misc);
+    ok = consumer_all<NT>(ok);
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        s.misc[0] = 1;
+      }
+      break;
     }
+    const DevItem w = s.fifo[fs];
+    consumer_sync<NT>();
+    if (threadIdx.x == 0) mbar_arrive(s.iempty + fs);
+    if (w.stage < 0) {
+      if (threadIdx.x == 0) hand_over(s, sigk, -1, 0, a.err);
+      break;
+    }
+    if (!process_item<T, CB>(a, s, w, q, sigk)) break;
+  }
+}
+
+template <typename T, int CB>
+__global__ void __launch_bounds__(consumers_for(CB) + 32, ctas_per_sm_for(CB)) k_propagate(const PropArgs<T> a) {
+  constexpr int NT = consumers_for(CB);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SmemLayout L(CB, a.ring, a.chunk, a.max_k, a.max_ports, a.max_fields, a.win_max, (int)sizeof(T));
+  const Smem s = carve(smem, L, a.ring);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.ring; ++i) {
+      mbar_init(s.full + i, 1);
+      mbar_init(s.empty + i, (NT / 32));
+    }
+    for (int i = 0; i < kFifo; ++i) {
+      mbar_init(s.ifull + i, 1);
+      mbar_init(s.iempty + i, 1);
+    }
+    for (int i = 0; i < kSig; ++i) {
+      mbar_init(s.sfull + i, 1);
+      mbar_init(s.sempty + i, 1);
+    }
+    s.misc[0] = 0;
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t seq = 0;  // bulk-copy chunks issued by this CTA so far
-  for (;;) {
-    if (threadIdx.x == 0) *s_item = (ld_acquire(a.err) != 0) ? a.n_items : atomicAdd(a.queue, 1);
-    __syncthreads();
-    const int it = *s_item;
-    __syncthreads();
-    if (it >= a.n_items) break;
-    const DevWork w = a.work[it];
-    const bool ok = w.collect ? process_item<T, true, CBMAX>(a, sp, w, w.cbk, smem, seq)
-                              : process_item<T, false, CBMAX>(a, sp, w, w.cbk, smem, seq);
-    if (!ok) break;
-    __syncthreads();
+  if (threadIdx.x >= NT) {
+    if (threadIdx.x == NT) producer<T>(a, s);
+    else if (threadIdx.x == NT + 1) signaller(a.err, a.done, a.n_cb, s);
+    __syncwarp();
+  } else {
+    consumer<T, CB>(a, s);
   }
+  __syncthreads();
 }
 
-// Normalised marginals (a warp per variable, binned from the variable's
-// source table) and log Z(e) (the last CTA along x), per case (y).
+// Normalised marginals (a warp per variable, binned from its source table)
+// and log Z(e) (the last CTA along x), per case (y).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_finalize(FinalArgs<T> a) {
-  __shared__ double red[kWarps];
+__global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
   const int cs = a.case0 + (int)blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T* acc = a.acc + (int64_t)cs * a.acc_stride;
+  const T* row = a.msg + (int64_t)cs * a.msg_stride;
+  const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
   if (blockIdx.x == gridDim.x - 1) {
-    double s = 0.0;
-    for (int c = 1 + tid; c < a.n_cliques; c += kThreads) s += a.ls[(int64_t)cs * a.n_cliques + c];
-    s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      int st = a.status[cs];
-      double tot = 0.0;
-      for (int i = 0; i < kWarps; ++i) tot += red[i];
-      const double R = (double)acc[0];  // the root's raw total (root slot at offset 0)
-      if (!(R > 0.0) || (st & kStatusZero)) {
-        st |= kStatusZero;
+    if (warp != 0) return;
+    double acc = 0.0;
+    bool zero = false;
+    for (int c = 1 + lane; c < a.n_cliques; c += 32) {
+      const double sg = sums[c];
+      if (!(sg > 0.0)) zero = true;
+      else acc += log(sg) - log((double)a.sep_size[c]);
+    }
+    acc = warp_sum(acc);
+    zero = __any_sync(kFull, zero);
+    if (lane == 0) {
+      const double R = sums[a.n_cliques];  // the root's distribute total
+      if (zero || !(R > 0.0)) {
+        atomicOr(&a.status[cs], kStatusZero);
         a.logz_out[cs] = -INFINITY;
       } else {
-        a.logz_out[cs] = tot + log(R);
+        a.logz_out[cs] = acc + log(R);
       }
-      a.status[cs] = st;
     }
     return;
   }
-  const int v = (int)blockIdx.x * kWarps + warp;
+  const int v = (int)blockIdx.x * 8 + warp;
   if (v >= a.n_vars) return;
   const VarSrc src = a.vs[v];
   double* out = a.marg_out + (int64_t)cs * a.marg_total + src.moff;
-  const T* tab = acc + src.off;
-  if (src.kind == 0) {
-    double z = 0.0;
-    for (int x = lane; x < src.card; x += 32) z += (double)tab[x];
-    z = warp_sum(z);
-    for (int x = lane; x < src.card; x += 32) out[x] = z > 0.0 ? (double)tab[x] / z : NAN;
-    return;
-  }
+  const T* tab = row + src.off;
   double z = 0.0;
   for (int j = lane; j < src.size; j += 32) z += (double)tab[j];
   z = warp_sum(z);
-  const int per = src.size / src.card;  // entries of one state
+  const int per = src.size / src.card;  // entries holding one state
   for (int x = 0; x < src.card; ++x) {
     double b = 0.0;
-    for (int q = lane; q < per; q += 32) {
-      const int hi = q / src.st, lo = q - hi * src.st;
-      b += (double)tab[(hi * src.card + x) * src.st + lo];
+    for (int qq = lane; qq < per; qq += 32) {
+      const int hi = qq / src.st, lo = qq - hi * src.st;
+      b += (double)tab[(int64_t)(hi * src.card + x) * src.st + lo];
     }
     b = warp_sum(b);
     if (lane == 0) out[x] = z > 0.0 ? b / z : NAN;
@@ -1127,15 +1102,15 @@ __global__ void __launch_bounds__(kThreads) k_finalize(FinalArgs<T> a) {
 
 template <typename T>
 __global__ void k_clique_sum(const T* p, int n, double* out) {
-  __shared__ double red[kWarps];
+  __shared__ double red[8];
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += kThreads) s += (double)p[i];
+  for (int i = threadIdx.x; i < n; i += 256) s += (double)p[i];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int i = 0; i < kWarps; ++i) t += red[i];
+    for (int i = 0; i < 8; ++i) t += red[i];
     *out = t;
   }
 }
@@ -1154,85 +1129,62 @@ __global__ void k_clique_gather(const T* p, CliqueOut co, const double* sum, dou
   }
 }
 
-// Every instance asks for the same shared-memory carveout, so SMs never
-// re-partition L1/shared memory between consecutive launches.
-template <typename T>
-void attr_all(int bytes) {
-  cudaFuncSetAttribute(k_propagate<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_propagate<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_propagate<T, 1>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(k_propagate<T, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       cudaSharedmemCarveoutMaxShared);
-}
-
-}  // namespace
-
-int32_t smem_budget(int device) {
-  int v = 0;
-  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 48 * 1024;
-  return v;
-}
-
-// Kernel attributes (maximum dynamic shared memory, carveout) are set once per
-// process, before the first occupancy query or launch.
-template <typename T>
-void ensure_attrs() {
+template <typename T, int CB>
+void set_attrs_once() {
   static bool done = false;
   if (!done) {
     int dev = 0;
     cudaGetDevice(&dev);
-    attr_all<T>(smem_budget(dev));
+    cudaFuncSetAttribute(k_propagate<T, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_budget(dev, 1));
+    cudaFuncSetAttribute(k_propagate<T, CB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     done = true;
   }
 }
 
-template <typename T>
-cudaError_t launch_propagate(const LevelArgs<T>& a, const SmemPlan& sp, int grid, cudaStream_t s) {
-  ensure_attrs<T>();
-  const int bytes = SmemLayout(sp).bytes;
-  if (sp.cb <= 1) {
-    k_propagate<T, 1><<<grid, kBlock, bytes, s>>>(a, sp);
-  } else {
-    k_propagate<T, 8><<<grid, kBlock, bytes, s>>>(a, sp);
-  }
-  return cudaGetLastError();
+}  // namespace
+
+int32_t smem_budget(int device, int ctas_per_sm) {
+  int blk = 0, sm = 0, rsv = 0;
+  if (cudaDeviceGetAttribute(&blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 48 * 1024;
+  if (ctas_per_sm <= 1) return blk;
+  if (cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) return 48 * 1024;
+  cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, device);
+  return std::min(blk, sm / ctas_per_sm - rsv);
 }
 
-int32_t propagate_occupancy(int elem, int cb, int bytes) {
-  int n = 0;
-  cudaError_t e;
-  if (elem == 8) ensure_attrs<double>();
-  else ensure_attrs<float>();
-  if (elem == 8) {
-    e = cb <= 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<double, 1>, kBlock, bytes)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<double, 8>, kBlock, bytes);
+template <typename T>
+cudaError_t launch_propagate(const PropArgs<T>& a, int cb, int grid, int smem, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  if (cb <= 1) {
+    set_attrs_once<T, 1>();
+    k_propagate<T, 1><<<grid, consumers_for(1) + 32, smem, s>>>(a);
   } else {
-    e = cb <= 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<float, 1>, kBlock, bytes)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<float, 8>, kBlock, bytes);
+    set_attrs_once<T, 8>();
+    k_propagate<T, 8><<<grid, consumers_for(8) + 32, smem, s>>>(a);
   }
-  return e == cudaSuccess ? n : 0;
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_finalize(const FinalArgs<T>& a, cudaStream_t s) {
   if (a.n_cases <= 0) return cudaSuccess;
-  dim3 grid((a.n_vars + kWarps - 1) / kWarps + 1, a.n_cases);
-  k_finalize<T><<<grid, kThreads, 0, s>>>(a);
+  dim3 grid((a.n_vars + 7) / 8 + 1, a.n_cases);
+  k_finalize<T><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_get_clique(const T* calib_clique, const CliqueOut& co, double* out_dev, double* sum_dev,
                               cudaStream_t s) {
-  k_clique_sum<T><<<1, kThreads, 0, s>>>(calib_clique, co.n, sum_dev);
-  const int blocks = (int)std::min<int64_t>(1024, (co.n + kThreads - 1) / kThreads);
-  k_clique_gather<T><<<blocks, kThreads, 0, s>>>(calib_clique, co, sum_dev, out_dev);
+  k_clique_sum<T><<<1, 256, 0, s>>>(calib_clique, co.n, sum_dev);
+  const int blocks = (int)std::min<int64_t>(1024, (co.n + 255) / 256);
+  k_clique_gather<T><<<blocks, 256, 0, s>>>(calib_clique, co, sum_dev, out_dev);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_propagate<float>(const LevelArgs<float>&, const SmemPlan&, int, cudaStream_t);
-template cudaError_t launch_propagate<double>(const LevelArgs<double>&, const SmemPlan&, int, cudaStream_t);
+template cudaError_t launch_propagate<float>(const PropArgs<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_propagate<double>(const PropArgs<double>&, int, int, int, cudaStream_t);
 template cudaError_t launch_finalize<float>(const FinalArgs<float>&, cudaStream_t);
 template cudaError_t launch_finalize<double>(const FinalArgs<double>&, cudaStream_t);
 template cudaError_t launch_get_clique<float>(const float*, const CliqueOut&, double*, double*, cudaStream_t);

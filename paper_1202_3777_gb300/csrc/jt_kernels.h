@@ -1,4 +1,5 @@
-// Launch interface of the message kernels (used by the C ABI layer).
+// Launch interface of the propagation kernels (used by the planner and the
+// C ABI layer).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,72 +8,52 @@
 
 namespace jt {
 
-// Per-level shared-memory plan, computed on the host and used identically by
-// the kernel to carve its dynamic shared memory.
-struct SmemPlan {
-  int32_t cb;                    // evidence cases handled by one CTA
-  int32_t n_child, n_field;      // maxima over the level's cliques
-  int32_t n_home, k;
-  int32_t tabs;                  // per case: entries of the table region (per-clique residency,
-                                 // see DevClique.sm_*)
-  int32_t win;                   // per case: collect window of parent-separator entries
-  int32_t elem;                  // sizeof(T)
-  int32_t stages;                // bulk-copy ring: number of chunk buffers
-  int32_t chunk;                 // entries per chunk (= threads x vector width)
-  int32_t rowmax;                // per case: rows of one slice (row sums, row factors)
-  int32_t pad;
-};
+// Shape of a propagation CTA for a case-block size: consumer threads (plus
+// one producer warp) and resident CTAs per SM.
+__host__ __device__ constexpr int consumers_for(int cb) { return cb > 0 ? 512 : 512; }
+__host__ __device__ constexpr int ctas_per_sm_for(int cb) { return cb > 0 ? 1 : 1; }
+constexpr int kChunkBytes = 16384;              // bytes per bulk-copy stage
+constexpr int kFifo = 1;                        // work items handed to the consumers ahead of time
+constexpr int kSig = 2;                         // finished items queued for the signalling lane
+constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
+constexpr int kMaxIter = 64;                    // consumer iterations of one fast-path block
 
+// Dynamic shared memory of a propagation CTA, carved identically by the
+// planner (host) and the kernel (device).
 struct SmemLayout {
-  int32_t off_ch, off_fld, off_hm, off_pos, off_obs, off_nobs;
-  int32_t off_facp, off_outp, off_rhop, off_houtp, off_jntp;
-  int32_t off_tabs, off_win, off_red, off_bar, off_rsum, off_gsm, off_buf;
-  int32_t bytes;
+  int32_t bar, fifo, sig, stage, ports, fields, pos, obs, nobs, pval, bf, red, misc, kiter, live, kt, win, ring, bytes;
 
   __host__ __device__ static int32_t a16(int32_t x) { return (x + 15) & ~15; }
 
-  __host__ __device__ explicit SmemLayout(const SmemPlan& s) {
+  __host__ __device__ SmemLayout(int cb, int ring_n, int chunk, int max_k, int max_ports, int max_fields,
+                                 int win_max, int elem) {
     int32_t o = 0;
-    off_ch = o;    o = a16(o + s.n_child * (int32_t)sizeof(DevChild));
-    off_fld = o;   o = a16(o + s.n_field * (int32_t)sizeof(DevField));
-    off_hm = o;    o = a16(o + s.n_home * (int32_t)sizeof(DevHome));
-    off_pos = o;   o = a16(o + s.k * (int32_t)sizeof(DevPos));
-    off_obs = o;   o = a16(o + 2 * s.cb * s.k * 8);      // row and column observations
-    off_nobs = o;  o = a16(o + 2 * s.cb * 4);
-    off_facp = o;  o = a16(o + s.cb * s.n_child * 8);
-    off_outp = o;  o = a16(o + s.cb * s.n_child * 8);
-    off_rhop = o;  o = a16(o + s.cb * 8);
-    off_houtp = o; o = a16(o + s.cb * 8);
-    off_jntp = o;  o = a16(o + s.cb * 8);
-    off_tabs = o;  o = a16(o + s.cb * s.tabs * s.elem);
-    off_win = o;   o = a16(o + s.cb * s.win * s.elem);
-    off_red = o;   o = a16(o + 80 * 8);
-    off_bar = o;   o = a16(o + 2 * s.stages * 8);   // full and empty barriers
-    off_rsum = o;  o = a16(o + s.cb * s.rowmax * s.elem);
-    off_gsm = o;   o = a16(o + s.cb * s.rowmax * s.elem);
-    o = (o + 127) & ~127;
-    off_buf = o;   o += s.stages * s.chunk * s.elem;
+    bar = o;    o += (2 * ring_n + 2 * kFifo + 2 * kSig) * 8;  // full/empty: per stage, item slot, signal slot
+    fifo = a16(o);   o = fifo + kFifo * (int32_t)sizeof(DevItem);
+    sig = a16(o);    o = sig + kSig * 8;                       // finished (stage, case block) pairs
+    stage = a16(o);  o = stage + (int32_t)sizeof(DevStage);
+    ports = a16(o);  o = ports + max_ports * (int32_t)sizeof(DevPort);
+    fields = a16(o); o = fields + max_fields * (int32_t)sizeof(DevField);
+    pos = a16(o);    o = pos + max_k * (int32_t)sizeof(DevPos);
+    obs = a16(o);    o = obs + cb * max_k * 16;             // in-block observations per case
+    nobs = a16(o);   o = nobs + cb * 4;
+    pval = a16(o);   o = pval + cb * max_ports * 8;         // per (case, port) scale or block value
+    bf = a16(o);     o = bf + cb * 8;                       // block factor per case
+    red = a16(o);    o = red + cb * (consumers_for(cb) / 32) * 8;  // block-total partials
+    misc = a16(o);   o = misc + 16 * 4;
+    kiter = a16(o);  o = kiter + kMaxFastPorts * kMaxIter * 4;  // per-iteration key part of every live port
+    live = a16(o);   o = live + kMaxFastPorts * 32;             // live ports: index, mode, dvec
+    kt = a16(o);     o = kt + kMaxFastPorts * consumers_for(cb) * 4;  // per-thread key part of every live port
+    win = (o + 127) & ~127;  o = win + cb * win_max * elem;
+    ring = (o + 127) & ~127; o = ring + ring_n * chunk * elem;
     bytes = o;
   }
 };
 
-// Cliques whose rows are short enough to be processed inline while streaming
-// (the kernel's stream_inline): power-of-two cardinalities, and either no
-// private variables with a vector-aligned fastest digit, or vector-aligned
-// rows of at most 32 vectors.
-__host__ __device__ inline bool inline_rows(const DevClique& c, int vec) {
-  if (!c.pow2) return false;
-  if (c.P == 1) return c.card_last % vec == 0;
-  return c.P % vec == 0 && c.P <= 32 * vec;
-}
-
-// Enqueue a whole propagation (collect and distribute of every clique for
-// the case range of `a`) as one persistent launch of `grid` CTAs on `s`.
+// Enqueue one persistent propagation launch of `grid` CTAs (collect and
+// distribute of every clique for the case range of `a`).
 template <typename T>
-cudaError_t launch_propagate(const LevelArgs<T>& a, const SmemPlan& sp, int grid, cudaStream_t s);
-
-// Resident CTAs per SM of the propagation kernel for a shared-memory plan.
-int32_t propagate_occupancy(int elem, int cb, int bytes);
+cudaError_t launch_propagate(const PropArgs<T>& a, int cb, int grid, int smem, cudaStream_t s);
 
 // Enqueue the finalisation (log Z and normalised marginals) for a case range.
 template <typename T>
@@ -88,10 +69,8 @@ template <typename T>
 cudaError_t launch_get_clique(const T* calib_clique, const CliqueOut& co, double* out_dev,
                               double* sum_dev, cudaStream_t s);
 
-// Maximum dynamic shared memory per CTA the kernels may use on this device.
-int32_t smem_budget(int device);
-
-// Consumer threads per CTA of the propagation kernel (plus one producer warp).
-constexpr int kLevelThreads = 512;
+// Maximum dynamic shared memory per CTA the kernels may use on this device
+// with `ctas_per_sm` resident CTAs per SM.
+int32_t smem_budget(int device, int ctas_per_sm = 1);
 
 }  // namespace jt

@@ -12,6 +12,7 @@
 #include <thread>
 
 #include "jt_internal.h"
+#include "jt_kernels.h"
 
 namespace jt {
 
@@ -21,9 +22,6 @@ uint32_t magic_for(uint32_t d) {
   if (d <= 1) return 0;
   return (uint32_t)(((1ull << 32) + d - 1) / d);
 }
-
-// Columns kept per row (product of the trailing private cardinalities).
-constexpr int64_t kMaxCols = 4096;
 
 static bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 static int32_t ilog2(int64_t x) {
@@ -155,9 +153,65 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
   }
   p->msg_total = (int32_t)off;
 
-  // marginal sources: a variable in some separator is read from the smallest
-  // such separator after distribution; any other variable lives in exactly
-  // one clique and is accumulated there ("home" variables).
+
+  // permuted order, top-down (a parent's order is fixed before its children's
+  // separators are laid out): the parent separator in the parent's order,
+  // then the variables of child separators (most child separators first),
+  // then the private variables
+  p->pvars.assign(nc, {});
+  p->n_private.assign(nc, 0);
+  p->pow2.assign(nc, 1);
+  std::vector<int32_t> share(nv, 0);
+  for (int dd = 0; dd <= p->max_depth; ++dd)
+    for (int c : p->levels[dd]) {
+      std::vector<int32_t>& pv = p->pvars[c];
+      if (c != 0) {
+        for (int v : p->sep[c]) mark[v] = 1;
+        std::vector<int32_t> s;
+        for (int v : p->pvars[p->parent[c]])
+          if (mark[v]) s.push_back(v);
+        for (int v : p->sep[c]) mark[v] = 0;
+        p->sep[c] = s;
+      }
+      for (int v : p->sep[c]) mark[v] = 1;
+      for (int g : p->children[c])
+        for (int v : p->sep[g]) share[v]++;
+      std::vector<int32_t> rest;
+      for (int v : p->vars[c])
+        if (!mark[v]) rest.push_back(v);
+      std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) {
+        if (share[a] != share[b]) return share[a] > share[b];
+        return a < b;
+      });
+      for (int v : rest) p->n_private[c] += share[v] == 0;
+      pv = p->sep[c];
+      pv.insert(pv.end(), rest.begin(), rest.end());
+      for (int v : p->vars[c]) {
+        mark[v] = 0;
+        share[v] = 0;
+        if (!is_pow2(p->card[v])) p->pow2[c] = 0;
+      }
+    }
+
+  // private joints
+  p->joint_off.assign(nc, -1);
+  p->joint_size.assign(nc, 0);
+  int64_t jo = 0;
+  for (int c = 0; c < nc; ++c) {
+    if (p->n_private[c] == 0) continue;
+    int64_t q = 1;
+    const auto& pv = p->pvars[c];
+    for (size_t i = pv.size() - p->n_private[c]; i < pv.size(); ++i) q *= p->card[pv[i]];
+    p->joint_off[c] = (int32_t)jo;
+    p->joint_size[c] = (int32_t)q;
+    jo += q;
+    if (jo > (1ll << 30)) FAIL(JT_ERR_UNSUPPORTED, "private-variable joints too large");
+  }
+  p->joint_total = (int32_t)jo;
+  p->msg_stride = (2ll * p->msg_total + p->joint_total + 31) / 32 * 32;
+
+  // marginals: a variable in some separator is binned from the smallest such
+  // separator's distribute message; a private variable from its clique's joint
   p->moff.assign(nv, 0);
   int64_t mo = 0;
   for (int v = 0; v < nv; ++v) {
@@ -165,52 +219,38 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     mo += p->card[v];
   }
   p->marg_total = (int32_t)mo;
-  p->home.assign(nv, -1);
-  p->src_edge.assign(nv, -1);
-  for (int c = 0; c < nc; ++c)
-    for (int v : p->vars[c])
-      if (holders[v] == 1) p->home[v] = c;
+  p->vsrc.assign(nv, VarSrc{});
+  std::vector<int32_t> src_edge(nv, -1);
   for (int c = 1; c < nc; ++c)
     for (int v : p->sep[c]) {
-      int e = p->src_edge[v];
-      if (e < 0 || p->sep_size[c] < p->sep_size[e]) p->src_edge[v] = c;
+      const int e = src_edge[v];
+      if (e < 0 || p->sep_size[c] < p->sep_size[e]) src_edge[v] = c;
     }
-
-  // permuted order: parent separator (ascending), variables of child
-  // separators (ascending), then the private variables (ascending) -- with a
-  // private variable whose cardinality is a multiple of 4 moved last when one
-  // exists, so a 4-wide vector of entries stays inside one row.
-  p->pvars.assign(nc, {});
-  std::vector<int32_t> n_private(nc, 0);
+  for (int v = 0; v < nv; ++v) {
+    VarSrc& q = p->vsrc[v];
+    q.card = p->card[v];
+    q.moff = p->moff[v];
+    const int e = src_edge[v];
+    if (e >= 0) {
+      q.off = p->msg_total + p->sep_off[e];
+      q.size = p->sep_size[e];
+      int64_t t = 1;
+      for (int i = (int)p->sep[e].size() - 1; i >= 0; --i) {
+        if (p->sep[e][i] == v) q.st = (int32_t)t;
+        t *= p->card[p->sep[e][i]];
+      }
+    }
+  }
   for (int c = 0; c < nc; ++c) {
-    std::vector<int32_t> a = p->sep[c], b, r;
-    for (int v : a) mark[v] = 1;
-    for (int g : p->children[c])
-      for (int v : p->sep[g])
-        if (!mark[v]) {
-          mark[v] = 2;
-          b.push_back(v);
-        }
-    for (int v : p->vars[c])
-      if (!mark[v]) r.push_back(v);
-    for (int v : p->vars[c]) mark[v] = 0;
-    std::sort(b.begin(), b.end());
-    std::sort(r.begin(), r.end());
-    std::vector<int32_t>& last = r.empty() ? b : r;
-    if (!last.empty() && p->card[last.back()] % 4 != 0) {
-      for (size_t i = 0; i < last.size(); ++i)
-        if (p->card[last[i]] % 4 == 0) {
-          int32_t v = last[i];
-          last.erase(last.begin() + i);
-          last.push_back(v);
-          break;
-        }
+    const auto& pv = p->pvars[c];
+    int64_t t = 1;
+    for (int i = (int)pv.size() - 1; i >= (int)pv.size() - p->n_private[c]; --i) {
+      VarSrc& q = p->vsrc[pv[i]];
+      q.off = 2 * p->msg_total + p->joint_off[c];
+      q.size = p->joint_size[c];
+      q.st = (int32_t)t;
+      t *= p->card[pv[i]];
     }
-    n_private[c] = (int32_t)r.size();
-    std::vector<int32_t>& pv = p->pvars[c];
-    pv.insert(pv.end(), a.begin(), a.end());
-    pv.insert(pv.end(), b.begin(), b.end());
-    pv.insert(pv.end(), r.begin(), r.end());
   }
 
   // padded offsets (multiples of 32 elements: 128 B for FP32, 256 B for FP64)
@@ -221,200 +261,344 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     bo += (p->n_entries[c] + 31) / 32 * 32;
   }
   p->base_len = bo;
+  return JT_OK;
+}
 
-  // device descriptors
-  p->dcl.resize(nc);
-  p->dpos.clear();
-  p->dch.clear();
-  p->dhm.clear();
-  p->dsrc.clear();
-  p->djh.clear();
-  p->dfld.clear();
-  p->fac_collect.assign(nc, 0);
-  p->out_dist.assign(nc, 0);
-  p->joint_total = 0;
-  std::vector<int64_t> st(JT_MAX_CLIQUE_VARS);
-  std::vector<int32_t> posof(nv, -1);
+// ---------------------------------------------------------------------------
+// Schedule of one propagation shape.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct PortSpec {
+  int32_t kind, tab, size, other, other2;
+  std::vector<char> in;   // positions of the clique inside the port's variable set
+};
+
+// Fields of a port: maximal runs of consecutive positions inside its
+// variable set (the table keeps the clique's order, first most significant).
+void port_fields(const std::vector<int64_t>& st, const std::vector<int32_t>& card, const std::vector<char>& in,
+                 bool pow2, std::vector<DevField>* out) {
+  const int k = (int)in.size();
+  int64_t w = 1;
+  int i = k - 1;
+  while (i >= 0) {
+    if (!in[i]) {
+      --i;
+      continue;
+    }
+    int j = i;
+    int64_t len = card[i];
+    while (j - 1 >= 0 && in[j - 1]) {
+      --j;
+      len *= card[j];
+    }
+    DevField f{};
+    f.st = (int32_t)st[i];
+    f.len = (int32_t)len;
+    f.st_magic = magic_for((uint32_t)st[i]);
+    f.len_magic = magic_for((uint32_t)len);
+    f.w = (int32_t)w;
+    f.sh = pow2 ? ilog2(st[i]) : 0;
+    f.lb = pow2 ? ilog2(len) : 0;
+    out->push_back(f);
+    w *= len;
+    i = j - 1;
+  }
+}
+
+int64_t eval_key(const std::vector<DevField>& f, int64_t x) {
+  int64_t key = 0;
+  for (const DevField& q : f) key += ((x / q.st) % q.len) * q.w;
+  return key;
+}
+
+}  // namespace
+
+jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm, int smem_bytes, Schedule* s,
+                         std::string* err) {
+  const int VEC = 16 / elem;
+  const int lv = VEC == 4 ? 2 : 1;
+  const int nc = p.n_cliques;
+  s->cb = cb;
+  s->n_cb = std::max(1, (n_cases + cb - 1) / cb);
+  s->chunk = kChunkBytes / elem;
+  s->ring = cb == 1 ? 8 : 6;
+  s->stages.assign(2 * nc, DevStage{});
+  s->ports.clear();
+  s->fields.clear();
+  s->pos.clear();
+  s->deps.clear();
+  s->items.clear();
+  s->streamed_entries = 0;
+
+  // positions of every clique
+  std::vector<int32_t> pos0(nc);
+  std::vector<std::vector<int64_t>> stv(nc);
+  std::vector<std::vector<int32_t>> cdv(nc);
+  s->max_k = 1;
   for (int c = 0; c < nc; ++c) {
-    const auto& pv = p->pvars[c];
+    const auto& pv = p.pvars[c];
     const int k = (int)pv.size();
-    bool pow2 = true;
-    for (int v : pv) pow2 = pow2 && is_pow2(p->card[v]);
-    // column suffix: trailing private variables while the product stays <= kMaxCols
-    int kr = k;
-    int64_t P = 1;
-    while (kr > k - n_private[c] && P * p->card[pv[kr - 1]] <= kMaxCols) {
-      P *= p->card[pv[kr - 1]];
-      --kr;
-    }
-    int64_t s = 1;
+    s->max_k = std::max(s->max_k, k);
+    stv[c].assign(k, 1);
+    cdv[c].assign(k, 0);
     for (int i = k - 1; i >= 0; --i) {
-      st[i] = s;
-      s *= p->card[pv[i]];
+      cdv[c][i] = p.card[pv[i]];
+      if (i + 1 < k) stv[c][i] = stv[c][i + 1] * cdv[c][i + 1];
     }
-    DevClique& dc = p->dcl[c];
-    std::memset(&dc, 0, sizeof(dc));
-    dc.base_off = p->base_off[c];
-    dc.n = (int32_t)p->n_entries[c];
-    dc.k = k;
-    dc.kr = kr;
-    dc.P = (int32_t)P;
-    dc.P_magic = magic_for((uint32_t)P);
-    dc.logP = pow2 ? ilog2(P) : 0;
-    dc.sep_size = p->sep_size[c];
-    dc.sep_off = p->sep_off[c];
-    const int64_t L = p->n_entries[c] / p->sep_size[c];
-    dc.LR = (int32_t)(L / P);
-    dc.LR_magic = magic_for((uint32_t)dc.LR);
-    dc.logLR = pow2 ? ilog2(dc.LR) : 0;
-    dc.pow2 = pow2 ? 1 : 0;
-    dc.depth = p->depth[c];
-    dc.card_last = p->card[pv[k - 1]];
-    dc.pos_first = (int32_t)p->dpos.size();
+    pos0[c] = (int32_t)s->pos.size();
     for (int i = 0; i < k; ++i) {
       DevPos q{};
       q.var = pv[i];
-      q.card = p->card[pv[i]];
-      q.is_col = i >= kr ? 1 : 0;
-      const int64_t sti = i >= kr ? st[i] : st[i] / P;   // column stride or row stride
-      q.st = (int32_t)sti;
-      q.st_magic = magic_for((uint32_t)sti);
+      q.card = cdv[c][i];
+      q.st = (int32_t)stv[c][i];
+      q.st_magic = magic_for((uint32_t)q.st);
       q.card_magic = magic_for((uint32_t)q.card);
-      q.sh = pow2 ? ilog2(sti) : 0;
-      q.cbits = pow2 ? ilog2(q.card) : 0;
-      p->dpos.push_back(q);
-      posof[pv[i]] = i;
+      q.sh = p.pow2[c] ? ilog2(stv[c][i]) : 0;
+      q.cb = p.pow2[c] ? ilog2(q.card) : 0;
+      s->pos.push_back(q);
     }
-    // children: digit-run fields of each child separator over the row index
-    dc.child_first = (int32_t)p->dch.size();
-    dc.n_child = (int32_t)p->children[c].size();
-    int32_t fac = 0;
-    const int32_t field0 = (int32_t)p->dfld.size();
-    for (int g : p->children[c]) {
-      const auto& sv = p->sep[g];  // ascending = table order, first most significant
-      std::vector<int64_t> ts(sv.size());
-      int64_t t = 1;
-      for (int i = (int)sv.size() - 1; i >= 0; --i) {
-        ts[i] = t;
-        t *= p->card[sv[i]];
-      }
-      std::vector<int64_t> tstride_at(k, 0);
-      std::vector<char> in(k, 0);
-      for (size_t i = 0; i < sv.size(); ++i) {
-        in[posof[sv[i]]] = 1;
-        tstride_at[posof[sv[i]]] = ts[i];
-      }
-      DevChild ch{};
-      ch.child = g;
-      ch.sep_size = p->sep_size[g];
-      ch.sep_off = p->sep_off[g];
-      ch.field_first = (int32_t)p->dfld.size();
-      ch.field_rel = ch.field_first - field0;
-      ch.fac_off = fac;
-      ch.w_last = (kr == k && in[k - 1]) ? (int32_t)tstride_at[k - 1] : 0;
-      int i = kr - 1;
-      while (i >= 0) {
-        if (!in[i]) {
-          --i;
-          continue;
-        }
-        int j = i;  // run [j, i]
-        int64_t len = p->card[pv[i]];
-        while (j - 1 >= 0 && in[j - 1] && tstride_at[j - 1] == tstride_at[j] * p->card[pv[j]]) {
-          --j;
-          len *= p->card[pv[j]];
-        }
-        DevField f{};
-        const int64_t rs = st[i] / P;
-        f.st = (int32_t)rs;
-        f.len = (int32_t)len;
-        f.st_magic = magic_for((uint32_t)rs);
-        f.len_magic = magic_for((uint32_t)len);
-        f.w = (int32_t)tstride_at[i];
-        f.sh = pow2 ? ilog2(rs) : 0;
-        f.lbits = pow2 ? ilog2(len) : 0;
-        p->dfld.push_back(f);
-        i = j - 1;
-      }
-      ch.n_field = (int32_t)p->dfld.size() - ch.field_first;
-      p->dch.push_back(ch);
-      fac += ch.sep_size;
-    }
-    dc.field_first = field0;
-    dc.n_field = (int32_t)p->dfld.size() - field0;
-    for (int v : pv) posof[v] = -1;
-    // private variables at row positions: marginal accumulated per row
-    dc.home_first = (int32_t)p->dhm.size();
-    int32_t homes = 0;
-    for (int i = 0; i < kr; ++i) {
-      int v = pv[i];
-      if (p->home[v] == c) {
-        p->dhm.push_back(DevHome{i, p->card[v], p->moff[v], fac + homes});
-        homes += p->card[v];
-      }
-    }
-    dc.n_home = (int32_t)p->dhm.size() - dc.home_first;
-    // private variables in the columns: marginal binned from the column joint
-    dc.jh_first = (int32_t)p->djh.size();
-    for (int i = kr; i < k; ++i) p->djh.push_back(DevSrc{pv[i], p->card[pv[i]], (int32_t)st[i], p->moff[pv[i]]});
-    dc.n_jh = (int32_t)p->djh.size() - dc.jh_first;
-    dc.joint_off = -1;
-    if (P > 1) {
-      dc.joint_off = p->joint_total;
-      p->joint_total += (int32_t)P;
-    }
-    // variables read from this clique's parent separator
-    dc.src_first = (int32_t)p->dsrc.size();
-    if (c > 0) {
-      const auto& sv = p->sep[c];
-      int64_t t = 1;
-      std::vector<int64_t> ts(sv.size());
-      for (int i = (int)sv.size() - 1; i >= 0; --i) {
-        ts[i] = t;
-        t *= p->card[sv[i]];
-      }
-      for (size_t i = 0; i < sv.size(); ++i)
-        if (p->src_edge[sv[i]] == c) p->dsrc.push_back(DevSrc{sv[i], p->card[sv[i]], (int32_t)ts[i], p->moff[sv[i]]});
-    }
-    dc.n_src = (int32_t)p->dsrc.size() - dc.src_first;
-    p->fac_collect[c] = fac;
-    p->out_dist[c] = fac + homes;
   }
-  // marginal sources, as offsets in the per-case array
-  // [up | down | rho | marg | joint] (see LevelArgs)
-  p->vsrc.assign(nv, VarSrc{});
-  for (int v = 0; v < nv; ++v) {
-    VarSrc& q = p->vsrc[v];
-    q.card = p->card[v];
-    q.moff = p->moff[v];
-    const int e = p->src_edge[v];
-    if (e >= 0) {           // separator-held: bin the distribute message of edge e
-      q.kind = 1;
-      q.off = (int64_t)p->msg_total + p->sep_off[e];
-      q.size = p->sep_size[e];
-      int64_t t = 1;
-      for (int i = (int)p->sep[e].size() - 1; i >= 0; --i) {
-        if (p->sep[e][i] == v) q.st = (int32_t)t;
-        t *= p->card[p->sep[e][i]];
+
+  // entries per (pass, depth), for the block-size target
+  std::vector<std::vector<int64_t>> level_n(2, std::vector<int64_t>(p.max_depth + 1, 0));
+  for (int c = 0; c < nc; ++c) {
+    if (c != 0) level_n[0][p.depth[c]] += p.n_entries[c];
+    level_n[1][p.depth[c]] += p.n_entries[c];
+  }
+
+  // ports of every stage
+  std::vector<std::vector<PortSpec>> specs(2 * nc);
+  s->max_ports = 1;
+  s->max_fields = 1;
+  for (int c = 0; c < nc; ++c) {
+    const auto& pv = p.pvars[c];
+    const int k = (int)pv.size();
+    auto in_of = [&](const std::vector<int32_t>& vs) {
+      std::vector<char> in(k, 0);
+      for (int v : vs)
+        for (int i = 0; i < k; ++i)
+          if (pv[i] == v) in[i] = 1;
+      return in;
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 0 && c == 0) continue;  // the root's collect total comes from its distribute pass
+      auto& sp = specs[pass * nc + c];
+      for (int g : p.children[c]) sp.push_back({kPortMu, p.sep_off[g], p.sep_size[g], g, -1, in_of(p.sep[g])});
+      if (pass == 1 && c != 0) sp.push_back({kPortRho, p.sep_off[c], p.sep_size[c], c, p.parent[c], in_of(p.sep[c])});
+      if (pass == 0) sp.push_back({kPortU, p.sep_off[c], p.sep_size[c], c, -1, in_of(p.sep[c])});
+      if (pass == 1) {
+        for (int g : p.children[c])
+          sp.push_back({kPortDelta, p.msg_total + p.sep_off[g], p.sep_size[g], g, -1, in_of(p.sep[g])});
+        if (p.n_private[c] > 0) {
+          std::vector<char> in(k, 0);
+          for (int i = k - p.n_private[c]; i < k; ++i) in[i] = 1;
+          sp.push_back({kPortJoint, 2 * p.msg_total + p.joint_off[c], p.joint_size[c], c, -1, in});
+        }
       }
-      continue;
+      s->max_ports = std::max(s->max_ports, (int)sp.size());
+      int nf = 0;
+      for (const PortSpec& q : sp) {
+        std::vector<DevField> f;
+        port_fields(stv[c], cdv[c], q.in, p.pow2[c], &f);
+        nf += (int)f.size();
+      }
+      s->max_fields = std::max(s->max_fields, nf);
     }
-    const int c = p->home[v];
-    const DevClique& dc = p->dcl[c];
-    int pos = -1;
-    for (int i = 0; i < dc.k; ++i)
-      if (p->pvars[c][i] == v) pos = i;
-    if (pos >= dc.kr) {     // in the column joint of its clique
-      q.kind = 1;
-      q.off = 3ll * p->msg_total + p->marg_total + dc.joint_off;
-      q.size = dc.P;
-      q.st = p->dpos[dc.pos_first + pos].st;
-    } else {                // accumulated per row
-      q.kind = 0;
-      q.off = 3ll * p->msg_total + p->moff[v];
+  }
+
+  // shared memory: what the windows may use once the ring and descriptors fit
+  const int fixed = SmemLayout(cb, s->ring, s->chunk, s->max_k, s->max_ports, s->max_fields, 0, elem).bytes;
+  const int64_t win_budget = (int64_t)(smem_bytes - fixed - 256) / ((int64_t)cb * elem);
+  if (win_budget < (int64_t)s->max_ports * VEC) {
+    *err = "the tree's descriptors do not fit in shared memory";
+    return JT_ERR_UNSUPPORTED;
+  }
+
+  s->win_max = 1;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int c = 0; c < nc; ++c) {
+      DevStage& S = s->stages[pass * nc + c];
+      S.clique = c;
+      S.pass = pass;
+      S.sum_slot = pass * nc + c;
+      S.base_off = p.base_off[c];
+      S.n = (int32_t)p.n_entries[c];
+      S.k = (int32_t)p.pvars[c].size();
+      S.pos0 = pos0[c];
+      S.port0 = (int32_t)s->ports.size();
+      S.field0 = (int32_t)s->fields.size();
+      S.dep0 = (int32_t)s->deps.size();
+      S.bits = -1;
+      if (pass == 0 && c == 0) continue;  // empty stage
+      const auto& sp = specs[pass * nc + c];
+      const int k = S.k;
+      const bool pow2 = p.pow2[c] != 0;
+      std::vector<std::vector<DevField>> pf(sp.size());
+      for (size_t i = 0; i < sp.size(); ++i) port_fields(stv[c], cdv[c], sp[i].in, pow2, &pf[i]);
+      // window entries of every port for a block of the lowest `inb` bits (power of
+      // two) or the lowest `inb` positions (generic)
+      auto windows = [&](int inb, bool bitwise, std::vector<int64_t>* K) {
+        int64_t tot = 0;
+        K->assign(sp.size(), 1);
+        for (size_t q = 0; q < sp.size(); ++q) {
+          int64_t kk = 1;
+          for (int i = 0; i < k; ++i) {
+            if (!sp[q].in[i]) continue;
+            if (bitwise) {
+              const int sh = ilog2(stv[c][i]), cbits = ilog2(cdv[c][i]);
+              const int inside = std::max(0, std::min(cbits, inb - sh));
+              kk <<= inside;
+            } else if (i >= k - inb) {
+              kk *= cdv[c][i];
+            }
+          }
+          (*K)[q] = kk;
+          if (kk > 1) tot += (kk + 3) / 4 * 4;
+        }
+        return tot;
+      };
+      const int64_t target = std::min<int64_t>(
+          std::min<int64_t>(1 << 16, (int64_t)kMaxIter * consumers_for(cb) * VEC),
+          std::max<int64_t>(4096, level_n[pass][p.depth[c]] * s->n_cb / (2ll * ctas_per_sm_for(cb) * n_sm)));
+      std::vector<int64_t> K;
+      int64_t B = 1;
+      if (pow2 && S.n >= VEC && (int)sp.size() <= kMaxFastPorts) {
+        const int nbits = ilog2(S.n);
+        int bits = lv;
+        for (int b = nbits; b >= lv; --b) {
+          if ((1ll << b) > target && b > lv) continue;
+          if (windows(b, true, &K) <= win_budget) {
+            bits = b;
+            break;
+          }
+        }
+        windows(bits, true, &K);
+        B = 1ll << bits;
+        S.bits = bits;
+        S.kin = -1;
+      } else {
+        int kin = 0;
+        for (int q = k; q >= 0; --q) {
+          int64_t b = 1;
+          for (int i = k - q; i < k; ++i) b *= cdv[c][i];
+          if (b > target && q > 0) continue;
+          if (windows(q, false, &K) <= win_budget) {
+            kin = q;
+            break;
+          }
+        }
+        windows(kin, false, &K);
+        for (int i = k - kin; i < k; ++i) B *= cdv[c][i];
+        S.kin = kin;
+      }
+      S.B = (int32_t)B;
+      S.n_blocks = (int32_t)(S.n / B);
+      int32_t win = 0, nin = 0;
+      for (size_t q = 0; q < sp.size(); ++q) {
+        DevPort P{};
+        P.kind = sp[q].kind;
+        P.tab = sp[q].tab;
+        P.size = sp[q].size;
+        P.K = (int32_t)K[q];
+        P.win = -1;
+        if (P.K > 1) {
+          P.win = win;
+          win += (P.K + 3) / 4 * 4;  // windows start on 16-byte boundaries
+        }
+        P.other = sp[q].other;
+        P.other2 = sp[q].other2;
+        P.nf = (int32_t)pf[q].size();
+        P.f0 = (int32_t)s->fields.size() - S.field0;
+        for (const DevField& f : pf[q]) s->fields.push_back(f);
+        if (S.bits >= 0) {
+          // lane bits (entry bits lv..lv+4) the key ignores
+          uint32_t lf = 0;
+          for (int L = 0; L < 5; ++L) {
+            const int eb = lv + L;
+            bool dep = false;
+            if (eb < S.bits)
+              for (int i = 0; i < k; ++i)
+                if (sp[q].in[i] && eb >= ilog2(stv[c][i]) && eb < ilog2(stv[c][i]) + ilog2(cdv[c][i])) dep = true;
+            if (!dep) lf |= 1u << L;
+          }
+          P.lane_free = lf;
+          bool any = false, seq = true;
+          for (int j = 0; j < VEC; ++j) {
+            P.dvec[j] = (int32_t)eval_key(pf[q], j);
+            any = any || P.dvec[j] != 0;
+            seq = seq && P.dvec[j] == j;
+          }
+          P.vmode = !any ? 0 : (seq ? 1 : 2);
+          // iteration bits: entry bits from log2(consumers * VEC) up to the
+          // block's bits; chunk bits: from log2(chunk) up
+          const int ib = ilog2((int64_t)consumers_for(cb) * VEC), cbit = ilog2((int64_t)s->chunk);
+          P.iter_dep = 0;
+          for (int i = 0; i < k; ++i) {
+            if (!sp[q].in[i]) continue;
+            const int lo = ilog2(stv[c][i]), hi = lo + ilog2(cdv[c][i]);
+            if (hi > ib && lo < S.bits) P.iter_dep |= 1;
+            if (hi > cbit && lo < S.bits) P.iter_dep |= 2;
+          }
+        }
+        if (P.kind == kPortMu || P.kind == kPortRho) ++nin;
+        s->ports.push_back(P);
+      }
+      S.np = (int32_t)sp.size();
+      S.nin = nin;
+      S.nf = (int32_t)s->fields.size() - S.field0;
+      S.win_len = win;
+      s->win_max = std::max(s->win_max, win);
+      s->streamed_entries += S.n;
     }
+  // dependencies need every stage's block count, so they come after the blocks
+  for (int pass = 0; pass < 2; ++pass)
+    for (int c = 0; c < nc; ++c) {
+      DevStage& S = s->stages[pass * nc + c];
+      S.dep0 = (int32_t)s->deps.size();
+      S.ndep = 0;
+      if (pass == 0 && c == 0) continue;
+      auto dep = [&](int stage) {
+        s->deps.push_back(stage);
+        s->deps.push_back(s->stages[stage].n_blocks);
+        ++S.ndep;
+      };
+      if (pass == 0 || c == 0) {
+        for (int g : p.children[c]) dep(g);            // collect of every child
+      } else {
+        dep(nc + p.parent[c]);                          // distribute of the parent
+      }
+    }
+
+  // work items: collect deepest level first, then distribute from the root;
+  // every item's dependencies come earlier in the list
+  auto add = [&](int stage) {
+    const DevStage& S = s->stages[stage];
+    for (int b = 0; b < S.n_blocks; ++b)
+      for (int q = 0; q < s->n_cb; ++q) {
+        DevItem it{};
+        it.off = S.base_off + (int64_t)b * S.B;
+        it.n = S.B;
+        it.stage = stage;
+        it.block = b;
+        it.cbk = q;
+        s->items.push_back(it);
+      }
+  };
+  for (int dd = p.max_depth; dd >= 1; --dd)
+    for (int c : p.levels[dd]) add(c);
+  for (int dd = 0; dd <= p.max_depth; ++dd)
+    for (int c : p.levels[dd]) add(nc + c);
+  if (prop_smem_bytes(*s, elem) > smem_bytes) {
+    *err = "propagation plan exceeds shared memory";
+    return JT_ERR_UNSUPPORTED;
   }
   return JT_OK;
+}
+
+int32_t prop_smem_bytes(const Schedule& s, int elem) {
+  return SmemLayout(s.cb, s.ring, s.chunk, s.max_k, s.max_ports, s.max_fields, s.win_max, elem).bytes;
 }
 
 template <typename T>
