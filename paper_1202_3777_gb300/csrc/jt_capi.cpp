@@ -52,6 +52,7 @@ struct GraphEntry {
   const DevField* fields = nullptr;
   const DevPos* pos = nullptr;
   const int32_t* deps = nullptr;
+  const uint4* blobs = nullptr;
   const DevItem* items = nullptr;
   int32_t grid = 0, smem = 0;
 };
@@ -169,6 +170,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   a.fields = ge.fields;
   a.pos = ge.pos;
   a.deps = ge.deps;
+  a.blobs = ge.blobs;
   a.items = ge.items;
   a.n_items = (int32_t)sc.items.size();
   a.case0 = case0;
@@ -231,6 +233,7 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, cudaStream_t s, Gra
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->fields, sc.fields, "schedule upload")) != JT_OK) return st;
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->pos, sc.pos, "schedule upload")) != JT_OK) return st;
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->deps, sc.deps, "schedule upload")) != JT_OK) return st;
+  if ((st = upload_vec(t, &ge->dev_bufs, &ge->blobs, sc.blobs, "schedule upload")) != JT_OK) return st;
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->items, sc.items, "schedule upload")) != JT_OK) return st;
   ge->smem = prop_smem_bytes(sc, (int)t->elem);
   ge->grid = (int32_t)std::min<int64_t>((int64_t)sc.items.size(), (int64_t)t->n_sm * ctas_per_sm_for(cb));
@@ -550,16 +553,16 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
       uint64_t t0 = ~0ull;
       for (size_t i = 0; i < n_items; ++i)
         if (h[i * kTraceSlots + 1]) t0 = std::min(t0, h[i * kTraceSlots + 1]);
-      std::fprintf(f, "item,stage,clique,pass,block,cbk,n,sm,start_ns,deps_ns,ready_ns,streamed_ns,end_ns,"
-                      "chunk_wait_ns,handover_ns,issued_ns\n");
+      std::fprintf(f, "item,stage,clique,pass,block,cbk,n,sm,start_ns,prepared_ns,stream_ns,streamed_ns,done_ns,"
+                      "chunk_wait_ns,claimed_ns,issued_ns,published_ns\n");
       for (size_t i = 0; i < n_items; ++i) {
         const DevItem& w = ge->sched.items[i];
         const DevStage& S = ge->sched.stages[w.stage];
         const uint64_t* r = &h[i * kTraceSlots];
-        std::fprintf(f, "%zu,%d,%d,%d,%d,%d,%d,%llu,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld\n", i, w.stage, S.clique,
-                     S.pass, w.block, w.cbk, w.n, (unsigned long long)r[0], (long long)(r[1] - t0),
+        std::fprintf(f, "%zu,%d,%d,%d,%d,%d,%d,%llu,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld\n", i, w.stage,
+                     S.clique, S.pass, w.block, w.cbk, w.n, (unsigned long long)r[0], (long long)(r[1] - t0),
                      (long long)(r[2] - t0), (long long)(r[3] - t0), (long long)(r[4] - t0), (long long)(r[5] - t0),
-                     (long long)r[6], (long long)(r[7] - t0), (long long)(r[8] - t0));
+                     (long long)r[6], (long long)(r[7] - t0), (long long)(r[8] - t0), (long long)(r[9] - t0));
       }
       std::fclose(f);
     }

@@ -2,6 +2,8 @@
 // (jt_capi.cpp) and the kernels (jt_kernels.cu).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -40,10 +42,11 @@ constexpr int32_t kPortU = 2;      // out: collect message to the parent (raw su
 constexpr int32_t kPortDelta = 3;  // out: distribute message to a child (raw sums)
 constexpr int32_t kPortJoint = 4;  // out: joint of the private variables (raw sums)
 
-// Optional per-item trace (global timer, ns): SM, start, dependencies met,
-// windows ready, streamed, end, time thread 0 waited for chunks, producer
-// hand-over, producer's last chunk issued.
-constexpr int kTraceSlots = 9;
+// Optional per-item trace (global timer, ns): SM, consumers start, item
+// prepared, streaming starts, streamed, consumers done, time consumer thread 0
+// waited for chunks, producer took the item, producer issued its last chunk,
+// block published.
+constexpr int kTraceSlots = 10;
 
 constexpr int kStatusZero = 1;      // P(e) = 0
 constexpr int kStatusBadState = 2;  // an evidence state >= card
@@ -105,8 +108,11 @@ struct DevStage {
   int32_t win_len;    // per-case window entries
   int32_t ndep, dep0; // dependencies: pairs (stage, blocks) in the dependency list
   int32_t sum_slot;   // index of this stage's total in the per-case sums (pass * n_cliques + clique)
-  int32_t pad[3];
+  int32_t pad[4];
 };
+
+static_assert(sizeof(DevField) % 16 == 0 && sizeof(DevPos) % 16 == 0, "descriptor blobs are 16-byte granular");
+static_assert(sizeof(DevPort) % 16 == 0 && sizeof(DevStage) % 16 == 0, "descriptor blobs are 16-byte granular");
 
 // One work item: one block of one stage for one block of evidence cases.
 struct DevItem {
@@ -115,7 +121,8 @@ struct DevItem {
   int32_t stage;
   int32_t block;
   int32_t cbk;        // case block
-  int32_t pad[2];
+  int32_t blob;       // the stage's descriptor blob: offset in 16-byte units
+  int32_t blob_bytes; //   and size (DevStage, DevPort[np], DevField[nf], DevPos[k])
 };
 
 // Where the finalisation reads a variable's marginal: a separator's
@@ -138,6 +145,7 @@ struct PropArgs {
   const DevField* fields;
   const DevPos* pos;
   const int32_t* deps;          // pairs (stage, blocks)
+  const uint4* blobs;           // per-stage descriptor blobs
   const DevItem* items;
   int32_t n_items;
   int32_t case0, n_cases;       // case range of this propagation
@@ -221,6 +229,7 @@ struct Schedule {
   std::vector<DevField> fields;
   std::vector<DevPos> pos;
   std::vector<int32_t> deps;
+  std::vector<uint4> blobs;                 // per stage: DevStage, DevPort[np], DevField[nf], DevPos[k]
   std::vector<DevItem> items;
   int32_t ring = 0, chunk = 0;
   int32_t max_k = 1, max_ports = 1, max_fields = 1, win_max = 1;

@@ -118,6 +118,9 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -127,6 +130,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Bulk reduction shared -> global (add), tracked by the bulk async-group of
+// the issuing thread.
+__device__ __forceinline__ void bulk_reduce_add(float* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_reduce_add(double* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -244,86 +262,154 @@ __device__ __forceinline__ void add_combined(uint32_t tab, uint32_t key, T v, in
   }
 }
 
+// A work item as handed from the producer to the preparation lanes and the
+// consumers, with its preparation status.
+struct ItemInfo {
+  DevItem w;
+  int32_t idx;        // item index (for the optional trace)
+  int32_t ok;         // preparation succeeded (dependencies met in time)
+  int32_t pad[6];
+};
+static_assert(sizeof(ItemInfo) == 64, "item info slot");
+
 struct Smem {
-  uint64_t *full, *empty, *ifull, *iempty, *sfull, *sempty;
-  DevItem* fifo;
-  int2* sig;
-  DevStage* stage;
-  DevPort* port;
-  DevField* fld;
-  DevPos* pos;
-  int4* obs;
-  int* nobs;
-  double* pval;
-  double* bf;
+  // barriers: ring stages; per buffer b: item written (producer -> prep),
+  // blob landed, item prepared (prep -> consumers, with the window copies'
+  // bytes), windows flushed (signaller -> producer); signal slots
+  uint64_t *full, *empty, *ifull, *bfull, *pfull, *wfree, *sfull, *sempty;
+  ItemInfo* info;           // [2]
+  int4* sig;                // [kSig] (stage, case block, buffer, block start)
+  unsigned char* blob0;     // two descriptor blobs, blob_stride apart
+  uint32_t blob_stride;
+  // the current item's descriptors (inside its blob)
+  const DevStage* stage;
+  const DevPort* port;
+  const DevField* fld;
+  const DevPos* pos;
+  // per-buffer state (the current item's buffer for the consumers)
+  int4* obs;                // [cb][max_k] in-block observations
+  int* nobs;                // [cb]
+  double* bf;               // [cb] block factor
+  double* pval;             // [cb][max_ports] per (case, input port) factor
+  unsigned char* win;       // [cb][win_max] windows
   double* red;
-  int* misc;          // [0] abort flag, [1] dependencies met
-  int* kiter;         // [kMaxFastPorts][kMaxIter] per-iteration key parts of the live ports
-  unsigned char* live;// [kMaxFastPorts] LivePort
-  int* kt;            // [kMaxFastPorts][consumers] per-thread key parts of the live ports
-  unsigned char* win;
+  int* misc;                // [0] abort flag, [2] current item index
+  int* kiter;               // [kMaxFastPorts][kMaxIter] per-iteration key parts of the live ports
+  unsigned char* live;      // [kMaxFastPorts] LivePort
+  int* kt;                  // [kMaxFastPorts][consumers] per-thread key parts of the live ports
   unsigned char* ring;
+  // buffer strides (bytes)
+  uint32_t obs_b, nobs_b, bf_b, pval_b, win_b;
 };
 
-__device__ __forceinline__ Smem carve(unsigned char* smem, const SmemLayout& L, int ring_n) {
+// Position in the bulk-copy ring: stage and the parity of its current round
+// (kept incrementally: no division in the hot loop).
+struct RingPos {
+  uint32_t st = 0, ph = 0;
+  __device__ __forceinline__ void advance(uint32_t stages) {
+    if (++st == stages) {
+      st = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
+__device__ __forceinline__ Smem carve(unsigned char* smem, const SmemLayout& L, int ring_n, int cb, int max_k,
+                                      int max_ports, int win_max, int elem) {
   Smem s;
   s.full = reinterpret_cast<uint64_t*>(smem + L.bar);
   s.empty = s.full + ring_n;
   s.ifull = s.empty + ring_n;
-  s.iempty = s.ifull + kFifo;
-  s.sfull = s.iempty + kFifo;
+  s.bfull = s.ifull + 2;
+  s.pfull = s.bfull + 2;
+  s.wfree = s.pfull + 2;
+  s.sfull = s.wfree + 2;
   s.sempty = s.sfull + kSig;
-  s.fifo = reinterpret_cast<DevItem*>(smem + L.fifo);
-  s.sig = reinterpret_cast<int2*>(smem + L.sig);
-  s.stage = reinterpret_cast<DevStage*>(smem + L.stage);
-  s.port = reinterpret_cast<DevPort*>(smem + L.ports);
-  s.fld = reinterpret_cast<DevField*>(smem + L.fields);
-  s.pos = reinterpret_cast<DevPos*>(smem + L.pos);
+  s.info = reinterpret_cast<ItemInfo*>(smem + L.info);
+  s.sig = reinterpret_cast<int4*>(smem + L.sig);
+  s.blob0 = smem + L.blob;
+  s.blob_stride = (uint32_t)L.blob_bytes;
+  s.stage = nullptr;
+  s.port = nullptr;
+  s.fld = nullptr;
+  s.pos = nullptr;
   s.obs = reinterpret_cast<int4*>(smem + L.obs);
   s.nobs = reinterpret_cast<int*>(smem + L.nobs);
-  s.pval = reinterpret_cast<double*>(smem + L.pval);
   s.bf = reinterpret_cast<double*>(smem + L.bf);
+  s.pval = reinterpret_cast<double*>(smem + L.pval);
+  s.win = smem + L.win;
   s.red = reinterpret_cast<double*>(smem + L.red);
   s.misc = reinterpret_cast<int*>(smem + L.misc);
   s.kiter = reinterpret_cast<int*>(smem + L.kiter);
   s.live = smem + L.live;
   s.kt = reinterpret_cast<int*>(smem + L.kt);
-  s.win = smem + L.win;
   s.ring = smem + L.ring;
+  s.obs_b = (uint32_t)(cb * max_k * 16);
+  s.nobs_b = (uint32_t)(cb * 4);
+  s.bf_b = (uint32_t)(cb * 8);
+  s.pval_b = (uint32_t)(cb * max_ports * 8);
+  s.win_b = (uint32_t)(cb * win_max * elem);
   return s;
 }
 
-// ---- producer: one thread streams the items' blocks into the ring --------
+// The per-buffer state of buffer b, with the descriptors of the blob in it.
+__device__ __forceinline__ Smem with_buffer(const Smem& s, uint32_t b) {
+  Smem r = s;
+  unsigned char* blob = s.blob0 + b * s.blob_stride;
+  r.stage = reinterpret_cast<const DevStage*>(blob);
+  r.port = reinterpret_cast<const DevPort*>(blob + sizeof(DevStage));
+  r.fld = reinterpret_cast<const DevField*>(r.port + r.stage->np);
+  r.pos = reinterpret_cast<const DevPos*>(r.fld + r.stage->nf);
+  r.obs = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(s.obs) + b * s.obs_b);
+  r.nobs = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(s.nobs) + b * s.nobs_b);
+  r.bf = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(s.bf) + b * s.bf_b);
+  r.pval = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(s.pval) + b * s.pval_b);
+  r.win = s.win + b * s.win_b;
+  return r;
+}
+
+// ---- control warp, lane 0: the producer -----------------------------------
+// Takes items from the queue into buffer slot & 1 (once the item two slots
+// back has been flushed), fetches the stage's descriptor blob, and streams the
+// block into the ring, running ahead of the consumers.
 template <typename T>
 __device__ __forceinline__ void producer(const PropArgs<T>& a, const Smem& s) {
   constexpr int VEC = VecT<T>::N;
   volatile int* abort = s.misc;
   T* ring = reinterpret_cast<T*>(s.ring);
   const uint32_t S = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
-  uint32_t q = 0;  // chunks issued
+  uint32_t q = 0;      // chunks issued
+  uint32_t nblob = 0;  // descriptor blobs issued
+  RingPos rp;
   bool ok = true;
   for (uint32_t slot = 0;; ++slot) {
-    int it = a.n_items;
-    if (!*abort && ld_relaxed(a.err) == 0) it = atomicAdd(a.queue, 1);
-    const uint32_t fs = slot % kFifo;
-    if (slot >= (uint32_t)kFifo && !mbar_wait(s.iempty + fs, ((slot / kFifo) - 1) & 1u, a.err, abort)) {
+    const uint32_t b = slot & 1u;
+    if (slot >= 2 && !mbar_wait(s.wfree + b, ((slot >> 1) - 1) & 1u, a.err, abort)) {
       ok = false;
       break;
     }
-    DevItem w{};
-    w.stage = -1;
+    int it = a.n_items;
+    if (!*abort && ld_relaxed(a.err) == 0) it = atomicAdd(a.queue, 1);
+    ItemInfo& inf = s.info[b];
+    inf.w.stage = -1;
+    inf.idx = -1;
     if (it < a.n_items) {
-      w = a.items[it];
-      w.pad[0] = it;  // item index, for the optional trace
+      inf.w = a.items[it];
+      inf.idx = it;
       if (a.trace != nullptr) a.trace[(int64_t)it * kTraceSlots + 7] = global_ns();
+      fence_proxy_async();
+      mbar_expect_tx(s.bfull + b, (uint32_t)inf.w.blob_bytes);
+      bulk_g2s(s.blob0 + b * s.blob_stride, a.blobs + inf.w.blob, (uint32_t)inf.w.blob_bytes, s.bfull + b);
+      ++nblob;
     }
-    s.fifo[fs] = w;
-    mbar_arrive(s.ifull + fs);
+    const DevItem w = inf.w;
+    mbar_arrive(s.ifull + b);
     if (w.stage < 0) break;
     const int64_t a0 = w.off / VEC * VEC, a1 = (w.off + w.n + VEC - 1) / VEC * VEC;
-    for (int64_t e = a0; e < a1; e += CH, ++q) {
-      const uint32_t st = q % S;
-      if (q >= S && !mbar_wait(s.empty + st, ((q / S) - 1) & 1u, a.err, abort)) {
+    for (int64_t e = a0; e < a1; e += CH, ++q, rp.advance(S)) {
+      const uint32_t st = rp.st;
+      // the stage's previous round must have been released by every consumer warp
+      if (q >= S && !mbar_wait(s.empty + st, rp.ph ^ 1u, a.err, abort)) {
         ok = false;
         break;
       }
@@ -341,31 +427,306 @@ __device__ __forceinline__ void producer(const PropArgs<T>& a, const Smem& s) {
   }
   // every issued copy lands before the CTA may exit (the last chunk of each stage)
   for (uint32_t j = q > S ? q - S : 0; j < q; ++j) mbar_wait(s.full + j % S, (j / S) & 1u, nullptr, nullptr);
+  for (uint32_t j = nblob > 2 ? nblob - 2 : 0; j < nblob; ++j) mbar_wait(s.bfull + (j & 1u), (j / 2) & 1u, nullptr, nullptr);
 }
 
-// ---- signalling lane: publishes finished blocks ---------------------------
-// The consumers hand each finished item's (stage, case block) over once every
-// consumer thread has issued the item's output reductions; this lane makes
-// them visible GPU-wide (fence) and counts the block as done, so the fence's
-// latency stays off the consumers' path.
-__device__ __forceinline__ void signaller(const int32_t* err, int32_t* done, int n_cb, const Smem& s) {
-  for (uint32_t k = 0;; ++k) {
-    const uint32_t sl = k % kSig;
-    if (!mbar_wait(s.sfull + sl, (k / kSig) & 1u, err, s.misc)) break;
-    const int2 w = s.sig[sl];
-    mbar_arrive(s.sempty + sl);
-    if (w.x < 0) break;
-    __threadfence();
-    atomicAdd(done + (int64_t)w.x * n_cb + w.y, 1);
+// Wait until every dependency of the item has all its blocks finished (one
+// dependency per lane of `lanes` lanes).  False if the wait limit passed or an
+// error was reported.
+__device__ __forceinline__ bool await_deps(const int32_t* deps, int ndep, const int32_t* done, int n_cb, int cbk,
+                                           const int32_t* err, const volatile int* abort, int lane, int lanes,
+                                           unsigned mask) {
+  bool ok = true;
+  for (int d = lane; d < ndep; d += lanes) {
+    const int32_t stg = deps[2 * d], need = deps[2 * d + 1];
+    const int32_t* ctr = done + (int64_t)stg * n_cb + cbk;
+    if (ld_acquire(ctr) >= need) continue;
+    const uint64_t t0 = global_ns();
+    while (ld_acquire(ctr) < need) {
+      if (*abort || ld_relaxed(err) != 0 || global_ns() - t0 > kWaitLimitNs) {
+        ok = false;
+        break;
+      }
+      __nanosleep(100);
+    }
+    if (!ok) break;
+  }
+  return __all_sync(mask, ok);
+}
+
+// Window copies need 16-byte aligned, 16-byte granular ranges on both sides.
+template <typename T>
+__device__ __forceinline__ bool bulk_window(const DevStage& S, const DevPort& P) {
+  return S.bits >= 0 && ((uint32_t)P.K * (uint32_t)sizeof(T)) % 16u == 0u;
+}
+
+// ---- control warp, lanes 2..31: preparation of the next item ---------------
+// For the item in buffer b: wait for its blob and dependencies, enter the
+// evidence (block-level digits into the block factor, in-block digits into
+// per-case lists), fold block-constant inputs and child-message scales into
+// the block factor, and fill the windows (child messages by bulk copy, own
+// separator ratios computed, outputs zeroed).  The item is ready for the
+// consumers when pfull[b] completes (including the copies' bytes).
+template <typename T, int CB>
+__device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0) {
+  constexpr unsigned kMask = 0xfffffffcu;   // lanes 2..31
+  constexpr int NL = 30;
+  constexpr int U = 4;                      // tasks per lane per round (their loads in flight together)
+  const int pl = (int)(threadIdx.x & 31) - 2;  // 0..29
+  for (uint32_t slot = 0;; ++slot) {
+    const uint32_t b = slot & 1u, par = (slot >> 1) & 1u;
+    bool ok = mbar_wait(s0.ifull + b, par, a.err, s0.misc);
+    ok = __all_sync(kMask, ok);
+    if (!ok) break;
+    ItemInfo& inf = s0.info[b];
+    const DevItem w = inf.w;
+    if (w.stage < 0) {  // sentinel: pass it on
+      __syncwarp(kMask);
+      if (pl == 0) mbar_arrive(s0.pfull + b);
+      break;
+    }
+    ok = __all_sync(kMask, mbar_wait(s0.bfull + b, par, a.err, s0.misc));
+    if (!ok) break;
+    const Smem s = with_buffer(s0, b);
+    const DevStage S = *s.stage;
+    const int cb0 = a.case0 + w.cbk * CB;
+    const int ncb = min(CB, a.case0 + a.n_cases - cb0);
+    const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
+    const bool fast = S.bits >= 0;
+    uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)inf.idx * kTraceSlots : nullptr;
+    // dependencies
+    bool dok = true;
+    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, pl, NL, kMask);
+    if (pl < CB) {
+      s.nobs[pl] = 0;
+      s.bf[pl] = 1.0;
+    }
+    // the child-message windows first (bulk copies; the consumers wait for their bytes)
+    uint32_t bulk_bytes = 0;
+    if (dok) {
+      for (int pi = 0; pi < S.nin; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K > 1 && P.kind == kPortMu && bulk_window<T>(S, P)) bulk_bytes += (uint32_t)(ncb * P.K) * (uint32_t)sizeof(T);
+      }
+      if (pl == 0) mbar_expect_tx_only(s.pfull + b, bulk_bytes);
+      __syncwarp(kMask);
+      if (bulk_bytes > 0) {
+        fence_proxy_async_all();  // the messages were written by other CTAs (generic and bulk-reduce writes)
+        int n = 0;
+        for (int pi = 0; pi < S.nin; ++pi) {
+          const DevPort& P = s.port[pi];
+          if (P.K <= 1 || P.kind != kPortMu || !bulk_window<T>(S, P)) continue;
+          const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
+          for (int cl = 0; cl < ncb; ++cl, ++n) {
+            if (n % NL != pl) continue;
+            const T* src = a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb;
+            bulk_g2s(s.win + (size_t)(cl * a.win_max + P.win) * sizeof(T), src, (uint32_t)P.K * (uint32_t)sizeof(T),
+                     s.pfull + b);
+          }
+        }
+      }
+    }
+    __syncwarp(kMask);
+    if (dok) {
+      // per (case, input port): the child message's scale |S|/sigma, or the
+      // value of a block-constant input
+      const int ntask = ncb * S.nin;
+      for (int t0 = pl; t0 < ntask; t0 += U * NL) {
+        double x0[U], x1[U], x2[U], x3[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+          x0[r] = x1[r] = x2[r] = x3[r] = 0.0;
+          const int t = t0 + r * NL;
+          if (t >= ntask) continue;
+          const int cl = t / S.nin, pi = t - cl * S.nin;
+          const DevPort& P = s.port[pi];
+          const int cs = cb0 + cl;
+          const T* row = a.msg + (int64_t)cs * a.msg_stride;
+          const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
+          if (P.kind == kPortMu) {
+            x0[r] = __ldcg(sums + P.other);
+            if (P.K <= 1) {
+              const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+              x1[r] = (double)__ldcg(row + P.tab + key);
+            }
+          } else if (P.kind == kPortRho && P.K <= 1) {
+            const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+            x0[r] = __ldcg(sums + P.other);
+            x1[r] = __ldcg(sums + a.n_cliques + P.other2);
+            x2[r] = (double)__ldcg(row + P.tab + key);
+            x3[r] = (double)__ldcg(row + a.delta_off + P.tab + key);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+          const int t = t0 + r * NL;
+          if (t >= ntask) continue;
+          const int cl = t / S.nin, pi = t - cl * S.nin;
+          const DevPort& P = s.port[pi];
+          double v = 1.0;
+          if (P.kind == kPortMu) {
+            v = x0[r] > 0.0 ? (double)P.size / x0[r] : 0.0;
+            if (P.K <= 1) v *= x1[r];
+          } else if (P.kind == kPortRho && P.K <= 1) {
+            v = (x1[r] > 0.0 && x2[r] > 0.0) ? x3[r] * (x0[r] / x1[r]) / x2[r] : 0.0;
+          }
+          s.pval[cl * a.max_ports + pi] = v;
+        }
+      }
+      // evidence (block-level digits into the block factor, in-block digits
+      // into per-case lists)
+      const int nev = ncb * S.k;
+      for (int t0 = pl; t0 < nev; t0 += U * NL) {
+        int sv[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+          const int t = t0 + r * NL;
+          sv[r] = -1;
+          if (t >= nev) continue;
+          const int cl = t / S.k, i = t - cl * S.k;
+          sv[r] = a.ev[(int64_t)(cb0 + cl) * a.n_vars + s.pos[i].var];
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+          const int t = t0 + r * NL;
+          const int st = sv[r];
+          if (t >= nev || st < 0) continue;
+          const int cl = t / S.k, i = t - cl * S.k;
+          const DevPos& P = s.pos[i];
+          if (st >= P.card) {
+            atomicOr(&a.status[cb0 + cl], kStatusBadState);
+            continue;
+          }
+          if (fast) {
+            const int inside = max(0, min(P.cb, S.bits - P.sh));
+            const uint32_t lo_m = (1u << inside) - 1u;
+            const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
+            if (hi_d != ((uint32_t)st & ~lo_m)) {
+              s.bf[cl] = 0.0;
+            } else if (lo_m != 0u) {
+              const int slot2 = atomicAdd(&s.nobs[cl], 1);
+              s.obs[cl * a.max_k + slot2] = make_int4(P.sh, (int)lo_m, st & (int)lo_m, i);
+            }
+          } else if (i < S.k - S.kin) {
+            if (digit_of(eb, P) != (uint32_t)st) s.bf[cl] = 0.0;
+          } else {
+            const int slot2 = atomicAdd(&s.nobs[cl], 1);
+            s.obs[cl * a.max_k + slot2] = make_int4(i, 0, st, i);
+          }
+        }
+      }
+      // windows that are not bulk copies: ratios of the own separator, child
+      // messages of unaligned windows, zeroed outputs
+      const uint32_t win32 = smem_u32(s.win);
+      for (int pi = 0; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1) continue;
+        if (P.kind == kPortMu && bulk_window<T>(S, P)) continue;
+        const bool output = P.kind != kPortMu && P.kind != kPortRho;
+        const uint32_t kb = output ? 0u : (fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf));
+        for (int cl = 0; cl < ncb; ++cl) {
+          const int cs = cb0 + cl;
+          const uint32_t dst = win32 + (uint32_t)(cl * a.win_max + P.win) * (uint32_t)sizeof(T);
+          if (output) {
+            for (int ii = pl; ii < P.K; ii += NL) sst<T>(dst + (uint32_t)ii * (uint32_t)sizeof(T), T(0));
+            continue;
+          }
+          const T* row = a.msg + (int64_t)cs * a.msg_stride + P.tab + kb;
+          double sc = 0.0;
+          if (P.kind == kPortRho) {
+            const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
+            const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
+            sc = dp > 0.0 ? sgc / dp : 0.0;
+          }
+          for (int i0 = pl; i0 < P.K; i0 += U * NL) {
+            double u[U], d[U];
+#pragma unroll
+            for (int r = 0; r < U; ++r) {
+              const int ii = i0 + r * NL;
+              u[r] = ii < P.K ? (double)__ldcg(row + ii) : 0.0;
+              d[r] = (ii < P.K && P.kind == kPortRho) ? (double)__ldcg(row + a.delta_off + ii) : 0.0;
+            }
+#pragma unroll
+            for (int r = 0; r < U; ++r) {
+              const int ii = i0 + r * NL;
+              if (ii >= P.K) continue;
+              const T v = P.kind == kPortMu ? (T)u[r] : (T)(u[r] > 0.0 ? d[r] * sc / u[r] : 0.0);
+              sst<T>(dst + (uint32_t)ii * (uint32_t)sizeof(T), v);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp(kMask);
+    // block factor per case
+    if (dok && pl < ncb) {
+      double bfv = s.bf[pl];
+      for (int pi = 0; pi < S.nin; ++pi) bfv *= s.pval[pl * a.max_ports + pi];
+      s.bf[pl] = bfv;
+    }
+    if (pl == 0) inf.ok = dok ? 1 : 0;
+    __syncwarp(kMask);
+    if (tr != nullptr && pl == 0) tr[2] = global_ns();
+    if (pl == 0) {
+      if (!dok) mbar_expect_tx_only(s.pfull + b, 0u);
+      mbar_arrive(s.pfull + b);  // completes once the bulk window bytes have landed
+    }
+    if (!dok) break;  // the consumers see ok = 0 and stop
   }
 }
 
-// Consumer thread 0: hand (stage, case block) to the signalling lane
-// (stage < 0 ends it).  False if the lane did not free the slot in time.
-__device__ __forceinline__ bool hand_over(const Smem& s, uint32_t& k, int stage, int cbk, const int32_t* err) {
+// ---- control warp, lane 1: the signalling lane ----------------------------
+// For each finished item: add the output windows into the message arrays
+// with bulk reductions (the consumers already added the rest), wait until
+// they completed, make them visible GPU-wide, count the block as done, and
+// free the item's buffer.
+template <typename T, int CB>
+__device__ __forceinline__ void signaller(const PropArgs<T>& a, const Smem& s0) {
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t sl = k % kSig;
+    if (!mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc)) break;
+    const int4 g = s0.sig[sl];   // stage, case block, buffer, item index
+    mbar_arrive(s0.sempty + sl);
+    if (g.x < 0) break;
+    const uint32_t b = (uint32_t)g.z;
+    const Smem s = with_buffer(s0, b);
+    const DevStage& S = *s.stage;
+    const DevItem& w = s0.info[b].w;
+    bool any = false;
+    if (S.bits >= 0) {
+      const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
+      const int c0 = a.case0 + g.y * CB;
+      const int ncb = min(CB, a.case0 + a.n_cases - c0);
+      for (int pi = S.nin; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1 || !bulk_window<T>(S, P)) continue;
+        const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
+        for (int cl = 0; cl < ncb; ++cl) {
+          T* dst = a.msg + (int64_t)(c0 + cl) * a.msg_stride + P.tab + kb;
+          bulk_reduce_add(dst, s.win + (size_t)(cl * a.win_max + P.win) * sizeof(T),
+                          (uint32_t)P.K * (uint32_t)sizeof(T));
+          any = true;
+        }
+      }
+    }
+    if (any) {
+      bulk_commit();
+      bulk_wait_all();
+      fence_proxy_async_all();
+    }
+    __threadfence();
+    atomicAdd(a.done + (int64_t)g.x * a.n_cb + g.y, 1);
+    if (a.trace != nullptr && g.w >= 0) a.trace[(int64_t)g.w * kTraceSlots + 9] = global_ns();
+    mbar_arrive(s0.wfree + b);
+  }
+}
+
+// Consumer thread 0: hand a finished item to the signalling lane (stage < 0
+// ends it).  False if the lane did not free the slot in time.
+__device__ __forceinline__ bool hand_over(const Smem& s, uint32_t& k, int4 g, const int32_t* err) {
   const uint32_t sl = k % kSig;
   if (k >= (uint32_t)kSig && !mbar_wait(s.sempty + sl, ((k / kSig) - 1) & 1u, err, s.misc)) return false;
-  s.sig[sl] = make_int2(stage, cbk);
+  s.sig[sl] = g;
   mbar_arrive(s.sfull + sl);
   ++k;
   return true;
@@ -399,7 +760,7 @@ constexpr int32_t kModeChunk = 256;
 template <typename T, int CB>
 __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s, const DevItem& w, int ncb, int cb0,
                                             int n_in, int n_live, bool any_obs, const T (&bfv)[CB], T (&tot)[CB],
-                                            uint32_t& q) {
+                                            RingPos& rp) {
   constexpr int NT = consumers_for(CB);
   constexpr int VEC = VecT<T>::N;
   constexpr int VPT = kChunkBytes / (16 * NT);  // vectors per thread per chunk
@@ -433,11 +794,11 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     for (int j = 0; j < VEC; ++j) jacc[it][j] = T(0);
   bool ok = true;
   uint64_t waited = 0;
-  for (int ci = 0; ci < nchunks; ++ci, ++q) {
-    const uint32_t st = q % RS;
+  for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
+    const uint32_t st = rp.st;
     const uint64_t tw = (a.trace != nullptr && tid == 0) ? global_ns() : 0;
     // the warp leaves together (its lanes reduce with shuffles below)
-    if (!__all_sync(kFull, mbar_wait(s.full + st, (q / RS) & 1u, a.err, s.misc))) {
+    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc))) {
       ok = false;
       break;
     }
@@ -584,7 +945,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     __syncwarp();
     if (lane == 0) mbar_arrive(s.empty + st);
   }
-  if (a.trace != nullptr && tid == 0) a.trace[(int64_t)w.pad[0] * kTraceSlots + 6] = waited;
+  if (a.trace != nullptr && tid == 0) a.trace[(int64_t)s.misc[2] * kTraceSlots + 6] = waited;
   if (!__all_sync(kFull, ok)) return false;
   // flush the register accumulators (inactive lanes hold zeros)
   if (ra >= 0) {
@@ -622,7 +983,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
 template <typename T, int CB>
 __device__ __forceinline__ bool stream_generic(const PropArgs<T>& a, const Smem& s, const DevStage& S,
                                                const DevItem& w, int ncb, int cb0, const T (&bfv)[CB],
-                                               T (&tot)[CB], uint32_t& q) {
+                                               T (&tot)[CB], RingPos& rp) {
   constexpr int NT = consumers_for(CB);
   constexpr int VEC = VecT<T>::N;
   constexpr int VPT = kChunkBytes / (16 * NT);
@@ -633,10 +994,10 @@ __device__ __forceinline__ bool stream_generic(const PropArgs<T>& a, const Smem&
   const int nchunks = (int)((a1 - a0 + CH - 1) / CH);
   const int np = S.np, nin = S.nin;
   bool ok = true;
-  for (int ci = 0; ci < nchunks; ++ci, ++q) {
-    const uint32_t st = q % RS;
+  for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
+    const uint32_t st = rp.st;
     // the warp leaves together (its lanes reduce with shuffles below)
-    if (!__all_sync(kFull, mbar_wait(s.full + st, (q / RS) & 1u, a.err, s.misc))) {
+    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc))) {
       ok = false;
       break;
     }
@@ -694,195 +1055,25 @@ __device__ __forceinline__ bool stream_generic(const PropArgs<T>& a, const Smem&
   return ok;
 }
 
-// Wait until every dependency of the item has all its blocks finished (warp 0,
-// one dependency per lane).  False if the wait limit passed or an error was
-// reported.
-__device__ __forceinline__ bool await_deps(const int32_t* deps, int ndep, const int32_t* done, int n_cb, int cbk,
-                                           const int32_t* err, const volatile int* abort) {
-  const int lane = threadIdx.x & 31;
-  bool ok = true;
-  for (int d = lane; d < ndep; d += 32) {
-    const int32_t stg = deps[2 * d], need = deps[2 * d + 1];
-    const int32_t* ctr = done + (int64_t)stg * n_cb + cbk;
-    if (ld_acquire(ctr) >= need) continue;
-    const uint64_t t0 = global_ns();
-    while (ld_acquire(ctr) < need) {
-      if (*abort || ld_relaxed(err) != 0 || global_ns() - t0 > kWaitLimitNs) {
-        ok = false;
-        break;
-      }
-      __nanosleep(100);
-    }
-    if (!ok) break;
-  }
-  return __all_sync(kFull, ok);
-}
-
-// One work item.  Every consumer thread runs every barrier; the result is
-// uniform over the consumers.
+// One work item (its buffer prepared by the control warp).  Every consumer
+// thread runs every barrier; the result is uniform over the consumers.
 template <typename T, int CB>
-__device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s, const DevItem& w, uint32_t& q,
-                                             uint32_t& sigk) {
+__device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s, const DevItem& w, uint32_t b,
+                                             RingPos& rp, uint32_t& sigk) {
   constexpr int NT = consumers_for(CB);
   constexpr int VEC = VecT<T>::N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const DevStage S = a.stages[w.stage];
+  const DevStage S = *s.stage;
   const int cb0 = a.case0 + w.cbk * CB;
   const int ncb = min(CB, a.case0 + a.n_cases - cb0);
   const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;  // block start inside the clique
   const bool fast = S.bits >= 0;
-  T* win = reinterpret_cast<T*>(s.win);
-  uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)w.pad[0] * kTraceSlots : nullptr;
-  if (tr != nullptr && tid == 0) {
-    uint32_t smid;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-    tr[0] = smid;
-    tr[1] = global_ns();
-  }
+  const int idx_item = s.misc[2];
+  uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)idx_item * kTraceSlots : nullptr;
 
-  // descriptors into shared memory (warps 1..); dependencies (warp 0)
-  if (tid == 0) s.misc[1] = 1;
-  if (tid < CB) {
-    s.nobs[tid] = 0;
-    s.bf[tid] = 1.0;
-  }
-  if (warp == 0) {
-    if (S.ndep > 0) {
-      const bool dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc);
-      if (lane == 0 && !dok) s.misc[1] = 0;
-    }
-    if (tr != nullptr && lane == 0) tr[2] = global_ns();
-  } else {
-    for (int i = tid - 32; i < S.np; i += NT - 32) s.port[i] = a.ports[S.port0 + i];
-    for (int i = tid - 32; i < S.nf; i += NT - 32) s.fld[i] = a.fields[S.field0 + i];
-    for (int i = tid - 32; i < S.k; i += NT - 32) s.pos[i] = a.pos[S.pos0 + i];
-  }
-  consumer_sync<NT>();
-  const bool ok = s.misc[1] != 0;
-
-  // evidence (block-level digits into the block factor, in-block digits
-  // into per-case lists), windows (inputs gathered and normalised, outputs
-  // zeroed), block-constant inputs, and the fast path's key parts
-  for (int idx = tid; idx < ncb * S.k; idx += NT) {
-    const int cl = idx / S.k, i = idx - cl * S.k;
-    const DevPos P = s.pos[i];
-    const int st = a.ev[(int64_t)(cb0 + cl) * a.n_vars + P.var];
-    if (st < 0) continue;
-    if (st >= P.card) {
-      atomicOr(&a.status[cb0 + cl], kStatusBadState);
-      continue;
-    }
-    if (fast) {
-      const int inside = max(0, min(P.cb, S.bits - P.sh));
-      const uint32_t lo_m = (1u << inside) - 1u;
-      const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
-      if (hi_d != ((uint32_t)st & ~lo_m)) {
-        s.bf[cl] = 0.0;
-      } else if (lo_m != 0u) {
-        const int slot = atomicAdd(&s.nobs[cl], 1);
-        s.obs[cl * a.max_k + slot] = make_int4(P.sh, (int)lo_m, st & (int)lo_m, i);
-      }
-    } else if (i < S.k - S.kin) {
-      if (digit_of(eb, P) != (uint32_t)st) s.bf[cl] = 0.0;
-    } else {
-      const int slot = atomicAdd(&s.nobs[cl], 1);
-      s.obs[cl * a.max_k + slot] = make_int4(i, 0, st, i);
-    }
-  }
-  if (ok) {
-    // per (case, port): a child message's normalisation |S|/sigma (applied
-    // through the block factor), or the value of a block-constant input
-    for (int idx = tid; idx < ncb * S.np; idx += NT) {
-      const int cl = idx / S.np, pi = idx - cl * S.np;
-      const DevPort& P = s.port[pi];
-      const int cs = cb0 + cl;
-      const T* row = a.msg + (int64_t)cs * a.msg_stride;
-      const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
-      double v = 1.0;
-      if (P.kind == kPortMu) {
-        const double sg = __ldcg(sums + P.other);
-        v = sg > 0.0 ? (double)P.size / sg : 0.0;
-        if (P.K <= 1) {
-          const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
-          v *= (double)__ldcg(row + P.tab + key);
-        }
-      } else if (P.kind == kPortRho && P.K <= 1) {
-        const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
-        const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
-        const double u = (double)__ldcg(row + P.tab + key);
-        const double d = (double)__ldcg(row + a.delta_off + P.tab + key);
-        v = (dp > 0.0 && u > 0.0) ? d * (sgc / dp) / u : 0.0;
-      }
-      s.pval[cl * a.max_ports + pi] = v;
-    }
-    // windows: raw child messages, ratios of the own separator, zeroed outputs
-    const uint32_t win32 = smem_u32(s.win);
-    for (int pi = 0; pi < S.np; ++pi) {
-      const DevPort& P = s.port[pi];
-      if (P.K <= 1) continue;
-      const uint32_t kb = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
-      const int K = P.K, total = ncb * K;
-      const uint32_t w0 = win32 + (uint32_t)P.win * (uint32_t)sizeof(T);
-      if (P.kind == kPortMu) {
-        // eight loads in flight per thread
-        for (int base = 0; base < total; base += 8 * NT) {
-          T u[8];
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int idx = base + r * NT + tid;
-            u[r] = T(0);
-            if (idx < total) {
-              const int cl = idx / K, ii = idx - cl * K;
-              u[r] = __ldcg(a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb + ii);
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int idx = base + r * NT + tid;
-            if (idx < total) {
-              const int cl = idx / K, ii = idx - cl * K;
-              sst<T>(w0 + (uint32_t)(cl * a.win_max + ii) * (uint32_t)sizeof(T), u[r]);
-            }
-          }
-        }
-      } else if (P.kind == kPortRho) {
-        for (int base = 0; base < total; base += 4 * NT) {
-          double u[4], d[4], sc[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int idx = base + r * NT + tid;
-            u[r] = 0.0;
-            d[r] = 0.0;
-            sc[r] = 0.0;
-            if (idx < total) {
-              const int cl = idx / K, ii = idx - cl * K;
-              const int cs = cb0 + cl;
-              const T* row = a.msg + (int64_t)cs * a.msg_stride;
-              const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
-              u[r] = (double)__ldcg(row + P.tab + kb + ii);
-              d[r] = (double)__ldcg(row + a.delta_off + P.tab + kb + ii);
-              const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
-              sc[r] = dp > 0.0 ? sgc / dp : 0.0;
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int idx = base + r * NT + tid;
-            if (idx < total) {
-              const int cl = idx / K, ii = idx - cl * K;
-              const double v = u[r] > 0.0 ? d[r] * sc[r] / u[r] : 0.0;
-              sst<T>(w0 + (uint32_t)(cl * a.win_max + ii) * (uint32_t)sizeof(T), (T)v);
-            }
-          }
-        }
-      } else {
-        for (int idx = tid; idx < total; idx += NT) {
-          const int cl = idx / K, ii = idx - cl * K;
-          sst<T>(w0 + (uint32_t)(cl * a.win_max + ii) * (uint32_t)sizeof(T), T(0));
-        }
-      }
-    }
-  }
+  // fast path: the ports with windows (inputs first), their per-thread and
+  // per-iteration key parts (iteration m covers block offsets
+  // [m, m + 1) * consumers * VEC)
   int n_in = 0, n_live = 0;
   if (fast) {
     for (int pi = 0; pi < S.np; ++pi) {
@@ -890,34 +1081,26 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
       if (pi < S.nin) ++n_in;
       ++n_live;
     }
-    if (ok) {
-      LivePort* lp = reinterpret_cast<LivePort*>(s.live);
-      const int mi = (w.n + NT * VEC - 1) / (NT * VEC);
-      int li = 0;
-      for (int pi = 0; pi < S.np; ++pi) {
-        const DevPort& P = s.port[pi];
-        if (P.K <= 1) continue;
-        if (tid == li) {
-          LivePort L;
-          L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
-                   (int32_t)((P.lane_free & 31u) << 3);
-          L.port = pi;
-          L.pad[0] = L.pad[1] = 0;
-          L.dvec = make_int4(P.dvec[0], P.dvec[1], P.dvec[2], P.dvec[3]);
-          lp[li] = L;
-        }
-        s.kt[li * NT + tid] = (int)(key_of<true>((uint32_t)tid * VEC, s.fld + P.f0, P.nf) + (uint32_t)P.win);
-        for (int m = tid; m < mi; m += NT)
-          s.kiter[li * kMaxIter + m] = (int)key_of<true>((uint32_t)m * NT * VEC, s.fld + P.f0, P.nf);
-        ++li;
+    LivePort* lp = reinterpret_cast<LivePort*>(s.live);
+    const int mi = (w.n + NT * VEC - 1) / (NT * VEC);
+    int li = 0;
+    for (int pi = 0; pi < S.np; ++pi) {
+      const DevPort& P = s.port[pi];
+      if (P.K <= 1) continue;
+      if (tid == li) {
+        LivePort L;
+        L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
+                 (int32_t)((P.lane_free & 31u) << 3);
+        L.port = pi;
+        L.pad[0] = L.pad[1] = 0;
+        L.dvec = make_int4(P.dvec[0], P.dvec[1], P.dvec[2], P.dvec[3]);
+        lp[li] = L;
       }
+      s.kt[li * NT + tid] = (int)(key_of<true>((uint32_t)tid * VEC, s.fld + P.f0, P.nf) + (uint32_t)P.win);
+      for (int m = tid; m < mi; m += NT)
+        s.kiter[li * kMaxIter + m] = (int)key_of<true>((uint32_t)m * NT * VEC, s.fld + P.f0, P.nf);
+      ++li;
     }
-  }
-  consumer_sync<NT>();
-  if (ok && tid < ncb) {
-    double b = s.bf[tid];
-    for (int pi = 0; pi < S.nin; ++pi) b *= s.pval[tid * a.max_ports + pi];
-    s.bf[tid] = b;
   }
   consumer_sync<NT>();
 
@@ -927,17 +1110,13 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
   bool any_obs = false;
 #pragma unroll
   for (int cl = 0; cl < CB; ++cl) {
-    bfv[cl] = (ok && cl < ncb) ? (T)s.bf[cl] : T(0);
+    bfv[cl] = cl < ncb ? (T)s.bf[cl] : T(0);
     tot[cl] = T(0);
     if (cl < ncb && s.nobs[cl] > 0) any_obs = true;
   }
-  bool sok = true;
-  if (ok) {
-    sok = fast ? stream_fast<T, CB>(a, s, w, ncb, cb0, n_in, n_live, any_obs, bfv, tot, q)
-               : stream_generic<T, CB>(a, s, S, w, ncb, cb0, bfv, tot, q);
-  }
-  const bool all_ok = consumer_all<NT>(ok && sok);
-  if (!all_ok) {
+  const bool sok = fast ? stream_fast<T, CB>(a, s, w, ncb, cb0, n_in, n_live, any_obs, bfv, tot, rp)
+                        : stream_generic<T, CB>(a, s, S, w, ncb, cb0, bfv, tot, rp);
+  if (!consumer_all<NT>(sok)) {
     if (tid == 0) {
       atomicExch(a.err, 1);
       s.misc[0] = 1;
@@ -946,7 +1125,8 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
   }
   if (tr != nullptr && tid == 0) tr[4] = global_ns();
 
-  // flush: block totals (stage total, block-constant outputs), then windows
+  // block totals (stage total, block-constant outputs); windows that are not
+  // bulk-reduced by the signalling lane
 #pragma unroll
   for (int cl = 0; cl < CB; ++cl) {
     const double v = warp_sum((double)tot[cl]);
@@ -955,7 +1135,7 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
   consumer_sync<NT>();
   if (tid < ncb) {
     double t = 0.0;
-    for (int i = 0; i < (NT / 32); ++i) t += s.red[tid * (NT / 32) + i];
+    for (int i = 0; i < NT / 32; ++i) t += s.red[tid * (NT / 32) + i];
     const int cs = cb0 + tid;
     T* row = a.msg + (int64_t)cs * a.msg_stride;
     if (t != 0.0) {
@@ -969,51 +1149,69 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
     }
   }
   for (int pi = S.nin; pi < S.np; ++pi) {
-    const DevPort P = s.port[pi];
-    if (P.K <= 1) continue;
+    const DevPort& P = s.port[pi];
+    if (P.K <= 1 || bulk_window<T>(S, P)) continue;
     const uint32_t kb = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
     const uint32_t win32 = smem_u32(s.win);
-    for (int idx = tid; idx < ncb * P.K; idx += NT) {
-      const int cl = idx / P.K, i = idx - cl * P.K;
-      const T v = sld<T>(win32 + (uint32_t)(cl * a.win_max + P.win + i) * (uint32_t)sizeof(T));
-      if (v != T(0)) atomicAdd(a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb + i, v);
+    for (int cl = 0; cl < ncb; ++cl) {
+      T* dst = a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb;
+      const uint32_t src = win32 + (uint32_t)(cl * a.win_max + P.win) * (uint32_t)sizeof(T);
+      for (int i = tid; i < P.K; i += NT) {
+        const T v = sld<T>(src + (uint32_t)i * (uint32_t)sizeof(T));
+        if (v != T(0)) atomicAdd(dst + i, v);
+      }
     }
   }
   consumer_sync<NT>();
   if (tid == 0) {
-    if (!hand_over(s, sigk, w.stage, w.cbk, a.err)) {
+    if (tr != nullptr) tr[5] = global_ns();
+    if (!hand_over(s, sigk, make_int4(w.stage, w.cbk, (int)b, idx_item), a.err)) {
       atomicExch(a.err, 1);
       s.misc[0] = 1;
     }
-    if (tr != nullptr) tr[5] = global_ns();
   }
   return true;
 }
 
 template <typename T, int CB>
-__device__ __forceinline__ void consumer(const PropArgs<T>& a, const Smem& s) {
+__device__ __forceinline__ void consumer(const PropArgs<T>& a, const Smem& s0) {
   constexpr int NT = consumers_for(CB);
-  uint32_t q = 0;     // chunks consumed (the producer's numbering)
+  RingPos rp;         // ring position of the next chunk (the producer's order)
   uint32_t sigk = 0;  // items handed to the signalling lane (thread 0)
   for (uint32_t slot = 0;; ++slot) {
-    const uint32_t fs = slot % kFifo;
-    bool ok = mbar_wait(s.ifull + fs, (slot / kFifo) & 1u, a.err, s.misc);
-    ok = consumer_all<NT>(ok);
+    const uint32_t b = slot & 1u;
+    const bool ok = consumer_all<NT>(mbar_wait(s0.pfull + b, (slot >> 1) & 1u, a.err, s0.misc));
     if (!ok) {
       if (threadIdx.x == 0) {
         atomicExch(a.err, 1);
-        s.misc[0] = 1;
+        s0.misc[0] = 1;
       }
       break;
     }
-    const DevItem w = s.fifo[fs];
-    consumer_sync<NT>();
-    if (threadIdx.x == 0) mbar_arrive(s.iempty + fs);
+    const ItemInfo& inf = s0.info[b];
+    const DevItem w = inf.w;
     if (w.stage < 0) {
-      if (threadIdx.x == 0) hand_over(s, sigk, -1, 0, a.err);
+      if (threadIdx.x == 0) hand_over(s0, sigk, make_int4(-1, 0, 0, -1), a.err);
       break;
     }
-    if (!process_item<T, CB>(a, s, w, q, sigk)) break;
+    if (!inf.ok) {
+      if (threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        s0.misc[0] = 1;
+      }
+      break;
+    }
+    if (threadIdx.x == 0) {
+      s0.misc[2] = inf.idx;
+      if (a.trace != nullptr) {
+        uint32_t smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        a.trace[(int64_t)inf.idx * kTraceSlots] = smid;
+        a.trace[(int64_t)inf.idx * kTraceSlots + 1] = global_ns();
+      }
+    }
+    consumer_sync<NT>();
+    if (!process_item<T, CB>(a, with_buffer(s0, b), w, b, rp, sigk)) break;
   }
 }
 
@@ -1022,15 +1220,17 @@ __global__ void __launch_bounds__(consumers_for(CB) + 32, ctas_per_sm_for(CB)) k
   constexpr int NT = consumers_for(CB);
   extern __shared__ __align__(128) unsigned char smem[];
   const SmemLayout L(CB, a.ring, a.chunk, a.max_k, a.max_ports, a.max_fields, a.win_max, (int)sizeof(T));
-  const Smem s = carve(smem, L, a.ring);
+  const Smem s = carve(smem, L, a.ring, CB, a.max_k, a.max_ports, a.win_max, (int)sizeof(T));
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.ring; ++i) {
       mbar_init(s.full + i, 1);
-      mbar_init(s.empty + i, (NT / 32));
+      mbar_init(s.empty + i, NT / 32);
     }
-    for (int i = 0; i < kFifo; ++i) {
+    for (int i = 0; i < 2; ++i) {
       mbar_init(s.ifull + i, 1);
-      mbar_init(s.iempty + i, 1);
+      mbar_init(s.bfull + i, 1);
+      mbar_init(s.pfull + i, 1);
+      mbar_init(s.wfree + i, 1);
     }
     for (int i = 0; i < kSig; ++i) {
       mbar_init(s.sfull + i, 1);
@@ -1041,8 +1241,10 @@ __global__ void __launch_bounds__(consumers_for(CB) + 32, ctas_per_sm_for(CB)) k
   }
   __syncthreads();
   if (threadIdx.x >= NT) {
-    if (threadIdx.x == NT) producer<T>(a, s);
-    else if (threadIdx.x == NT + 1) signaller(a.err, a.done, a.n_cb, s);
+    const int l = threadIdx.x - NT;
+    if (l == 0) producer<T>(a, s);
+    else if (l == 1) signaller<T, CB>(a, s);
+    else prep_lanes<T, CB>(a, s);
     __syncwarp();
   } else {
     consumer<T, CB>(a, s);

@@ -13,38 +13,45 @@ namespace jt {
 __host__ __device__ constexpr int consumers_for(int cb) { return cb > 0 ? 512 : 512; }
 __host__ __device__ constexpr int ctas_per_sm_for(int cb) { return cb > 0 ? 1 : 1; }
 constexpr int kChunkBytes = 16384;              // bytes per bulk-copy stage
-constexpr int kFifo = 1;                        // work items handed to the consumers ahead of time
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
 constexpr int kMaxIter = 64;                    // consumer iterations of one fast-path block
 
+// Bytes of the largest descriptor blob of a schedule.
+__host__ __device__ inline int32_t blob_max(int max_k, int max_ports, int max_fields) {
+  return (int32_t)sizeof(DevStage) + max_ports * (int32_t)sizeof(DevPort) + max_fields * (int32_t)sizeof(DevField) +
+         max_k * (int32_t)sizeof(DevPos);
+}
+
 // Dynamic shared memory of a propagation CTA, carved identically by the
-// planner (host) and the kernel (device).
+// planner (host) and the kernel (device).  Everything an item needs besides
+// the streamed table (descriptor blob, evidence lists, block factors,
+// windows) is double-buffered: the control warp prepares item i+1 and
+// flushes item i-1 while the consumers stream item i.
 struct SmemLayout {
-  int32_t bar, fifo, sig, stage, ports, fields, pos, obs, nobs, pval, bf, red, misc, kiter, live, kt, win, ring, bytes;
+  int32_t bar, info, sig, blob, blob_bytes, obs, nobs, bf, pval, red, misc, kiter, live, kt, win, ring, bytes;
 
   __host__ __device__ static int32_t a16(int32_t x) { return (x + 15) & ~15; }
 
   __host__ __device__ SmemLayout(int cb, int ring_n, int chunk, int max_k, int max_ports, int max_fields,
                                  int win_max, int elem) {
     int32_t o = 0;
-    bar = o;    o += (2 * ring_n + 2 * kFifo + 2 * kSig) * 8;  // full/empty: per stage, item slot, signal slot
-    fifo = a16(o);   o = fifo + kFifo * (int32_t)sizeof(DevItem);
-    sig = a16(o);    o = sig + kSig * 8;                       // finished (stage, case block) pairs
-    stage = a16(o);  o = stage + (int32_t)sizeof(DevStage);
-    ports = a16(o);  o = ports + max_ports * (int32_t)sizeof(DevPort);
-    fields = a16(o); o = fields + max_fields * (int32_t)sizeof(DevField);
-    pos = a16(o);    o = pos + max_k * (int32_t)sizeof(DevPos);
-    obs = a16(o);    o = obs + cb * max_k * 16;             // in-block observations per case
-    nobs = a16(o);   o = nobs + cb * 4;
-    pval = a16(o);   o = pval + cb * max_ports * 8;         // per (case, port) scale or block value
-    bf = a16(o);     o = bf + cb * 8;                       // block factor per case
+    bar = o;  o += (2 * ring_n + 8 + 2 * kSig) * 8;   // ring full/empty; per buffer: item, blob, prepared,
+                                                      // flushed; signal slots full/empty
+    info = a16(o);   o = info + 2 * 64;                // per buffer: the item and its preparation status
+    sig = a16(o);    o = sig + kSig * 16;              // finished items for the signalling lane
+    blob_bytes = blob_max(max_k, max_ports, max_fields);
+    blob = (o + 127) & ~127; o = blob + 2 * blob_bytes;
+    obs = a16(o);    o = obs + 2 * cb * max_k * 16;    // in-block observations per case
+    nobs = a16(o);   o = nobs + 2 * cb * 4;
+    bf = a16(o);     o = bf + 2 * cb * 8;              // block factor per case
+    pval = a16(o);   o = pval + 2 * cb * max_ports * 8;  // per (case, input port) factor
     red = a16(o);    o = red + cb * (consumers_for(cb) / 32) * 8;  // block-total partials
     misc = a16(o);   o = misc + 16 * 4;
     kiter = a16(o);  o = kiter + kMaxFastPorts * kMaxIter * 4;  // per-iteration key part of every live port
     live = a16(o);   o = live + kMaxFastPorts * 32;             // live ports: index, mode, dvec
     kt = a16(o);     o = kt + kMaxFastPorts * consumers_for(cb) * 4;  // per-thread key part of every live port
-    win = (o + 127) & ~127;  o = win + cb * win_max * elem;
+    win = (o + 127) & ~127;  o = win + 2 * cb * win_max * elem;
     ring = (o + 127) & ~127; o = ring + ring_n * chunk * elem;
     bytes = o;
   }

@@ -142,13 +142,13 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
   // separator tables: root gets a 1-entry slot (its total), edges follow
   p->sep_size.assign(nc, 1);
   p->sep_off.assign(nc, 0);
-  int64_t off = 1;
+  int64_t off = 4;
   for (int c = 1; c < nc; ++c) {
     int64_t s = 1;
     for (int v : p->sep[c]) s *= p->card[v];
     p->sep_size[c] = (int32_t)s;
     p->sep_off[c] = (int32_t)off;
-    off += s;
+    off += (s + 3) / 4 * 4;  // tables start on 16-byte boundaries (FP32), for bulk copies
     if (off > (1ll << 30)) FAIL(JT_ERR_UNSUPPORTED, "separator tables too large");
   }
   p->msg_total = (int32_t)off;
@@ -204,7 +204,7 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     for (size_t i = pv.size() - p->n_private[c]; i < pv.size(); ++i) q *= p->card[pv[i]];
     p->joint_off[c] = (int32_t)jo;
     p->joint_size[c] = (int32_t)q;
-    jo += q;
+    jo += (q + 3) / 4 * 4;
     if (jo > (1ll << 30)) FAIL(JT_ERR_UNSUPPORTED, "private-variable joints too large");
   }
   p->joint_total = (int32_t)jo;
@@ -323,7 +323,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
   s->cb = cb;
   s->n_cb = std::max(1, (n_cases + cb - 1) / cb);
   s->chunk = kChunkBytes / elem;
-  s->ring = cb == 1 ? 8 : 6;
+  s->ring = cb == 1 ? 8 : 4;
   s->stages.assign(2 * nc, DevStage{});
   s->ports.clear();
   s->fields.clear();
@@ -410,13 +410,13 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
 
   // shared memory: what the windows may use once the ring and descriptors fit
   const int fixed = SmemLayout(cb, s->ring, s->chunk, s->max_k, s->max_ports, s->max_fields, 0, elem).bytes;
-  const int64_t win_budget = (int64_t)(smem_bytes - fixed - 256) / ((int64_t)cb * elem);
+  const int64_t win_budget = (int64_t)(smem_bytes - fixed - 256) / (2ll * cb * elem);  // two buffers
   if (win_budget < (int64_t)s->max_ports * VEC) {
     *err = "the tree's descriptors do not fit in shared memory";
     return JT_ERR_UNSUPPORTED;
   }
 
-  s->win_max = 1;
+  s->win_max = 4;
   for (int pass = 0; pass < 2; ++pass)
     for (int c = 0; c < nc; ++c) {
       DevStage& S = s->stages[pass * nc + c];
@@ -571,6 +571,25 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       }
     }
 
+  // descriptor blobs: one contiguous copy per stage of everything a work
+  // item reads about its stage (one bulk copy fetches it)
+  std::vector<int32_t> blob_at(2 * nc, 0), blob_len(2 * nc, 0);
+  s->blobs.clear();
+  for (int st = 0; st < 2 * nc; ++st) {
+    const DevStage& S = s->stages[st];
+    if (S.n_blocks == 0) continue;
+    blob_at[st] = (int32_t)s->blobs.size();
+    auto put = [&](const void* src, size_t bytes) {
+      const uint4* q = static_cast<const uint4*>(src);
+      for (size_t i = 0; i < bytes / sizeof(uint4); ++i) s->blobs.push_back(q[i]);
+    };
+    put(&S, sizeof(DevStage));
+    if (S.np) put(&s->ports[S.port0], S.np * sizeof(DevPort));
+    if (S.nf) put(&s->fields[S.field0], S.nf * sizeof(DevField));
+    put(&s->pos[S.pos0], S.k * sizeof(DevPos));
+    blob_len[st] = (int32_t)((s->blobs.size() - blob_at[st]) * sizeof(uint4));
+  }
+
   // work items: collect deepest level first, then distribute from the root;
   // every item's dependencies come earlier in the list
   auto add = [&](int stage) {
@@ -583,6 +602,8 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         it.stage = stage;
         it.block = b;
         it.cbk = q;
+        it.blob = blob_at[stage];
+        it.blob_bytes = blob_len[stage];
         s->items.push_back(it);
       }
   };
