@@ -763,7 +763,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
                                             RingPos& rp) {
   constexpr int NT = consumers_for(CB);
   constexpr int VEC = VecT<T>::N;
-  constexpr int VPT = kChunkBytes / (16 * NT);  // vectors per thread per chunk
+  constexpr int VPT = chunk_bytes_for(CB) / (16 * NT);  // vectors per thread per chunk
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t RS = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
   const uint32_t ring32 = smem_u32(s.ring), win32 = smem_u32(s.win);
@@ -806,19 +806,24 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     const uint32_t sb = ring32 + st * CH * (uint32_t)sizeof(T);
     const uint32_t cbase = (uint32_t)ci * CH;
     const int nvec = (int)(min((uint32_t)w.n - cbase, CH) / VEC);
+    // all of this thread's vectors of the chunk first (their loads overlap)
+    T xs[VPT][VEC];
+#pragma unroll
+    for (int it = 0; it < VPT; ++it) {
+      if (it * NT + tid < nvec) {
+        sld_vec(sb + (uint32_t)(it * NT + tid) * (VEC * (uint32_t)sizeof(T)), xs[it]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) xs[it][j] = T(0);
+      }
+    }
 #pragma unroll
     for (int it = 0; it < VPT; ++it) {
       if (it * NT + warp * 32 >= nvec) break;  // warp-uniform
       const int vi = it * NT + tid;
       const bool act = vi < nvec;
       const int m = ci * VPT + it;             // iteration index within the block
-      T x[VEC];
-      if (act) {
-        sld_vec(sb + (uint32_t)vi * (VEC * (uint32_t)sizeof(T)), x);
-      } else {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) x[j] = T(0);
-      }
+      const T (&x)[VEC] = xs[it];
       const uint32_t o0 = cbase + (uint32_t)vi * VEC;
       T f[CB][VEC];
 #pragma unroll
@@ -986,7 +991,7 @@ __device__ __forceinline__ bool stream_generic(const PropArgs<T>& a, const Smem&
                                                T (&tot)[CB], RingPos& rp) {
   constexpr int NT = consumers_for(CB);
   constexpr int VEC = VecT<T>::N;
-  constexpr int VPT = kChunkBytes / (16 * NT);
+  constexpr int VPT = chunk_bytes_for(CB) / (16 * NT);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t RS = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
   const uint32_t ring32 = smem_u32(s.ring), win32 = smem_u32(s.win);

@@ -12,7 +12,8 @@ namespace jt {
 // one producer warp) and resident CTAs per SM.
 __host__ __device__ constexpr int consumers_for(int cb) { return cb > 0 ? 512 : 512; }
 __host__ __device__ constexpr int ctas_per_sm_for(int cb) { return cb > 0 ? 1 : 1; }
-constexpr int kChunkBytes = 16384;              // bytes per bulk-copy stage
+// Bytes per bulk-copy stage (two vectors per consumer thread per stage).
+__host__ __device__ constexpr int chunk_bytes_for(int cb) { return cb > 0 ? 16384 : 16384; }
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
 constexpr int kMaxIter = 64;                    // consumer iterations of one fast-path block
