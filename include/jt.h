@@ -170,6 +170,30 @@ jt_status jt_get_status(jt_tree t, int32_t first_case, int32_t n_cases, int32_t*
  */
 jt_status jt_get_clique(jt_tree t, int32_t case_id, int32_t clique, double* out);
 
+/*
+ * The calibrated table of jt_get_clique, written to DEVICE memory without
+ * allocating anything: no cudaMalloc, cudaFree or allocating library call,
+ * so callers that must not allocate device memory can use it -- code that
+ * runs while another component owns the device's memory (a fixed-size
+ * arena or pool handed out up front), or a latency-critical serving path
+ * whose policy forbids allocation (an allocation can synchronise the device
+ * or fail under memory pressure).  The paper has no counterpart; it is a
+ * read-out variant of the library.
+ *
+ * `out_device`: clique-size doubles of device memory owned by the caller,
+ * filled with P(x_C | e) in the caller's listed variable order.  The work is
+ * enqueued on `stream` (ordered after the last propagation) and the call
+ * returns without waiting; check jt_get_status for the case before using the
+ * values.  The normalising sum goes through a scratch array that lives in
+ * the library for as long as it is loaded (every GPU that loads the library
+ * holds it): the first call on a device looks its address up, so make that
+ * first call before any stream capture.  Every call shares that array:
+ * calls whose work overlaps on the GPU (different streams, no ordering)
+ * race and give wrong results.  Cliques of more than 4,194,304 entries are
+ * rejected with JT_ERR_UNSUPPORTED; JT_ERR_STATE as jt_get_clique.
+ */
+jt_status jt_get_clique_noalloc(jt_tree t, int32_t case_id, int32_t clique, double* out_device, void* stream);
+
 /* Sizes and schedule facts of a loaded tree. */
 typedef struct {
   int32_t n_vars, n_cliques, depth;  /* depth = largest clique depth (root 0) */

@@ -89,6 +89,7 @@ struct jt_tree_s {
   std::vector<uint8_t> dirty;     // host mirror row newer than the device row
   std::vector<uint8_t> ready;     // a propagation covered the case since its evidence changed
   cudaEvent_t upload_done = nullptr;
+  cudaEvent_t readout_ready = nullptr;  // orders the allocation-free read-out after a propagation
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   std::map<std::pair<int, int>, GraphEntry> graphs;
@@ -126,6 +127,7 @@ void destroy(jt_tree t) {
     if (p) cudaFree(p);
   if (t->h_ev) cudaFreeHost(t->h_ev);
   if (t->upload_done) cudaEventDestroy(t->upload_done);
+  if (t->readout_ready) cudaEventDestroy(t->readout_ready);
   if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
   delete t;
 }
@@ -362,6 +364,28 @@ jt_status upload_dirty(jt_tree t, int first, int n, cudaStream_t s) {
   return JT_OK;
 }
 
+// Read-out geometry of a clique: listed cardinalities and the permuted stride
+// of each listed position.
+CliqueOut clique_out(const Plan& p, int clique) {
+  CliqueOut co{};
+  co.n = (int32_t)p.n_entries[clique];
+  co.k = (int32_t)p.vars[clique].size();
+  const auto& lv = p.vars[clique];
+  const auto& pv = p.pvars[clique];
+  std::vector<int64_t> pst(pv.size());
+  int64_t s = 1;
+  for (int i = (int)pv.size() - 1; i >= 0; --i) {
+    pst[i] = s;
+    s *= p.card[pv[i]];
+  }
+  for (int i = 0; i < co.k; ++i) {
+    co.lcard[i] = p.card[lv[i]];
+    for (int j = 0; j < co.k; ++j)
+      if (pv[j] == lv[i]) co.pst[i] = (int32_t)pst[j];
+  }
+  return co;
+}
+
 }  // namespace
 
 extern "C" {
@@ -441,6 +465,8 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   if ((e = cudaEventCreateWithFlags(&raw->upload_done, cudaEventDisableTiming)) != cudaSuccess)
     return bail(cuda_fail(e, "event"));
   if ((e = cudaEventRecord(raw->upload_done, s)) != cudaSuccess) return bail(cuda_fail(e, "event"));
+  if ((e = cudaEventCreateWithFlags(&raw->readout_ready, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(cuda_fail(e, "event"));
   if ((e = cudaStreamCreateWithFlags(&raw->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(e, "stream"));
   raw->last_stream = s;
@@ -667,22 +693,7 @@ jt_status jt_get_clique(jt_tree t, int32_t case_id, int32_t clique, double* out)
     return fail(JT_ERR_INVALID_ARG, "bad case, clique or output");
   if (!(t->flags & JT_MATERIALIZE_CLIQUES)) return fail(JT_ERR_STATE, "tree loaded without JT_MATERIALIZE_CLIQUES");
   if (!t->ready[case_id]) return fail(JT_ERR_STATE, "case not propagated since its evidence changed");
-  CliqueOut co{};
-  co.n = (int32_t)p.n_entries[clique];
-  co.k = (int32_t)p.vars[clique].size();
-  const auto& lv = p.vars[clique];
-  const auto& pv = p.pvars[clique];
-  std::vector<int64_t> pst(pv.size());
-  int64_t s = 1;
-  for (int i = (int)pv.size() - 1; i >= 0; --i) {
-    pst[i] = s;
-    s *= p.card[pv[i]];
-  }
-  for (int i = 0; i < co.k; ++i) {
-    co.lcard[i] = p.card[lv[i]];
-    for (int j = 0; j < co.k; ++j)
-      if (pv[j] == lv[i]) co.pst[i] = (int32_t)pst[j];
-  }
+  const CliqueOut co = clique_out(p, clique);
   cudaStream_t strm = t->last_stream;
   const int64_t off = (int64_t)case_id * p.base_len + p.base_off[clique];
   cudaError_t e = t->compute == JT_F64
@@ -697,6 +708,32 @@ jt_status jt_get_clique(jt_tree t, int32_t case_id, int32_t clique, double* out)
   int32_t code = 0;
   if ((st = case_status(t, case_id, &code)) != JT_OK) return st;
   if (code != JT_OK) return fail((jt_status)code, "case has no posterior");
+  return JT_OK;
+}
+
+jt_status jt_get_clique_noalloc(jt_tree t, int32_t case_id, int32_t clique, double* out_device, void* stream) {
+  jt_status st = check_tree(t);
+  if (st != JT_OK) return st;
+  const Plan& p = t->plan;
+  if (case_id < 0 || case_id >= t->max_cases || clique < 0 || clique >= p.n_cliques || !out_device)
+    return fail(JT_ERR_INVALID_ARG, "bad case, clique or output");
+  if (p.n_entries[clique] > kNoAllocMaxEntries)
+    return fail(JT_ERR_UNSUPPORTED, "clique has " + std::to_string(p.n_entries[clique]) +
+                                        " entries; the allocation-free read-out handles at most " +
+                                        std::to_string(kNoAllocMaxEntries));
+  if (!(t->flags & JT_MATERIALIZE_CLIQUES)) return fail(JT_ERR_STATE, "tree loaded without JT_MATERIALIZE_CLIQUES");
+  if (!t->ready[case_id]) return fail(JT_ERR_STATE, "case not propagated since its evidence changed");
+  const CliqueOut co = clique_out(p, clique);
+  cudaStream_t strm = (cudaStream_t)stream;
+  if (strm != t->last_stream) {  // after the propagation that wrote the table (event made at load)
+    CU(cudaEventRecord(t->readout_ready, t->last_stream), "read-out ordering");
+    CU(cudaStreamWaitEvent(strm, t->readout_ready, 0), "read-out ordering");
+  }
+  const int64_t off = (int64_t)case_id * p.base_len + p.base_off[clique];
+  cudaError_t e = t->compute == JT_F64
+                      ? launch_get_clique_noalloc<double>((const double*)t->d_calib + off, co, out_device, strm)
+                      : launch_get_clique_noalloc<float>((const float*)t->d_calib + off, co, out_device, strm);
+  if (e != cudaSuccess) return cuda_fail(e, "allocation-free clique read-out");
   return JT_OK;
 }
 

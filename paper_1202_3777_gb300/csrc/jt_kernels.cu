@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "jt_kernels.h"
 
@@ -1336,6 +1337,55 @@ __global__ void k_clique_gather(const T* p, CliqueOut co, const double* sum, dou
   }
 }
 
+// ---- clique read-out without allocation ------------------------------------
+// Scratch of the allocation-free read-out: one partial sum per CTA of the
+// first pass.  Every call shares it (calls that overlap on the GPU race); it
+// lives as long as the library is loaded on a device.
+__device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
+
+// Pass 1: CTA b sums entries [b * E, (b + 1) * E) of the table into partials[b]
+// (every slot in use is overwritten, so nothing needs clearing).
+template <typename T>
+__global__ void __launch_bounds__(256) k_clique_partials(const T* p, int64_t n, double* partials) {
+  __shared__ double red[8];
+  const int64_t e0 = (int64_t)blockIdx.x * kNoAllocPerBlock;
+  const int64_t e1 = min(n, e0 + kNoAllocPerBlock);
+  double s = 0.0;
+  for (int64_t i = e0 + threadIdx.x; i < e1; i += 256) s += (double)p[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// Pass 2: every CTA adds the partials (at most kNoAllocMaxBlocks), then
+// writes its share of the normalised table in the caller's listed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_clique_gather_partials(const T* p, CliqueOut co, const double* partials,
+                                                                int nb, double* out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 256) s += partials[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double z = 0.0;
+  for (int i = 0; i < 8; ++i) z += red[i];
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < co.n; u += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = u, src = 0;
+    for (int i = co.k - 1; i >= 0; --i) {
+      const int64_t d = rem % co.lcard[i];
+      rem /= co.lcard[i];
+      src += d * co.pst[i];
+    }
+    out[u] = z > 0.0 ? (double)p[src] / z : NAN;
+  }
+}
+
 template <typename T, int CB>
 void set_attrs_once() {
   static bool done = false;
@@ -1390,6 +1440,41 @@ cudaError_t launch_get_clique(const T* calib_clique, const CliqueOut& co, double
   return cudaGetLastError();
 }
 
+// Device address of the read-out scratch on the current device, looked up
+// once per device (with that device current) and cached.
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_get_clique_noalloc(const T* calib_clique, const CliqueOut& co, double* out_dev, cudaStream_t s) {
+  double* partials = nullptr;
+  cudaError_t e = noalloc_scratch(&partials);
+  if (e != cudaSuccess) return e;
+  const int nb = (int)((co.n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+  k_clique_partials<T><<<nb, 256, 0, s>>>(calib_clique, (int64_t)co.n, partials);
+  const int blocks = (int)std::min<int64_t>(1024, (co.n + 255) / 256);
+  k_clique_gather_partials<T><<<blocks, 256, 0, s>>>(calib_clique, co, partials, nb, out_dev);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_get_clique_noalloc<float>(const float*, const CliqueOut&, double*, cudaStream_t);
+template cudaError_t launch_get_clique_noalloc<double>(const double*, const CliqueOut&, double*, cudaStream_t);
 template cudaError_t launch_propagate<float>(const PropArgs<float>&, int, int, int, cudaStream_t);
 template cudaError_t launch_propagate<double>(const PropArgs<double>&, int, int, int, cudaStream_t);
 template cudaError_t launch_finalize<float>(const FinalArgs<float>&, cudaStream_t);

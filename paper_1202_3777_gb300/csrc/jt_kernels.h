@@ -77,6 +77,17 @@ template <typename T>
 cudaError_t launch_get_clique(const T* calib_clique, const CliqueOut& co, double* out_dev,
                               double* sum_dev, cudaStream_t s);
 
+// Allocation-free calibrated-clique read-out (jt_get_clique_noalloc): the
+// normalising sum is reduced through a file-scope device array of
+// kNoAllocMaxBlocks partial sums, one per kNoAllocPerBlock table entries, so
+// tables of at most kNoAllocMaxEntries entries are accepted.
+constexpr int kNoAllocMaxBlocks = 1024;
+constexpr int kNoAllocPerBlock = 4096;
+constexpr int64_t kNoAllocMaxEntries = (int64_t)kNoAllocMaxBlocks * kNoAllocPerBlock;
+constexpr int kNoAllocMaxDevices = 64;
+template <typename T>
+cudaError_t launch_get_clique_noalloc(const T* calib_clique, const CliqueOut& co, double* out_dev, cudaStream_t s);
+
 // Maximum dynamic shared memory per CTA the kernels may use on this device
 // with `ctas_per_sm` resident CTAs per SM.
 int32_t smem_budget(int device, int ctas_per_sm = 1);

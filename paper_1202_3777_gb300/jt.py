@@ -82,6 +82,7 @@ _sig = {
     "jt_get_log_evidence": (C.c_int, [_vp, _i32, _i32, _vp, _i32, _vp]),
     "jt_get_status": (C.c_int, [_vp, _i32, _i32, _vp]),
     "jt_get_clique": (C.c_int, [_vp, _i32, _i32, _vp]),
+    "jt_get_clique_noalloc": (C.c_int, [_vp, _i32, _i32, _vp, _vp]),
     "jt_get_info": (C.c_int, [_vp, C.POINTER(jt_tree_info)]),
     "jt_free": (None, [_vp]),
     "jt_strerror": (C.c_char_p, [C.c_int]),
@@ -255,6 +256,14 @@ def jt_get_status(t: Tree, first_case: int, n_cases: int) -> np.ndarray:
 def jt_get_clique(t: Tree, case_id: int, clique: int, size: int) -> np.ndarray:
     out = np.empty(size, dtype=np.float64)
     _check(_lib.jt_get_clique(t.handle, case_id, clique, _ptr(out)), "jt_get_clique")
+    return out
+
+
+def jt_get_clique_noalloc(t: Tree, case_id: int, clique: int, out, stream=None):
+    """Allocation-free read-out into ``out``, a torch float64 CUDA tensor of
+    the clique's size (enqueued only)."""
+    _check(_lib.jt_get_clique_noalloc(t.handle, case_id, clique, C.c_void_p(out.data_ptr()), _stream(stream)),
+           "jt_get_clique_noalloc")
     return out
 
 
