@@ -169,12 +169,58 @@ def run_reference(args, rank, world):
     return 0
 
 
+def measure_serving(rank):
+    """Continuous batching over the four resident trees (small, large-clique,
+    high-cardinality, 1024-clique binary): a burst of queries gives the
+    sustained rate, then Poisson arrivals at half of it give p50/p99 latency."""
+    from paper_1202_3777_gb300 import serve
+    trees = {
+        "small": synth.small_tree().as_dtype(np.float32),
+        "large_clique": synth.large_clique_tree().as_dtype(np.float32),
+        "high_card": synth.high_card_tree().as_dtype(np.float32),
+        "binary": synth.binary_serving_tree().as_dtype(np.float32),
+    }
+    srv = serve.Server(trees, budget_bytes=60 << 30, max_batch=64)
+    srv.warm_up()
+    work = {n: r.work for n, r in srv.trees.items()}
+    names = list(trees)
+    rng = np.random.default_rng(20000 + rank)
+
+    def queries(n, base):
+        out = []
+        for i in range(n):
+            name = names[rng.integers(len(names))]
+            ev = synth.evidence_matrix(trees[name], 1, (0.01, 0.20), base + i)[0]
+            out.append(serve.Query(base + i, name, ev))
+        return out
+
+    burst = queries(512, 30000)
+    srv.completed = []
+    done = srv.run_arrivals([(0.0, q) for q in burst])
+    burst_s = max(q.done for q in done) - min(q.arrival for q in done)
+    rate = len(done) / burst_s
+    srv.completed = []
+    load = 0.5
+    qs = queries(int(load * rate * 1.5) + 1, 40000)
+    t, arr = 0.0, []
+    for q in qs:
+        t += rng.exponential(1.0 / (load * rate))
+        arr.append((t, q))
+    done = srv.run_arrivals(arr)
+    summ = serve.latency_summary(done, work)
+    srv.free()
+    return {"trees": names, "budget_gb": 60, "max_batch": 64, "burst_queries_per_s": rate,
+            "offered_queries_per_s": load * rate, "burst_clique_entries_per_s": sum(work[q.tree] for q in burst) / burst_s,
+            **summ}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -260,10 +306,11 @@ def main():
     streamed = 2 * entries - root_entries   # collect reads every non-root table, distribute every table
 
     def alg_bytes(cases):
-        # every clique table read once per pass and per block of 8 cases,
-        # plus per case: messages written and read in each pass
-        n_cb = (cases + 7) // 8
-        return w * streamed * n_cb + cases * w * (4 * msg_total(tree) + info.marginal_len)
+        # per case: every clique table read once per pass (the root's collect
+        # total comes from its distribute pass), messages written and read in
+        # each pass; a batch of cases counts each case's bytes (the kernel
+        # shares each table read among a block of 8 cases)
+        return cases * (w * streamed + w * (4 * msg_total(tree) + info.marginal_len))
 
     ach_b = alg_bytes(B) / (prof_b[0] * 1e-3) / 1e9
     ach_1 = alg_bytes(1) / (prof_1[0] * 1e-3) / 1e9
@@ -286,6 +333,10 @@ def main():
     total_cases = B * world
     value = W * total_cases / (step_ms * 1e-3)
     plain_value = W * world / (plain_ms * 1e-3)
+    h.free()
+    serving = None
+    if not args.no_serving:
+        serving = measure_serving(rank)
     if rank != 0:
         return 0
     cpu = None
@@ -314,6 +365,7 @@ def main():
         "finalize_ms": {"batched": float(prof_b[1]), "plain": float(prof_1[1])},
         "e2e": {"value": W * total_cases / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(ev.nbytes), "d2h_bytes_per_step": int(md.nbytes + lzh.nbytes)},
+        "serving": serving,
         "gpu_launches": int(2 * args.steps),   # k_propagate + k_finalize per step
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -201,6 +201,7 @@ typedef struct {
   int64_t work_per_case;             /* sum over the 2(n-1) messages of |phi_src| + |phi_dst| (Eq. 4 numerator) */
   int64_t marginal_len;              /* sum_v card[v] */
   int64_t device_bytes;              /* device memory held by the tree */
+  int64_t case_bytes;                /* of which per evidence-case slot (messages, evidence, results) */
   int32_t max_cases;
   jt_dtype compute;
   uint32_t flags;

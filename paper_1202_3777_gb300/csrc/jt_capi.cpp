@@ -746,6 +746,13 @@ jt_status jt_get_info(jt_tree t, jt_tree_info* out) {
   out->work_per_case = t->plan.work_per_case;
   out->marginal_len = t->plan.marg_total;
   out->device_bytes = t->device_bytes;
+  {
+    const Plan& p = t->plan;
+    int64_t cb = p.msg_stride * (int64_t)t->elem + 2ll * p.n_cliques * 8 + 4 + (int64_t)p.marg_total * 8 + 8 +
+                 (int64_t)p.n_vars * 2 + 2ll * p.n_cliques * 4;
+    if (t->flags & JT_MATERIALIZE_CLIQUES) cb += p.base_len * (int64_t)t->elem;
+    out->case_bytes = cb;
+  }
   out->max_cases = t->max_cases;
   out->compute = t->compute;
   out->flags = t->flags;

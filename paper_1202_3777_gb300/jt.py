@@ -63,7 +63,7 @@ class jt_tree_info(C.Structure):
     _fields_ = [
         ("n_vars", C.c_int32), ("n_cliques", C.c_int32), ("depth", C.c_int32),
         ("entries", C.c_int64), ("work_per_case", C.c_int64), ("marginal_len", C.c_int64),
-        ("device_bytes", C.c_int64), ("max_cases", C.c_int32), ("compute", C.c_int),
+        ("device_bytes", C.c_int64), ("case_bytes", C.c_int64), ("max_cases", C.c_int32), ("compute", C.c_int),
         ("flags", C.c_uint32),
     ]
 

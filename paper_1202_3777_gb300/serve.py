@@ -1,0 +1,186 @@
+"""Continuous-batching server over several resident junction trees.
+
+Queries (a tree and its evidence) arrive over time.  Each tree is loaded
+once and keeps its potentials on the device; it owns one CUDA stream and a
+number of evidence-case slots sized to a device-memory budget.  Whenever a
+tree's previous batch has finished, every query waiting for that tree (up to
+its slots) is admitted into the next batch: its evidence is copied into the
+slots and one jt_propagate covers the batch, so queries that arrive while
+other work is on the GPU join the next batch.  Batches of different trees run
+concurrently on their own streams.  Per query the server records arrival and
+completion times, from which p50/p99 latency follow.
+
+This module only schedules: every step of a propagation runs in libjt's
+kernels (jt_set_evidence_dense, jt_propagate, jt_get_marginals,
+jt_get_log_evidence, jt_get_status).
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import jt as _jt
+
+
+def batch_size_class(n: int) -> int:
+    """Slots a batch of n queries occupies: 1, or n rounded up to a multiple
+    of 8 (the library propagates cases in blocks of 8, so the padding adds no
+    work and keeps the number of recorded propagation shapes small)."""
+    if n <= 1:
+        return 1
+    return (n + 7) // 8 * 8
+
+
+def slots_within_budget(budget_bytes: int, table_bytes: int, case_bytes: int, max_batch: int) -> int:
+    """Evidence-case slots a tree may keep when its tables take table_bytes of
+    budget_bytes and every slot takes case_bytes (0 if even one slot does not
+    fit)."""
+    room = budget_bytes - table_bytes
+    if room < case_bytes:
+        return 0
+    n = min(max_batch, room // max(1, case_bytes))
+    if n >= 8:
+        n = n // 8 * 8
+    return int(n)
+
+
+@dataclass
+class Query:
+    qid: int
+    tree: str
+    states: np.ndarray               # int16 [n_vars], -1 = unobserved
+    arrival: float = 0.0
+    done: float = 0.0
+    marginals: Optional[np.ndarray] = None
+    log_z: float = float("nan")
+    status: int = -1
+
+
+@dataclass
+class _Resident:
+    name: str
+    handle: object
+    n_vars: int
+    slots: int
+    stream: object
+    work: int                        # clique entries per case (Eq. 4 numerator)
+    queue: collections.deque = field(default_factory=collections.deque)
+    batch: List[Query] = field(default_factory=list)
+    event: object = None
+
+
+class Server:
+    """Keeps trees resident and serves queries with continuous batching.
+
+    trees: name -> synth.Tree (or any object with card, cliques, parent,
+    pot); budget_bytes bounds the device memory of all trees together;
+    max_batch bounds the slots of one tree."""
+
+    def __init__(self, trees: Dict[str, object], budget_bytes: int = 60 << 30, max_batch: int = 64,
+                 compute: int = _jt.JT_F32):
+        import torch
+        self._torch = torch
+        self.trees: Dict[str, _Resident] = {}
+        used = 0
+        for name, tree in trees.items():
+            h = _jt.jt_load_synth(tree, compute=compute, max_cases=max_batch)
+            info = h.info
+            if used + info.device_bytes > budget_bytes:
+                # admission by memory: keep as many slots as the budget allows
+                table_bytes = int(info.device_bytes - max_batch * info.case_bytes)
+                slots = slots_within_budget(budget_bytes - used, table_bytes, int(info.case_bytes), max_batch)
+                h.free()
+                if slots == 0:
+                    raise MemoryError(f"tree {name} does not fit in the remaining device-memory budget")
+                h = _jt.jt_load_synth(tree, compute=compute, max_cases=slots)
+            slots = int(h.info.max_cases)
+            used += int(h.info.device_bytes)
+            self.trees[name] = _Resident(name, h, int(h.info.n_vars), slots, torch.cuda.Stream(),
+                                         int(h.info.work_per_case))
+        self.device_bytes = used
+        self.completed: List[Query] = []
+
+    def warm_up(self):
+        """Record every batch shape once (propagation graphs are built on first use)."""
+        for r in self.trees.values():
+            sizes = sorted({batch_size_class(n) for n in range(1, r.slots + 1)})
+            for n in sizes:
+                _jt.jt_set_evidence_dense(r.handle, 0, np.full((n, r.n_vars), -1, np.int16), stream=r.stream)
+                _jt.jt_propagate(r.handle, 0, n, r.stream)
+            r.stream.synchronize()
+
+    def submit(self, q: Query, now: Optional[float] = None):
+        q.arrival = time.perf_counter() if now is None else now
+        self.trees[q.tree].queue.append(q)
+
+    def _finish(self, r: _Resident):
+        n = len(r.batch)
+        m = _jt.jt_get_marginals(r.handle, 0, n, stream=r.stream)
+        lz = _jt.jt_get_log_evidence(r.handle, 0, n, stream=r.stream)
+        st = _jt.jt_get_status(r.handle, 0, n)
+        t = time.perf_counter()
+        for i, q in enumerate(r.batch):
+            q.marginals, q.log_z, q.status, q.done = m[i], float(lz[i]), int(st[i]), t
+            self.completed.append(q)
+        r.batch, r.event = [], None
+
+    def _launch(self, r: _Resident):
+        take = min(len(r.queue), r.slots)
+        batch = [r.queue.popleft() for _ in range(take)]
+        n = batch_size_class(take)
+        ev = np.full((n, r.n_vars), -1, np.int16)
+        for i, q in enumerate(batch):
+            ev[i] = q.states
+        _jt.jt_set_evidence_dense(r.handle, 0, ev, stream=r.stream)
+        _jt.jt_propagate(r.handle, 0, n, r.stream)
+        r.event = self._torch.cuda.Event()
+        r.event.record(r.stream)
+        r.batch = batch
+
+    def poll(self) -> int:
+        """Finish completed batches and start the next batch of every idle
+        tree with waiting queries; returns the number of batches in flight."""
+        busy = 0
+        for r in self.trees.values():
+            if r.event is not None and r.event.query():
+                self._finish(r)
+            if r.event is None and r.queue:
+                self._launch(r)
+            busy += r.event is not None
+        return busy
+
+    def drain(self):
+        while self.poll() or any(r.queue for r in self.trees.values()):
+            pass
+
+    def run_arrivals(self, arrivals: List[tuple]):
+        """Serve (offset_seconds, Query) arrivals in real time: each query is
+        submitted once its offset has passed; returns the completed queries."""
+        arrivals = sorted(arrivals, key=lambda a: a[0])
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(arrivals) or self.poll() or any(r.queue for r in self.trees.values()):
+            now = time.perf_counter() - t0
+            while i < len(arrivals) and arrivals[i][0] <= now:
+                self.submit(arrivals[i][1], t0 + arrivals[i][0])
+                i += 1
+        return self.completed
+
+    def free(self):
+        for r in self.trees.values():
+            r.handle.free()
+        self.trees = {}
+
+
+def latency_summary(queries: List[Query], work: Dict[str, int]) -> dict:
+    """p50/p99 latency (ms), throughput in clique entries per second."""
+    lat = np.array([q.done - q.arrival for q in queries]) * 1e3
+    span = max(q.done for q in queries) - min(q.arrival for q in queries)
+    entries = sum(work[q.tree] for q in queries)
+    return {"queries": len(queries), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "clique_entries_per_s": entries / span if span > 0 else float("nan"), "span_s": span}
