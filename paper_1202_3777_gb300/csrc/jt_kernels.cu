@@ -470,10 +470,10 @@ __device__ __forceinline__ bool bulk_window(const DevStage& S, const DevPort& P)
 // consumers when pfull[b] completes (including the copies' bytes).
 template <typename T, int CB>
 __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0) {
-  constexpr unsigned kMask = 0xfffffffcu;   // lanes 2..31
-  constexpr int NL = 30;
+  constexpr unsigned kMask = kFull;         // the whole preparation warp
+  constexpr int NL = 32;
   constexpr int U = 4;                      // tasks per lane per round (their loads in flight together)
-  const int pl = (int)(threadIdx.x & 31) - 2;  // 0..29
+  const int pl = (int)(threadIdx.x & 31);
   for (uint32_t slot = 0;; ++slot) {
     const uint32_t b = slot & 1u, par = (slot >> 1) & 1u;
     bool ok = mbar_wait(s0.ifull + b, par, a.err, s0.misc);
@@ -797,13 +797,13 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
   uint64_t waited = 0;
   for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
     const uint32_t st = rp.st;
-    const uint64_t tw = (a.trace != nullptr && tid == 0) ? global_ns() : 0;
+    const uint64_t tw = (a.trace != nullptr && lane == 0) ? global_ns() : 0;
     // the warp leaves together (its lanes reduce with shuffles below)
     if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc))) {
       ok = false;
       break;
     }
-    if (a.trace != nullptr && tid == 0) waited += global_ns() - tw;
+    if (a.trace != nullptr && lane == 0) waited += global_ns() - tw;
     const uint32_t sb = ring32 + st * CH * (uint32_t)sizeof(T);
     const uint32_t cbase = (uint32_t)ci * CH;
     const int nvec = (int)(min((uint32_t)w.n - cbase, CH) / VEC);
@@ -951,7 +951,10 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     __syncwarp();
     if (lane == 0) mbar_arrive(s.empty + st);
   }
-  if (a.trace != nullptr && tid == 0) a.trace[(int64_t)s.misc[2] * kTraceSlots + 6] = waited;
+  // average over the consumer warps of the time spent waiting for chunks
+  if (a.trace != nullptr && lane == 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.trace + (int64_t)s.misc[2] * kTraceSlots + 6),
+              (unsigned long long)(waited / (NT / 32)));
   if (!__all_sync(kFull, ok)) return false;
   // flush the register accumulators (inactive lanes hold zeros)
   if (ra >= 0) {
@@ -1222,7 +1225,7 @@ __device__ __forceinline__ void consumer(const PropArgs<T>& a, const Smem& s0) {
 }
 
 template <typename T, int CB>
-__global__ void __launch_bounds__(consumers_for(CB) + 32, ctas_per_sm_for(CB)) k_propagate(const PropArgs<T> a) {
+__global__ void __launch_bounds__(consumers_for(CB) + kControlThreads, ctas_per_sm_for(CB)) k_propagate(const PropArgs<T> a) {
   constexpr int NT = consumers_for(CB);
   extern __shared__ __align__(128) unsigned char smem[];
   const SmemLayout L(CB, a.ring, a.chunk, a.max_k, a.max_ports, a.max_fields, a.win_max, (int)sizeof(T));
@@ -1247,10 +1250,16 @@ __global__ void __launch_bounds__(consumers_for(CB) + 32, ctas_per_sm_for(CB)) k
   }
   __syncthreads();
   if (threadIdx.x >= NT) {
-    const int l = threadIdx.x - NT;
-    if (l == 0) producer<T>(a, s);
-    else if (l == 1) signaller<T, CB>(a, s);
-    else prep_lanes<T, CB>(a, s);
+    // control warps: each role has a warp of its own, so no role's waits
+    // (a blocking bulk-group wait, a sleeping poll) hold up another
+    const int cw = (threadIdx.x - NT) >> 5, l = threadIdx.x & 31;
+    if (cw == 0) {
+      if (l == 0) producer<T>(a, s);
+    } else if (cw == 1) {
+      if (l == 0) signaller<T, CB>(a, s);
+    } else {
+      prep_lanes<T, CB>(a, s);
+    }
     __syncwarp();
   } else {
     consumer<T, CB>(a, s);
@@ -1415,10 +1424,10 @@ cudaError_t launch_propagate(const PropArgs<T>& a, int cb, int grid, int smem, c
   if (grid <= 0) return cudaSuccess;
   if (cb <= 1) {
     set_attrs_once<T, 1>();
-    k_propagate<T, 1><<<grid, consumers_for(1) + 32, smem, s>>>(a);
+    k_propagate<T, 1><<<grid, consumers_for(1) + kControlThreads, smem, s>>>(a);
   } else {
     set_attrs_once<T, 8>();
-    k_propagate<T, 8><<<grid, consumers_for(8) + 32, smem, s>>>(a);
+    k_propagate<T, 8><<<grid, consumers_for(8) + kControlThreads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -15,6 +15,7 @@ __host__ __device__ constexpr int ctas_per_sm_for(int cb) { return cb > 0 ? 1 : 
 // Bytes per bulk-copy stage (two vectors per consumer thread per stage).
 __host__ __device__ constexpr int chunk_bytes_for(int cb) { return cb > 0 ? 16384 : 16384; }
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
+constexpr int kControlThreads = 96;             // producer, signalling and preparation warps
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
 constexpr int kMaxIter = 64;                    // consumer iterations of one fast-path block
 
