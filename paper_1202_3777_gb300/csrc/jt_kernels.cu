@@ -633,25 +633,27 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
             continue;
           }
           const T* row = a.msg + (int64_t)cs * a.msg_stride + P.tab + kb;
-          double sc = 0.0;
+          T sc = T(0);
           if (P.kind == kPortRho) {
             const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
             const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
-            sc = dp > 0.0 ? sgc / dp : 0.0;
+            sc = dp > 0.0 ? (T)(sgc / dp) : T(0);
           }
+          // per entry in the element type (the messages are stored in it;
+          // FP64 issue is scarce on this part)
           for (int i0 = pl; i0 < P.K; i0 += U * NL) {
-            double u[U], d[U];
+            T u[U], d[U];
 #pragma unroll
             for (int r = 0; r < U; ++r) {
               const int ii = i0 + r * NL;
-              u[r] = ii < P.K ? (double)__ldcg(row + ii) : 0.0;
-              d[r] = (ii < P.K && P.kind == kPortRho) ? (double)__ldcg(row + a.delta_off + ii) : 0.0;
+              u[r] = ii < P.K ? __ldcg(row + ii) : T(0);
+              d[r] = (ii < P.K && P.kind == kPortRho) ? __ldcg(row + a.delta_off + ii) : T(0);
             }
 #pragma unroll
             for (int r = 0; r < U; ++r) {
               const int ii = i0 + r * NL;
               if (ii >= P.K) continue;
-              const T v = P.kind == kPortMu ? (T)u[r] : (T)(u[r] > 0.0 ? d[r] * sc / u[r] : 0.0);
+              const T v = P.kind == kPortMu ? u[r] : (u[r] > T(0) ? d[r] * sc / u[r] : T(0));
               sst<T>(dst + (uint32_t)ii * (uint32_t)sizeof(T), v);
             }
           }
@@ -1136,10 +1138,12 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
 
   // block totals (stage total, block-constant outputs); windows that are not
   // bulk-reduced by the signalling lane
+  // (lanes reduce in the element type -- FP64 issue is scarce on this part;
+  // the warps' partials are added in double)
 #pragma unroll
   for (int cl = 0; cl < CB; ++cl) {
-    const double v = warp_sum((double)tot[cl]);
-    if (lane == 0) s.red[cl * (NT / 32) + warp] = v;
+    const T v = warp_sum(tot[cl]);
+    if (lane == 0) s.red[cl * (NT / 32) + warp] = (double)v;
   }
   consumer_sync<NT>();
   if (tid < ncb) {
