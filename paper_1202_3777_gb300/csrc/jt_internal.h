@@ -73,6 +73,7 @@ struct DevPos {       // one digit (position) of a clique's permuted layout
   int32_t pad;
 };
 
+constexpr int32_t kVmodeStore = 4;
 struct DevPort {
   int32_t kind;       // kPort*
   int32_t tab;        // offset of the table in the per-case message array
@@ -85,7 +86,8 @@ struct DevPort {
   int32_t f0;         // first field (index relative to the stage's first field)
   uint32_t lane_free; // fast path: lane bits the key does not depend on
   int32_t vmode;      // fast path: a vector's entries have keys key0 + dvec[j]: 0 = all dvec 0,
-                      // 1 = dvec[j] = j, 2 = other
+                      // 1 = dvec[j] = j, 2 = other; | kVmodeStore: an output whose window
+                      // has one entry per block entry (no two entries share a key)
   int32_t dvec[4];    // fast path: key offsets of the entries of a vector
   int32_t iter_dep;   // fast path: bit 0: the key depends on the iteration bits (entry bits above
                       // the thread's vector index); bit 1: on the chunk bits (above one chunk)

@@ -95,6 +95,13 @@ __device__ __forceinline__ void sld_vec(uint32_t a, float (&x)[4]) {
 __device__ __forceinline__ void sld_vec(uint32_t a, double (&x)[2]) {
   asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x[0]), "=d"(x[1]) : "r"(a));
 }
+__device__ __forceinline__ void sst_vec(uint32_t a, const float (&x)[4]) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x[0]), "f"(x[1]), "f"(x[2]), "f"(x[3])
+               : "memory");
+}
+__device__ __forceinline__ void sst_vec(uint32_t a, const double (&x)[2]) {
+  asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(x[0]), "d"(x[1]) : "memory");
+}
 template <typename T>
 __device__ __forceinline__ void sst(uint32_t a, T v);
 template <>
@@ -261,6 +268,69 @@ __device__ __forceinline__ void add_combined(uint32_t tab, uint32_t key, T v, in
   } else if (v != T(0)) {
     sred_add(tab + key * (uint32_t)sizeof(T), v);
   }
+}
+
+// Add the entries of a vector (keys ka + dva[j]) summed over the lanes that
+// differ from this one only in the bits of `lf` (lanes that share the keys).
+// Instead of one butterfly per entry, the first free lane bit halves the
+// entries each lane carries, the second halves them again, and the remaining
+// bits reduce the one entry left: 6 shuffles and one atomic per lane group
+// for four entries and five free bits, where separate butterflies take 20
+// shuffles and four atomics.  `ka` is the group's lowest lane's (that lane
+// is active whenever any lane of the group is).
+__device__ __forceinline__ void scatter_vec(uint32_t ka, const float (&v)[4], uint32_t lf, int lane, bool act,
+                                            const int4 dv) {
+  if (lf == 0u) {
+    if (act) {
+      if (v[0] != 0.f) sred_add(ka + (uint32_t)dv.x * 4u, v[0]);
+      if (v[1] != 0.f) sred_add(ka + (uint32_t)dv.y * 4u, v[1]);
+      if (v[2] != 0.f) sred_add(ka + (uint32_t)dv.z * 4u, v[2]);
+      if (v[3] != 0.f) sred_add(ka + (uint32_t)dv.w * 4u, v[3]);
+    }
+    return;
+  }
+  const uint32_t m1 = lf & (0u - lf);
+  const bool h1 = (lane & m1) != 0u;
+  float s0 = h1 ? v[2] : v[0], s1 = h1 ? v[3] : v[1];
+  s0 += __shfl_xor_sync(kFull, h1 ? v[0] : v[2], m1);
+  s1 += __shfl_xor_sync(kFull, h1 ? v[1] : v[3], m1);
+  // this lane now carries entries (0, 1) or (2, 3)
+  const int d0 = h1 ? dv.z : dv.x, d1 = h1 ? dv.w : dv.y;
+  uint32_t rest = lf & ~m1;
+  if (rest == 0u) {
+    if (s0 != 0.f) sred_add(ka + (uint32_t)d0 * 4u, s0);
+    if (s1 != 0.f) sred_add(ka + (uint32_t)d1 * 4u, s1);
+    return;
+  }
+  const uint32_t m2 = rest & (0u - rest);
+  const bool h2 = (lane & m2) != 0u;
+  float t = h2 ? s1 : s0;
+  t += __shfl_xor_sync(kFull, h2 ? s0 : s1, m2);
+  const int dj = h2 ? d1 : d0;
+  rest &= ~m2;
+#pragma unroll
+  for (int b = 1; b < 32; b <<= 1)
+    if (rest & (uint32_t)b) t += __shfl_xor_sync(kFull, t, b);
+  if ((lane & rest) == 0u && t != 0.f) sred_add(ka + (uint32_t)dj * 4u, t);
+}
+__device__ __forceinline__ void scatter_vec(uint32_t ka, const double (&v)[2], uint32_t lf, int lane, bool act,
+                                            const int4 dv) {
+  if (lf == 0u) {
+    if (act) {
+      if (v[0] != 0.0) sred_add(ka + (uint32_t)dv.x * 8u, v[0]);
+      if (v[1] != 0.0) sred_add(ka + (uint32_t)dv.y * 8u, v[1]);
+    }
+    return;
+  }
+  const uint32_t m1 = lf & (0u - lf);
+  const bool h1 = (lane & m1) != 0u;
+  double t = h1 ? v[1] : v[0];
+  t += __shfl_xor_sync(kFull, h1 ? v[0] : v[1], m1);
+  const uint32_t rest = lf & ~m1;
+#pragma unroll
+  for (int b = 1; b < 32; b <<= 1)
+    if (rest & (uint32_t)b) t += __shfl_xor_sync(kFull, t, b);
+  if ((lane & rest) == 0u && t != 0.0) sred_add(ka + (uint32_t)(h1 ? dv.y : dv.x) * 8u, t);
 }
 
 // A work item as handed from the producer to the preparation lanes and the
@@ -740,13 +810,14 @@ __device__ __forceinline__ bool hand_over(const Smem& s, uint32_t& k, int4 g, co
 // A port with a window, as the fast path reads it (shared memory).
 struct LivePort {
   int32_t mode;       // bits 0-1 vmode, bit 2 key depends on the iteration, bits 3-7 lane_free,
-                      // bit 8 key depends on the chunk
+                      // bit 8 key depends on the chunk, bit 9 the window is the block itself
   int32_t port;
   int32_t pad[2];
   int4 dvec;
 };
 constexpr int32_t kModeIter = 4;
 constexpr int32_t kModeChunk = 256;
+constexpr int32_t kModeStore = 512;
 
 // Stream the chunks of one item (fast path: power-of-two clique, the block
 // starts on a vector boundary, at most kMaxFastPorts ports).  An entry's
@@ -929,19 +1000,17 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
               if (lead && v != T(0)) sred_add(ka + (uint32_t)cl * wstride, v);
             }
           }
+        } else if (md & kModeStore) {
+          // every entry of the block has a key of its own: store, no reduction
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl)
+            if (act && cl < ncb && bfv[cl] != T(0)) sst_vec(ka + (uint32_t)cl * wstride, f[cl]);
         } else {
           const int4 dv = lp[i].dvec;
-          const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
+          const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka, lane & ~(int)lf) : ka;
 #pragma unroll
-          for (int cl = 0; cl < CB; ++cl) {
-            if (cl < ncb && bfv[cl] != T(0)) {
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) {
-                const T v = lane_reduce(f[cl][j], lf);
-                if (lead && v != T(0)) sred_add(ka + (uint32_t)cl * wstride + (uint32_t)dva[j] * (uint32_t)sizeof(T), v);
-              }
-            }
-          }
+          for (int cl = 0; cl < CB; ++cl)
+            if (cl < ncb && bfv[cl] != T(0)) scatter_vec(kg + (uint32_t)cl * wstride, f[cl], lf, lane, act, dv);
         }
       }
       if (a.calib != nullptr && act) {
@@ -1101,6 +1170,7 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
       if (tid == li) {
         LivePort L;
         L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
+                 ((P.vmode & kVmodeStore) ? kModeStore : 0) |
                  (int32_t)((P.lane_free & 31u) << 3);
         L.port = pi;
         L.pad[0] = L.pad[1] = 0;

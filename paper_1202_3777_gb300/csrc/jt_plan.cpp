@@ -531,6 +531,9 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
             seq = seq && P.dvec[j] == j;
           }
           P.vmode = !any ? 0 : (seq ? 1 : 2);
+          // an output window with as many entries as the block: the key map
+          // is one-to-one, so the consumers store instead of accumulating
+          if (P.kind != kPortMu && P.kind != kPortRho && P.vmode == 1 && (int64_t)P.K == B) P.vmode |= kVmodeStore;
           // iteration bits: entry bits from log2(consumers * VEC) up to the
           // block's bits; chunk bits: from log2(chunk) up
           const int ib = ilog2((int64_t)consumers_for(cb) * VEC), cbit = ilog2((int64_t)s->chunk);
