@@ -695,11 +695,17 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
         if (P.kind == kPortMu && bulk_window<T>(S, P)) continue;
         const bool output = P.kind != kPortMu && P.kind != kPortRho;
         const uint32_t kb = output ? 0u : (fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf));
+        // (a window the consumers store whole needs no zeros)
+        if (output && (P.vmode & kVmodeStore) && fast) continue;
         for (int cl = 0; cl < ncb; ++cl) {
           const int cs = cb0 + cl;
           const uint32_t dst = win32 + (uint32_t)(cl * a.win_max + P.win) * (uint32_t)sizeof(T);
           if (output) {
-            for (int ii = pl; ii < P.K; ii += NL) sst<T>(dst + (uint32_t)ii * (uint32_t)sizeof(T), T(0));
+            // 16-byte stores (windows are allocated in whole groups of 4 entries)
+            constexpr int VEC = VecT<T>::N;
+            const T z[VEC] = {};
+            const int kr = (P.K + 3) / 4 * 4;
+            for (int ii = pl * VEC; ii < kr; ii += NL * VEC) sst_vec(dst + (uint32_t)ii * (uint32_t)sizeof(T), z);
             continue;
           }
           const T* row = a.msg + (int64_t)cs * a.msg_stride + P.tab + kb;
@@ -850,7 +856,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
   for (int i = n_in; i < n_live; ++i) {
     const int32_t md = lp[i].mode;
     if (ra < 0 && (md & 3) == 0) ra = i;
-    else if (CB == 1 && ja < 0 && (md & 3) != 0 && !(md & kModeChunk)) ja = i;
+    else if (CB == 1 && ja < 0 && (md & 3) != 0 && !(md & (kModeChunk | kModeStore))) ja = i;
   }
   T racc[CB];
 #pragma unroll
@@ -1001,10 +1007,11 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
             }
           }
         } else if (md & kModeStore) {
-          // every entry of the block has a key of its own: store, no reduction
+          // every entry of the block has a key of its own: store, no
+          // reduction, zeros included (the window is not zeroed beforehand)
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl)
-            if (act && cl < ncb && bfv[cl] != T(0)) sst_vec(ka + (uint32_t)cl * wstride, f[cl]);
+            if (act && cl < ncb) sst_vec(ka + (uint32_t)cl * wstride, f[cl]);
         } else {
           const int4 dv = lp[i].dvec;
           const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka, lane & ~(int)lf) : ka;

@@ -593,27 +593,44 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
     blob_len[st] = (int32_t)((s->blobs.size() - blob_at[st]) * sizeof(uint4));
   }
 
-  // work items: collect deepest level first, then distribute from the root;
-  // every item's dependencies come earlier in the list
-  auto add = [&](int stage) {
+  // work items: collect deepest level first, then distribute from the root,
+  // one case block at a time and skewed across case blocks: the steps of
+  // the sweep (collect levels max_depth..1, then distribute levels
+  // 0..max_depth) of case block q come at wave step + q, so while one case
+  // block waits for a level to finish, the next one's previous level fills
+  // the queue.  Every item's dependencies (same case block, an earlier step)
+  // come earlier in the list.
+  auto add = [&](int stage, int q) {
     const DevStage& S = s->stages[stage];
-    for (int b = 0; b < S.n_blocks; ++b)
-      for (int q = 0; q < s->n_cb; ++q) {
-        DevItem it{};
-        it.off = S.base_off + (int64_t)b * S.B;
-        it.n = S.B;
-        it.stage = stage;
-        it.block = b;
-        it.cbk = q;
-        it.blob = blob_at[stage];
-        it.blob_bytes = blob_len[stage];
-        s->items.push_back(it);
-      }
+    for (int b = 0; b < S.n_blocks; ++b) {
+      DevItem it{};
+      it.off = S.base_off + (int64_t)b * S.B;
+      it.n = S.B;
+      it.stage = stage;
+      it.block = b;
+      it.cbk = q;
+      it.blob = blob_at[stage];
+      it.blob_bytes = blob_len[stage];
+      s->items.push_back(it);
+    }
   };
-  for (int dd = p.max_depth; dd >= 1; --dd)
-    for (int c : p.levels[dd]) add(c);
-  for (int dd = 0; dd <= p.max_depth; ++dd)
-    for (int c : p.levels[dd]) add(nc + c);
+  const int n_steps = 2 * p.max_depth + 1;
+  auto step_stages = [&](int step, std::vector<int>& out) {
+    out.clear();
+    if (step < p.max_depth) {
+      for (int c : p.levels[p.max_depth - step]) out.push_back(c);
+    } else {
+      for (int c : p.levels[step - p.max_depth]) out.push_back(nc + c);
+    }
+  };
+  std::vector<int> st_list;
+  for (int wave = 0; wave < n_steps + s->n_cb - 1; ++wave)
+    for (int q = 0; q < s->n_cb; ++q) {
+      const int step = wave - q;
+      if (step < 0 || step >= n_steps) continue;
+      step_stages(step, st_list);
+      for (int stage : st_list) add(stage, q);
+    }
   if (prop_smem_bytes(*s, elem) > smem_bytes) {
     *err = "propagation plan exceeds shared memory";
     return JT_ERR_UNSUPPORTED;
