@@ -89,6 +89,11 @@ __device__ __forceinline__ int32_t sld_s32(uint32_t a) {
   asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
   return v;
 }
+__device__ __forceinline__ int4 sld_v4s32(uint32_t a) {
+  int4 v;
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
 __device__ __forceinline__ void sld_vec(uint32_t a, float (&x)[4]) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(a));
 }
@@ -332,6 +337,44 @@ __device__ __forceinline__ void scatter_vec(uint32_t ka, const double (&v)[2], u
     if (rest & (uint32_t)b) t += __shfl_xor_sync(kFull, t, b);
   if ((lane & rest) == 0u && t != 0.0) sred_add(ka + (uint32_t)(h1 ? dv.y : dv.x) * 8u, t);
 }
+
+// Add, for every case c of a case block, v[c] summed over the lanes that
+// differ from this one only in the bits of `rest` at ka + (c0 + c) * wstride
+// (one key per lane group; `ka` the group's).  Each free lane bit first
+// halves the cases a lane carries (the lane keeps one half, sends the other
+// to its partner), so the cases end up spread over the group's lanes and one
+// atomic per holding lane adds them: for 8 cases and 4 free bits, 9 shuffles
+// instead of 32.
+template <typename T, int N>
+struct CaseScatter {
+  __device__ __forceinline__ static void run(uint32_t ka, uint32_t wstride, const T (&v)[N], uint32_t c0,
+                                             uint32_t rest, int lane) {
+    if (rest == 0u) {
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (v[i] != T(0)) sred_add(ka + (c0 + (uint32_t)i) * wstride, v[i]);
+      return;
+    }
+    const uint32_t m = rest & (0u - rest);
+    const bool h = (lane & m) != 0u;
+    T w[N / 2];
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i)
+      w[i] = (h ? v[i + N / 2] : v[i]) + __shfl_xor_sync(kFull, h ? v[i] : v[i + N / 2], m);
+    CaseScatter<T, N / 2>::run(ka, wstride, w, c0 + (h ? (uint32_t)(N / 2) : 0u), rest & ~m, lane);
+  }
+};
+template <typename T>
+struct CaseScatter<T, 1> {
+  __device__ __forceinline__ static void run(uint32_t ka, uint32_t wstride, const T (&v)[1], uint32_t c0,
+                                             uint32_t rest, int lane) {
+    T t = v[0];
+#pragma unroll
+    for (int b = 1; b < 32; b <<= 1)
+      if (rest & (uint32_t)b) t += __shfl_xor_sync(kFull, t, b);
+    if ((lane & rest) == 0u && t != T(0)) sred_add(ka + c0 * wstride, t);
+  }
+};
 
 // A work item as handed from the producer to the preparation lanes and the
 // consumers, with its preparation status.
@@ -821,6 +864,7 @@ struct LivePort {
   int32_t pad[2];
   int4 dvec;
 };
+static_assert(sizeof(LivePort) == 32 && offsetof(LivePort, dvec) == 16, "live-port table layout");
 constexpr int32_t kModeIter = 4;
 constexpr int32_t kModeChunk = 256;
 constexpr int32_t kModeStore = 512;
@@ -850,11 +894,14 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
   const uint32_t kt32 = smem_u32(s.kt) + 4u * (uint32_t)tid, ki32 = smem_u32(s.kiter);
   const uint32_t wstride = (uint32_t)a.win_max * (uint32_t)sizeof(T);  // bytes between cases' windows
   const LivePort* lp = reinterpret_cast<const LivePort*>(s.live);
+  // (the hot loop reads the live-port table and the evidence lists with
+  // explicit shared-memory loads)
+  const uint32_t lp32 = smem_u32(s.live), nobs32 = smem_u32(s.nobs), obs32 = smem_u32(s.obs);
   const int nchunks = (int)((w.n + CH - 1) / CH);
   // register-accumulated outputs
   int ra = -1, ja = -1;
   for (int i = n_in; i < n_live; ++i) {
-    const int32_t md = lp[i].mode;
+    const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
     if (ra < 0 && (md & 3) == 0) ra = i;
     else if (CB == 1 && ja < 0 && (md & 3) != 0 && !(md & (kModeChunk | kModeStore))) ja = i;
   }
@@ -910,10 +957,10 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       for (int cl = 0; cl < CB; ++cl) {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) f[cl][j] = x[j] * bfv[cl];
-        if (any_obs && cl < ncb && bfv[cl] != T(0)) {
-          const int no = s.nobs[cl];
+        if (any_obs && bfv[cl] != T(0)) {
+          const int no = sld_s32(nobs32 + 4u * (uint32_t)cl);
           for (int e = 0; e < no; ++e) {
-            const int4 ob = s.obs[cl * a.max_k + e];
+            const int4 ob = sld_v4s32(obs32 + 16u * (uint32_t)(cl * a.max_k + e));
             const uint32_t d = (o0 >> ob.x) & (uint32_t)ob.y;
 #pragma unroll
             for (int j = 0; j < VEC; ++j)
@@ -923,15 +970,17 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       }
       // input gathers
       for (int i = 0; i < n_in; ++i) {
-        const int32_t md = lp[i].mode;
+        const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
         uint32_t k = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
         if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + m));
-        const uint32_t ka = win32 + k * (uint32_t)sizeof(T);
+        // (a lane past the block's end reads the window's first entry: its
+        // key may lie outside the window)
+        const uint32_t ka = win32 + (act ? k : 0u) * (uint32_t)sizeof(T);
         const int vm = md & 3;
         if (vm == 1) {
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl) {
-            if (cl < ncb && bfv[cl] != T(0)) {
+            if (bfv[cl] != T(0)) {
               T g[VEC];
               sld_vec(ka + (uint32_t)cl * wstride, g);
 #pragma unroll
@@ -941,18 +990,18 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
         } else if (vm == 0) {
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl) {
-            if (cl < ncb && bfv[cl] != T(0)) {
+            if (bfv[cl] != T(0)) {
               const T g = sld<T>(ka + (uint32_t)cl * wstride);
 #pragma unroll
               for (int j = 0; j < VEC; ++j) f[cl][j] *= g;
             }
           }
         } else {
-          const int4 dv = lp[i].dvec;
+          const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
           const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl) {
-            if (cl < ncb && bfv[cl] != T(0)) {
+            if (bfv[cl] != T(0)) {
 #pragma unroll
               for (int j = 0; j < VEC; ++j) f[cl][j] *= sld<T>(ka + (uint32_t)cl * wstride + (uint32_t)dva[j] * (uint32_t)sizeof(T));
             }
@@ -971,15 +1020,11 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       if (ra >= 0) {
         const uint32_t kc = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter + m));
         if (kc != rcur) {
-          const bool lead = (lane & rlf) == 0u;
+          const uint32_t ra_a = win32 + (rkt + rcur) * (uint32_t)sizeof(T);
+          CaseScatter<T, CB>::run(rlf != 0u ? __shfl_sync(kFull, ra_a, lane & ~(int)rlf) : ra_a, wstride, racc, 0u,
+                                  rlf, lane);
 #pragma unroll
-          for (int cl = 0; cl < CB; ++cl) {
-            if (cl < ncb) {
-              const T v = lane_reduce(racc[cl], rlf);
-              if (lead && v != T(0)) sred_add(win32 + (uint32_t)cl * wstride + (rkt + rcur) * (uint32_t)sizeof(T), v);
-              racc[cl] = T(0);
-            }
-          }
+          for (int cl = 0; cl < CB; ++cl) racc[cl] = T(0);
           rcur = kc;
         }
 #pragma unroll
@@ -992,32 +1037,31 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       // output scatters, reduced over the lanes that share the key
       for (int i = n_in; i < n_live; ++i) {
         if (i == ra || i == ja) continue;
-        const int32_t md = lp[i].mode;
+        const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
         uint32_t k = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
         if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + m));
         const uint32_t ka = win32 + k * (uint32_t)sizeof(T);
         const uint32_t lf = (uint32_t)(md >> 3) & 31u;
-        const bool lead = act && (lane & lf) == 0u;
         if ((md & 3) == 0) {
-#pragma unroll
-          for (int cl = 0; cl < CB; ++cl) {
-            if (cl < ncb && bfv[cl] != T(0)) {
-              const T v = lane_reduce(sum[cl], lf);
-              if (lead && v != T(0)) sred_add(ka + (uint32_t)cl * wstride, v);
-            }
+          if (CB == 1) {
+            const T v = lane_reduce(sum[0], lf);
+            if (act && (lane & lf) == 0u && v != T(0)) sred_add(ka, v);
+          } else {
+            const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka, lane & ~(int)lf) : ka;
+            CaseScatter<T, CB>::run(kg, wstride, sum, 0u, lf, lane);
           }
         } else if (md & kModeStore) {
           // every entry of the block has a key of its own: store, no
           // reduction, zeros included (the window is not zeroed beforehand)
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl)
-            if (act && cl < ncb) sst_vec(ka + (uint32_t)cl * wstride, f[cl]);
+            if (act) sst_vec(ka + (uint32_t)cl * wstride, f[cl]);
         } else {
-          const int4 dv = lp[i].dvec;
+          const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
           const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka, lane & ~(int)lf) : ka;
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl)
-            if (cl < ncb && bfv[cl] != T(0)) scatter_vec(kg + (uint32_t)cl * wstride, f[cl], lf, lane, act, dv);
+            if (bfv[cl] != T(0)) scatter_vec(kg + (uint32_t)cl * wstride, f[cl], lf, lane, act, dv);
         }
       }
       if (a.calib != nullptr && act) {
@@ -1036,14 +1080,9 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
   if (!__all_sync(kFull, ok)) return false;
   // flush the register accumulators (inactive lanes hold zeros)
   if (ra >= 0) {
-    const bool lead = (lane & rlf) == 0u;
-#pragma unroll
-    for (int cl = 0; cl < CB; ++cl) {
-      if (cl < ncb) {
-        const T v = lane_reduce(racc[cl], rlf);
-        if (lead && v != T(0)) sred_add(win32 + (uint32_t)cl * wstride + (rkt + rcur) * (uint32_t)sizeof(T), v);
-      }
-    }
+    const uint32_t ra_a = win32 + (rkt + rcur) * (uint32_t)sizeof(T);
+    CaseScatter<T, CB>::run(rlf != 0u ? __shfl_sync(kFull, ra_a, lane & ~(int)rlf) : ra_a, wstride, racc, 0u, rlf,
+                            lane);
   }
   if (ja >= 0) {
     const uint32_t kt = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(ja * NT));
