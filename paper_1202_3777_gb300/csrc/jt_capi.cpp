@@ -81,7 +81,8 @@ struct jt_tree_s {
   void* d_calib = nullptr;        // [max_cases][base_len] (JT_MATERIALIZE_CLIQUES)
   double* d_scratch = nullptr;    // read-out scratch (sum + clique table)
   int64_t scratch_len = 0;
-  VarSrc* d_vs = nullptr;
+  VarSrc* d_vs = nullptr;         // marginal sources, joint layout 0 (one-case schedules)
+  VarSrc* d_vs_fine = nullptr;    // joint layout 1 (case-block schedules)
   int32_t* d_sep_size = nullptr;
   int64_t device_bytes = 0;
   // host state
@@ -122,7 +123,7 @@ void destroy(jt_tree t) {
   cudaDeviceSynchronize();
   free_graphs(t);
   void* ptrs[] = {t->base,   t->d_msg,  t->d_sums,  t->d_done,    t->d_err, t->d_status, t->d_marg,
-                  t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_sep_size};
+                  t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_sep_size};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->h_ev) cudaFreeHost(t->h_ev);
@@ -202,7 +203,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
   if (ev) chk(cudaEventRecord(ev[1], s));
   FinalArgs<T> f{};
-  f.vs = t->d_vs;
+  f.vs = sc.cb > 1 ? t->d_vs_fine : t->d_vs;  // the joint layout the schedule's ports write
   f.n_vars = p.n_vars;
   f.n_cliques = p.n_cliques;
   f.case0 = case0;
@@ -448,7 +449,11 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   if ((st = alloc(raw, &raw->d_ev, nev, "evidence")) != JT_OK) return bail(st);
   if (cudaMemset(raw->d_ev, 0xFF, nev * sizeof(int16_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
   if ((st = alloc(raw, &raw->d_vs, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
-  if (cudaMemcpy(raw->d_vs, p.vsrc.data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpy(raw->d_vs, p.vsrc[0].data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(JT_ERR_CUDA, "descriptor upload"));
+  if ((st = alloc(raw, &raw->d_vs_fine, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
+  if (cudaMemcpy(raw->d_vs_fine, p.vsrc[1].data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
     return bail(fail(JT_ERR_CUDA, "descriptor upload"));
   if ((st = alloc(raw, &raw->d_sep_size, nc, "separator sizes")) != JT_OK) return bail(st);
   if (cudaMemcpy(raw->d_sep_size, p.sep_size.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -193,19 +193,34 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
       }
     }
 
-  // private joints
-  p->joint_off.assign(nc, -1);
-  p->joint_size.assign(nc, 0);
+  // private joints, both layouts; a layout-1 joint grows from the least
+  // significant private position up while it stays within kFineJointEntries
   int64_t jo = 0;
-  for (int c = 0; c < nc; ++c) {
-    if (p->n_private[c] == 0) continue;
-    int64_t q = 1;
-    const auto& pv = p->pvars[c];
-    for (size_t i = pv.size() - p->n_private[c]; i < pv.size(); ++i) q *= p->card[pv[i]];
-    p->joint_off[c] = (int32_t)jo;
-    p->joint_size[c] = (int32_t)q;
-    jo += (q + 3) / 4 * 4;
-    if (jo > (1ll << 30)) FAIL(JT_ERR_UNSUPPORTED, "private-variable joints too large");
+  for (int L = 0; L < 2; ++L) {
+    p->joints[L].assign(nc, {});
+    for (int c = 0; c < nc; ++c) {
+      const int npv = p->n_private[c];
+      if (npv == 0) continue;
+      const auto& pv = p->pvars[c];
+      const int k = (int)pv.size();
+      auto add = [&](int lo, int hi, int64_t q) {
+        p->joints[L][c].push_back({(int32_t)jo, (int32_t)q, lo, hi - lo});
+        jo += (q + 3) / 4 * 4;
+      };
+      int hi = k;
+      int64_t q = 1;
+      for (int i = k - 1; i >= k - npv; --i) {
+        const int64_t cq = p->card[pv[i]];
+        if (L == 1 && q > 1 && q * cq > kFineJointEntries) {
+          add(i + 1, hi, q);
+          hi = i + 1;
+          q = 1;
+        }
+        q *= cq;
+      }
+      add(k - npv, hi, q);
+      if (jo > (1ll << 30)) FAIL(JT_ERR_UNSUPPORTED, "private-variable joints too large");
+    }
   }
   p->joint_total = (int32_t)jo;
   p->msg_stride = (2ll * p->msg_total + p->joint_total + 31) / 32 * 32;
@@ -219,37 +234,42 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     mo += p->card[v];
   }
   p->marg_total = (int32_t)mo;
-  p->vsrc.assign(nv, VarSrc{});
   std::vector<int32_t> src_edge(nv, -1);
   for (int c = 1; c < nc; ++c)
     for (int v : p->sep[c]) {
       const int e = src_edge[v];
       if (e < 0 || p->sep_size[c] < p->sep_size[e]) src_edge[v] = c;
     }
-  for (int v = 0; v < nv; ++v) {
-    VarSrc& q = p->vsrc[v];
-    q.card = p->card[v];
-    q.moff = p->moff[v];
-    const int e = src_edge[v];
-    if (e >= 0) {
-      q.off = p->msg_total + p->sep_off[e];
-      q.size = p->sep_size[e];
-      int64_t t = 1;
-      for (int i = (int)p->sep[e].size() - 1; i >= 0; --i) {
-        if (p->sep[e][i] == v) q.st = (int32_t)t;
-        t *= p->card[p->sep[e][i]];
+  for (int L = 0; L < 2; ++L) {
+    std::vector<VarSrc>& vs = p->vsrc[L];
+    vs.assign(nv, VarSrc{});
+    for (int v = 0; v < nv; ++v) {
+      VarSrc& q = vs[v];
+      q.card = p->card[v];
+      q.moff = p->moff[v];
+      const int e = src_edge[v];
+      if (e >= 0) {
+        q.off = p->msg_total + p->sep_off[e];
+        q.size = p->sep_size[e];
+        int64_t t = 1;
+        for (int i = (int)p->sep[e].size() - 1; i >= 0; --i) {
+          if (p->sep[e][i] == v) q.st = (int32_t)t;
+          t *= p->card[p->sep[e][i]];
+        }
       }
     }
-  }
-  for (int c = 0; c < nc; ++c) {
-    const auto& pv = p->pvars[c];
-    int64_t t = 1;
-    for (int i = (int)pv.size() - 1; i >= (int)pv.size() - p->n_private[c]; --i) {
-      VarSrc& q = p->vsrc[pv[i]];
-      q.off = 2 * p->msg_total + p->joint_off[c];
-      q.size = p->joint_size[c];
-      q.st = (int32_t)t;
-      t *= p->card[pv[i]];
+    for (int c = 0; c < nc; ++c) {
+      const auto& pv = p->pvars[c];
+      for (const Plan::JointGroup& g : p->joints[L][c]) {
+        int64_t t = 1;
+        for (int i = g.pos0 + g.npos - 1; i >= g.pos0; --i) {
+          VarSrc& q = vs[pv[i]];
+          q.off = 2 * p->msg_total + g.off;
+          q.size = g.size;
+          q.st = (int32_t)t;
+          t *= p->card[pv[i]];
+        }
+      }
     }
   }
 
@@ -391,10 +411,10 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       if (pass == 1) {
         for (int g : p.children[c])
           sp.push_back({kPortDelta, p.msg_total + p.sep_off[g], p.sep_size[g], g, -1, in_of(p.sep[g])});
-        if (p.n_private[c] > 0) {
+        for (const Plan::JointGroup& g : p.joints[cb > 1 ? 1 : 0][c]) {
           std::vector<char> in(k, 0);
-          for (int i = k - p.n_private[c]; i < k; ++i) in[i] = 1;
-          sp.push_back({kPortJoint, 2 * p.msg_total + p.joint_off[c], p.joint_size[c], c, -1, in});
+          for (int i = g.pos0; i < g.pos0 + g.npos; ++i) in[i] = 1;
+          sp.push_back({kPortJoint, 2 * p.msg_total + g.off, g.size, c, -1, in});
         }
       }
       s->max_ports = std::max(s->max_ports, (int)sp.size());
