@@ -262,6 +262,17 @@ __device__ __forceinline__ T lane_reduce(T v, uint32_t mask) {
   return v;
 }
 
+// lane_reduce of N independent values at once (their shuffle chains overlap).
+template <typename T, int N>
+__device__ __forceinline__ void lane_reduce_n(T (&v)[N], uint32_t mask) {
+#pragma unroll
+  for (int b = 1; b < 32; b <<= 1)
+    if (mask & (uint32_t)b) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(kFull, v[i], b);
+    }
+}
+
 // Add v at tab[key] for every lane of a full warp; when every lane has the
 // same key the warp reduces first and issues one atomic.
 template <typename T>
@@ -888,7 +899,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
   constexpr int NT = consumers_for(CB);
   constexpr int VEC = VecT<T>::N;
   constexpr int VPT = chunk_bytes_for(CB) / (16 * NT);  // vectors per thread per chunk
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t RS = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
   const uint32_t ring32 = smem_u32(s.ring), win32 = smem_u32(s.win);
   const uint32_t kt32 = smem_u32(s.kt) + 4u * (uint32_t)tid, ki32 = smem_u32(s.kiter);
@@ -944,81 +955,103 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
         for (int j = 0; j < VEC; ++j) xs[it][j] = T(0);
       }
     }
+    // every vector of this thread in the chunk at once (VPT of them): their
+    // gathers and reductions are independent, so their latencies overlap.
+    // Lanes past the chunk's end carry zeros.
+    bool act[VPT];
+    int mi[VPT];               // iteration index within the block
+    uint32_t o0[VPT];
+    T f[VPT][CB][VEC];
 #pragma unroll
     for (int it = 0; it < VPT; ++it) {
-      if (it * NT + warp * 32 >= nvec) break;  // warp-uniform
       const int vi = it * NT + tid;
-      const bool act = vi < nvec;
-      const int m = ci * VPT + it;             // iteration index within the block
-      const T (&x)[VEC] = xs[it];
-      const uint32_t o0 = cbase + (uint32_t)vi * VEC;
-      T f[CB][VEC];
+      act[it] = vi < nvec;
+      mi[it] = ci * VPT + it;
+      o0[it] = cbase + (uint32_t)vi * VEC;
 #pragma unroll
       for (int cl = 0; cl < CB; ++cl) {
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) f[cl][j] = x[j] * bfv[cl];
+        for (int j = 0; j < VEC; ++j) f[it][cl][j] = xs[it][j] * bfv[cl];
         if (any_obs && bfv[cl] != T(0)) {
           const int no = sld_s32(nobs32 + 4u * (uint32_t)cl);
           for (int e = 0; e < no; ++e) {
             const int4 ob = sld_v4s32(obs32 + 16u * (uint32_t)(cl * a.max_k + e));
-            const uint32_t d = (o0 >> ob.x) & (uint32_t)ob.y;
+            const uint32_t d = (o0[it] >> ob.x) & (uint32_t)ob.y;
 #pragma unroll
             for (int j = 0; j < VEC; ++j)
-              if (d + (((uint32_t)j >> ob.x) & (uint32_t)ob.y) != (uint32_t)ob.z) f[cl][j] = T(0);
+              if (d + (((uint32_t)j >> ob.x) & (uint32_t)ob.y) != (uint32_t)ob.z) f[it][cl][j] = T(0);
           }
         }
       }
-      // input gathers
-      for (int i = 0; i < n_in; ++i) {
-        const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
-        uint32_t k = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
-        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + m));
+    }
+    // input gathers
+    for (int i = 0; i < n_in; ++i) {
+      const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
+      const uint32_t kti = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+      uint32_t ka[VPT];
+#pragma unroll
+      for (int it = 0; it < VPT; ++it) {
+        uint32_t k = kti;
+        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + mi[it]));
         // (a lane past the block's end reads the window's first entry: its
         // key may lie outside the window)
-        const uint32_t ka = win32 + (act ? k : 0u) * (uint32_t)sizeof(T);
-        const int vm = md & 3;
-        if (vm == 1) {
+        ka[it] = win32 + (act[it] ? k : 0u) * (uint32_t)sizeof(T);
+      }
+      const int vm = md & 3;
+      if (vm == 1) {
+#pragma unroll
+        for (int it = 0; it < VPT; ++it)
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl) {
             if (bfv[cl] != T(0)) {
               T g[VEC];
-              sld_vec(ka + (uint32_t)cl * wstride, g);
+              sld_vec(ka[it] + (uint32_t)cl * wstride, g);
 #pragma unroll
-              for (int j = 0; j < VEC; ++j) f[cl][j] *= g[j];
+              for (int j = 0; j < VEC; ++j) f[it][cl][j] *= g[j];
             }
           }
-        } else if (vm == 0) {
+      } else if (vm == 0) {
+#pragma unroll
+        for (int it = 0; it < VPT; ++it)
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl) {
             if (bfv[cl] != T(0)) {
-              const T g = sld<T>(ka + (uint32_t)cl * wstride);
+              const T g = sld<T>(ka[it] + (uint32_t)cl * wstride);
 #pragma unroll
-              for (int j = 0; j < VEC; ++j) f[cl][j] *= g;
+              for (int j = 0; j < VEC; ++j) f[it][cl][j] *= g;
             }
           }
-        } else {
-          const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
-          const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
+      } else {
+        const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
+        const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+        for (int it = 0; it < VPT; ++it)
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl) {
             if (bfv[cl] != T(0)) {
 #pragma unroll
-              for (int j = 0; j < VEC; ++j) f[cl][j] *= sld<T>(ka + (uint32_t)cl * wstride + (uint32_t)dva[j] * (uint32_t)sizeof(T));
+              for (int j = 0; j < VEC; ++j)
+                f[it][cl][j] *= sld<T>(ka[it] + (uint32_t)cl * wstride + (uint32_t)dva[j] * (uint32_t)sizeof(T));
             }
           }
-        }
       }
-      T sum[CB];
+    }
+    T sum[VPT][CB];
+#pragma unroll
+    for (int it = 0; it < VPT; ++it)
 #pragma unroll
       for (int cl = 0; cl < CB; ++cl) {
-        sum[cl] = T(0);
+        sum[it][cl] = T(0);
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) sum[cl] += f[cl][j];
-        tot[cl] += sum[cl];
+        for (int j = 0; j < VEC; ++j) sum[it][cl] += f[it][cl][j];
+        tot[cl] += sum[it][cl];
       }
-      // the register-accumulated output: flush when its key changes
-      if (ra >= 0) {
-        const uint32_t kc = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter + m));
+    // the register-accumulated output: flush when its key changes (the
+    // iterations in order)
+    if (ra >= 0) {
+#pragma unroll
+      for (int it = 0; it < VPT; ++it) {
+        const uint32_t kc = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter + mi[it]));
         if (kc != rcur) {
           const uint32_t ra_a = win32 + (rkt + rcur) * (uint32_t)sizeof(T);
           CaseScatter<T, CB>::run(rlf != 0u ? __shfl_sync(kFull, ra_a, lane & ~(int)rlf) : ra_a, wstride, racc, 0u,
@@ -1028,47 +1061,71 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
           rcur = kc;
         }
 #pragma unroll
-        for (int cl = 0; cl < CB; ++cl) racc[cl] += sum[cl];
+        for (int cl = 0; cl < CB; ++cl) racc[cl] += sum[it][cl];
       }
-      if (ja >= 0) {
+    }
+    if (ja >= 0) {
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) jacc[it][j] += f[0][j];
+      for (int it = 0; it < VPT; ++it)
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) jacc[it][j] += f[it][0][j];
+    }
+    // output scatters, reduced over the lanes that share the key
+    for (int i = n_in; i < n_live; ++i) {
+      if (i == ra || i == ja) continue;
+      const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
+      const uint32_t kti = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+      uint32_t ka[VPT];
+#pragma unroll
+      for (int it = 0; it < VPT; ++it) {
+        uint32_t k = kti;
+        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + mi[it]));
+        ka[it] = win32 + k * (uint32_t)sizeof(T);
       }
-      // output scatters, reduced over the lanes that share the key
-      for (int i = n_in; i < n_live; ++i) {
-        if (i == ra || i == ja) continue;
-        const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
-        uint32_t k = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
-        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + m));
-        const uint32_t ka = win32 + k * (uint32_t)sizeof(T);
-        const uint32_t lf = (uint32_t)(md >> 3) & 31u;
-        if ((md & 3) == 0) {
-          if (CB == 1) {
-            const T v = lane_reduce(sum[0], lf);
-            if (act && (lane & lf) == 0u && v != T(0)) sred_add(ka, v);
-          } else {
-            const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka, lane & ~(int)lf) : ka;
-            CaseScatter<T, CB>::run(kg, wstride, sum, 0u, lf, lane);
-          }
-        } else if (md & kModeStore) {
-          // every entry of the block has a key of its own: store, no
-          // reduction, zeros included (the window is not zeroed beforehand)
+      const uint32_t lf = (uint32_t)(md >> 3) & 31u;
+      if ((md & 3) == 0) {
+        if (CB == 1) {
+          T v[VPT];
 #pragma unroll
-          for (int cl = 0; cl < CB; ++cl)
-            if (act) sst_vec(ka + (uint32_t)cl * wstride, f[cl]);
+          for (int it = 0; it < VPT; ++it) v[it] = sum[it][0];
+          lane_reduce_n<T, VPT>(v, lf);
+#pragma unroll
+          for (int it = 0; it < VPT; ++it)
+            if (act[it] && (lane & lf) == 0u && v[it] != T(0)) sred_add(ka[it], v[it]);
         } else {
-          const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
-          const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka, lane & ~(int)lf) : ka;
+#pragma unroll
+          for (int it = 0; it < VPT; ++it) {
+            const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka[it], lane & ~(int)lf) : ka[it];
+            CaseScatter<T, CB>::run(kg, wstride, sum[it], 0u, lf, lane);
+          }
+        }
+      } else if (md & kModeStore) {
+        // every entry of the block has a key of its own: store, no
+        // reduction, zeros included (the window is not zeroed beforehand)
+#pragma unroll
+        for (int it = 0; it < VPT; ++it)
 #pragma unroll
           for (int cl = 0; cl < CB; ++cl)
-            if (bfv[cl] != T(0)) scatter_vec(kg + (uint32_t)cl * wstride, f[cl], lf, lane, act, dv);
+            if (act[it]) sst_vec(ka[it] + (uint32_t)cl * wstride, f[it][cl]);
+      } else {
+        const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
+#pragma unroll
+        for (int it = 0; it < VPT; ++it) {
+          const uint32_t kg = lf != 0u ? __shfl_sync(kFull, ka[it], lane & ~(int)lf) : ka[it];
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl)
+            if (bfv[cl] != T(0)) scatter_vec(kg + (uint32_t)cl * wstride, f[it][cl], lf, lane, act[it], dv);
         }
       }
-      if (a.calib != nullptr && act) {
+    }
+    if (a.calib != nullptr) {
 #pragma unroll
-        for (int cl = 0; cl < CB; ++cl)
-          if (cl < ncb) VecT<T>::stg(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + w.off + o0, f[cl]);
-      }
+      for (int it = 0; it < VPT; ++it)
+        if (act[it]) {
+#pragma unroll
+          for (int cl = 0; cl < CB; ++cl)
+            if (cl < ncb) VecT<T>::stg(a.calib + (int64_t)(cb0 + cl) * a.calib_stride + w.off + o0[it], f[it][cl]);
+        }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(s.empty + st);
