@@ -12,9 +12,10 @@ namespace jt {
 // one producer warp) and resident CTAs per SM.
 __host__ __device__ constexpr int consumers_for(int cb) { return cb > 0 ? 512 : 512; }
 __host__ __device__ constexpr int ctas_per_sm_for(int cb) { return cb > 0 ? 1 : 1; }
-// Bytes per bulk-copy stage (two vectors per consumer thread per stage for
-// one case, one vector for a block of cases, whose windows need the room).
-__host__ __device__ constexpr int chunk_bytes_for(int cb) { return cb > 1 ? 8192 : 16384; }
+// Bytes per bulk-copy stage: four vectors per consumer thread for one case
+// (processed together, so their latencies overlap), one vector for a block
+// of cases (eight cases already overlap; their windows need the room).
+__host__ __device__ constexpr int chunk_bytes_for(int cb) { return cb > 1 ? 8192 : 32768; }
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
 constexpr int kControlThreads = 96;             // producer, signalling and preparation warps
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path

@@ -343,7 +343,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
   s->cb = cb;
   s->n_cb = std::max(1, (n_cases + cb - 1) / cb);
   s->chunk = chunk_bytes_for(cb) / elem;
-  s->ring = cb == 1 ? 8 : 4;
+  s->ring = 4;
   s->stages.assign(2 * nc, DevStage{});
   s->ports.clear();
   s->fields.clear();
