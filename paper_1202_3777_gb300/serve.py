@@ -163,11 +163,15 @@ class Server:
         arrivals = sorted(arrivals, key=lambda a: a[0])
         t0 = time.perf_counter()
         i = 0
-        while i < len(arrivals) or self.poll() or any(r.queue for r in self.trees.values()):
+        while True:
             now = time.perf_counter() - t0
             while i < len(arrivals) and arrivals[i][0] <= now:
                 self.submit(arrivals[i][1], t0 + arrivals[i][0])
                 i += 1
+            # batches start and finish while later queries are still to arrive
+            busy = self.poll()
+            if i >= len(arrivals) and busy == 0 and not any(r.queue for r in self.trees.values()):
+                break
         return self.completed
 
     def free(self):
