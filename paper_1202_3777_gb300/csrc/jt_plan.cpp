@@ -634,13 +634,48 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       s->items.push_back(it);
     }
   };
+  // Order inside a level, so that the items whose dependencies finish first
+  // come first: a collect stage by the queue position of its last child (a
+  // clique without children first), a distribute stage by its parent's
+  // position, the deeper subtree first among siblings.
+  std::vector<int32_t> height(nc, 0);
+  for (int dd = p.max_depth; dd >= 1; --dd)
+    for (int c : p.levels[dd]) height[p.parent[c]] = std::max(height[p.parent[c]], height[c] + 1);
+  std::vector<std::vector<int32_t>> corder(p.max_depth + 1), dorder(p.max_depth + 1);
+  std::vector<int32_t> qpos(nc, 0);
+  corder[p.max_depth] = p.levels[p.max_depth];
+  for (size_t i = 0; i < corder[p.max_depth].size(); ++i) qpos[corder[p.max_depth][i]] = (int32_t)i;
+  for (int dd = p.max_depth - 1; dd >= 1; --dd) {
+    std::vector<std::pair<int64_t, int32_t>> key;
+    for (int c : p.levels[dd]) {
+      int64_t k = -1;
+      for (int g : p.children[c]) k = std::max<int64_t>(k, qpos[g]);
+      key.push_back({k, c});
+    }
+    std::stable_sort(key.begin(), key.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (size_t i = 0; i < key.size(); ++i) {
+      corder[dd].push_back(key[i].second);
+      qpos[key[i].second] = (int32_t)i;
+    }
+  }
+  dorder[0] = p.levels[0];
+  for (size_t i = 0; i < dorder[0].size(); ++i) qpos[dorder[0][i]] = (int32_t)i;
+  for (int dd = 1; dd <= p.max_depth; ++dd) {
+    std::vector<std::pair<int64_t, int32_t>> key;
+    for (int c : p.levels[dd]) key.push_back({(int64_t)qpos[p.parent[c]] * (nc + 1) + (nc - height[c]), c});
+    std::stable_sort(key.begin(), key.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (size_t i = 0; i < key.size(); ++i) {
+      dorder[dd].push_back(key[i].second);
+      qpos[key[i].second] = (int32_t)i;
+    }
+  }
   const int n_steps = 2 * p.max_depth + 1;
   auto step_stages = [&](int step, std::vector<int>& out) {
     out.clear();
     if (step < p.max_depth) {
-      for (int c : p.levels[p.max_depth - step]) out.push_back(c);
+      for (int c : corder[p.max_depth - step]) out.push_back(c);
     } else {
-      for (int c : p.levels[step - p.max_depth]) out.push_back(nc + c);
+      for (int c : dorder[step - p.max_depth]) out.push_back(nc + c);
     }
   };
   std::vector<int> st_list;
