@@ -585,15 +585,16 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
       for (size_t i = 0; i < n_items; ++i)
         if (h[i * kTraceSlots + 1]) t0 = std::min(t0, h[i * kTraceSlots + 1]);
       std::fprintf(f, "item,stage,clique,pass,block,cbk,n,sm,start_ns,prepared_ns,stream_ns,streamed_ns,done_ns,"
-                      "chunk_wait_ns,claimed_ns,issued_ns,published_ns\n");
+                      "chunk_wait_ns,claimed_ns,issued_ns,published_ns,deps_met_ns,prep_start_ns\n");
       for (size_t i = 0; i < n_items; ++i) {
         const DevItem& w = ge->sched.items[i];
         const DevStage& S = ge->sched.stages[w.stage];
         const uint64_t* r = &h[i * kTraceSlots];
-        std::fprintf(f, "%zu,%d,%d,%d,%d,%d,%d,%llu,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld\n", i, w.stage,
-                     S.clique, S.pass, w.block, w.cbk, w.n, (unsigned long long)r[0], (long long)(r[1] - t0),
+        std::fprintf(f, "%zu,%d,%d,%d,%d,%d,%d,%llu,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld,%lld\n", i,
+                     w.stage, S.clique, S.pass, w.block, w.cbk, w.n, (unsigned long long)r[0], (long long)(r[1] - t0),
                      (long long)(r[2] - t0), (long long)(r[3] - t0), (long long)(r[4] - t0), (long long)(r[5] - t0),
-                     (long long)r[6], (long long)(r[7] - t0), (long long)(r[8] - t0), (long long)(r[9] - t0));
+                     (long long)r[6], (long long)(r[7] - t0), (long long)(r[8] - t0), (long long)(r[9] - t0),
+                     (long long)(r[10] - t0), (long long)(r[11] - t0));
       }
       std::fclose(f);
     }

@@ -46,7 +46,7 @@ constexpr int32_t kPortJoint = 4;  // out: joint of the private variables (raw s
 // prepared, streaming starts, streamed, consumers done, time consumer thread 0
 // waited for chunks, producer took the item, producer issued its last chunk,
 // block published.
-constexpr int kTraceSlots = 10;
+constexpr int kTraceSlots = 12;
 
 constexpr int kStatusZero = 1;      // P(e) = 0
 constexpr int kStatusBadState = 2;  // an evidence state >= card

@@ -619,9 +619,11 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
     const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
     const bool fast = S.bits >= 0;
     uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)inf.idx * kTraceSlots : nullptr;
+    if (tr != nullptr && pl == 0) tr[11] = global_ns();
     // dependencies
     bool dok = true;
     if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, pl, NL, kMask);
+    if (tr != nullptr && pl == 0) tr[10] = global_ns();
     if (pl < CB) {
       s.nobs[pl] = 0;
       s.bf[pl] = 1.0;
