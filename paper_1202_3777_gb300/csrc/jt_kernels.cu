@@ -823,6 +823,8 @@ __device__ __forceinline__ void signaller(const PropArgs<T>& a, const Smem& s0) 
     const int4 g = s0.sig[sl];   // stage, case block, buffer, item index
     mbar_arrive(s0.sempty + sl);
     if (g.x < 0) break;
+    // the consumers' window writes (generic proxy) before the bulk reads
+    fence_proxy_async();
     const uint32_t b = (uint32_t)g.z;
     const Smem s = with_buffer(s0, b);
     const DevStage& S = *s.stage;
@@ -874,10 +876,12 @@ struct LivePort {
   int32_t mode;       // bits 0-1 vmode, bit 2 key depends on the iteration, bits 3-7 lane_free,
                       // bit 8 key depends on the chunk, bit 9 the window is the block itself
   int32_t port;
-  int32_t pad[2];
+  int32_t win;        // start of the port's window (in every case's window row)
+  int32_t pad;
   int4 dvec;
 };
-static_assert(sizeof(LivePort) == 32 && offsetof(LivePort, dvec) == 16, "live-port table layout");
+static_assert(sizeof(LivePort) == 32 && offsetof(LivePort, win) == 8 && offsetof(LivePort, dvec) == 16,
+              "live-port table layout");
 constexpr int32_t kModeIter = 4;
 constexpr int32_t kModeChunk = 256;
 constexpr int32_t kModeStore = 512;
@@ -990,14 +994,15 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     for (int i = 0; i < n_in; ++i) {
       const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
       const uint32_t kti = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+      // (a lane past the block's end reads its port window's first entries,
+      // which are always filled: its own key may lie outside the window)
+      const uint32_t kwin = (uint32_t)sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 8u);
       uint32_t ka[VPT];
 #pragma unroll
       for (int it = 0; it < VPT; ++it) {
         uint32_t k = kti;
         if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + mi[it]));
-        // (a lane past the block's end reads the window's first entry: its
-        // key may lie outside the window)
-        ka[it] = win32 + (act[it] ? k : 0u) * (uint32_t)sizeof(T);
+        ka[it] = win32 + (act[it] ? k : kwin) * (uint32_t)sizeof(T);
       }
       const int vm = md & 3;
       if (vm == 1) {
@@ -1278,7 +1283,8 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
                  ((P.vmode & kVmodeStore) ? kModeStore : 0) |
                  (int32_t)((P.lane_free & 31u) << 3);
         L.port = pi;
-        L.pad[0] = L.pad[1] = 0;
+        L.win = P.win;
+        L.pad = 0;
         L.dvec = make_int4(P.dvec[0], P.dvec[1], P.dvec[2], P.dvec[3]);
         lp[li] = L;
       }
@@ -1350,6 +1356,14 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
       }
     }
   }
+  // Every thread's global additions above (stage totals, block-constant
+  // outputs, windows the bulk unit cannot reduce) are made visible GPU-wide
+  // by the thread itself before the hand-over: the signalling lane's fence
+  // orders only what it wrote, and the item counts as done once it
+  // publishes.  Likewise every thread's shared-memory writes to the output
+  // windows are ordered before the bulk unit (the async proxy) reads them.
+  __threadfence();
+  fence_proxy_async();
   consumer_sync<NT>();
   if (tid == 0) {
     if (tr != nullptr) tr[5] = global_ns();

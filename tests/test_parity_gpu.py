@@ -142,6 +142,31 @@ def test_binary_serving_tree(jt):
     _check(t, cases, lz, m, "f32", idx=[0, 4, 8])
 
 
+def test_results_do_not_depend_on_stale_shared_memory(jt):
+    """A propagation reads no shared memory it did not write: an FP64
+    propagation first leaves its own values (NaN and Inf bit patterns as
+    FP32) in every SM's shared memory, and ragged case blocks of tiny cliques
+    (lanes past the block end, two-entry windows) must still give the
+    oracle's results."""
+    big = _prep(synth.high_card_tree(), "f64")
+    hb = jt.jt_load_synth(big, compute=jt.JT_F64, max_cases=16)
+    jt.jt_set_evidence_dense(hb, 0, synth.evidence_matrix(big, 16, 0.05, 3))
+    t = _prep(synth.binary_serving_tree(), "f32")
+    ev = synth.evidence_matrix(t, 9, (0.01, 0.20), 99)
+    cases = [synth.case_from_row(r) for r in ev]
+    first = None
+    for rep in range(8):
+        jt.jt_propagate(hb, 0, 16)
+        lz, m, h = _run_cases(jt, t, "f32", cases)
+        h.free()
+        if first is None:
+            first = (lz, m)
+            _check(t, cases, lz, m, "f32", idx=[0, 5, 8])
+        else:
+            assert np.array_equal(lz, first[0])
+    hb.free()
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_calibrated_cliques(jt, prec):
     """Materialised cliques equal the oracle's calibrated tables P(x_C | e)."""
