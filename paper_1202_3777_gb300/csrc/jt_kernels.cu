@@ -1327,12 +1327,14 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
     if (lane == 0) s.red[cl * (NT / 32) + warp] = (double)v;
   }
   consumer_sync<NT>();
+  bool wrote_global = false;
   if (tid < ncb) {
     double t = 0.0;
     for (int i = 0; i < NT / 32; ++i) t += s.red[tid * (NT / 32) + i];
     const int cs = cb0 + tid;
     T* row = a.msg + (int64_t)cs * a.msg_stride;
     if (t != 0.0) {
+      wrote_global = true;
       for (int pi = S.nin; pi < S.np; ++pi) {
         const DevPort& P = s.port[pi];
         if (P.K > 1) continue;
@@ -1352,7 +1354,10 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
       const uint32_t src = win32 + (uint32_t)(cl * a.win_max + P.win) * (uint32_t)sizeof(T);
       for (int i = tid; i < P.K; i += NT) {
         const T v = sld<T>(src + (uint32_t)i * (uint32_t)sizeof(T));
-        if (v != T(0)) atomicAdd(dst + i, v);
+        if (v != T(0)) {
+          atomicAdd(dst + i, v);
+          wrote_global = true;
+        }
       }
     }
   }
@@ -1362,7 +1367,7 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
   // orders only what it wrote, and the item counts as done once it
   // publishes.  Likewise every thread's shared-memory writes to the output
   // windows are ordered before the bulk unit (the async proxy) reads them.
-  __threadfence();
+  if (wrote_global) __threadfence();
   fence_proxy_async();
   consumer_sync<NT>();
   if (tid == 0) {
