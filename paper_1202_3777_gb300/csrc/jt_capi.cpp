@@ -199,6 +199,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   a.max_ports = sc.max_ports;
   a.max_fields = sc.max_fields;
   a.win_max = sc.win_max;
+  a.blob_max = sc.blob_max;
   if (ev) chk(cudaEventRecord(ev[0], s));
   chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
   if (ev) chk(cudaEventRecord(ev[1], s));

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -111,8 +112,37 @@ struct DevStage {
   int32_t win_len;    // per-case window entries
   int32_t ndep, dep0; // dependencies: pairs (stage, blocks) in the dependency list
   int32_t sum_slot;   // index of this stage's total in the per-case sums (pass * n_cliques + clique)
-  int32_t pad[4];
+  // fast path: the ports with windows and their key tables, precomputed and
+  // carried in the stage's descriptor blob (byte offsets from its start):
+  // LivePort[n_live] at live_off, then int32 kiter[n_live][kMaxIter] (entries
+  // past the block's n_iter repeat its last one), then uint16
+  // kt[n_live][consumers]
+  int32_t n_live, n_in_live;  // ports with windows, of which [0, n_in_live) are inputs
+  int32_t n_iter;             // consumer iterations of one block
+  int32_t live_off;
 };
+
+// A port with a window, as the fast path reads it.  An entry at block offset
+// o = m * (consumers * VEC) + tid * VEC + j has the key
+// kt[port][tid] + kiter[port][m] + dvec[j] (kt includes the window start).
+struct LivePort {
+  int32_t mode;       // bits 0-1 vmode, bit 2 key depends on the iteration, bits 3-7 lane_free,
+                      // bit 8 key depends on the chunk, bit 9 the window is the block itself
+  int32_t port;
+  int32_t win;        // start of the port's window (in every case's window row)
+  int32_t pad;
+  int32_t dvec[4];
+};
+static_assert(sizeof(LivePort) == 32 && offsetof(LivePort, win) == 8 && offsetof(LivePort, dvec) == 16,
+              "live-port table layout");
+constexpr int32_t kModeIter = 4;
+constexpr int32_t kModeChunk = 256;
+constexpr int32_t kModeStore = 512;
+
+// Byte offsets of the key tables inside a stage blob.
+__host__ __device__ inline int32_t kiter_off(const DevStage& S) { return S.live_off + S.n_live * 32; }
+constexpr int kMaxIter = 64;                    // consumer iterations of one fast-path block
+__host__ __device__ inline int32_t kt_off(const DevStage& S) { return kiter_off(S) + S.n_live * kMaxIter * 4; }
 
 static_assert(sizeof(DevField) % 16 == 0 && sizeof(DevPos) % 16 == 0, "descriptor blobs are 16-byte granular");
 static_assert(sizeof(DevPort) % 16 == 0 && sizeof(DevStage) % 16 == 0, "descriptor blobs are 16-byte granular");
@@ -171,6 +201,7 @@ struct PropArgs {
   int32_t ring;                 // bulk-copy stages
   int32_t chunk;                // entries per stage
   int32_t max_k, max_ports, max_fields, win_max;
+  int32_t blob_max;             // bytes of the largest stage blob
 };
 
 template <typename T>
@@ -243,10 +274,12 @@ struct Schedule {
   std::vector<DevField> fields;
   std::vector<DevPos> pos;
   std::vector<int32_t> deps;
-  std::vector<uint4> blobs;                 // per stage: DevStage, DevPort[np], DevField[nf], DevPos[k]
+  std::vector<uint4> blobs;                 // per stage: DevStage, DevPort[np], DevField[nf], DevPos[k],
+                                            // and on the fast path the live ports and key tables
   std::vector<DevItem> items;
   int32_t ring = 0, chunk = 0;
   int32_t max_k = 1, max_ports = 1, max_fields = 1, win_max = 1;
+  int32_t blob_max = 16;                    // bytes of the largest stage blob
   int64_t streamed_entries = 0;             // entries streamed per case block (all stages)
 };
 

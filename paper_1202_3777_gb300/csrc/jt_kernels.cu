@@ -94,6 +94,11 @@ __device__ __forceinline__ int4 sld_v4s32(uint32_t a) {
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
   return v;
 }
+__device__ __forceinline__ uint32_t sld_u16(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
 __device__ __forceinline__ void sld_vec(uint32_t a, float (&x)[4]) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(a));
 }
@@ -419,9 +424,11 @@ struct Smem {
   unsigned char* win;       // [cb][win_max] windows
   double* red;
   int* misc;                // [0] abort flag, [2] current item index
-  int* kiter;               // [kMaxFastPorts][kMaxIter] per-iteration key parts of the live ports
+  // case blocks: the live ports' key tables, computed per item (one-case
+  // schedules read them from the blob)
+  int* kiter;               // [kMaxFastPorts][kMaxIter]
   unsigned char* live;      // [kMaxFastPorts] LivePort
-  int* kt;                  // [kMaxFastPorts][consumers] per-thread key parts of the live ports
+  int* kt;                  // [kMaxFastPorts][consumers]
   unsigned char* ring;
   // buffer strides (bytes)
   uint32_t obs_b, nobs_b, bf_b, pval_b, win_b;
@@ -871,20 +878,6 @@ __device__ __forceinline__ bool hand_over(const Smem& s, uint32_t& k, int4 g, co
 
 // ---- consumers ------------------------------------------------------------
 
-// A port with a window, as the fast path reads it (shared memory).
-struct LivePort {
-  int32_t mode;       // bits 0-1 vmode, bit 2 key depends on the iteration, bits 3-7 lane_free,
-                      // bit 8 key depends on the chunk, bit 9 the window is the block itself
-  int32_t port;
-  int32_t win;        // start of the port's window (in every case's window row)
-  int32_t pad;
-  int4 dvec;
-};
-static_assert(sizeof(LivePort) == 32 && offsetof(LivePort, win) == 8 && offsetof(LivePort, dvec) == 16,
-              "live-port table layout");
-constexpr int32_t kModeIter = 4;
-constexpr int32_t kModeChunk = 256;
-constexpr int32_t kModeStore = 512;
 
 // Stream the chunks of one item (fast path: power-of-two clique, the block
 // starts on a vector boundary, at most kMaxFastPorts ports).  An entry's
@@ -900,20 +893,30 @@ constexpr int32_t kModeStore = 512;
 // (flushed at the end of the item).
 template <typename T, int CB>
 __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s, const DevItem& w, int ncb, int cb0,
-                                            int n_in, int n_live, bool any_obs, const T (&bfv)[CB], T (&tot)[CB],
-                                            RingPos& rp) {
+                                            int n_in, int n_live, int live_off, int ki_off, int kt_o, bool any_obs,
+                                            const T (&bfv)[CB], T (&tot)[CB], RingPos& rp) {
   constexpr int NT = consumers_for(CB);
   constexpr int VEC = VecT<T>::N;
   constexpr int VPT = chunk_bytes_for(CB) / (16 * NT);  // vectors per thread per chunk
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t RS = (uint32_t)a.ring, CH = (uint32_t)a.chunk;
   const uint32_t ring32 = smem_u32(s.ring), win32 = smem_u32(s.win);
-  const uint32_t kt32 = smem_u32(s.kt) + 4u * (uint32_t)tid, ki32 = smem_u32(s.kiter);
+  // the live ports and key tables in the blob: kt (16-bit) per thread,
+  // kiter per iteration, rows of kMaxIter (past the block: the last entry)
+  constexpr bool kBlob = CB == 1;   // tables in the blob (16-bit kt) or computed per item (32-bit kt)
+  const uint32_t blob32 = smem_u32(s.stage);
+  const uint32_t kt32 = kBlob ? blob32 + (uint32_t)kt_o + 2u * (uint32_t)tid : smem_u32(s.kt) + 4u * (uint32_t)tid;
+  const uint32_t ki32 = kBlob ? blob32 + (uint32_t)ki_off : smem_u32(s.kiter);
+  auto ktld = [&](int i) -> uint32_t {
+    return kBlob ? sld_u16(kt32 + 2u * (uint32_t)(i * NT)) : (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+  };
   const uint32_t wstride = (uint32_t)a.win_max * (uint32_t)sizeof(T);  // bytes between cases' windows
-  const LivePort* lp = reinterpret_cast<const LivePort*>(s.live);
+  const LivePort* lp = kBlob ? reinterpret_cast<const LivePort*>(reinterpret_cast<const unsigned char*>(s.stage) + live_off)
+                             : reinterpret_cast<const LivePort*>(s.live);
   // (the hot loop reads the live-port table and the evidence lists with
   // explicit shared-memory loads)
-  const uint32_t lp32 = smem_u32(s.live), nobs32 = smem_u32(s.nobs), obs32 = smem_u32(s.obs);
+  const uint32_t lp32 = kBlob ? blob32 + (uint32_t)live_off : smem_u32(s.live);
+  const uint32_t nobs32 = smem_u32(s.nobs), obs32 = smem_u32(s.obs);
   const int nchunks = (int)((w.n + CH - 1) / CH);
   // register-accumulated outputs
   int ra = -1, ja = -1;
@@ -927,7 +930,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
   for (int cl = 0; cl < CB; ++cl) racc[cl] = T(0);
   uint32_t rkt = 0, rlf = 0, rcur = 0;
   if (ra >= 0) {
-    rkt = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(ra * NT));
+    rkt = (uint32_t)ktld(ra);
     rlf = (uint32_t)(lp[ra].mode >> 3) & 31u;
     rcur = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter));
   }
@@ -993,7 +996,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     // input gathers
     for (int i = 0; i < n_in; ++i) {
       const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
-      const uint32_t kti = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+      const uint32_t kti = (uint32_t)ktld(i);
       // (a lane past the block's end reads its port window's first entries,
       // which are always filled: its own key may lie outside the window)
       const uint32_t kwin = (uint32_t)sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 8u);
@@ -1081,7 +1084,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     for (int i = n_in; i < n_live; ++i) {
       if (i == ra || i == ja) continue;
       const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
-      const uint32_t kti = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(i * NT));
+      const uint32_t kti = (uint32_t)ktld(i);
       uint32_t ka[VPT];
 #pragma unroll
       for (int it = 0; it < VPT; ++it) {
@@ -1149,9 +1152,9 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
                             lane);
   }
   if (ja >= 0) {
-    const uint32_t kt = (uint32_t)sld_s32(kt32 + 4u * (uint32_t)(ja * NT));
+    const uint32_t kt = (uint32_t)ktld(ja);
     const uint32_t lf = (uint32_t)(lp[ja].mode >> 3) & 31u;
-    const int4 dv = lp[ja].dvec;
+    const int4 dv = make_int4(lp[ja].dvec[0], lp[ja].dvec[1], lp[ja].dvec[2], lp[ja].dvec[3]);
     const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
     const bool lead = (lane & lf) == 0u;
 #pragma unroll
@@ -1251,7 +1254,6 @@ template <typename T, int CB>
 __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s, const DevItem& w, uint32_t b,
                                              RingPos& rp, uint32_t& sigk) {
   constexpr int NT = consumers_for(CB);
-  constexpr int VEC = VecT<T>::N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const DevStage S = *s.stage;
   const int cb0 = a.case0 + w.cbk * CB;
@@ -1261,41 +1263,36 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
   const int idx_item = s.misc[2];
   uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)idx_item * kTraceSlots : nullptr;
 
-  // fast path: the ports with windows (inputs first), their per-thread and
-  // per-iteration key parts (iteration m covers block offsets
-  // [m, m + 1) * consumers * VEC)
-  int n_in = 0, n_live = 0;
-  if (fast) {
-    for (int pi = 0; pi < S.np; ++pi) {
-      if (s.port[pi].K <= 1) continue;
-      if (pi < S.nin) ++n_in;
-      ++n_live;
-    }
-    LivePort* lp = reinterpret_cast<LivePort*>(s.live);
-    const int mi = (w.n + NT * VEC - 1) / (NT * VEC);
-    int li = 0;
-    for (int pi = 0; pi < S.np; ++pi) {
-      const DevPort& P = s.port[pi];
-      if (P.K <= 1) continue;
-      if (tid == li) {
-        LivePort L;
-        L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
-                 ((P.vmode & kVmodeStore) ? kModeStore : 0) |
-                 (int32_t)((P.lane_free & 31u) << 3);
-        L.port = pi;
-        L.win = P.win;
-        L.pad = 0;
-        L.dvec = make_int4(P.dvec[0], P.dvec[1], P.dvec[2], P.dvec[3]);
-        lp[li] = L;
+  // fast path: the ports with windows (inputs first) and their key tables:
+  // precomputed in the stage's blob for one case; computed here for a case
+  // block (iteration m covers block offsets [m, m + 1) * consumers * VEC)
+  if constexpr (CB > 1) {
+    constexpr int VEC = VecT<T>::N;
+    if (fast) {
+      LivePort* lp = reinterpret_cast<LivePort*>(s.live);
+      const int mi = (w.n + NT * VEC - 1) / (NT * VEC);
+      int li = 0;
+      for (int pi = 0; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1) continue;
+        if (tid == li) {
+          LivePort L;
+          L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
+                   ((P.vmode & kVmodeStore) ? kModeStore : 0) | (int32_t)((P.lane_free & 31u) << 3);
+          L.port = pi;
+          L.win = P.win;
+          L.pad = 0;
+          for (int j = 0; j < 4; ++j) L.dvec[j] = P.dvec[j];
+          lp[li] = L;
+        }
+        s.kt[li * NT + tid] = (int)(key_of<true>((uint32_t)tid * VEC, s.fld + P.f0, P.nf) + (uint32_t)P.win);
+        for (int m = tid; m < mi; m += NT)
+          s.kiter[li * kMaxIter + m] = (int)key_of<true>((uint32_t)m * NT * VEC, s.fld + P.f0, P.nf);
+        ++li;
       }
-      s.kt[li * NT + tid] = (int)(key_of<true>((uint32_t)tid * VEC, s.fld + P.f0, P.nf) + (uint32_t)P.win);
-      for (int m = tid; m < mi; m += NT)
-        s.kiter[li * kMaxIter + m] = (int)key_of<true>((uint32_t)m * NT * VEC, s.fld + P.f0, P.nf);
-      ++li;
     }
+    consumer_sync<NT>();
   }
-  consumer_sync<NT>();
-
   // stream the block
   if (tr != nullptr && tid == 0) tr[3] = global_ns();
   T bfv[CB], tot[CB];
@@ -1306,7 +1303,8 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
     tot[cl] = T(0);
     if (cl < ncb && s.nobs[cl] > 0) any_obs = true;
   }
-  const bool sok = fast ? stream_fast<T, CB>(a, s, w, ncb, cb0, n_in, n_live, any_obs, bfv, tot, rp)
+  const bool sok = fast ? stream_fast<T, CB>(a, s, w, ncb, cb0, S.n_in_live, S.n_live, S.live_off, kiter_off(S),
+                                              kt_off(S), any_obs, bfv, tot, rp)
                         : stream_generic<T, CB>(a, s, S, w, ncb, cb0, bfv, tot, rp);
   if (!consumer_all<NT>(sok)) {
     if (tid == 0) {
@@ -1426,7 +1424,7 @@ template <typename T, int CB>
 __global__ void __launch_bounds__(consumers_for(CB) + kControlThreads, ctas_per_sm_for(CB)) k_propagate(const PropArgs<T> a) {
   constexpr int NT = consumers_for(CB);
   extern __shared__ __align__(128) unsigned char smem[];
-  const SmemLayout L(CB, a.ring, a.chunk, a.max_k, a.max_ports, a.max_fields, a.win_max, (int)sizeof(T));
+  const SmemLayout L(CB, a.ring, a.chunk, a.max_k, a.max_ports, a.blob_max, a.win_max, (int)sizeof(T));
   const Smem s = carve(smem, L, a.ring, CB, a.max_k, a.max_ports, a.win_max, (int)sizeof(T));
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.ring; ++i) {

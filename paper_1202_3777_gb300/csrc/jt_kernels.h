@@ -19,32 +19,38 @@ __host__ __device__ constexpr int chunk_bytes_for(int cb) { return cb > 1 ? 8192
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
 constexpr int kControlThreads = 96;             // producer, signalling and preparation warps
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
-constexpr int kMaxIter = 64;                    // consumer iterations of one fast-path block
 
-// Bytes of the largest descriptor blob of a schedule.
-__host__ __device__ inline int32_t blob_max(int max_k, int max_ports, int max_fields) {
-  return (int32_t)sizeof(DevStage) + max_ports * (int32_t)sizeof(DevPort) + max_fields * (int32_t)sizeof(DevField) +
-         max_k * (int32_t)sizeof(DevPos);
+// Bytes of a stage's descriptors (DevStage, ports, fields, positions).
+__host__ __device__ inline int32_t desc_bytes(int k, int np, int nf) {
+  return (int32_t)sizeof(DevStage) + np * (int32_t)sizeof(DevPort) + nf * (int32_t)sizeof(DevField) +
+         k * (int32_t)sizeof(DevPos);
+}
+// Bytes of a fast-path stage's live ports and key tables.
+// (one-case schedules carry them in the blob; case-block schedules compute
+// them per item into shared memory, which leaves their hot loop's registers
+// as they are)
+__host__ __device__ inline int32_t table_bytes(int cb, int n_live) {
+  return cb == 1 ? n_live * (32 + kMaxIter * 4 + consumers_for(cb) * 2) : 0;
 }
 
 // Dynamic shared memory of a propagation CTA, carved identically by the
 // planner (host) and the kernel (device).  Everything an item needs besides
-// the streamed table (descriptor blob, evidence lists, block factors,
-// windows) is double-buffered: the control warp prepares item i+1 and
-// flushes item i-1 while the consumers stream item i.
+// the streamed table (descriptor blob with its key tables, evidence lists,
+// block factors, windows) is double-buffered: the control warps prepare item
+// i+1 and flush item i-1 while the consumers stream item i.
 struct SmemLayout {
   int32_t bar, info, sig, blob, blob_bytes, obs, nobs, bf, pval, red, misc, kiter, live, kt, win, ring, bytes;
 
   __host__ __device__ static int32_t a16(int32_t x) { return (x + 15) & ~15; }
 
-  __host__ __device__ SmemLayout(int cb, int ring_n, int chunk, int max_k, int max_ports, int max_fields,
+  __host__ __device__ SmemLayout(int cb, int ring_n, int chunk, int max_k, int max_ports, int blob_max,
                                  int win_max, int elem) {
     int32_t o = 0;
     bar = o;  o += (2 * ring_n + 8 + 2 * kSig) * 8;   // ring full/empty; per buffer: item, blob, prepared,
                                                       // flushed; signal slots full/empty
     info = a16(o);   o = info + 2 * 64;                // per buffer: the item and its preparation status
     sig = a16(o);    o = sig + kSig * 16;              // finished items for the signalling lane
-    blob_bytes = blob_max(max_k, max_ports, max_fields);
+    blob_bytes = a16(blob_max);
     blob = (o + 127) & ~127; o = blob + 2 * blob_bytes;
     obs = a16(o);    o = obs + 2 * cb * max_k * 16;    // in-block observations per case
     nobs = a16(o);   o = nobs + 2 * cb * 4;
@@ -52,9 +58,12 @@ struct SmemLayout {
     pval = a16(o);   o = pval + 2 * cb * max_ports * 8;  // per (case, input port) factor
     red = a16(o);    o = red + cb * (consumers_for(cb) / 32) * 8;  // block-total partials
     misc = a16(o);   o = misc + 16 * 4;
-    kiter = a16(o);  o = kiter + kMaxFastPorts * kMaxIter * 4;  // per-iteration key part of every live port
-    live = a16(o);   o = live + kMaxFastPorts * 32;             // live ports: index, mode, dvec
-    kt = a16(o);     o = kt + kMaxFastPorts * consumers_for(cb) * 4;  // per-thread key part of every live port
+    kiter = live = kt = 0;
+    if (cb > 1) {  // key tables computed per item (case blocks)
+      kiter = a16(o);  o = kiter + kMaxFastPorts * kMaxIter * 4;
+      live = a16(o);   o = live + kMaxFastPorts * 32;
+      kt = a16(o);     o = kt + kMaxFastPorts * consumers_for(cb) * 4;
+    }
     win = (o + 127) & ~127;  o = win + 2 * cb * win_max * elem;
     ring = (o + 127) & ~127; o = ring + ring_n * chunk * elem;
     bytes = o;

@@ -429,7 +429,11 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
   }
 
   // shared memory: what the windows may use once the ring and descriptors fit
-  const int fixed = SmemLayout(cb, s->ring, s->chunk, s->max_k, s->max_ports, s->max_fields, 0, elem).bytes;
+  // (the blob bound: every descriptor at its maximum plus the key tables of
+  // the most live ports and iterations a fast-path block can have)
+  const int blob_bound = desc_bytes(s->max_k, s->max_ports, s->max_fields) +
+                         table_bytes(cb, std::min(s->max_ports, kMaxFastPorts));
+  const int fixed = SmemLayout(cb, s->ring, s->chunk, s->max_k, s->max_ports, blob_bound, 0, elem).bytes;
   const int64_t win_budget = (int64_t)(smem_bytes - fixed - 256) / (2ll * cb * elem);  // two buffers
   if (win_budget < (int64_t)s->max_ports * VEC) {
     *err = "the tree's descriptors do not fit in shared memory";
@@ -598,19 +602,91 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
   // item reads about its stage (one bulk copy fetches it)
   std::vector<int32_t> blob_at(2 * nc, 0), blob_len(2 * nc, 0);
   s->blobs.clear();
+  s->blob_max = 16;
+  const int NT = consumers_for(cb);
   for (int st = 0; st < 2 * nc; ++st) {
-    const DevStage& S = s->stages[st];
+    DevStage& S = s->stages[st];
     if (S.n_blocks == 0) continue;
+    // fast path: the ports with windows (inputs first, port order) and their
+    // key tables: kt[port][tid] = key(tid * VEC) + window start (16-bit),
+    // kiter[port][m] = key(m * consumers * VEC), from the block's own bits
+    std::vector<LivePort> live;
+    std::vector<int32_t> kit;
+    std::vector<uint16_t> ktab;
+    S.n_live = S.n_in_live = S.n_iter = 0;
+    S.live_off = 0;
+    if (S.bits >= 0) {
+      const int64_t per_it = (int64_t)NT * VEC;
+      S.n_iter = (int32_t)((S.B + per_it - 1) / per_it);
+      for (int pi = 0; pi < S.np; ++pi) {
+        const DevPort& P = s->ports[S.port0 + pi];
+        if (P.K <= 1) continue;
+        LivePort L{};
+        L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
+                 ((P.vmode & kVmodeStore) ? kModeStore : 0) | (int32_t)((P.lane_free & 31u) << 3);
+        L.port = pi;
+        L.win = P.win;
+        for (int j = 0; j < 4; ++j) L.dvec[j] = P.dvec[j];
+        live.push_back(L);
+        if (pi < S.nin) ++S.n_in_live;
+      }
+      S.n_live = (int32_t)live.size();
+    }
+    if (S.bits >= 0 && cb == 1) {  // one-case schedules carry the tables in the blob
+      const int64_t per_it = (int64_t)NT * VEC;
+      if (S.n_iter > kMaxIter) {
+        *err = "block longer than the iteration table";
+        return JT_ERR_UNSUPPORTED;
+      }
+      kit.assign((size_t)S.n_live * kMaxIter, 0);
+      ktab.assign((size_t)S.n_live * NT, 0);
+      const uint32_t bmask = (uint32_t)S.B - 1u;
+      for (int li = 0; li < S.n_live; ++li) {
+        const DevPort& P = s->ports[S.port0 + live[li].port];
+        const DevField* f = &s->fields[S.field0 + P.f0];
+        auto key = [&](uint32_t x) {
+          uint32_t k = 0;
+          for (int q = 0; q < P.nf; ++q) k += ((x >> f[q].sh) & ((1u << f[q].lb) - 1u)) * (uint32_t)f[q].w;
+          return k;
+        };
+        for (int m = 0; m < kMaxIter; ++m)
+          kit[(size_t)li * kMaxIter + m] = (int32_t)key((uint32_t)(std::min(m, S.n_iter - 1) * per_it));
+        for (int t = 0; t < NT; ++t) {
+          // (a thread past the block's end gets a key inside the window)
+          const uint32_t v = key(((uint32_t)t * VEC) & bmask) + (uint32_t)P.win;
+          if (v > 0xFFFFu) {
+            *err = "window keys exceed 16 bits";
+            return JT_ERR_UNSUPPORTED;
+          }
+          ktab[(size_t)li * NT + t] = (uint16_t)v;
+        }
+      }
+      S.live_off = desc_bytes(S.k, S.np, S.nf);
+    }
     blob_at[st] = (int32_t)s->blobs.size();
     auto put = [&](const void* src, size_t bytes) {
-      const uint4* q = static_cast<const uint4*>(src);
-      for (size_t i = 0; i < bytes / sizeof(uint4); ++i) s->blobs.push_back(q[i]);
+      const unsigned char* q = static_cast<const unsigned char*>(src);
+      for (size_t i = 0; i < bytes; i += sizeof(uint4)) {
+        uint4 u{};
+        std::memcpy(&u, q + i, std::min(sizeof(uint4), bytes - i));
+        s->blobs.push_back(u);
+      }
     };
     put(&S, sizeof(DevStage));
     if (S.np) put(&s->ports[S.port0], S.np * sizeof(DevPort));
     if (S.nf) put(&s->fields[S.field0], S.nf * sizeof(DevField));
     put(&s->pos[S.pos0], S.k * sizeof(DevPos));
+    if (S.n_live && cb == 1) {
+      put(live.data(), live.size() * sizeof(LivePort));
+      put(kit.data(), kit.size() * sizeof(int32_t));     // padded to 16 bytes
+      put(ktab.data(), ktab.size() * sizeof(uint16_t));
+    }
     blob_len[st] = (int32_t)((s->blobs.size() - blob_at[st]) * sizeof(uint4));
+    if (S.n_live && cb == 1 && blob_len[st] != S.live_off + table_bytes(cb, S.n_live)) {
+      *err = "stage blob layout mismatch";
+      return JT_ERR_UNSUPPORTED;
+    }
+    s->blob_max = std::max(s->blob_max, blob_len[st]);
   }
 
   // work items: collect deepest level first, then distribute from the root,
@@ -694,7 +770,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
 }
 
 int32_t prop_smem_bytes(const Schedule& s, int elem) {
-  return SmemLayout(s.cb, s.ring, s.chunk, s.max_k, s.max_ports, s.max_fields, s.win_max, elem).bytes;
+  return SmemLayout(s.cb, s.ring, s.chunk, s.max_k, s.max_ports, s.blob_max, s.win_max, elem).bytes;
 }
 
 template <typename T>
