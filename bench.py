@@ -123,9 +123,9 @@ class Clocks:
 # captured; every case block streams the tables again, so traffic grows with
 # their number).
 TRAFFIC = {
-    "sources_sha256": "818ff6acb73afd29b549e23589b5c31c504d7f55dde8f9138952d5d788608845",
-    "plain": 473324800 + 4078848,
-    "per_case_block": (966231040 + 18713856) / 2,
+    "sources_sha256": "56fbbfc808536fb9f9992da04c27e58f4b69d36f316ed2b0bbad5e4e0667e021",
+    "plain": 469917184 + 4596224,
+    "per_case_block": (966790912 + 19120640) / 2,
 }
 TRAFFIC_SOURCES = ["paper_1202_3777_gb300/csrc/jt_kernels.cu", "paper_1202_3777_gb300/csrc/jt_kernels.h",
                    "paper_1202_3777_gb300/csrc/jt_internal.h", "paper_1202_3777_gb300/csrc/jt_plan.cpp"]
