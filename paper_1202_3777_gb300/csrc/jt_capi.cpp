@@ -225,8 +225,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
 // Plan the schedule of a case range, upload it, and record the propagation
 // into a CUDA graph.
 template <typename T>
-jt_status record_schedule(jt_tree t, int case0, int n_cases, cudaStream_t s, GraphEntry* ge) {
-  const int cb = n_cases > 1 ? kCaseBlock : 1;
+jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, cudaStream_t s, GraphEntry* ge) {
   std::string err;
   const int smem_cap = smem_budget(t->device, ctas_per_sm_for(cb)) - 256;
   jt_status st = build_schedule(t->plan, (int)t->elem, cb, n_cases, t->n_sm, smem_cap, &ge->sched, &err);
@@ -264,7 +263,40 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, cudaStream_t s, Gra
   return JT_OK;
 }
 
-jt_status get_graph(jt_tree t, int first, int n, GraphEntry** out) {
+void drop_graph(GraphEntry& ge) {
+  if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  if (ge.graph) cudaGraphDestroy(ge.graph);
+  for (void* p : ge.dev_bufs) cudaFree(p);
+  ge.exec = nullptr;
+  ge.graph = nullptr;
+  ge.dev_bufs.clear();
+}
+
+// Device time of one launch of a recorded propagation on `s` (ms), or a
+// negative value on error.
+float time_graph(const GraphEntry& ge, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = -1.f;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+      cudaEventRecord(e0, s) == cudaSuccess && cudaGraphLaunch(ge.exec, s) == cudaSuccess &&
+      cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
+    cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return ms;
+}
+
+// The propagation graph of a case range, recorded on first use.  Several
+// cases can go one per work item (more, shorter items; every item streams
+// its table for one case) or in blocks of kCaseBlock (each streamed table
+// chunk serves 8 cases).  Which is faster depends on the tree and the
+// number of cases: blocks pay off for cliques with many ports and many
+// cases, single cases for small trees, few cases or few ports.  So the
+// first use of a multi-case range times both schedules once (after a
+// warm-up launch of each; the launches compute the same propagation the
+// caller asked for) and keeps the faster.  JT_CASE_BLOCK=1 or 8 in the
+// environment fixes the choice instead.
+jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** out) {
   auto key = std::make_pair(first, n);
   auto it = t->graphs.find(key);
   if (it == t->graphs.end()) {
@@ -272,14 +304,30 @@ jt_status get_graph(jt_tree t, int first, int n, GraphEntry** out) {
       CU(cudaDeviceSynchronize(), "graph cache eviction");
       free_graphs(t);
     }
+    int forced = 0;
+    if (const char* f = std::getenv("JT_CASE_BLOCK"); f && (*f == '1' || *f == '8') && f[1] == 0) forced = *f - '0';
+    auto record = [&](int cb, GraphEntry* ge) {
+      return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, t->cap_stream, ge)
+                                  : record_schedule<float>(t, first, n, cb, t->cap_stream, ge);
+    };
     GraphEntry ge;
-    jt_status st = t->compute == JT_F64 ? record_schedule<double>(t, first, n, t->cap_stream, &ge)
-                                        : record_schedule<float>(t, first, n, t->cap_stream, &ge);
+    const int cb0 = n == 1 ? 1 : (forced ? forced : kCaseBlock);
+    jt_status st = record(cb0, &ge);
     if (st != JT_OK) {
-      if (ge.exec) cudaGraphExecDestroy(ge.exec);
-      if (ge.graph) cudaGraphDestroy(ge.graph);
-      for (void* p : ge.dev_bufs) cudaFree(p);
+      drop_graph(ge);
       return st;
+    }
+    if (n > 1 && !forced) {
+      const std::string keep = g_err;   // a failed alternative leaves the chosen graph usable
+      GraphEntry ge1;
+      if (record(1, &ge1) == JT_OK) {
+        time_graph(ge, s);
+        time_graph(ge1, s);
+        const float t8 = time_graph(ge, s), t1 = time_graph(ge1, s);
+        if (t1 >= 0.f && t8 >= 0.f && t1 < t8) std::swap(ge, ge1);
+      }
+      drop_graph(ge1);
+      g_err = keep;
     }
     it = t->graphs.emplace(key, std::move(ge)).first;
   }
@@ -541,7 +589,7 @@ jt_status jt_propagate(jt_tree t, int32_t first, int32_t n, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
-  if ((st = get_graph(t, first, n, &ge)) != JT_OK) return st;
+  if ((st = get_graph(t, first, n, s, &ge)) != JT_OK) return st;
   CU(cudaGraphLaunch(ge->exec, s), "graph launch");
   for (int i = first; i < first + n; ++i) t->ready[i] = 1;
   t->last_stream = s;
@@ -560,7 +608,7 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
-  if ((st = get_graph(t, first, n, &ge)) != JT_OK) return st;
+  if ((st = get_graph(t, first, n, s, &ge)) != JT_OK) return st;
   // JT_TRACE=<file>: also record every work item's SM and timeline
   // (global timer, ns) and write them to <file> as CSV
   const char* trace_path = std::getenv("JT_TRACE");

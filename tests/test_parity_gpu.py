@@ -24,6 +24,15 @@ def jt():
     return mod
 
 
+@pytest.fixture(params=["1", "8"])
+def case_block(request, monkeypatch):
+    """Multi-case propagations pick one case per work item or blocks of 8 by
+    timing both on first use; these tests pin each schedule in turn so both
+    stay covered."""
+    monkeypatch.setenv("JT_CASE_BLOCK", request.param)
+    return int(request.param)
+
+
 def _prep(tree, prec):
     return tree.as_dtype(np.float32) if prec == "f32" else tree.as_dtype(np.float64)
 
@@ -58,7 +67,7 @@ def _check(tree, cases, lz, margs, prec, idx=None):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_small_tree(jt, prec):
+def test_small_tree(jt, case_block, prec):
     t = _prep(synth.small_tree(), prec)
     cases = [synth.random_evidence(t, 4, s) for s in range(5)] + [(np.zeros(0, np.int32),) * 2]
     lz, m, _ = _run_cases(jt, t, prec, cases)
@@ -66,7 +75,7 @@ def test_small_tree(jt, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_brute_force_variant(jt, prec):
+def test_brute_force_variant(jt, case_block, prec):
     t = _prep(synth.small_brute_tree(), prec)
     cases = [synth.random_evidence(t, k, k) for k in range(4)]
     lz, m, _ = _run_cases(jt, t, prec, cases)
@@ -75,7 +84,7 @@ def test_brute_force_variant(jt, prec):
 
 @pytest.mark.parametrize("seed", range(16))
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_random_small_trees(jt, seed, prec):
+def test_random_small_trees(jt, case_block, seed, prec):
     """Random cardinalities 2-5, empty separators, separator variables in any
     position of the listed order."""
     t = _prep(synth.random_small_tree(seed, n_cliques=3 + seed % 9, allow_empty_sep=True,
@@ -86,7 +95,7 @@ def test_random_small_trees(jt, seed, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_batched_tree_ragged_batch(jt, prec):
+def test_batched_tree_ragged_batch(jt, case_block, prec):
     """256-clique tree with mixed cardinalities; 37 cases (a ragged last
     case block), compared on a sample of cases."""
     t = _prep(synth.batched_tree(), prec)
@@ -96,7 +105,7 @@ def test_batched_tree_ragged_batch(jt, prec):
     _check(t, cases, lz, m, prec, idx=[0, 7, 8, 21, 36])
 
 
-def test_batched_equals_one_at_a_time(jt):
+def test_batched_equals_one_at_a_time(jt, case_block):
     """Each case's result is the same alone and inside a batch."""
     t = _prep(synth.batched_tree(n_cliques=64), "f32")
     ev = synth.evidence_matrix(t, 19, 0.10, 77)
@@ -109,7 +118,7 @@ def test_batched_equals_one_at_a_time(jt):
 
 
 @pytest.mark.parametrize("builder", ["large_clique", "high_card"])
-def test_reduced_large_configs(jt, builder):
+def test_reduced_large_configs(jt, case_block, builder):
     """Smaller members of the large-clique families: several tiles per
     clique and ragged tails, FP32 and FP64."""
     if builder == "large_clique":
@@ -125,7 +134,7 @@ def test_reduced_large_configs(jt, builder):
 
 @pytest.mark.parametrize("name", ["large_clique", "high_card"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_full_size_configs(jt, name, prec):
+def test_full_size_configs(jt, case_block, name, prec):
     """64 x 2^20 and 48 x 2^20 entry trees at the sizes the benchmark runs."""
     w = synth.WORKLOADS[name]
     t = _prep(w["build"](), prec)
@@ -134,7 +143,7 @@ def test_full_size_configs(jt, name, prec):
     _check(t, cases, lz, m, prec)
 
 
-def test_binary_serving_tree(jt):
+def test_binary_serving_tree(jt, case_block):
     t = _prep(synth.binary_serving_tree(), "f32")
     ev = synth.evidence_matrix(t, 9, (0.01, 0.20), 99)
     cases = [synth.case_from_row(r) for r in ev]
@@ -142,12 +151,13 @@ def test_binary_serving_tree(jt):
     _check(t, cases, lz, m, "f32", idx=[0, 4, 8])
 
 
-def test_results_do_not_depend_on_stale_shared_memory(jt):
+def test_results_do_not_depend_on_stale_shared_memory(jt, monkeypatch):
     """A propagation reads no shared memory it did not write: an FP64
     propagation first leaves its own values (NaN and Inf bit patterns as
     FP32) in every SM's shared memory, and ragged case blocks of tiny cliques
     (lanes past the block end, two-entry windows) must still give the
     oracle's results."""
+    monkeypatch.setenv("JT_CASE_BLOCK", "8")   # the case-block schedule (ragged: 9 cases)
     big = _prep(synth.high_card_tree(), "f64")
     hb = jt.jt_load_synth(big, compute=jt.JT_F64, max_cases=16)
     jt.jt_set_evidence_dense(hb, 0, synth.evidence_matrix(big, 16, 0.05, 3))
@@ -163,8 +173,25 @@ def test_results_do_not_depend_on_stale_shared_memory(jt):
             first = (lz, m)
             _check(t, cases, lz, m, "f32", idx=[0, 5, 8])
         else:
-            assert np.array_equal(lz, first[0])
+            assert np.all(np.abs(lz - first[0]) <= 1e-6 * np.maximum(1.0, np.abs(first[0])))
     hb.free()
+
+
+def test_case_block_choice_by_timing(jt, monkeypatch):
+    """Without JT_CASE_BLOCK the first multi-case propagation of a range
+    times both schedules and keeps one: the results match the oracle and
+    later propagations of the range reuse the choice (same results up to the
+    order of atomic additions)."""
+    monkeypatch.delenv("JT_CASE_BLOCK", raising=False)
+    t = _prep(synth.small_tree(), "f32")
+    ev = synth.evidence_matrix(t, 12, 0.10, 5)
+    cases = [synth.case_from_row(r) for r in ev]
+    lz, m, h = _run_cases(jt, t, "f32", cases)
+    _check(t, cases, lz, m, "f32", idx=[0, 11])
+    jt.jt_propagate(h, 0, len(cases))
+    lz2 = jt.jt_get_log_evidence(h, 0, len(cases))
+    assert np.all(np.abs(lz2 - lz) <= 1e-6 * np.maximum(1.0, np.abs(lz)))
+    h.free()
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
