@@ -837,6 +837,26 @@ __device__ __forceinline__ void signaller(const PropArgs<T>& a, const Smem& s0) 
     const DevStage& S = *s.stage;
     const DevItem& w = s0.info[b].w;
     bool any = false;
+    if constexpr (CB == 1) {
+      // the block total (left in the block-factor slot): stage total and
+      // block-constant outputs
+      const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
+      const int c0 = a.case0 + g.y * CB;
+      const int ncb = min(CB, a.case0 + a.n_cases - c0);
+      const bool fast = S.bits >= 0;
+      for (int cl = 0; cl < ncb; ++cl) {
+        const double t = s.bf[cl];
+        if (t == 0.0) continue;
+        T* row = a.msg + (int64_t)(c0 + cl) * a.msg_stride;
+        for (int pi = S.nin; pi < S.np; ++pi) {
+          const DevPort& P = s.port[pi];
+          if (P.K > 1) continue;
+          const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+          atomicAdd(row + P.tab + key, (T)t);
+        }
+        atomicAdd(a.sums + (int64_t)(c0 + cl) * 2 * a.n_cliques + S.sum_slot, t);
+      }
+    }
     if (S.bits >= 0) {
       const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
       const int c0 = a.case0 + g.y * CB;
@@ -1325,21 +1345,30 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
     if (lane == 0) s.red[cl * (NT / 32) + warp] = (double)v;
   }
   consumer_sync<NT>();
+  // One case: the block total goes to the signalling lane through the
+  // buffer's block-factor slot (read by nothing else once the block has
+  // streamed), which adds it to the stage total and the block-constant
+  // outputs: the consumers then need no global fence.  A case block adds
+  // its totals here.
   bool wrote_global = false;
   if (tid < ncb) {
     double t = 0.0;
     for (int i = 0; i < NT / 32; ++i) t += s.red[tid * (NT / 32) + i];
-    const int cs = cb0 + tid;
-    T* row = a.msg + (int64_t)cs * a.msg_stride;
-    if (t != 0.0) {
-      wrote_global = true;
-      for (int pi = S.nin; pi < S.np; ++pi) {
-        const DevPort& P = s.port[pi];
-        if (P.K > 1) continue;
-        const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
-        atomicAdd(row + P.tab + key, (T)t);
+    if constexpr (CB == 1) {
+      s.bf[tid] = t;
+    } else {
+      const int cs = cb0 + tid;
+      T* row = a.msg + (int64_t)cs * a.msg_stride;
+      if (t != 0.0) {
+        wrote_global = true;
+        for (int pi = S.nin; pi < S.np; ++pi) {
+          const DevPort& P = s.port[pi];
+          if (P.K > 1) continue;
+          const uint32_t key = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
+          atomicAdd(row + P.tab + key, (T)t);
+        }
+        atomicAdd(a.sums + (int64_t)cs * 2 * a.n_cliques + S.sum_slot, t);
       }
-      atomicAdd(a.sums + (int64_t)cs * 2 * a.n_cliques + S.sum_slot, t);
     }
   }
   for (int pi = S.nin; pi < S.np; ++pi) {
@@ -1359,12 +1388,12 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
       }
     }
   }
-  // Every thread's global additions above (stage totals, block-constant
-  // outputs, windows the bulk unit cannot reduce) are made visible GPU-wide
-  // by the thread itself before the hand-over: the signalling lane's fence
-  // orders only what it wrote, and the item counts as done once it
-  // publishes.  Likewise every thread's shared-memory writes to the output
-  // windows are ordered before the bulk unit (the async proxy) reads them.
+  // Every thread's global additions above (case-block totals, windows the
+  // bulk unit cannot reduce) are made visible GPU-wide by the thread itself
+  // before the hand-over: the signalling lane's fence orders only what it
+  // wrote, and the item counts as done once it publishes.  Likewise every
+  // thread's shared-memory writes to the output windows are ordered before
+  // the bulk unit (the async proxy) reads them.
   if (wrote_global) __threadfence();
   fence_proxy_async();
   consumer_sync<NT>();
