@@ -627,14 +627,75 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
     const bool fast = S.bits >= 0;
     uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)inf.idx * kTraceSlots : nullptr;
     if (tr != nullptr && pl == 0) tr[11] = global_ns();
-    // dependencies
-    bool dok = true;
-    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, pl, NL, kMask);
-    if (tr != nullptr && pl == 0) tr[10] = global_ns();
+    // what needs no other item comes before the dependency wait (off the
+    // critical path): the evidence and the zeroed output windows
     if (pl < CB) {
       s.nobs[pl] = 0;
       s.bf[pl] = 1.0;
     }
+    __syncwarp(kMask);
+    // evidence (block-level digits into the block factor, in-block digits
+    // into per-case lists)
+    const int nev = ncb * S.k;
+    for (int t0 = pl; t0 < nev; t0 += U * NL) {
+      int sv[U];
+#pragma unroll
+      for (int r = 0; r < U; ++r) {
+        const int t = t0 + r * NL;
+        sv[r] = -1;
+        if (t >= nev) continue;
+        const int cl = t / S.k, i = t - cl * S.k;
+        sv[r] = a.ev[(int64_t)(cb0 + cl) * a.n_vars + s.pos[i].var];
+      }
+#pragma unroll
+      for (int r = 0; r < U; ++r) {
+        const int t = t0 + r * NL;
+        const int st = sv[r];
+        if (t >= nev || st < 0) continue;
+        const int cl = t / S.k, i = t - cl * S.k;
+        const DevPos& P = s.pos[i];
+        if (st >= P.card) {
+          atomicOr(&a.status[cb0 + cl], kStatusBadState);
+          continue;
+        }
+        if (fast) {
+          const int inside = max(0, min(P.cb, S.bits - P.sh));
+          const uint32_t lo_m = (1u << inside) - 1u;
+          const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
+          if (hi_d != ((uint32_t)st & ~lo_m)) {
+            s.bf[cl] = 0.0;
+          } else if (lo_m != 0u) {
+            const int slot2 = atomicAdd(&s.nobs[cl], 1);
+            s.obs[cl * a.max_k + slot2] = make_int4(P.sh, (int)lo_m, st & (int)lo_m, i);
+          }
+        } else if (i < S.k - S.kin) {
+          if (digit_of(eb, P) != (uint32_t)st) s.bf[cl] = 0.0;
+        } else {
+          const int slot2 = atomicAdd(&s.nobs[cl], 1);
+          s.obs[cl * a.max_k + slot2] = make_int4(i, 0, st, i);
+        }
+      }
+    }
+    {
+      // (a window the consumers store whole needs no zeros; 16-byte stores:
+      // windows are allocated in whole groups of 4 entries)
+      const uint32_t win32 = smem_u32(s.win);
+      constexpr int VEC = VecT<T>::N;
+      const T z[VEC] = {};
+      for (int pi = S.nin; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1 || ((P.vmode & kVmodeStore) && fast)) continue;
+        const int kr = (P.K + 3) / 4 * 4;
+        for (int cl = 0; cl < ncb; ++cl) {
+          const uint32_t dst = win32 + (uint32_t)(cl * a.win_max + P.win) * (uint32_t)sizeof(T);
+          for (int ii = pl * VEC; ii < kr; ii += NL * VEC) sst_vec(dst + (uint32_t)ii * (uint32_t)sizeof(T), z);
+        }
+      }
+    }
+    // dependencies
+    bool dok = true;
+    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, pl, NL, kMask);
+    if (tr != nullptr && pl == 0) tr[10] = global_ns();
     // the child-message windows first (bulk copies; the consumers wait for their bytes)
     uint32_t bulk_bytes = 0;
     if (dok) {
@@ -707,70 +768,17 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
           s.pval[cl * a.max_ports + pi] = v;
         }
       }
-      // evidence (block-level digits into the block factor, in-block digits
-      // into per-case lists)
-      const int nev = ncb * S.k;
-      for (int t0 = pl; t0 < nev; t0 += U * NL) {
-        int sv[U];
-#pragma unroll
-        for (int r = 0; r < U; ++r) {
-          const int t = t0 + r * NL;
-          sv[r] = -1;
-          if (t >= nev) continue;
-          const int cl = t / S.k, i = t - cl * S.k;
-          sv[r] = a.ev[(int64_t)(cb0 + cl) * a.n_vars + s.pos[i].var];
-        }
-#pragma unroll
-        for (int r = 0; r < U; ++r) {
-          const int t = t0 + r * NL;
-          const int st = sv[r];
-          if (t >= nev || st < 0) continue;
-          const int cl = t / S.k, i = t - cl * S.k;
-          const DevPos& P = s.pos[i];
-          if (st >= P.card) {
-            atomicOr(&a.status[cb0 + cl], kStatusBadState);
-            continue;
-          }
-          if (fast) {
-            const int inside = max(0, min(P.cb, S.bits - P.sh));
-            const uint32_t lo_m = (1u << inside) - 1u;
-            const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
-            if (hi_d != ((uint32_t)st & ~lo_m)) {
-              s.bf[cl] = 0.0;
-            } else if (lo_m != 0u) {
-              const int slot2 = atomicAdd(&s.nobs[cl], 1);
-              s.obs[cl * a.max_k + slot2] = make_int4(P.sh, (int)lo_m, st & (int)lo_m, i);
-            }
-          } else if (i < S.k - S.kin) {
-            if (digit_of(eb, P) != (uint32_t)st) s.bf[cl] = 0.0;
-          } else {
-            const int slot2 = atomicAdd(&s.nobs[cl], 1);
-            s.obs[cl * a.max_k + slot2] = make_int4(i, 0, st, i);
-          }
-        }
-      }
-      // windows that are not bulk copies: ratios of the own separator, child
-      // messages of unaligned windows, zeroed outputs
+      // input windows that are not bulk copies: ratios of the own separator,
+      // child messages of unaligned windows
       const uint32_t win32 = smem_u32(s.win);
-      for (int pi = 0; pi < S.np; ++pi) {
+      for (int pi = 0; pi < S.nin; ++pi) {
         const DevPort& P = s.port[pi];
         if (P.K <= 1) continue;
         if (P.kind == kPortMu && bulk_window<T>(S, P)) continue;
-        const bool output = P.kind != kPortMu && P.kind != kPortRho;
-        const uint32_t kb = output ? 0u : (fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf));
-        // (a window the consumers store whole needs no zeros)
-        if (output && (P.vmode & kVmodeStore) && fast) continue;
+        const uint32_t kb = fast ? key_of<true>(eb, s.fld + P.f0, P.nf) : key_of<false>(eb, s.fld + P.f0, P.nf);
         for (int cl = 0; cl < ncb; ++cl) {
           const int cs = cb0 + cl;
           const uint32_t dst = win32 + (uint32_t)(cl * a.win_max + P.win) * (uint32_t)sizeof(T);
-          if (output) {
-            // 16-byte stores (windows are allocated in whole groups of 4 entries)
-            constexpr int VEC = VecT<T>::N;
-            const T z[VEC] = {};
-            const int kr = (P.K + 3) / 4 * 4;
-            for (int ii = pl * VEC; ii < kr; ii += NL * VEC) sst_vec(dst + (uint32_t)ii * (uint32_t)sizeof(T), z);
-            continue;
-          }
           const T* row = a.msg + (int64_t)cs * a.msg_stride + P.tab + kb;
           T sc = T(0);
           if (P.kind == kPortRho) {
