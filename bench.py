@@ -123,9 +123,9 @@ class Clocks:
 # captured; every case block streams the tables again, so traffic grows with
 # their number).
 TRAFFIC = {
-    "sources_sha256": "65dcb6fa8ceb10adc2f6d7b61d55841197c119f9460966d951ee94ed2e059d6f",
-    "plain": 470381312 + 4203008,
-    "per_case_block": (965691904 + 19374080) / 2,
+    "sources_sha256": "a0adc786159d16ebef5dc10f50658c6929beb986413abcfbfdf813a9180a73ca",
+    "plain": 470127360 + 4597504,
+    "per_case_block": (966917888 + 19331584) / 2,
 }
 TRAFFIC_SOURCES = ["paper_1202_3777_gb300/csrc/jt_kernels.cu", "paper_1202_3777_gb300/csrc/jt_kernels.h",
                    "paper_1202_3777_gb300/csrc/jt_internal.h", "paper_1202_3777_gb300/csrc/jt_plan.cpp"]
