@@ -119,10 +119,10 @@ jt_status jt_set_evidence_dense(jt_tree t, int32_t first_case, int32_t n_cases,
  * work on `stream`.  Per-message rescaling keeps FP32 in range; log Z(e) is
  * accumulated in FP64.
  * The first call for a given (first_case, n_cases) with n_cases > 1 records
- * two schedules (one case per work item, or blocks of 8 cases sharing each
- * table read), runs each twice on `stream` and keeps the faster: that call
- * synchronises `stream`.  The environment variable JT_CASE_BLOCK=1 or 8
- * fixes the choice instead.
+ * the schedules (one case per work item, or blocks of 4 or 8 cases sharing
+ * each table read), runs each twice on `stream` and keeps the fastest: that
+ * call synchronises `stream`.  The environment variable JT_CASE_BLOCK=1, 4
+ * or 8 fixes the choice instead.
  */
 jt_status jt_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* stream);
 

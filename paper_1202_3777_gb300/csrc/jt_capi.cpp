@@ -288,13 +288,13 @@ float time_graph(const GraphEntry& ge, cudaStream_t s) {
 
 // The propagation graph of a case range, recorded on first use.  Several
 // cases can go one per work item (more, shorter items; every item streams
-// its table for one case) or in blocks of kCaseBlock (each streamed table
-// chunk serves 8 cases).  Which is faster depends on the tree and the
+// its table for one case) or in blocks of 4 or kCaseBlock = 8 (each
+// streamed table chunk serves the block's cases).  Which is faster depends on the tree and the
 // number of cases: blocks pay off for cliques with many ports and many
 // cases, single cases for small trees, few cases or few ports.  So the
-// first use of a multi-case range times both schedules once (after a
+// first use of a multi-case range times the schedules once each (after a
 // warm-up launch of each; the launches compute the same propagation the
-// caller asked for) and keeps the faster.  JT_CASE_BLOCK=1 or 8 in the
+// caller asked for) and keeps the fastest.  JT_CASE_BLOCK=1, 4 or 8 in the
 // environment fixes the choice instead.
 jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** out) {
   auto key = std::make_pair(first, n);
@@ -305,7 +305,8 @@ jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** ou
       free_graphs(t);
     }
     int forced = 0;
-    if (const char* f = std::getenv("JT_CASE_BLOCK"); f && (*f == '1' || *f == '8') && f[1] == 0) forced = *f - '0';
+    if (const char* f = std::getenv("JT_CASE_BLOCK"); f && (*f == '1' || *f == '4' || *f == '8') && f[1] == 0)
+      forced = *f - '0';
     auto record = [&](int cb, GraphEntry* ge) {
       return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, t->cap_stream, ge)
                                   : record_schedule<float>(t, first, n, cb, t->cap_stream, ge);
@@ -319,14 +320,21 @@ jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** ou
     }
     if (n > 1 && !forced) {
       const std::string keep = g_err;   // a failed alternative leaves the chosen graph usable
-      GraphEntry ge1;
-      if (record(1, &ge1) == JT_OK) {
-        time_graph(ge, s);
-        time_graph(ge1, s);
-        const float t8 = time_graph(ge, s), t1 = time_graph(ge1, s);
-        if (t1 >= 0.f && t8 >= 0.f && t1 < t8) std::swap(ge, ge1);
+      time_graph(ge, s);
+      float best = time_graph(ge, s);
+      for (int cb : {4, 1}) {
+        if (cb >= n && cb != 1) continue;   // a block wider than the cases: no gain over one case
+        GraphEntry alt;
+        if (record(cb, &alt) == JT_OK) {
+          time_graph(alt, s);
+          const float ta = time_graph(alt, s);
+          if (ta >= 0.f && (best < 0.f || ta < best)) {
+            std::swap(ge, alt);
+            best = ta;
+          }
+        }
+        drop_graph(alt);
       }
-      drop_graph(ge1);
       g_err = keep;
     }
     it = t->graphs.emplace(key, std::move(ge)).first;

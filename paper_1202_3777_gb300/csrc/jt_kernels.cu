@@ -1658,6 +1658,9 @@ cudaError_t launch_propagate(const PropArgs<T>& a, int cb, int grid, int smem, c
   if (cb <= 1) {
     set_attrs_once<T, 1>();
     k_propagate<T, 1><<<grid, consumers_for(1) + kControlThreads, smem, s>>>(a);
+  } else if (cb <= 4) {
+    set_attrs_once<T, 4>();
+    k_propagate<T, 4><<<grid, consumers_for(4) + kControlThreads, smem, s>>>(a);
   } else {
     set_attrs_once<T, 8>();
     k_propagate<T, 8><<<grid, consumers_for(8) + kControlThreads, smem, s>>>(a);

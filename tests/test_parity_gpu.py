@@ -24,11 +24,11 @@ def jt():
     return mod
 
 
-@pytest.fixture(params=["1", "8"])
+@pytest.fixture(params=["1", "4", "8"])
 def case_block(request, monkeypatch):
-    """Multi-case propagations pick one case per work item or blocks of 8 by
-    timing both on first use; these tests pin each schedule in turn so both
-    stay covered."""
+    """Multi-case propagations pick one case per work item or blocks of 4 or
+    8 by timing them on first use; these tests pin each schedule in turn so
+    all stay covered."""
     monkeypatch.setenv("JT_CASE_BLOCK", request.param)
     return int(request.param)
 
@@ -179,7 +179,7 @@ def test_results_do_not_depend_on_stale_shared_memory(jt, monkeypatch):
 
 def test_case_block_choice_by_timing(jt, monkeypatch):
     """Without JT_CASE_BLOCK the first multi-case propagation of a range
-    times both schedules and keeps one: the results match the oracle and
+    times the schedules and keeps one: the results match the oracle and
     later propagations of the range reuse the choice (same results up to the
     order of atomic additions)."""
     monkeypatch.delenv("JT_CASE_BLOCK", raising=False)
