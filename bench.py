@@ -115,7 +115,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# DRAM traffic of the propagation kernel from one ncu capture
+# DRAM traffic of the propagation kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, summarised in
 # profiles/k_propagate_large_clique.md), valid only while the kernel and
 # planner sources are the ones it was taken on.  One-case launch: bytes per
@@ -123,9 +123,9 @@ class Clocks:
 # captured; every case block streams the tables again, so traffic grows with
 # their number).
 TRAFFIC = {
-    "sources_sha256": "a0adc786159d16ebef5dc10f50658c6929beb986413abcfbfdf813a9180a73ca",
-    "plain": 470127360 + 4597504,
-    "per_case_block": (966917888 + 19331584) / 2,
+    "sources_sha256": "27880be660118a84204f0f9bfb448eab6e1f46c027f138488e74533a445bc024",
+    "plain": 470327552 + 1783552,       # mean of 4 launches
+    "per_case_block": (964865664 + 15754880) / 2,   # mean of 2 launches
 }
 TRAFFIC_SOURCES = ["paper_1202_3777_gb300/csrc/jt_kernels.cu", "paper_1202_3777_gb300/csrc/jt_kernels.h",
                    "paper_1202_3777_gb300/csrc/jt_internal.h", "paper_1202_3777_gb300/csrc/jt_plan.cpp"]
