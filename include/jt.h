@@ -132,7 +132,10 @@ jt_status jt_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* str
  * milliseconds, launch_ms[0] = the propagation kernel (every collect and
  * distribute message) and launch_ms[1] = the finalisation (marginals and
  * log Z).  max_launches must be >= 2; *n_launches is always set.  Results are
- * the same as jt_propagate's.
+ * the same as jt_propagate's.  With the environment variable JT_TRACE=<file>
+ * it also records every work item's SM and timeline (global timer, ns) and
+ * writes them to <file> as CSV; JT_DEBUG_PLAN=1 prints each newly recorded
+ * schedule's stages to stderr.
  */
 jt_status jt_profile_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* stream,
                                float* launch_ms, int32_t max_launches, int32_t* n_launches);
