@@ -149,6 +149,30 @@ def measured_traffic(cases):
     return int(TRAFFIC["per_case_block"] * ((cases + 7) // 8))
 
 
+def evidence_seed(rank: int) -> int:
+    """Seed of a rank's evidence cases: every replica propagates its own."""
+    return 7000 + 100000 * rank
+
+
+def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
+    """The largest of every rank's value (the job's time is its slowest
+    rank's); `device` is where the collective's tensor lives (cuda for NCCL,
+    cpu for gloo)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(work_per_case: int, cases_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (each rank propagates its own cases: weak scaling)."""
+    return work_per_case * cases_per_rank * world / (ms_per_step * 1e-3)
+
+
 def msg_total(tree):
     """Entries of all separator tables (the per-case message arrays)."""
     from math import prod
@@ -286,7 +310,7 @@ def main():
     B = args.batch
     tree = synth.WORKLOADS[WORKLOAD]["build"]().as_dtype(np.float32)
     W = tree.work_per_case()
-    ev = synth.evidence_matrix(tree, B, 0.05, 7000 + 100000 * rank)
+    ev = synth.evidence_matrix(tree, B, 0.05, evidence_seed(rank))
     h = jt.jt_load_synth(tree, compute=jt.JT_F32, max_cases=B)
     jt.jt_set_evidence_dense(h, 0, ev)
     stream = torch.cuda.current_stream()
@@ -309,17 +333,13 @@ def main():
         barrier()
         return s0.elapsed_time(s1) / steps   # ms per step
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over(x):
+        return max_over_ranks(x, world, "cuda")
 
     # plain: one case per jt_propagate call
     for _ in range(args.warmup):
         jt.jt_propagate(h, 0, 1, stream)
-    plain_ms = max_over_ranks(timed(0, 1, args.steps))
+    plain_ms = max_over(timed(0, 1, args.steps))
 
     # batched (the timed step)
     for _ in range(args.warmup):
@@ -327,7 +347,7 @@ def main():
     gi = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES") else local
     with Clocks(gi) as clk:
-        step_ms = max_over_ranks(timed(0, B, args.steps))
+        step_ms = max_over(timed(0, B, args.steps))
     clocks = clk.summary()
 
     # correctness guard on the timed results
@@ -369,11 +389,11 @@ def main():
         lzh = jt.jt_get_log_evidence(h, 0, B, stream=stream)
     sync()
     barrier()
-    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps)
+    e2e_ms = max_over(1e3 * (time.perf_counter() - t0) / args.steps)
 
     total_cases = B * world
-    value = W * total_cases / (step_ms * 1e-3)
-    plain_value = W * world / (plain_ms * 1e-3)
+    value = job_rate(W, B, world, step_ms)
+    plain_value = job_rate(W, 1, world, plain_ms)
     h.free()
     serving = None
     if not args.no_serving:
@@ -405,7 +425,7 @@ def main():
                            "traffic": measured_traffic(1), "kernel_ms": float(prof_1[0]),
                            "alg_bytes": int(alg_bytes(1))},
         "finalize_ms": {"batched": float(prof_b[1]), "plain": float(prof_1[1])},
-        "e2e": {"value": W * total_cases / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": job_rate(W, B, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(ev.nbytes), "d2h_bytes_per_step": int(md.nbytes + lzh.nbytes)},
         "serving": serving,
         "gpu_launches": int(2 * args.steps),   # k_propagate + k_finalize per step
