@@ -8,6 +8,7 @@ is clique-entries per second: each case counts the numerator of Eq. 4 over
 its 2(n-1) messages, sum of |phi_src| + |phi_dst|.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl cuda|reference]
+                    [--no-serving] [--no-cpu-baseline] [--no-ablation]
 
 Under torchrun every rank runs its own replica on its own evidence cases
 (the path shards by case; there is no data-path collective), and rank 0
@@ -123,7 +124,7 @@ class Clocks:
 # captured; every case block streams the tables again, so traffic grows with
 # their number).
 TRAFFIC = {
-    "sources_sha256": "27880be660118a84204f0f9bfb448eab6e1f46c027f138488e74533a445bc024",
+    "sources_sha256": "098c56d37a44ff565234dc6ac4bc37760ab6b6059cc2d317a29250cbe56ed8c1",
     "plain": 470327552 + 1783552,       # mean of 4 launches
     "per_case_block": (964865664 + 15754880) / 2,   # mean of 2 launches
 }
@@ -227,6 +228,24 @@ def run_reference(args, rank, world):
     return 0
 
 
+def measure_per_message(tree, ev_row):
+    """The paper's own propagation (one kernel launch pair per message, index-
+    mapping tables; Algorithm 1) for one case of the workload, in the naive
+    and the interleaved mapping-table layout: device time of the whole
+    propagation, best of three after a first run that also builds the
+    tables."""
+    from paper_1202_3777_gb300 import jt
+    h = jt.jt_load_synth(tree, compute=jt.JT_F32, max_cases=1, flags=jt.JT_MATERIALIZE_CLIQUES)
+    jt.jt_set_evidence_dense(h, 0, ev_row[None, :])
+    out = {}
+    for layout, name in ((0, "naive"), (1, "interleaved")):
+        jt.jt_propagate_per_message(h, 0, layout)
+        out[name + "_ms"] = min(jt.jt_propagate_per_message(h, 0, layout) for _ in range(3))
+    assert jt.jt_get_status(h, 0, 1)[0] == jt.JT_OK
+    h.free()
+    return out
+
+
 def measure_serving(rank):
     """Continuous batching over the four resident trees (small, large-clique,
     high-cardinality, 1024-clique binary): a burst of queries gives the
@@ -288,6 +307,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -395,6 +415,11 @@ def main():
     value = job_rate(W, B, world, step_ms)
     plain_value = job_rate(W, 1, world, plain_ms)
     h.free()
+    per_message = None
+    if not args.no_ablation:
+        per_message = measure_per_message(tree, ev[0])
+        per_message["fused_kernel_ms"] = float(prof_1[0])
+        per_message["fused_with_finalisation_ms"] = float(prof_1[0] + prof_1[1])
     serving = None
     if not args.no_serving:
         serving = measure_serving(rank)
@@ -428,6 +453,7 @@ def main():
         "e2e": {"value": job_rate(W, B, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(ev.nbytes), "d2h_bytes_per_step": int(md.nbytes + lzh.nbytes)},
         "serving": serving,
+        "per_message": per_message,
         "gpu_launches": int(2 * args.steps),   # k_propagate + k_finalize per step
         "clocks": clocks,
         "cpu_baseline": cpu,

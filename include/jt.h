@@ -202,6 +202,26 @@ jt_status jt_get_clique(jt_tree t, int32_t case_id, int32_t clique, double* out)
  */
 jt_status jt_get_clique_noalloc(jt_tree t, int32_t case_id, int32_t clique, double* out_device, void* stream);
 
+/*
+ * The paper's own propagation, for comparison (not the library's fast
+ * path): collect then distribute (Algorithms 2-4) for case `case_id`, every
+ * message by the per-message kernel of Algorithm 1 (Sec. 3.2): one launch
+ * pair per message, one thread per separator entry, gathering and
+ * scattering through precomputed index-mapping tables (Fig. 3) in the
+ * layout `layout`: 0 = naive (each separator entry's list contiguous),
+ * 1 = interleaved (the m-th elements of all lists adjacent; Sec. 4.5,
+ * Fig. 8).  Collect messages are normalised by their totals (log Z
+ * accumulates in FP64).  The tables are built on the host on first use of a
+ * layout (one int32 per clique entry per incident separator) and kept until
+ * jt_free.  Needs JT_MATERIALIZE_CLIQUES at load: it works in the case's
+ * calibrated tables, which jt_get_clique then reads; the case's marginals
+ * and log Z are then as after jt_propagate.  Synchronises `stream`;
+ * `kernel_ms` (may be null) receives the device time of the whole
+ * propagation.  JT_ERR_INVALID_ARG: bad case, layout or evidence state;
+ * JT_ERR_STATE: loaded without JT_MATERIALIZE_CLIQUES.
+ */
+jt_status jt_propagate_per_message(jt_tree t, int32_t case_id, int32_t layout, void* stream, float* kernel_ms);
+
 /* Sizes and schedule facts of a loaded tree. */
 typedef struct {
   int32_t n_vars, n_cliques, depth;  /* depth = largest clique depth (root 0) */

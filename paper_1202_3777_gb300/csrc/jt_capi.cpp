@@ -57,6 +57,22 @@ struct GraphEntry {
   int32_t grid = 0, smem = 0;
 };
 
+// State of the paper-literal per-message propagation (jt_propagate_per_message),
+// built on first use: the index-mapping tables of every separator, on both of
+// its sides, in one layout, and the scratch of the separator updates.
+struct PerMsg {
+  int layout = -1;
+  std::vector<void*> bufs;                  // every device buffer below
+  std::vector<const int32_t*> mu_child;     // [c]: entries of clique c per entry of its parent separator
+  std::vector<const int32_t*> mu_parent;    // [c]: entries of the parent of c per entry of that separator
+  double* snew = nullptr;                   // [msg_total] the message being sent
+  void* sold = nullptr;                     // [msg_total] separator tables (element type)
+  void* ones = nullptr;                     // [msg_total] ones, their start value
+  double* sigma = nullptr;                  // [n_cliques + 2]: collect totals, root total, scratch
+  int4* obs = nullptr;                      // [sum of clique sizes] evidence of every clique
+  VarSrc* vs = nullptr;                     // marginal sources in the calibrated tables
+};
+
 }  // namespace
 
 struct jt_tree_s {
@@ -94,6 +110,7 @@ struct jt_tree_s {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   std::map<std::pair<int, int>, GraphEntry> graphs;
+  std::unique_ptr<PerMsg> permsg;
 };
 
 namespace {
@@ -122,6 +139,8 @@ void destroy(jt_tree t) {
   cudaSetDevice(t->device);
   cudaDeviceSynchronize();
   free_graphs(t);
+  if (t->permsg)
+    for (void* q : t->permsg->bufs) cudaFree(q);
   void* ptrs[] = {t->base,   t->d_msg,  t->d_sums,  t->d_done,    t->d_err, t->d_status, t->d_marg,
                   t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_sep_size};
   for (void* p : ptrs)
@@ -442,6 +461,181 @@ CliqueOut clique_out(const Plan& p, int clique) {
       if (pv[j] == lv[i]) co.pst[i] = (int32_t)pst[j];
   }
   return co;
+}
+
+}  // namespace
+
+namespace {
+
+// Index-mapping tables of the per-message propagation in `layout` (0 naive:
+// entry j's list contiguous; 1 interleaved: the m-th elements of all lists
+// adjacent), one per side of every separator, over the permuted tables.
+jt_status build_permsg(jt_tree t, int layout) {
+  const Plan& p = t->plan;
+  const int nc = p.n_cliques;
+  auto pm = std::make_unique<PerMsg>();
+  pm->layout = layout;
+  pm->mu_child.assign(nc, nullptr);
+  pm->mu_parent.assign(nc, nullptr);
+  auto dalloc = [&](size_t bytes, void** q, const char* what) -> jt_status {
+    cudaError_t e = cudaMalloc(q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    pm->bufs.push_back(*q);
+    return JT_OK;
+  };
+  auto release = [&]() {
+    for (void* q : pm->bufs) cudaFree(q);
+  };
+  // strides of every variable in a clique's permuted table
+  auto stride_of = [&](int q, int v) -> int64_t {
+    const auto& pv = p.pvars[q];
+    int64_t st = 1;
+    for (int i = (int)pv.size() - 1; i >= 0; --i) {
+      if (pv[i] == v) return st;
+      st *= p.card[pv[i]];
+    }
+    return -1;
+  };
+  std::vector<int32_t> mu;
+  for (int c = 1; c < nc; ++c) {
+    const auto& sv = p.sep[c];
+    const int32_t S = p.sep_size[c];
+    for (int side = 0; side < 2; ++side) {
+      const int q = side == 0 ? c : p.parent[c];
+      const int64_t N = p.n_entries[q], L = N / S;
+      std::vector<int64_t> st(sv.size());
+      for (size_t i = 0; i < sv.size(); ++i) st[i] = stride_of(q, sv[i]);
+      mu.assign((size_t)N, 0);
+      std::vector<int32_t> cnt((size_t)S, 0);
+      for (int64_t x = 0; x < N; ++x) {
+        int64_t j = 0;
+        for (size_t i = 0; i < sv.size(); ++i) j = j * p.card[sv[i]] + (x / st[i]) % p.card[sv[i]];
+        const int64_t m = cnt[(size_t)j]++;
+        mu[(size_t)(layout ? m * S + j : j * L + m)] = (int32_t)x;
+      }
+      void* d = nullptr;
+      jt_status st2 = dalloc((size_t)N * sizeof(int32_t), &d, "mapping tables");
+      if (st2 != JT_OK) {
+        release();
+        return st2;
+      }
+      if (cudaMemcpy(d, mu.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        release();
+        return fail(JT_ERR_CUDA, "mapping table upload");
+      }
+      (side == 0 ? pm->mu_child : pm->mu_parent)[c] = static_cast<const int32_t*>(d);
+    }
+  }
+  const size_t mt = (size_t)std::max(1, p.msg_total);
+  void* q = nullptr;
+  jt_status st = JT_OK;
+  if ((st = dalloc(mt * sizeof(double), &q, "separator scratch")) != JT_OK) return release(), st;
+  pm->snew = static_cast<double*>(q);
+  if ((st = dalloc(mt * t->elem, &pm->sold, "separator tables")) != JT_OK) return release(), st;
+  if ((st = dalloc(mt * t->elem, &pm->ones, "separator start values")) != JT_OK) return release(), st;
+  if ((st = dalloc((size_t)(nc + 2) * sizeof(double), &q, "message totals")) != JT_OK) return release(), st;
+  pm->sigma = static_cast<double*>(q);
+  size_t kk = 0;
+  for (int c = 0; c < nc; ++c) kk += p.pvars[c].size();
+  if ((st = dalloc(std::max<size_t>(kk, 1) * sizeof(int4), &q, "evidence lists")) != JT_OK) return release(), st;
+  pm->obs = static_cast<int4*>(q);
+  if ((st = dalloc((size_t)p.n_vars * sizeof(VarSrc), &q, "marginal sources")) != JT_OK) return release(), st;
+  pm->vs = static_cast<VarSrc*>(q);
+  // ones
+  if (t->compute == JT_F64) {
+    std::vector<double> o(mt, 1.0);
+    if (cudaMemcpy(pm->ones, o.data(), mt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return release(), fail(JT_ERR_CUDA, "upload");
+  } else {
+    std::vector<float> o(mt, 1.0f);
+    if (cudaMemcpy(pm->ones, o.data(), mt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return release(), fail(JT_ERR_CUDA, "upload");
+  }
+  // every variable's marginal from the smallest calibrated clique holding it
+  std::vector<VarSrc> vs((size_t)p.n_vars);
+  for (int v = 0; v < p.n_vars; ++v) {
+    int best = -1;
+    for (int c = 0; c < nc; ++c)
+      if (stride_of(c, v) > 0 && (best < 0 || p.n_entries[c] < p.n_entries[best])) best = c;
+    VarSrc& r = vs[(size_t)v];
+    r.card = p.card[v];
+    r.moff = p.moff[v];
+    r.off = (int32_t)p.base_off[best];
+    r.size = (int32_t)p.n_entries[best];
+    r.st = (int32_t)stride_of(best, v);
+  }
+  if (cudaMemcpy(pm->vs, vs.data(), vs.size() * sizeof(VarSrc), cudaMemcpyHostToDevice) != cudaSuccess)
+    return release(), fail(JT_ERR_CUDA, "upload");
+  if (t->permsg)
+    for (void* b : t->permsg->bufs) cudaFree(b);
+  t->permsg = std::move(pm);
+  return JT_OK;
+}
+
+// Collect then distribute (Algorithms 2-4) for one case, one launch pair per
+// message, into the case's calibrated tables.
+template <typename T>
+cudaError_t run_permsg(jt_tree t, int cs, const std::vector<int4>& obs, const std::vector<int>& obs_off,
+                       cudaStream_t s) {
+  const Plan& p = t->plan;
+  const PerMsg& pm = *t->permsg;
+  const int nc = p.n_cliques, lay = pm.layout;
+  T* row = (T*)t->d_calib + (int64_t)cs * p.base_len;
+  T* sold = (T*)pm.sold;
+  cudaError_t err = cudaSuccess;
+  auto chk = [&](cudaError_t e) {
+    if (err == cudaSuccess && e != cudaSuccess) err = e;
+  };
+  chk(cudaMemcpyAsync(row, t->base, (size_t)p.base_len * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  chk(cudaMemcpyAsync(sold, pm.ones, (size_t)std::max(1, p.msg_total) * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  chk(cudaMemsetAsync(pm.sigma, 0, (size_t)(nc + 2) * sizeof(double), s));
+  chk(cudaMemsetAsync(t->d_status + cs, 0, sizeof(int32_t), s));
+  if (!obs.empty())
+    chk(cudaMemcpyAsync(pm.obs, obs.data(), obs.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  for (int c = 0; c < nc; ++c)
+    chk(launch_clique_evidence<T>(row + p.base_off[c], p.n_entries[c], pm.obs + obs_off[c],
+                                  obs_off[c + 1] - obs_off[c], s));
+  // collect: child to parent, deepest level first, each message normalised
+  for (int dd = p.max_depth; dd >= 1; --dd)
+    for (int c : p.levels[dd]) {
+      const int q = p.parent[c];
+      const int32_t S = p.sep_size[c];
+      double* sn = pm.snew + p.sep_off[c];
+      chk(launch_msg_marg<T>(row + p.base_off[c], pm.mu_child[c], (int32_t)(p.n_entries[c] / S), S, lay, sn,
+                             pm.sigma + c, s));
+      chk(launch_msg_scatter<T>(row + p.base_off[q], pm.mu_parent[c], (int32_t)(p.n_entries[q] / S), S, lay, sn,
+                                sold + p.sep_off[c], pm.sigma + c, 1, s));
+    }
+  // the root normalised to total one (its total is the evidence's last factor)
+  chk(launch_table_normalise<T>(row + p.base_off[0], p.n_entries[0], pm.sigma + nc, s));
+  // distribute: parent to child, from the root
+  for (int dd = 0; dd < p.max_depth; ++dd)
+    for (int q : p.levels[dd])
+      for (int c : p.children[q]) {
+        const int32_t S = p.sep_size[c];
+        double* sn = pm.snew + p.sep_off[c];
+        chk(launch_msg_marg<T>(row + p.base_off[q], pm.mu_parent[c], (int32_t)(p.n_entries[q] / S), S, lay, sn,
+                               pm.sigma + nc + 1, s));
+        chk(launch_msg_scatter<T>(row + p.base_off[c], pm.mu_child[c], (int32_t)(p.n_entries[c] / S), S, lay, sn,
+                                  sold + p.sep_off[c], pm.sigma + nc + 1, 0, s));
+      }
+  chk(launch_pack_totals(pm.sigma, t->d_sep_size, nc, pm.sigma + nc, t->d_sums + (int64_t)cs * 2 * nc, s));
+  FinalArgs<T> f{};
+  f.vs = pm.vs;
+  f.n_vars = p.n_vars;
+  f.n_cliques = nc;
+  f.case0 = cs;
+  f.n_cases = 1;
+  f.msg = (const T*)t->d_calib;
+  f.msg_stride = p.base_len;
+  f.sums = t->d_sums;
+  f.sep_size = t->d_sep_size;
+  f.status = t->d_status;
+  f.marg_total = p.marg_total;
+  f.marg_out = t->d_marg;
+  f.logz_out = t->d_logz;
+  chk(launch_finalize<T>(f, s));
+  return err;
 }
 
 }  // namespace
@@ -823,5 +1017,60 @@ jt_status jt_get_info(jt_tree t, jt_tree_info* out) {
 }
 
 void jt_free(jt_tree t) { destroy(t); }
+
+
+jt_status jt_propagate_per_message(jt_tree t, int32_t case_id, int32_t layout, void* stream, float* kernel_ms) {
+  jt_status st = check_tree(t);
+  if (st != JT_OK) return st;
+  const Plan& p = t->plan;
+  if (case_id < 0 || case_id >= t->max_cases) return fail(JT_ERR_INVALID_ARG, "bad case");
+  if (layout != 0 && layout != 1) return fail(JT_ERR_INVALID_ARG, "layout is 0 (naive) or 1 (interleaved)");
+  if (!(t->flags & JT_MATERIALIZE_CLIQUES))
+    return fail(JT_ERR_STATE, "the per-message propagation works in the calibrated tables: load with "
+                              "JT_MATERIALIZE_CLIQUES");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = upload_dirty(t, case_id, 1, s)) != JT_OK) return st;
+  if (!t->permsg || t->permsg->layout != layout) {
+    CU(cudaStreamSynchronize(s), "per-message setup");
+    if ((st = build_permsg(t, layout)) != JT_OK) return st;
+  }
+  // the case's evidence, per clique (stride, cardinality, state)
+  std::vector<int16_t> ev((size_t)p.n_vars);
+  CU(cudaMemcpyAsync(ev.data(), t->d_ev + (int64_t)case_id * p.n_vars, (size_t)p.n_vars * sizeof(int16_t),
+                     cudaMemcpyDeviceToHost, s),
+     "evidence read");
+  CU(cudaStreamSynchronize(s), "evidence read");
+  std::vector<int4> obs;
+  std::vector<int> obs_off(1, 0);
+  for (int c = 0; c < p.n_cliques; ++c) {
+    const auto& pv = p.pvars[c];
+    int64_t stv = 1;
+    for (int i = (int)pv.size() - 1; i >= 0; --i) {
+      const int v = pv[i], e = ev[(size_t)v];
+      if (e >= p.card[v]) return fail(JT_ERR_INVALID_ARG, "evidence state out of range");
+      if (e >= 0) obs.push_back(make_int4((int)stv, p.card[v], e, 0));
+      stv *= p.card[v];
+    }
+    obs_off.push_back((int)obs.size());
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0), "event");
+  CU(cudaEventCreate(&e1), "event");
+  cudaError_t err = cudaEventRecord(e0, s);
+  if (err == cudaSuccess)
+    err = t->compute == JT_F64 ? run_permsg<double>(t, case_id, obs, obs_off, s)
+                               : run_permsg<float>(t, case_id, obs, obs_off, s);
+  if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "per-message propagation");
+  if (kernel_ms) *kernel_ms = ms;
+  t->ready[case_id] = 1;
+  t->last_stream = s;
+  return JT_OK;
+}
 
 }  // extern "C"

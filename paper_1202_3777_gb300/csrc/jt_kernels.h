@@ -100,6 +100,25 @@ constexpr int kNoAllocMaxDevices = 64;
 template <typename T>
 cudaError_t launch_get_clique_noalloc(const T* calib_clique, const CliqueOut& co, double* out_dev, cudaStream_t s);
 
+// The paper's per-message kernels (Algorithm 1) with index-mapping tables,
+// for comparison (jt_propagate_per_message): marginalise a clique onto a
+// separator through its mapping table (snew, and the total into *sigma);
+// ratio and scatter into the neighbour (normalising by *sigma when asked);
+// evidence per clique; a table normalised to total one (its total into
+// *total); the stage totals the finalisation reads.
+template <typename T>
+cudaError_t launch_msg_marg(const T* phi, const int32_t* mu, int32_t L, int32_t S, int interleaved, double* snew,
+                            double* sigma, cudaStream_t s);
+template <typename T>
+cudaError_t launch_msg_scatter(T* phi, const int32_t* mu, int32_t L, int32_t S, int interleaved,
+                               const double* snew, T* sold, const double* sigma, int normalise, cudaStream_t s);
+template <typename T>
+cudaError_t launch_clique_evidence(T* phi, int64_t n, const int4* obs, int n_obs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_table_normalise(T* phi, int64_t n, double* total, cudaStream_t s);
+cudaError_t launch_pack_totals(const double* sigma, const int32_t* sep_size, int nc, const double* root_total,
+                               double* sums, cudaStream_t s);
+
 // Maximum dynamic shared memory per CTA the kernels may use on this device
 // with `ctas_per_sm` resident CTAs per SM.
 int32_t smem_budget(int device, int ctas_per_sm = 1);

@@ -83,6 +83,7 @@ _sig = {
     "jt_get_status": (C.c_int, [_vp, _i32, _i32, _vp]),
     "jt_get_clique": (C.c_int, [_vp, _i32, _i32, _vp]),
     "jt_get_clique_noalloc": (C.c_int, [_vp, _i32, _i32, _vp, _vp]),
+    "jt_propagate_per_message": (C.c_int, [_vp, _i32, _i32, _vp, C.POINTER(C.c_float)]),
     "jt_get_info": (C.c_int, [_vp, C.POINTER(jt_tree_info)]),
     "jt_free": (None, [_vp]),
     "jt_strerror": (C.c_char_p, [C.c_int]),
@@ -265,6 +266,16 @@ def jt_get_clique_noalloc(t: Tree, case_id: int, clique: int, out, stream=None):
     _check(_lib.jt_get_clique_noalloc(t.handle, case_id, clique, C.c_void_p(out.data_ptr()), _stream(stream)),
            "jt_get_clique_noalloc")
     return out
+
+
+def jt_propagate_per_message(t: Tree, case_id: int, layout: int = 1, stream=None) -> float:
+    """The paper's per-message propagation (Algorithm 1 with index-mapping
+    tables, layout 0 naive / 1 interleaved) for one case; returns its device
+    time in ms (the tree needs JT_MATERIALIZE_CLIQUES)."""
+    ms = C.c_float(0.0)
+    _check(_lib.jt_propagate_per_message(t.handle, case_id, layout, _stream(stream), C.byref(ms)),
+           "jt_propagate_per_message")
+    return float(ms.value)
 
 
 def jt_free(t: Tree):
