@@ -12,6 +12,8 @@ Contents:
   Algorithms 2-4) in plain numpy FP64, plus the index mapping of Sec. 3.1.
 * :mod:`oracle.brute`   -- enumeration of the joint distribution (the exact
   definition that propagation reaches), for tiny trees.
+* :mod:`oracle.cpt`     -- clique tables from a Bayesian network's CPTs (the
+  Initialization step of Algorithm 4).
 
 Parity status of every function is stated in its module header: all are
 pinned by ``tests/test_oracle_pins.py`` except where a header says

@@ -335,6 +335,36 @@ def product_form(tree: Tree, seed: int):
     return tree.with_pot(np.concatenate(tables), tree.name + "-product"), f
 
 
+def bn_for_tree(tree: Tree, seed: int, max_parents: int = 3, alpha: float = 1.0):
+    """A Bayesian network whose every family fits in a clique of ``tree``.
+
+    Each variable v gets one CPT P(v | pa(v)), with pa(v) up to
+    ``max_parents`` variables drawn from the clique that introduces v among
+    those created before v (so the network is acyclic and its family lies in
+    that clique).  Every CPT column is Dirichlet(alpha * 1) in FP64.  Each
+    family is listed in a random order (the table transposed to match), so
+    the first-listed variable is the table's most significant digit, as in
+    a clique table.  Returns (families: list of int32 arrays, tables: list
+    of flat float64 arrays), one per variable, in variable order."""
+    rng = np.random.default_rng(seed)
+    fam_of, tab_of = {}, {}
+    for c, vars_c in enumerate(tree.cliques):
+        for v in sorted(int(x) for x in tree.fresh[c]):
+            earlier = [int(u) for u in vars_c if int(u) < v]
+            k = int(rng.integers(0, min(max_parents, len(earlier)) + 1))
+            pa = [int(u) for u in rng.choice(np.array(earlier, dtype=np.int64), size=k, replace=False)] if k else []
+            kv = int(tree.card[v])
+            n_cols = int(np.prod([int(tree.card[u]) for u in pa], dtype=np.int64))
+            cols = rng.dirichlet(np.full(kv, alpha), size=n_cols)          # last axis: v
+            t = cols.reshape([int(tree.card[u]) for u in pa] + [kv])
+            perm = rng.permutation(k + 1)
+            fam = (pa + [v])
+            fam_of[v] = np.array([fam[i] for i in perm], dtype=np.int32)
+            tab_of[v] = np.ascontiguousarray(np.transpose(t, perm)).reshape(-1)
+    order = sorted(fam_of)
+    return [fam_of[v] for v in order], [tab_of[v] for v in order]
+
+
 # --------------------------------------------------------------------------
 # Evidence.
 # --------------------------------------------------------------------------

@@ -384,3 +384,117 @@ def test_plant_scatter_wrong_operand(monkeypatch):
     t, ev = _case()
     monkeypatch.setattr(hugin, "sepset_ratio", lambda new, old: np.where(old != 0, old, 0.0))
     assert not _brute_agrees(t, ev)
+
+
+# ------------------------------------------ initialisation from CPTs (Alg. 4)
+
+from oracle import cpt  # noqa: E402
+
+# A -> B -> C, binary: P(A), P(B | A), P(C | B); a junction tree {A,B} - {B,C}
+# with the cliques listed out of variable order, so the state-string mapping
+# between a clique and a CPT is exercised.
+_PA = [0.3, 0.7]
+_PB_A = [[0.9, 0.1], [0.2, 0.8]]       # row a, column b
+_PC_B = [[0.6, 0.4], [0.25, 0.75]]     # row b, column c
+
+
+def _chain():
+    card = [2, 2, 2]
+    cliques = [[1, 0], [2, 1]]
+    fams = [[0], [0, 1], [1, 2]]
+    vals = [np.array(_PA), np.array(_PB_A).ravel(), np.array(_PC_B).ravel()]
+    return card, cliques, [-1, 0], fams, vals
+
+
+def test_cpt_chain_tables_and_closed_forms():
+    card, cliques, parent, fams, vals = _chain()
+    pot = cpt.cpt_potentials(card, cliques, fams, vals)
+    # clique 0 lists (B, A): entry (b, a) = P(a) P(b | a); clique 1 lists
+    # (C, B): entry (c, b) = P(c | b).  P(A) and P(B|A) both go to clique 0,
+    # the only one holding A.
+    for b in range(2):
+        for a in range(2):
+            assert pot[0][2 * b + a] == pytest.approx(_PA[a] * _PB_A[a][b], abs=0, rel=1e-15)
+    for c in range(2):
+        for b in range(2):
+            assert pot[1][2 * c + b] == _PC_B[b][c]
+    # ancestral marginals and a posterior, by hand
+    pb0 = 0.3 * 0.9 + 0.7 * 0.2                       # 0.41
+    pc0 = pb0 * 0.6 + (1 - pb0) * 0.25
+    r = hugin.propagate(card, cliques, parent, pot, {})
+    assert abs(r.log_z) < 1e-15
+    assert r.marginals[1][0] == pytest.approx(pb0, rel=1e-14)
+    assert r.marginals[2][0] == pytest.approx(pc0, rel=1e-14)
+    # P(A=0 | C=0) = sum_b P(a=0) P(b|a=0) P(c=0|b) / P(c=0)
+    num = 0.3 * (0.9 * 0.6 + 0.1 * 0.25)
+    r = hugin.propagate(card, cliques, parent, pot, {2: 0})
+    assert r.log_z == pytest.approx(math.log(pc0), rel=1e-14)
+    assert r.marginals[0][0] == pytest.approx(num / pc0, rel=1e-14)
+
+
+def test_cpt_planted_mistakes_fail_the_closed_forms():
+    card, cliques, parent, fams, vals = _chain()
+    pb0 = 0.41
+    # a transposed operand: P(B|A)'s table read as if listed (B, A)
+    bad = cpt.cpt_potentials(card, cliques, [[0], [1, 0], [1, 2]], vals)
+    assert abs(hugin.propagate(card, cliques, parent, bad, {}).marginals[1][0] - pb0) > 0.05
+    # a dropped CPT: Z is no longer one
+    bad = cpt.cpt_potentials(card, cliques, fams[:2], vals[:2])
+    assert abs(hugin.propagate(card, cliques, parent, bad, {}).log_z) > 0.5
+    # a CPT multiplied in twice
+    bad = cpt.cpt_potentials(card, cliques, fams + [fams[1]], vals + [vals[1]])
+    assert abs(hugin.propagate(card, cliques, parent, bad, {}).log_z) > 0.1
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cpt_network_matches_its_own_factorisation(seed):
+    """The cliques built from a network's CPTs represent the network: every
+    posterior and P(e) equal brute force over prod_v P(v | pa(v)), enumerated
+    from the CPTs themselves (not from the clique tables)."""
+    t = synth.random_small_tree(seed, n_cliques=int(3 + seed % 4))
+    fams, vals = synth.bn_for_tree(t, seed, max_parents=3)
+    pot = cpt.cpt_potentials(t.card, t.cliques, fams, vals)
+    for n_obs in (0, 2):
+        ev = hugin.evidence_dict(*synth.random_evidence(t, n_obs, seed + 7))
+        r = hugin.propagate(t.card, t.cliques, t.parent, pot, ev)
+        lz, m = brute.brute_force(t.card, fams, vals, ev)
+        assert abs(r.log_z - lz) <= 1e-12 * max(1.0, abs(lz))
+        assert max_marg_err(r.marginals, m) < 1e-12
+        if n_obs == 0:
+            assert abs(r.log_z) < 1e-12       # a normalised network: Z = 1
+
+
+def test_cpt_home_rule_and_empty_cliques():
+    card = [2, 3, 2, 2]
+    #            0: 12 entries   1: 8 entries   2: 6 entries  3: 6 entries
+    cliques = [[0, 1, 2], [0, 2, 3], [1, 2], [2, 1]]
+    # {1, 2} fits 0, 2 and 3: cliques 2 and 3 are the smallest; tie -> 2
+    assert cpt.home_clique([2, 1], card, cliques) == 2
+    # {0, 2} fits 0 (12 entries) and 1 (8 entries) -> 1
+    assert cpt.home_clique([0, 2], card, cliques) == 1
+    assert cpt.home_clique([3], card, cliques) == 1
+    with pytest.raises(ValueError):
+        cpt.home_clique([1, 3], card, cliques)
+    pot = cpt.cpt_potentials(card, cliques, [[2, 1]], [np.arange(6.0)])
+    assert [p.size for p in pot] == [12, 8, 6, 6]
+    assert np.all(pot[0] == 1) and np.all(pot[1] == 1) and np.all(pot[3] == 1)
+    # clique 2 lists (1, 2), the CPT (2, 1): entry (x1, x2) = table[x2 * 3 + x1]
+    assert [pot[2][2 * x1 + x2] for x1 in range(3) for x2 in range(2)] == \
+        [float(x2 * 3 + x1) for x1 in range(3) for x2 in range(2)]
+    # an explicit home overrides the rule
+    pot = cpt.cpt_potentials(card, cliques, [[2, 1]], [np.arange(6.0)], home=[0])
+    assert np.all(pot[2] == 1) and sorted(pot[0]) == sorted(np.repeat(np.arange(6.0), 2))
+
+
+def test_cpt_rejects_bad_tables():
+    card, cliques, parent, fams, vals = _chain()
+    with pytest.raises(ValueError):
+        cpt.cpt_potentials(card, cliques, [[0, 2]], [np.ones(4)])        # no clique holds {A, C}
+    with pytest.raises(ValueError):
+        cpt.cpt_potentials(card, cliques, [[0, 0]], [np.ones(4)])        # repeated variable
+    with pytest.raises(ValueError):
+        cpt.cpt_potentials(card, cliques, [[0]], [np.array([0.5, -0.1])])
+    with pytest.raises(ValueError):
+        cpt.cpt_potentials(card, cliques, [[0]], [np.ones(3)])           # wrong size
+    with pytest.raises(ValueError):
+        cpt.cpt_potentials(card, cliques, [[0]], [np.ones(2)], home=[1])  # clique 1 lacks A

@@ -45,3 +45,21 @@ def test_large_clique_structure_small_variant():
         s = len(hugin.separator(t.cliques[c], t.cliques[t.parent[c]]))
         assert 4 <= s <= 6
     hugin.validate(t.card, t.cliques, t.parent)
+
+
+def test_bn_for_tree_is_a_network_over_the_tree():
+    """One CPT per variable, its family inside one clique, its parents created
+    before it (acyclic), every column a distribution; same seed, same net."""
+    t = synth.small_tree()
+    fams, vals = synth.bn_for_tree(t, 3)
+    assert len(fams) == t.n_vars
+    sets = [set(int(v) for v in c) for c in t.cliques]
+    for v, (fam, tab) in enumerate(zip(fams, vals)):
+        assert v in set(fam.tolist()) and max(fam.tolist()) == v
+        assert any(set(fam.tolist()) <= s for s in sets)
+        shape = [int(t.card[u]) for u in fam]
+        ax = fam.tolist().index(v)
+        sums = tab.reshape(shape).sum(axis=ax)
+        assert np.allclose(sums, 1.0, atol=1e-12) and np.all(tab >= 0)
+    f2, v2 = synth.bn_for_tree(t, 3)
+    assert all(np.array_equal(a, b) for a, b in zip(vals, v2))
