@@ -74,7 +74,8 @@ typedef struct {
   const int64_t* clique_off;    /* [n_cliques+1] CSR offsets into clique_vars */
   const int32_t* clique_vars;   /* listed order = table order (first most significant) */
   const int32_t* parent;        /* [n_cliques] parent[0] = -1 (root = clique 0) */
-  const void* potentials;       /* host; tables concatenated in clique order, >= 0, finite */
+  const void* potentials;       /* host; tables concatenated in clique order, >= 0, finite;
+                                   NULL: every table starts at one (then jt_init_from_cpts) */
   jt_dtype potentials_dtype;    /* element type of `potentials` */
   jt_dtype compute;             /* arithmetic type on the device (JT_F32 or JT_F64) */
   int32_t max_cases;            /* evidence-case slots kept resident, >= 1 */
@@ -221,6 +222,50 @@ jt_status jt_get_clique_noalloc(jt_tree t, int32_t case_id, int32_t clique, doub
  * JT_ERR_STATE: loaded without JT_MATERIALIZE_CLIQUES.
  */
 jt_status jt_propagate_per_message(jt_tree t, int32_t case_id, int32_t layout, void* stream, float* kernel_ms);
+
+/*
+ * Conditional probability tables of a Bayesian network over the tree's
+ * variables, for jt_init_from_cpts.  CPT i is a table over its family
+ * fam_vars[fam_off[i] .. fam_off[i+1]) (for P(v | pa(v)) the family is v and
+ * its parents, in any order), laid out like a clique table: the
+ * first-listed variable is the most significant digit.  Any non-negative
+ * table over variables that share a clique is accepted; nothing requires
+ * the columns to sum to one.
+ */
+typedef struct {
+  int32_t n_cpts;
+  const int32_t* fam_off;       /* [n_cpts+1] offsets into fam_vars, fam_off[0] = 0 */
+  const int32_t* fam_vars;      /* families, each non-empty, no variable twice */
+  const double* values;         /* host; tables concatenated in CPT order, >= 0, finite */
+  const int32_t* home;          /* [n_cpts] clique that receives each CPT (it must hold the
+                                   family), or NULL: the clique with the fewest entries that
+                                   holds the family, ties to the lowest clique index */
+} jt_cpt_desc;
+
+/*
+ * The Initialization step of Algorithm 4 (Sec. 3.3), on the device: every
+ * clique table of the loaded tree is overwritten with the product of the
+ * CPTs assigned to it, in ascending CPT order (one where a clique receives
+ * none), computed in the tree's compute precision straight into the
+ * resident table layout.  Together with separators that start at one, the
+ * tree then represents the network's joint distribution.  Evidence slots are
+ * kept, but every case must be propagated again before its results are read
+ * (JT_ERR_STATE until then).  Work is enqueued on `stream` and the call
+ * returns after it completes; `kernel_ms` (may be null) receives the device
+ * time of the initialisation kernel.  All inputs are copied.
+ * JT_ERR_INVALID_ARG: a null array, an empty or repeating family, a variable
+ * id out of range, a negative or non-finite value, a family that no clique
+ * (or not the named home clique) holds; the tables are then unchanged.
+ */
+jt_status jt_init_from_cpts(jt_tree t, const jt_cpt_desc* cpts, void* stream, float* kernel_ms);
+
+/*
+ * The resident (uncalibrated) table of clique `clique` -- as loaded, or as
+ * jt_init_from_cpts built it -- in the caller's listed variable order and
+ * compute precision widened to double: writes the clique's table size of
+ * doubles to host `out`.  Synchronises with the tree's last stream.
+ */
+jt_status jt_get_potential(jt_tree t, int32_t clique, double* out);
 
 /* Sizes and schedule facts of a loaded tree. */
 typedef struct {

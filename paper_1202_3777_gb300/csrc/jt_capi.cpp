@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "jt_internal.h"
+#include "jt_init.h"
 #include "jt_kernels.h"
 
 using namespace jt;
@@ -640,6 +641,74 @@ cudaError_t run_permsg(jt_tree t, int cs, const std::vector<int4>& obs, const st
 
 }  // namespace
 
+namespace {
+
+// Device buffers of one call, freed on every path out of it.
+struct TempBufs {
+  std::vector<void*> p;
+  ~TempBufs() {
+    for (void* x : p) cudaFree(x);
+  }
+  template <typename U>
+  cudaError_t upload(U** d, const std::vector<U>& h, cudaStream_t s) {
+    *d = nullptr;
+    if (h.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(U));
+    if (e != cudaSuccess) return e;
+    p.push_back(*d);
+    return cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice, s);
+  }
+};
+
+// Multiplier and shifts of UDiv for a divisor 1 <= d < 2^31.
+UDiv make_udiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((uint64_t{1} << l) < d) ++l;
+  const uint64_t mul = ((uint64_t{1} << 32) * ((uint64_t{1} << l) - d)) / d + 1;
+  return UDiv{(uint32_t)mul, (uint16_t)std::min<uint32_t>(l, 1), (uint16_t)(l > 0 ? l - 1 : 0)};
+}
+
+int32_t log2_exact(int64_t x) {
+  int32_t r = 0;
+  while ((int64_t{1} << r) < x) ++r;
+  return r;
+}
+
+template <typename T>
+jt_status init_typed(jt_tree t, const std::vector<InitItem>& items, const std::vector<InitClique>& cl,
+                     const std::vector<InitFactor>& fac, const std::vector<InitTerm>& terms,
+                     const std::vector<double>& values, cudaStream_t s, float* kernel_ms) {
+  std::vector<T> vals(values.begin(), values.end());
+  TempBufs tb;
+  InitItem* d_items;
+  InitClique* d_cl;
+  InitFactor* d_fac;
+  InitTerm* d_terms;
+  T* d_vals;
+  CU(tb.upload(&d_items, items, s), "initialisation upload");
+  CU(tb.upload(&d_cl, cl, s), "initialisation upload");
+  CU(tb.upload(&d_fac, fac, s), "initialisation upload");
+  CU(tb.upload(&d_terms, terms, s), "initialisation upload");
+  CU(tb.upload(&d_vals, vals, s), "initialisation upload");
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (kernel_ms) {
+    CU(cudaEventCreate(&ev[0]), "event");
+    CU(cudaEventCreate(&ev[1]), "event");
+    CU(cudaEventRecord(ev[0], s), "event");
+  }
+  cudaError_t e = launch_init_cliques<T>((T*)t->base, d_items, (int32_t)items.size(), d_cl, d_fac, d_terms, d_vals,
+                                         t->n_sm, s);
+  if (e == cudaSuccess && kernel_ms) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && kernel_ms) e = cudaEventElapsedTime(kernel_ms, ev[0], ev[1]);
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(e, "clique initialisation");
+  return JT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* jt_strerror(jt_status s) {
@@ -991,6 +1060,125 @@ jt_status jt_get_clique_noalloc(jt_tree t, int32_t case_id, int32_t clique, doub
                       ? launch_get_clique_noalloc<double>((const double*)t->d_calib + off, co, out_device, strm)
                       : launch_get_clique_noalloc<float>((const float*)t->d_calib + off, co, out_device, strm);
   if (e != cudaSuccess) return cuda_fail(e, "allocation-free clique read-out");
+  return JT_OK;
+}
+
+jt_status jt_init_from_cpts(jt_tree t, const jt_cpt_desc* cp, void* stream, float* kernel_ms) {
+  jt_status st = check_tree(t);
+  if (st != JT_OK) return st;
+  if (!cp || cp->n_cpts < 0) return fail(JT_ERR_INVALID_ARG, "null CPT descriptor or negative count");
+  const int32_t n = cp->n_cpts;
+  if (n > 0 && (!cp->fam_off || !cp->fam_vars || !cp->values)) return fail(JT_ERR_INVALID_ARG, "null CPT array");
+  const Plan& p = t->plan;
+  const int nc = p.n_cliques;
+  // cliques holding each variable, ascending
+  std::vector<std::vector<int32_t>> holders(p.n_vars);
+  for (int c = 0; c < nc; ++c)
+    for (int v : p.vars[c]) holders[v].push_back(c);
+  auto position = [&](int c, int v) {  // permuted position of v in clique c, or -1
+    const auto& pv = p.pvars[c];
+    for (int i = 0; i < (int)pv.size(); ++i)
+      if (pv[i] == v) return i;
+    return -1;
+  };
+  std::vector<int32_t> home(n);
+  std::vector<int64_t> val_off(n + 1, 0);
+  std::vector<int32_t> seen(p.n_vars, -1);
+  if (n > 0 && cp->fam_off[0] != 0) return fail(JT_ERR_INVALID_ARG, "fam_off[0] must be 0");
+  for (int i = 0; i < n; ++i) {
+    const int32_t a = cp->fam_off[i], b = cp->fam_off[i + 1];
+    const std::string who = "CPT " + std::to_string(i);
+    if (b <= a) return fail(JT_ERR_INVALID_ARG, who + " has an empty family");
+    int64_t size = 1;
+    for (int32_t j = a; j < b; ++j) {
+      const int32_t v = cp->fam_vars[j];
+      if (v < 0 || v >= p.n_vars) return fail(JT_ERR_INVALID_ARG, who + ": variable id out of range");
+      if (seen[v] == i) return fail(JT_ERR_INVALID_ARG, who + ": a variable appears twice in its family");
+      seen[v] = i;
+      size *= p.card[v];
+      if (size > JT_MAX_TABLE_ENTRIES) return fail(JT_ERR_INVALID_ARG, who + ": no clique holds its family");
+    }
+    auto holds = [&](int c) {
+      for (int32_t j = a; j < b; ++j)
+        if (position(c, cp->fam_vars[j]) < 0) return false;
+      return true;
+    };
+    int32_t h = -1;
+    if (cp->home) {
+      h = cp->home[i];
+      if (h < 0 || h >= nc) return fail(JT_ERR_INVALID_ARG, who + ": home clique out of range");
+      if (!holds(h)) return fail(JT_ERR_INVALID_ARG, who + ": its home clique does not hold its family");
+    } else {
+      for (int32_t c : holders[cp->fam_vars[a]])
+        if ((h < 0 || p.n_entries[c] < p.n_entries[h]) && holds(c)) h = c;
+      if (h < 0) return fail(JT_ERR_INVALID_ARG, who + ": no clique holds its family");
+    }
+    home[i] = h;
+    val_off[i + 1] = val_off[i] + size;
+  }
+  std::vector<double> values(cp->values, cp->values + val_off[n]);
+  for (double x : values)
+    if (!(x >= 0.0) || !std::isfinite(x)) return fail(JT_ERR_INVALID_ARG, "CPT values must be finite and >= 0");
+
+  // descriptors: per clique its CPTs in ascending order, per CPT the
+  // permuted stride and CPT stride of each family variable
+  std::vector<std::vector<int32_t>> by_clique(nc);
+  for (int i = 0; i < n; ++i) by_clique[home[i]].push_back(i);
+  std::vector<InitClique> cl(nc);
+  std::vector<InitFactor> fac;
+  std::vector<InitTerm> terms;
+  std::vector<InitItem> items;
+  for (int c = 0; c < nc; ++c) {
+    const auto& pv = p.pvars[c];
+    std::vector<int64_t> pst(pv.size());
+    int64_t sacc = 1;
+    for (int i = (int)pv.size() - 1; i >= 0; --i) {
+      pst[i] = sacc;
+      sacc *= p.card[pv[i]];
+    }
+    cl[c] = InitClique{p.base_off[c], (int32_t)p.n_entries[c], (int32_t)fac.size(), (int32_t)by_clique[c].size(),
+                       (int32_t)p.pow2[c]};
+    for (int i : by_clique[c]) {
+      const int32_t a = cp->fam_off[i], b = cp->fam_off[i + 1];
+      fac.push_back(InitFactor{val_off[i], (int32_t)terms.size(), b - a});
+      int64_t fst = 1;
+      std::vector<InitTerm> tt(b - a);
+      for (int32_t j = b - 1; j >= a; --j) {
+        const int32_t v = cp->fam_vars[j];
+        const int64_t ps = pst[position(c, v)];
+        tt[j - a] = InitTerm{make_udiv((uint32_t)ps), make_udiv((uint32_t)p.card[v]),
+                             p.pow2[c] ? log2_exact(ps) : 0, p.card[v], (int32_t)fst, 0};
+        fst *= p.card[v];
+      }
+      terms.insert(terms.end(), tt.begin(), tt.end());
+    }
+    for (int64_t e0 = 0; e0 < p.n_entries[c]; e0 += kInitChunk) items.push_back(InitItem{c, (int32_t)e0});
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // the tables may still be read by earlier work on the tree's last stream
+  CU(cudaStreamSynchronize(t->last_stream), "synchronising the tree's last stream");
+  st = t->compute == JT_F64 ? init_typed<double>(t, items, cl, fac, terms, values, s, kernel_ms)
+                            : init_typed<float>(t, items, cl, fac, terms, values, s, kernel_ms);
+  if (st != JT_OK) return st;
+  std::fill(t->ready.begin(), t->ready.end(), 0);
+  return JT_OK;
+}
+
+jt_status jt_get_potential(jt_tree t, int32_t clique, double* out) {
+  jt_status st = check_tree(t);
+  if (st != JT_OK) return st;
+  const Plan& p = t->plan;
+  if (clique < 0 || clique >= p.n_cliques || !out) return fail(JT_ERR_INVALID_ARG, "bad clique or output");
+  const CliqueOut co = clique_out(p, clique);
+  cudaStream_t strm = t->last_stream;
+  cudaError_t e = t->compute == JT_F64
+                      ? launch_table_unpermute<double>((const double*)t->base + p.base_off[clique], co,
+                                                       t->d_scratch, strm)
+                      : launch_table_unpermute<float>((const float*)t->base + p.base_off[clique], co,
+                                                      t->d_scratch, strm);
+  if (e != cudaSuccess) return cuda_fail(e, "table read-out");
+  CU(cudaMemcpyAsync(out, t->d_scratch, (size_t)co.n * sizeof(double), cudaMemcpyDeviceToHost, strm), "table read");
+  CU(cudaStreamSynchronize(strm), "table read");
   return JT_OK;
 }
 

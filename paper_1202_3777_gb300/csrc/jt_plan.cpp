@@ -39,7 +39,7 @@ static int32_t ilog2(int64_t x) {
 jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
   if (!d) FAIL(JT_ERR_INVALID_ARG, "null descriptor");
   if (d->n_vars < 1 || d->n_cliques < 1) FAIL(JT_ERR_INVALID_ARG, "need n_vars >= 1 and n_cliques >= 1");
-  if (!d->card || !d->clique_off || !d->clique_vars || !d->parent || !d->potentials)
+  if (!d->card || !d->clique_off || !d->clique_vars || !d->parent)
     FAIL(JT_ERR_INVALID_ARG, "null array in descriptor");
   if (d->compute != JT_F32 && d->compute != JT_F64) FAIL(JT_ERR_INVALID_ARG, "bad compute dtype");
   if (d->potentials_dtype != JT_F32 && d->potentials_dtype != JT_F64)
@@ -131,7 +131,7 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     p->n_entries[c] = n;
     p->entries += n;
   }
-  for (int64_t i = 0; i < p->entries; ++i) {
+  for (int64_t i = 0; d->potentials && i < p->entries; ++i) {
     double x = d->potentials_dtype == JT_F64 ? ((const double*)d->potentials)[i]
                                              : (double)((const float*)d->potentials)[i];
     if (!(x >= 0.0) || !std::isfinite(x)) FAIL(JT_ERR_INVALID_ARG, "potentials must be finite and >= 0");
@@ -803,7 +803,9 @@ void permute_tables(const Plan& p, const void* pot, jt_dtype pot_dtype, T* out) 
     const int64_t n = p.n_entries[c];
     const int64_t so = src_off[c];
     for (int64_t e = 0; e < n; ++e) {
-      double x = pot_dtype == JT_F64 ? ((const double*)pot)[so + src] : (double)((const float*)pot)[so + src];
+      double x = !pot                  ? 1.0
+                 : pot_dtype == JT_F64 ? ((const double*)pot)[so + src]
+                                       : (double)((const float*)pot)[so + src];
       dst[e] = (T)x;
       for (int i = k - 1; i >= 0; --i) {  // odometer increment
         if (++dig[i] < pc[i]) {

@@ -68,6 +68,16 @@ class jt_tree_info(C.Structure):
     ]
 
 
+class jt_cpt_desc(C.Structure):
+    _fields_ = [
+        ("n_cpts", C.c_int32),
+        ("fam_off", C.POINTER(C.c_int32)),
+        ("fam_vars", C.POINTER(C.c_int32)),
+        ("values", C.POINTER(C.c_double)),
+        ("home", C.POINTER(C.c_int32)),
+    ]
+
+
 _vp = C.c_void_p
 _i32 = C.c_int32
 _sig = {
@@ -84,6 +94,8 @@ _sig = {
     "jt_get_clique": (C.c_int, [_vp, _i32, _i32, _vp]),
     "jt_get_clique_noalloc": (C.c_int, [_vp, _i32, _i32, _vp, _vp]),
     "jt_propagate_per_message": (C.c_int, [_vp, _i32, _i32, _vp, C.POINTER(C.c_float)]),
+    "jt_init_from_cpts": (C.c_int, [_vp, C.POINTER(jt_cpt_desc), _vp, C.POINTER(C.c_float)]),
+    "jt_get_potential": (C.c_int, [_vp, _i32, _vp]),
     "jt_get_info": (C.c_int, [_vp, C.POINTER(jt_tree_info)]),
     "jt_free": (None, [_vp]),
     "jt_strerror": (C.c_char_p, [C.c_int]),
@@ -146,25 +158,30 @@ def jt_load_tree(card, cliques, parent, potentials, compute: int = JT_F32, max_c
     """Load a tree given as numpy arrays / lists: ``card`` [n_vars],
     ``cliques`` (list of variable arrays, table order), ``parent`` [n]
     (parent[0] = -1), ``potentials`` (concatenated tables, float64 or
-    float32)."""
+    float32; None: every table starts at one, for jt_init_from_cpts)."""
     card = np.ascontiguousarray(card, dtype=np.int32)
     cl = [np.asarray(c, dtype=np.int32) for c in cliques]
     off = np.concatenate([[0], np.cumsum([len(c) for c in cl])]).astype(np.int64)
     flat = np.ascontiguousarray(np.concatenate(cl) if cl else np.zeros(0, np.int32), dtype=np.int32)
     par = np.ascontiguousarray(parent, dtype=np.int32)
-    pot = np.ascontiguousarray(potentials)
-    if all(0 <= int(v) < len(card) for c in cl for v in c) and len(cl) and max(len(c) for c in cl) <= 32:
+    if potentials is None:
+        pot = None
+    else:
+        pot = np.ascontiguousarray(potentials)
+    if pot is not None and all(0 <= int(v) < len(card) for c in cl for v in c) and len(cl) and max(len(c) for c in cl) <= 32:
         need = sum(int(np.prod([int(card[v]) for v in c], dtype=np.float64)) for c in cl)
         if pot.size < need:
             raise ValueError(f"potentials hold {pot.size} entries, the tables need {need}")
-    if pot.dtype == np.float32:
+    if pot is None:
+        pdt = JT_F64
+    elif pot.dtype == np.float32:
         pdt = JT_F32
     else:
         pot = np.ascontiguousarray(pot, dtype=np.float64)
         pdt = JT_F64
     d = jt_tree_desc(len(card), card.ctypes.data_as(C.POINTER(C.c_int32)), len(cl),
                      off.ctypes.data_as(C.POINTER(C.c_int64)), flat.ctypes.data_as(C.POINTER(C.c_int32)),
-                     par.ctypes.data_as(C.POINTER(C.c_int32)), pot.ctypes.data_as(C.c_void_p), pdt,
+                     par.ctypes.data_as(C.POINTER(C.c_int32)), None if pot is None else pot.ctypes.data_as(C.c_void_p), pdt,
                      compute, max_cases, flags)
     h = C.c_void_p()
     _check(_lib.jt_load_tree(C.byref(d), _stream(stream), C.byref(h)), "jt_load_tree")
@@ -276,6 +293,33 @@ def jt_propagate_per_message(t: Tree, case_id: int, layout: int = 1, stream=None
     _check(_lib.jt_propagate_per_message(t.handle, case_id, layout, _stream(stream), C.byref(ms)),
            "jt_propagate_per_message")
     return float(ms.value)
+
+
+def jt_init_from_cpts(t: Tree, families, tables, home=None, stream=None) -> float:
+    """Overwrite the tree's clique tables with the product of the CPTs homed
+    in each (Algorithm 4's initialisation, on the device).  ``families[i]``
+    lists CPT i's variables in its table order, ``tables[i]`` is that table
+    (flattened), ``home`` optionally names each CPT's clique.  Returns the
+    device time of the initialisation kernel in ms."""
+    fams = [np.ascontiguousarray(f, dtype=np.int32) for f in families]
+    off = np.concatenate([[0], np.cumsum([len(f) for f in fams])]).astype(np.int32)
+    flat = np.ascontiguousarray(np.concatenate(fams) if fams else np.zeros(0, np.int32), dtype=np.int32)
+    vals = np.ascontiguousarray(np.concatenate([np.ravel(x) for x in tables]) if len(tables) else np.zeros(0),
+                                dtype=np.float64)
+    hm = None if home is None else np.ascontiguousarray(home, dtype=np.int32)
+    d = jt_cpt_desc(len(fams), off.ctypes.data_as(C.POINTER(C.c_int32)), flat.ctypes.data_as(C.POINTER(C.c_int32)),
+                    vals.ctypes.data_as(C.POINTER(C.c_double)),
+                    None if hm is None else hm.ctypes.data_as(C.POINTER(C.c_int32)))
+    ms = C.c_float(0.0)
+    _check(_lib.jt_init_from_cpts(t.handle, C.byref(d), _stream(stream), C.byref(ms)), "jt_init_from_cpts")
+    return float(ms.value)
+
+
+def jt_get_potential(t: Tree, clique: int, size: int) -> np.ndarray:
+    """Resident (uncalibrated) table of ``clique`` in its listed order."""
+    out = np.empty(size, dtype=np.float64)
+    _check(_lib.jt_get_potential(t.handle, clique, _ptr(out)), "jt_get_potential")
+    return out
 
 
 def jt_free(t: Tree):
