@@ -1128,6 +1128,8 @@ jt_status jt_init_from_cpts(jt_tree t, const jt_cpt_desc* cp, void* stream, floa
   std::vector<InitFactor> fac;
   std::vector<InitTerm> terms;
   std::vector<InitItem> items;
+  std::vector<double> cvals;  // the CPTs regrouped clique by clique
+  cvals.reserve(values.size());
   for (int c = 0; c < nc; ++c) {
     const auto& pv = p.pvars[c];
     std::vector<int64_t> pst(pv.size());
@@ -1136,11 +1138,11 @@ jt_status jt_init_from_cpts(jt_tree t, const jt_cpt_desc* cp, void* stream, floa
       pst[i] = sacc;
       sacc *= p.card[pv[i]];
     }
-    cl[c] = InitClique{p.base_off[c], (int32_t)p.n_entries[c], (int32_t)fac.size(), (int32_t)by_clique[c].size(),
-                       (int32_t)p.pow2[c]};
+    const int64_t cv0 = (int64_t)cvals.size();
     for (int i : by_clique[c]) {
       const int32_t a = cp->fam_off[i], b = cp->fam_off[i + 1];
-      fac.push_back(InitFactor{val_off[i], (int32_t)terms.size(), b - a});
+      fac.push_back(InitFactor{(int64_t)cvals.size() - cv0, (int32_t)terms.size(), b - a});
+      cvals.insert(cvals.end(), values.begin() + val_off[i], values.begin() + val_off[i + 1]);
       int64_t fst = 1;
       std::vector<InitTerm> tt(b - a);
       for (int32_t j = b - 1; j >= a; --j) {
@@ -1152,13 +1154,17 @@ jt_status jt_init_from_cpts(jt_tree t, const jt_cpt_desc* cp, void* stream, floa
       }
       terms.insert(terms.end(), tt.begin(), tt.end());
     }
+    const int64_t nvals = (int64_t)cvals.size() - cv0;
+    cl[c] = InitClique{p.base_off[c], cv0, (int32_t)p.n_entries[c], (int32_t)(fac.size() - by_clique[c].size()),
+                       (int32_t)by_clique[c].size(), (int32_t)p.pow2[c],
+                       (int32_t)std::min<int64_t>(nvals, INT32_MAX), 0};
     for (int64_t e0 = 0; e0 < p.n_entries[c]; e0 += kInitChunk) items.push_back(InitItem{c, (int32_t)e0});
   }
   cudaStream_t s = (cudaStream_t)stream;
   // the tables may still be read by earlier work on the tree's last stream
   CU(cudaStreamSynchronize(t->last_stream), "synchronising the tree's last stream");
-  st = t->compute == JT_F64 ? init_typed<double>(t, items, cl, fac, terms, values, s, kernel_ms)
-                            : init_typed<float>(t, items, cl, fac, terms, values, s, kernel_ms);
+  st = t->compute == JT_F64 ? init_typed<double>(t, items, cl, fac, terms, cvals, s, kernel_ms)
+                            : init_typed<float>(t, items, cl, fac, terms, cvals, s, kernel_ms);
   if (st != JT_OK) return st;
   std::fill(t->ready.begin(), t->ready.end(), 0);
   return JT_OK;

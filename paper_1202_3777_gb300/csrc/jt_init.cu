@@ -28,53 +28,77 @@ __device__ __forceinline__ uint32_t udiv(uint32_t n, UDiv d) {
   return (t + ((n - t) >> d.sh1)) >> d.sh2;
 }
 
-// Each thread takes kInitPerThread entries of an item, blockDim apart (so
-// every store instruction of a warp covers consecutive entries), and runs
-// the factor and term loops once for all of them.
+// The entries [start, end) of one clique: each thread takes kInitPerThread
+// of them, blockDim apart (so every store instruction of a warp covers
+// consecutive entries), and runs the factor and term loops once for all of
+// them.  `cv` holds the clique's CPTs (shared or global memory).
+template <typename T>
+__device__ __forceinline__ void init_range(T* out, uint32_t start, uint32_t end, const InitClique& q,
+                                           const InitFactor* factors, const InitTerm* terms, const T* cv) {
+  constexpr int J = kInitPerThread;
+  for (uint32_t e0 = start + threadIdx.x; e0 < end; e0 += J * blockDim.x) {
+    T v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) v[j] = T(1);
+    for (int32_t f = q.f0; f < q.f0 + q.nf; ++f) {
+      const InitFactor F = factors[f];
+      int32_t idx[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) idx[j] = 0;
+      for (int32_t t = F.t0; t < F.t0 + F.nt; ++t) {
+        const InitTerm m = terms[t];
+        if (q.pow2) {
+#pragma unroll
+          for (int j = 0; j < J; ++j)
+            idx[j] += (int32_t)(((e0 + j * blockDim.x) >> m.shift) & (uint32_t)(m.card - 1)) * m.fstride;
+        } else {
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            const uint32_t q1 = udiv(e0 + j * blockDim.x, m.pdiv);
+            const uint32_t q2 = udiv(q1, m.cdiv);
+            idx[j] += (int32_t)(q1 - q2 * (uint32_t)m.card) * m.fstride;
+          }
+        }
+      }
+      // every idx is a valid CPT index (each decoded state is below its
+      // cardinality), but only entries of the range are read and written
+      const T* tab = cv + F.val_off;
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if (e0 + j * blockDim.x < end) v[j] *= tab[idx[j]];
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (e0 + j * blockDim.x < end) out[e0 + j * blockDim.x] = v[j];
+  }
+}
+
+// A CTA walks items; when an item's clique changes and its CPTs fit, they
+// are copied to shared memory first, so the per-entry gathers hit shared
+// memory rather than L1 lines.
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_cliques(T* base, const InitItem* items, int32_t n_items,
                                                       const InitClique* cliques, const InitFactor* factors,
                                                       const InitTerm* terms, const T* vals) {
-  constexpr int J = kInitPerThread;
+  extern __shared__ __align__(16) unsigned char init_smem[];
+  T* s_vals = reinterpret_cast<T*>(init_smem);
+  constexpr int32_t cap = kInitSmemBytes / (int32_t)sizeof(T);
+  int32_t staged_clique = -1;
   for (int32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const InitItem w = items[it];
     const InitClique q = cliques[w.clique];
+    const uint32_t start = (uint32_t)w.start;
     const uint32_t end = (uint32_t)min(w.start + kInitChunk, q.n);
-    T* out = base + q.base_off;
-    for (uint32_t e0 = (uint32_t)w.start + threadIdx.x; e0 < end; e0 += J * blockDim.x) {
-      T v[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) v[j] = T(1);
-      for (int32_t f = q.f0; f < q.f0 + q.nf; ++f) {
-        const InitFactor F = factors[f];
-        int32_t idx[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) idx[j] = 0;
-        for (int32_t t = F.t0; t < F.t0 + F.nt; ++t) {
-          const InitTerm m = terms[t];
-          if (q.pow2) {
-#pragma unroll
-            for (int j = 0; j < J; ++j)
-              idx[j] += (int32_t)(((e0 + j * blockDim.x) >> m.shift) & (uint32_t)(m.card - 1)) * m.fstride;
-          } else {
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-              const uint32_t q1 = udiv(e0 + j * blockDim.x, m.pdiv);
-              const uint32_t q2 = udiv(q1, m.cdiv);
-              idx[j] += (int32_t)(q1 - q2 * (uint32_t)m.card) * m.fstride;
-            }
-          }
-        }
-        // every idx is a valid CPT index (each decoded state is below its
-        // cardinality), but only entries of the item are read and written
-        const T* tab = vals + F.val_off;
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-          if (e0 + j * blockDim.x < end) v[j] *= tab[idx[j]];
+    if (q.nvals <= cap) {
+      if (w.clique != staged_clique) {  // uniform over the CTA
+        __syncthreads();                // the previous item's gathers are done
+        for (int32_t i = threadIdx.x; i < q.nvals; i += blockDim.x) s_vals[i] = vals[q.vals_off + i];
+        __syncthreads();
+        staged_clique = w.clique;
       }
-#pragma unroll
-      for (int j = 0; j < J; ++j)
-        if (e0 + j * blockDim.x < end) out[e0 + j * blockDim.x] = v[j];
+      init_range<T>(base + q.base_off, start, end, q, factors, terms, s_vals);
+    } else {
+      init_range<T>(base + q.base_off, start, end, q, factors, terms, vals + q.vals_off);
     }
   }
 }
@@ -100,8 +124,12 @@ cudaError_t launch_init_cliques(T* base, const InitItem* items, int32_t n_items,
                                 const InitFactor* factors, const InitTerm* terms, const T* vals, int n_sm,
                                 cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  const int grid = std::min<int>(n_items, std::max(1, n_sm) * 8);
-  k_init_cliques<T><<<grid, 256, 0, s>>>(base, items, n_items, cliques, factors, terms, vals);
+  // one wave of resident CTAs, each walking its share of the items
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_init_cliques<T>, 256, kInitSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min<int>(n_items, std::max(1, n_sm) * std::max(1, per_sm));
+  k_init_cliques<T><<<grid, 256, kInitSmemBytes, s>>>(base, items, n_items, cliques, factors, terms, vals);
   return cudaGetLastError();
 }
 

@@ -36,9 +36,13 @@ struct UDiv {
 struct InitItem {
   int32_t clique, start;
 };
+// A clique's CPTs are stored contiguously ([vals_off, vals_off + nvals) of
+// the value array, each factor's val_off relative to vals_off), so a CTA can
+// stage them in shared memory when they fit kInitSmemBytes.
+constexpr int kInitSmemBytes = 32768;
 struct InitClique {
-  int64_t base_off;
-  int32_t n, f0, nf, pow2;
+  int64_t base_off, vals_off;
+  int32_t n, f0, nf, pow2, nvals, pad;
 };
 struct InitFactor {
   int64_t val_off;
