@@ -265,6 +265,59 @@ def measure_cpt_init(tree, hbm):
             "alg_bytes": alg, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm}
 
 
+def separator_sweep():
+    """Analogues of Fig. 6 and Fig. 7 on trees that differ only in separator
+    size (32 cliques of 4^8 entries, separators of 4^1 .. 4^7 entries), one
+    case without evidence, FP32 on the GPU:
+
+    * speedup over the sequential FP64 oracle (one core) of the fused
+      propagation (propagation kernel + finalisation, device time) and of
+      the paper's per-message propagation (naive mapping tables), against
+      the average separator table size (Fig. 6);
+    * the launch-overhead share of the per-message propagation (Fig. 7),
+      with the paper's model of a constant cost tau per launch (Eq. 5-6):
+      tau is the per-launch time of the per-message propagation of a floor
+      tree (cliques of two binary variables, one shared), where every
+      kernel has almost nothing to do; a tree's share is
+      launches x tau / its per-message time.  A per-message propagation
+      issues 4(n-1) + 4 kernels and 2 memsets (2 kernels per message, the
+      root's normalisation, the totals and the finalisation).
+    Device times are best of three after a first run."""
+    from oracle import hugin
+    from paper_1202_3777_gb300 import jt
+    configs = [("floor", dict(sep_vars=1, k=2, card=2))] + \
+        [(f"sep4^{s}", dict(sep_vars=s, k=8)) for s in range(1, 8)]
+    rows = []
+    for name, kw in configs:
+        tree = synth.separator_sweep_tree(**kw)
+        n = tree.n_cliques
+        seps = [int(np.prod([int(tree.card[v]) for v in
+                             set(tree.cliques[c].tolist()) & set(tree.cliques[int(tree.parent[c])].tolist())]))
+                for c in range(1, n)]
+        t32 = tree.as_dtype(np.float32)
+        cpu = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            hugin.propagate_tree(t32, {})
+            cpu.append(1e3 * (time.perf_counter() - t0))
+        h = jt.jt_load_synth(t32, compute=jt.JT_F32, max_cases=1, flags=jt.JT_MATERIALIZE_CLIQUES)
+        jt.jt_profile_propagate(h, 0, 1)
+        fused = min(float(np.sum(jt.jt_profile_propagate(h, 0, 1))) for _ in range(3))
+        jt.jt_propagate_per_message(h, 0, 0)
+        pm = min(jt.jt_propagate_per_message(h, 0, 0) for _ in range(3))
+        assert jt.jt_get_status(h, 0, 1)[0] == jt.JT_OK
+        h.free()
+        rows.append({"tree": tree.name, "avg_separator_entries": float(np.mean(seps)),
+                     "clique_entries": int(tree.entries()), "cpu_oracle_ms": min(cpu), "fused_ms": fused,
+                     "per_message_ms": pm, "launches_per_message_path": 4 * (n - 1) + 6,
+                     "speedup_fused": min(cpu) / fused, "speedup_per_message": min(cpu) / pm})
+    tau = rows[0]["per_message_ms"] / rows[0]["launches_per_message_path"]
+    for r in rows:
+        r["launch_overhead_share"] = min(1.0, r["launches_per_message_path"] * tau / r["per_message_ms"])
+    return {"sweep": "separator_size", "tau_us": 1e3 * tau, "cpu": "FP64 numpy oracle, one core",
+            "rows": rows}
+
+
 def measure_serving(rank):
     """Continuous batching over the four resident trees (small, large-clique,
     high-cardinality, 1024-clique binary): a burst of queries gives the
@@ -327,6 +380,8 @@ def main():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--sweep-separators", action="store_true",
+                    help="print the separator-size sweep (Fig. 6 / Fig. 7 analogues) instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -345,6 +400,11 @@ def main():
     from paper_1202_3777_gb300 import build
     build.build()
     from paper_1202_3777_gb300 import jt
+
+    if args.sweep_separators:
+        if rank == 0:
+            print(json.dumps(separator_sweep(), default=_json_default), flush=True)
+        return 0
 
     B = args.batch
     tree = synth.WORKLOADS[WORKLOAD]["build"]().as_dtype(np.float32)

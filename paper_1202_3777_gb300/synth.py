@@ -308,6 +308,22 @@ def random_small_tree(seed: int, n_cliques: int = 5, max_states: float = 1 << 14
     raise RuntimeError("could not draw a small tree")
 
 
+def separator_sweep_tree(sep_vars: int, seed: int = 1006, n_cliques: int = 32, k: int = 6,
+                         card: int = 4) -> Tree:
+    """Trees that differ only in separator size, for the analogue of Fig. 6
+    (speedup against average separator table size): ``n_cliques`` cliques
+    of ``k`` variables of cardinality ``card``; every child shares exactly
+    ``sep_vars`` variables with a uniformly chosen earlier clique, so every
+    separator table has card**sep_vars entries and every clique card**k.
+    Potentials Uniform(0.01, 1] in FP64."""
+    if not 1 <= sep_vars < k:
+        raise ValueError("need 1 <= sep_vars < k")
+    rng = np.random.default_rng(seed + 97 * sep_vars)
+    c_, cl, par, fr = _build(rng, n_cliques, lambda: k, lambda pk: (sep_vars, k - sep_vars),
+                             lambda: card, _uniform_parent(rng))
+    return _finish(rng, c_, cl, par, fr, f"sep-sweep-{n_cliques}x{card}^{k}-sep{card}^{sep_vars}")
+
+
 # --------------------------------------------------------------------------
 # Alternative potentials with known closed forms (inputs only).
 # --------------------------------------------------------------------------

@@ -63,3 +63,14 @@ def test_bn_for_tree_is_a_network_over_the_tree():
         assert np.allclose(sums, 1.0, atol=1e-12) and np.all(tab >= 0)
     f2, v2 = synth.bn_for_tree(t, 3)
     assert all(np.array_equal(a, b) for a, b in zip(vals, v2))
+
+
+def test_separator_sweep_trees_differ_only_in_separator_size():
+    for s in (1, 3, 5):
+        t = synth.separator_sweep_tree(s)
+        assert t.n_cliques == 32 and all(len(c) == 6 for c in t.cliques)
+        assert np.all(t.table_sizes() == 4 ** 6)
+        for c in range(1, t.n_cliques):
+            sep = set(t.cliques[c].tolist()) & set(t.cliques[int(t.parent[c])].tolist())
+            assert len(sep) == s
+        hugin.validate(t.card, [c.tolist() for c in t.cliques], t.parent)
