@@ -74,3 +74,20 @@ def test_bad_descriptor_fields(jt):
     assert jt.raw_load_status(c, q, p, x, max_cases=0) == jt.JT_ERR_INVALID_ARG
     assert jt.raw_load_status(c, q, p, x, flags=0x80) == jt.JT_ERR_INVALID_ARG
     assert jt.raw_load_status(c, q, p, x, compute=7) == jt.JT_ERR_INVALID_ARG
+
+
+def test_tree_without_tables_is_still_validated(jt):
+    """potentials = NULL (tables start at one, for jt_init_from_cpts) skips
+    only the value checks: the structure is validated before any device
+    work."""
+    c, q, p, x = _tiny()
+    assert jt.raw_load_status(c, [[0, 1], [1, 2], [0, 2]], [-1, 0, 1], None) == jt.JT_ERR_NOT_A_JUNCTION_TREE
+    assert jt.raw_load_status([1, 3, 2], q, p, None) == jt.JT_ERR_INVALID_ARG
+
+
+def test_initialisation_entry_points_reject_a_null_tree(jt):
+    import ctypes as C
+    d = jt.jt_cpt_desc(0, None, None, None, None)
+    assert jt._lib.jt_init_from_cpts(None, C.byref(d), None, None) == jt.JT_ERR_INVALID_ARG
+    out = np.zeros(4)
+    assert jt._lib.jt_get_potential(None, 0, out.ctypes.data_as(C.c_void_p)) == jt.JT_ERR_INVALID_ARG
