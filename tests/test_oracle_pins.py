@@ -498,3 +498,34 @@ def test_cpt_rejects_bad_tables():
         cpt.cpt_potentials(card, cliques, [[0]], [np.ones(3)])           # wrong size
     with pytest.raises(ValueError):
         cpt.cpt_potentials(card, cliques, [[0]], [np.ones(2)], home=[1])  # clique 1 lacks A
+
+
+def test_cpt_deterministic_network():
+    """Deterministic CPTs put exact zeros in the clique tables, so separator
+    entries are zero and the 0/0 rule decides: B copies A, C = A xor B' where
+    B' is a noisy copy of B.  Posteriors by hand and by brute force over the
+    factorisation; contradicting evidence gives P(e) = 0."""
+    card = [2, 2, 2, 2]                       # A, B, B', C
+    cliques = [[0, 1, 2], [0, 2, 3]]          # {A,B,B'} - {A,B',C}
+    parent = [-1, 0]
+    fams = [[0], [0, 1], [1, 2], [0, 2, 3]]
+    pa = np.array([0.3, 0.7])
+    copy = np.eye(2).ravel()                  # P(B = a | A = a) = 1
+    noisy = np.array([[0.9, 0.1], [0.2, 0.8]]).ravel()
+    xor = np.array([[[1, 0], [0, 1]], [[0, 1], [1, 0]]], float).ravel()   # C = A xor B'
+    vals = [pa, copy, noisy, xor]
+    pot = cpt.cpt_potentials(card, cliques, fams, vals)
+    assert np.count_nonzero(pot[0] == 0) > 0 and np.count_nonzero(pot[1] == 0) > 0
+    # C = 0  <=>  B' = A; P(C=0) = 0.3*0.9 + 0.7*0.8
+    pc0 = 0.3 * 0.9 + 0.7 * 0.8
+    r = hugin.propagate(card, cliques, parent, pot, {})
+    assert abs(r.log_z) < 1e-15 and r.marginals[3][0] == pytest.approx(pc0, rel=1e-14)
+    r = hugin.propagate(card, cliques, parent, pot, {3: 0})
+    assert r.marginals[1][0] == pytest.approx(0.3 * 0.9 / pc0, rel=1e-14)   # B = A, given C = 0
+    for ev in ({3: 1}, {1: 1, 3: 0}, {}):
+        r = hugin.propagate(card, cliques, parent, pot, ev)
+        lz, m = brute.brute_force(card, fams, vals, ev)
+        assert abs(r.log_z - lz) <= 1e-13 and max_marg_err(r.marginals, m) < 1e-13
+    # B must equal A: observing A = 0 and B = 1 has probability zero
+    with pytest.raises(hugin.ZeroEvidence):
+        hugin.propagate(card, cliques, parent, pot, {0: 0, 1: 1})
