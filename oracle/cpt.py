@@ -21,10 +21,11 @@ Readings where the paper is silent (each also listed in the design notes):
 * the CPTs of one clique are multiplied in ascending CPT order, starting
   from one.
 
-Pinned by ``tests/test_oracle_pins.py``: a two-node network with its
-posterior in closed form, ancestral marginals of a chain, Z = 1 for any
-normalised network, the home-clique rule, and brute force over the
-network's own factorisation.
+Pinned by ``tests/test_oracle_pins.py``: a three-node chain whose tables,
+ancestral marginals and posterior are written out by hand, a deterministic
+network (exact zeros), Z = 1 for any normalised network, the home-clique
+rule, brute force over the network's own factorisation, and planted
+mistakes (a transposed, a dropped and a doubled CPT).
 """
 from __future__ import annotations
 
