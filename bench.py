@@ -280,8 +280,10 @@ def separator_sweep():
       tree (cliques of two binary variables, one shared), where every
       kernel has almost nothing to do; a tree's share is
       launches x tau / its per-message time.  A per-message propagation
-      issues 4(n-1) + 4 kernels and 2 memsets (2 kernels per message, the
-      root's normalisation, the totals and the finalisation).
+      without evidence issues 4(n-1) + 8 stream operations: 2 kernels per
+      message, 2 for the root's normalisation, 1 for the totals, 1 for the
+      finalisation, 2 memsets and 2 device copies (the tables and the
+      separators' start values).
     Device times are best of three after a first run."""
     from oracle import hugin
     from paper_1202_3777_gb300 import jt
@@ -309,7 +311,7 @@ def separator_sweep():
         h.free()
         rows.append({"tree": tree.name, "avg_separator_entries": float(np.mean(seps)),
                      "clique_entries": int(tree.entries()), "cpu_oracle_ms": min(cpu), "fused_ms": fused,
-                     "per_message_ms": pm, "launches_per_message_path": 4 * (n - 1) + 6,
+                     "per_message_ms": pm, "launches_per_message_path": 4 * (n - 1) + 8,
                      "speedup_fused": min(cpu) / fused, "speedup_per_message": min(cpu) / pm})
     tau = rows[0]["per_message_ms"] / rows[0]["launches_per_message_path"]
     for r in rows:
