@@ -320,6 +320,39 @@ def separator_sweep():
             "rows": rows}
 
 
+def merging_sweep():
+    """Merging small separators (the remedy of Sec. 5) on the latency-bound
+    trees: the fused propagation (kernel + finalisation, device time, one
+    case without evidence, FP32, best of three after a first run) of the
+    original tree against merged trees at a few separator thresholds (the
+    merged table capped at 3^8 entries for the small tree, 2^10 for the
+    binary one)."""
+    from paper_1202_3777_gb300 import jt
+    from paper_1202_3777_gb300.merge import load_merged
+    rows = []
+    for tree, thresholds, cap in ((synth.small_tree(), (10,), 3 ** 8),
+                                  (synth.binary_serving_tree(), (4, 8, 16), 1 << 10)):
+        t32 = tree.as_dtype(np.float32)
+        pot = t32.pot.astype(np.float64)
+
+        def fused(h):
+            jt.jt_profile_propagate(h, 0, 1)
+            ms = min(float(np.sum(jt.jt_profile_propagate(h, 0, 1))) for _ in range(3))
+            assert jt.jt_get_status(h, 0, 1)[0] == jt.JT_OK
+            return ms
+
+        h = jt.jt_load_synth(t32, compute=jt.JT_F32, max_cases=1)
+        rows.append({"tree": tree.name, "min_separator_entries": 0, "cliques": tree.n_cliques,
+                     "depth": int(h.info.depth), "fused_ms": fused(h)})
+        h.free()
+        for th in thresholds:
+            h, m = load_merged(tree.card, tree.cliques, tree.parent, pot, th, cap, compute=jt.JT_F32)
+            rows.append({"tree": tree.name, "min_separator_entries": th, "max_clique_entries": cap,
+                         "cliques": len(m.cliques), "depth": int(h.info.depth), "fused_ms": fused(h)})
+            h.free()
+    return {"sweep": "merging", "rows": rows}
+
+
 def measure_serving(rank):
     """Continuous batching over the four resident trees (small, large-clique,
     high-cardinality, 1024-clique binary): a burst of queries gives the
@@ -384,6 +417,8 @@ def main():
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--sweep-separators", action="store_true",
                     help="print the separator-size sweep (Fig. 6 / Fig. 7 analogues) instead of the bench line")
+    ap.add_argument("--sweep-merging", action="store_true",
+                    help="print original against merged-tree propagation times instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -403,9 +438,10 @@ def main():
     build.build()
     from paper_1202_3777_gb300 import jt
 
-    if args.sweep_separators:
+    if args.sweep_separators or args.sweep_merging:
         if rank == 0:
-            print(json.dumps(separator_sweep(), default=_json_default), flush=True)
+            out = separator_sweep() if args.sweep_separators else merging_sweep()
+            print(json.dumps(out, default=_json_default), flush=True)
         return 0
 
     B = args.batch
