@@ -1,0 +1,155 @@
+// Host-side check of the propagation planner (no GPU): builds the plan and
+// the schedules of a tree read from stdin and checks the invariants the
+// persistent kernel relies on.
+//
+//   * Every block of every stage is one work item per case block, and the
+//     items tile the stage's table.
+//   * Dependencies follow Algorithms 2-4: a collect stage waits for every
+//     child's collect stage, the root's distribute stage for every child's
+//     collect stage, any other distribute stage for its parent's distribute
+//     stage, each for all of that stage's blocks.
+//   * Work items are claimed in queue order and an item waits only for the
+//     blocks it depends on, so the kernel cannot wait forever on work no
+//     CTA has claimed: every block an item waits for comes earlier in the
+//     queue.
+//
+// Input (whitespace-separated integers): n_vars, card[n_vars], n_cliques,
+// then per clique k followed by its k variables, then parent[n_cliques].
+// Output: one line per (case-block width, case count):
+//   "cb=<cb> cases=<n> OK items=<i> stages=<s>" or "... UNSUPPORTED <why>" or
+//   "... FAIL <what>".
+#include <cstdio>
+#include <iostream>
+#include <string>
+#include <vector>
+
+#include "jt_internal.h"
+
+using namespace jt;
+
+namespace {
+
+std::string check(const Plan& p, const Schedule& s) {
+  const int nc = p.n_cliques;
+  const int nst = (int)s.stages.size();
+  if (nst != 2 * nc) return "stage count";
+  // tiling: per (stage, case block) every block once, in order of offsets
+  std::vector<std::vector<int>> seen((size_t)nst * s.n_cb);
+  for (const DevItem& it : s.items) {
+    if (it.stage < 0 || it.stage >= nst || it.cbk < 0 || it.cbk >= s.n_cb) return "item index out of range";
+    const DevStage& S = s.stages[it.stage];
+    if (it.block < 0 || it.block >= S.n_blocks) return "block out of range";
+    if (it.off != S.base_off + (int64_t)it.block * S.B || it.n != S.B) return "item does not tile its stage";
+    seen[(size_t)it.stage * s.n_cb + it.cbk].push_back(it.block);
+  }
+  for (int st = 0; st < nst; ++st) {
+    const DevStage& S = s.stages[st];
+    if (S.n_blocks > 0 && ((int64_t)S.n_blocks * S.B < S.n || (int64_t)(S.n_blocks - 1) * S.B >= S.n))
+      return "blocks do not cover stage " + std::to_string(st);
+    for (int q = 0; q < s.n_cb; ++q) {
+      std::vector<int> b = seen[(size_t)st * s.n_cb + q];
+      if ((int)b.size() != S.n_blocks) return "stage " + std::to_string(st) + " has a missing or repeated block";
+      std::vector<char> got(S.n_blocks, 0);
+      for (int x : b) {
+        if (got[x]) return "repeated block";
+        got[x] = 1;
+      }
+    }
+  }
+  // dependencies as Algorithms 2-4 order them
+  for (int pass = 0; pass < 2; ++pass)
+    for (int c = 0; c < nc; ++c) {
+      const DevStage& S = s.stages[pass * nc + c];
+      std::vector<std::pair<int, int>> want;
+      if (pass == 0 || c == 0) {
+        if (!(pass == 0 && c == 0))
+          for (int g : p.children[c]) want.push_back({g, s.stages[g].n_blocks});
+      } else {
+        want.push_back({nc + p.parent[c], s.stages[nc + p.parent[c]].n_blocks});
+      }
+      if (S.ndep != (int)want.size()) return "dependency count of stage " + std::to_string(pass * nc + c);
+      for (int i = 0; i < S.ndep; ++i)
+        if (s.deps[S.dep0 + 2 * i] != want[i].first || s.deps[S.dep0 + 2 * i + 1] != want[i].second)
+          return "dependency of stage " + std::to_string(pass * nc + c);
+    }
+  // queue order: the blocks an item waits for are all claimed before it
+  std::vector<int> done((size_t)nst * s.n_cb, 0);
+  for (size_t i = 0; i < s.items.size(); ++i) {
+    const DevItem& it = s.items[i];
+    const DevStage& S = s.stages[it.stage];
+    for (int d = 0; d < S.ndep; ++d) {
+      const int st = s.deps[S.dep0 + 2 * d], need = s.deps[S.dep0 + 2 * d + 1];
+      if (done[(size_t)st * s.n_cb + it.cbk] < need)
+        return "item " + std::to_string(i) + " waits for blocks queued after it";
+    }
+    ++done[(size_t)it.stage * s.n_cb + it.cbk];
+  }
+  return "";
+}
+
+}  // namespace
+
+int main() {
+  int nv = 0, nc = 0;
+  if (!(std::cin >> nv) || nv <= 0) return 2;
+  std::vector<int32_t> card(nv);
+  for (auto& x : card) std::cin >> x;
+  std::cin >> nc;
+  std::vector<int64_t> off(1, 0);
+  std::vector<int32_t> vars;
+  for (int c = 0; c < nc; ++c) {
+    int k = 0;
+    std::cin >> k;
+    for (int i = 0; i < k; ++i) {
+      int v = 0;
+      std::cin >> v;
+      vars.push_back(v);
+    }
+    off.push_back((int64_t)vars.size());
+  }
+  std::vector<int32_t> parent(nc);
+  for (auto& x : parent) std::cin >> x;
+  if (!std::cin) return 2;
+  jt_tree_desc d{};
+  d.n_vars = nv;
+  d.card = card.data();
+  d.n_cliques = nc;
+  d.clique_off = off.data();
+  d.clique_vars = vars.data();
+  d.parent = parent.data();
+  d.potentials = nullptr;
+  d.potentials_dtype = JT_F64;
+  d.compute = JT_F32;
+  d.max_cases = 64;
+  Plan p;
+  std::string err;
+  if (build_plan(&d, &p, &err) != JT_OK) {
+    std::printf("PLAN FAIL %s\n", err.c_str());
+    return 1;
+  }
+  const int smem = 232448 - 256;  // the opt-in shared memory of one CTA on this GPU, less the reserve
+  const int shapes[][2] = {{1, 1}, {4, 16}, {8, 16}, {8, 64}};
+  int bad = 0;
+  for (const auto& sh : shapes) {
+    Schedule s;
+    err.clear();
+    const jt_status st = build_schedule(p, 4, sh[0], sh[1], 152, smem, &s, &err);
+    if (st == JT_ERR_UNSUPPORTED) {
+      std::printf("cb=%d cases=%d UNSUPPORTED %s\n", sh[0], sh[1], err.c_str());
+      continue;
+    }
+    if (st != JT_OK) {
+      std::printf("cb=%d cases=%d FAIL status %d %s\n", sh[0], sh[1], (int)st, err.c_str());
+      ++bad;
+      continue;
+    }
+    const std::string why = check(p, s);
+    if (why.empty()) {
+      std::printf("cb=%d cases=%d OK items=%zu stages=%zu\n", sh[0], sh[1], s.items.size(), s.stages.size());
+    } else {
+      std::printf("cb=%d cases=%d FAIL %s\n", sh[0], sh[1], why.c_str());
+      ++bad;
+    }
+  }
+  return bad ? 1 : 0;
+}

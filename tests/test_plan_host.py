@@ -1,0 +1,68 @@
+"""The propagation planner on the host (no GPU): ``tests/plan_check.cpp``
+links the library's planner (csrc/jt_plan.cpp), builds the schedules of a
+tree for one case, 4- and 8-case blocks, and checks what the persistent
+kernel relies on: every block of every stage is one work item per case
+block, the dependencies are those of Algorithms 2-4, and no item waits for
+a block queued after it.  Run on the workloads, on merged trees (high
+fan-out), on trees with empty separators and on the separator sweep."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+from paper_1202_3777_gb300 import synth
+from paper_1202_3777_gb300.merge import merge_small_separators
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CUDA_INC = "/usr/local/cuda/include"
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    if shutil.which("g++") is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path_factory.mktemp("plan") / "plan_check")
+    csrc = os.path.join(ROOT, "paper_1202_3777_gb300", "csrc")
+    cmd = ["g++", "-std=c++17", "-O2", "-I", csrc, "-I", os.path.join(ROOT, "include"), "-I", CUDA_INC,
+           os.path.join(ROOT, "tests", "plan_check.cpp"), os.path.join(csrc, "jt_plan.cpp"), "-o", exe, "-lpthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def _run(exe, card, cliques, parent):
+    words = [len(card), *[int(x) for x in card], len(cliques)]
+    for c in cliques:
+        words += [len(c), *[int(v) for v in c]]
+    words += [int(x) for x in parent]
+    r = subprocess.run([exe], input=" ".join(map(str, words)), capture_output=True, text=True)
+    return r.returncode, r.stdout.strip().splitlines()
+
+
+TREES = {
+    "small": lambda: synth.small_tree(),
+    "large-clique": lambda: synth.large_clique_tree(),
+    "high-card": lambda: synth.high_card_tree(),
+    "batched": lambda: synth.batched_tree(),
+    "binary-serving": lambda: synth.binary_serving_tree(),
+    "sep-sweep-4^1": lambda: synth.separator_sweep_tree(1, k=8),
+    "sep-sweep-4^7": lambda: synth.separator_sweep_tree(7, k=8),
+    "empty-separators": lambda: synth.random_small_tree(7, n_cliques=9, allow_empty_sep=True, max_states=1 << 40),
+}
+
+
+@pytest.mark.parametrize("name", list(TREES))
+def test_schedules_of_the_workloads(checker, name):
+    t = TREES[name]()
+    rc, lines = _run(checker, t.card, t.cliques, t.parent)
+    assert rc == 0 and len(lines) == 4, lines
+    assert all(" OK " in ln for ln in lines), lines
+
+
+@pytest.mark.parametrize("min_sep,cap", [(8, 1 << 8), (16, 1 << 10), (1 << 20, 1 << 12)])
+def test_schedules_of_merged_trees(checker, min_sep, cap):
+    t = synth.binary_serving_tree()
+    m = merge_small_separators(t.card, t.cliques, t.parent, min_sep, cap)
+    rc, lines = _run(checker, t.card, m.cliques, m.parent)
+    assert rc == 0 and all(" OK " in ln for ln in lines), lines
