@@ -15,9 +15,12 @@
 //
 // Input (whitespace-separated integers): n_vars, card[n_vars], n_cliques,
 // then per clique k followed by its k variables, then parent[n_cliques].
+// With argument "plant-order" the queue is reversed, with "plant-repeat" one
+// item is queued twice, before the checks (each must then fail).
 // Output: one line per (case-block width, case count):
 //   "cb=<cb> cases=<n> OK items=<i> stages=<s>" or "... UNSUPPORTED <why>" or
 //   "... FAIL <what>".
+#include <algorithm>
 #include <cstdio>
 #include <iostream>
 #include <string>
@@ -33,7 +36,7 @@ std::string check(const Plan& p, const Schedule& s) {
   const int nc = p.n_cliques;
   const int nst = (int)s.stages.size();
   if (nst != 2 * nc) return "stage count";
-  // tiling: per (stage, case block) every block once, in order of offsets
+  // tiling: per (stage, case block) every block exactly once
   std::vector<std::vector<int>> seen((size_t)nst * s.n_cb);
   for (const DevItem& it : s.items) {
     if (it.stage < 0 || it.stage >= nst || it.cbk < 0 || it.cbk >= s.n_cb) return "item index out of range";
@@ -89,7 +92,8 @@ std::string check(const Plan& p, const Schedule& s) {
 
 }  // namespace
 
-int main() {
+int main(int argc, char** argv) {
+  const std::string plant = argc > 1 ? argv[1] : "";
   int nv = 0, nc = 0;
   if (!(std::cin >> nv) || nv <= 0) return 2;
   std::vector<int32_t> card(nv);
@@ -143,6 +147,8 @@ int main() {
       ++bad;
       continue;
     }
+    if (plant == "plant-order") std::reverse(s.items.begin(), s.items.end());
+    if (plant == "plant-repeat" && s.items.size() > 1) s.items.back() = s.items.front();
     const std::string why = check(p, s);
     if (why.empty()) {
       std::printf("cb=%d cases=%d OK items=%zu stages=%zu\n", sh[0], sh[1], s.items.size(), s.stages.size());

@@ -31,12 +31,12 @@ def checker(tmp_path_factory):
     return exe
 
 
-def _run(exe, card, cliques, parent):
+def _run(exe, card, cliques, parent, *extra):
     words = [len(card), *[int(x) for x in card], len(cliques)]
     for c in cliques:
         words += [len(c), *[int(v) for v in c]]
     words += [int(x) for x in parent]
-    r = subprocess.run([exe], input=" ".join(map(str, words)), capture_output=True, text=True)
+    r = subprocess.run([exe, *extra], input=" ".join(map(str, words)), capture_output=True, text=True)
     return r.returncode, r.stdout.strip().splitlines()
 
 
@@ -66,3 +66,11 @@ def test_schedules_of_merged_trees(checker, min_sep, cap):
     m = merge_small_separators(t.card, t.cliques, t.parent, min_sep, cap)
     rc, lines = _run(checker, t.card, m.cliques, m.parent)
     assert rc == 0 and all(" OK " in ln for ln in lines), lines
+
+
+@pytest.mark.parametrize("plant,what", [("plant-order", "queued after"), ("plant-repeat", "block")])
+def test_planted_schedule_mistakes_are_caught(checker, plant, what):
+    t = synth.small_tree()
+    rc, lines = _run(checker, t.card, t.cliques, t.parent, plant)
+    assert rc == 1 and all(" FAIL " in ln and what in ln for ln in lines), lines
+
