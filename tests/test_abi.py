@@ -91,3 +91,25 @@ def test_initialisation_entry_points_reject_a_null_tree(jt):
     assert jt._lib.jt_init_from_cpts(None, C.byref(d), None, None) == jt.JT_ERR_INVALID_ARG
     out = np.zeros(4)
     assert jt._lib.jt_get_potential(None, 0, out.ctypes.data_as(C.c_void_p)) == jt.JT_ERR_INVALID_ARG
+
+
+def test_plain_c_program_links_and_runs(jt, tmp_path):
+    """The header is C99 (no C++ in the ABI): a C program that takes the
+    address of every declared entry point compiles with warnings as errors,
+    links against libjt.so and runs the calls that need no GPU."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    src = os.path.join(ROOT, "tests", "abi_consumer.c")
+    body = open(src).read()
+    for name in _declared():
+        assert f"(any_fn){name}," in body or f"(any_fn){name}\n" in body, name
+    libdir = os.path.dirname(jt.LIB)
+    exe = str(tmp_path / "abi_consumer")
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), src,
+           "-o", exe, "-L", libdir, "-ljt", f"-Wl,-rpath,{libdir}", "-Wl,--allow-shlib-undefined"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.startswith("c-abi ok")
