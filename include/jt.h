@@ -282,6 +282,23 @@ typedef struct {
 
 jt_status jt_get_info(jt_tree t, jt_tree_info* out);
 
+/* The schedule a propagation of the case range [first, first + n) uses
+ * (recorded, and for several cases chosen by timing, on the range's first
+ * jt_propagate).  Not part of the paper's method: it reports how the
+ * library laid out the work (Sec. 3.4's per-message launches become one
+ * persistent launch over work items).  JT_ERR_STATE if the range has not been
+ * propagated yet; JT_ERR_INVALID_ARG for a bad range or a null `out`. */
+typedef struct {
+  int32_t case_block;   /* evidence cases per work item: 1, 4, 8, or 32 (one case per lane) */
+  int32_t n_items;      /* work items of one propagation */
+  int32_t grid;         /* CTAs of the persistent launch */
+  int32_t smem_bytes;   /* dynamic shared memory per CTA */
+  int32_t window_entries; /* largest per-case window set of a work item */
+  int32_t reserved[3];
+} jt_schedule_info;
+
+jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info* out);
+
 /* Release every resource of the tree (waits for its pending work). NULL is a no-op. */
 void jt_free(jt_tree t);
 

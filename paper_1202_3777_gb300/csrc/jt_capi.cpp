@@ -11,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "jt_internal.h"
@@ -56,6 +57,7 @@ struct GraphEntry {
   const uint4* blobs = nullptr;
   const DevItem* items = nullptr;
   int32_t grid = 0, smem = 0;
+  cudaEvent_t done = nullptr;   // recorded after every launch of the graph
 };
 
 // State of the paper-literal per-message propagation (jt_propagate_per_message),
@@ -130,6 +132,7 @@ void free_graphs(jt_tree t) {
   for (auto& kv : t->graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    if (kv.second.done) cudaEventDestroy(kv.second.done);
     for (void* p : kv.second.dev_bufs) cudaFree(p);
   }
   t->graphs.clear();
@@ -180,8 +183,9 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   auto chk = [&](cudaError_t e) {
     if (err == cudaSuccess && e != cudaSuccess) err = e;
   };
+  const int64_t msg_rows = sc.cb == kCaseLanes ? (int64_t)sc.n_cb * kCaseLanes : n_cases;
   chk(cudaMemsetAsync((T*)t->d_msg + (int64_t)case0 * p.msg_stride, 0,
-                      (size_t)n_cases * p.msg_stride * sizeof(T), s));
+                      (size_t)msg_rows * p.msg_stride * sizeof(T), s));
   chk(cudaMemsetAsync(t->d_sums + (int64_t)case0 * 2 * p.n_cliques, 0,
                       (size_t)n_cases * 2 * p.n_cliques * sizeof(double), s));
   chk(cudaMemsetAsync(t->d_status + case0, 0, (size_t)n_cases * sizeof(int32_t), s));
@@ -221,7 +225,12 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   a.win_max = sc.win_max;
   a.blob_max = sc.blob_max;
   if (ev) chk(cudaEventRecord(ev[0], s));
-  chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
+  if constexpr (std::is_same<T, float>::value) {
+    if (sc.cb == kCaseLanes) chk(launch_propagate_cl(a, ge.grid, ge.smem, s));
+    else chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
+  } else {
+    chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
+  }
   if (ev) chk(cudaEventRecord(ev[1], s));
   FinalArgs<T> f{};
   f.vs = sc.cb > 1 ? t->d_vs_fine : t->d_vs;  // the joint layout the schedule's ports write
@@ -237,7 +246,13 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   f.marg_total = p.marg_total;
   f.marg_out = t->d_marg;
   f.logz_out = t->d_logz;
-  chk(launch_finalize<T>(f, s));
+  f.lanes = sc.cb == kCaseLanes ? kCaseLanes : 1;
+  if constexpr (std::is_same<T, float>::value) {
+    if (sc.cb == kCaseLanes) chk(launch_finalize_cl(f, s));
+    else chk(launch_finalize<T>(f, s));
+  } else {
+    chk(launch_finalize<T>(f, s));
+  }
   if (ev) chk(cudaEventRecord(ev[2], s));
   return err;
 }
@@ -286,9 +301,11 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, cudaStream_
 void drop_graph(GraphEntry& ge) {
   if (ge.exec) cudaGraphExecDestroy(ge.exec);
   if (ge.graph) cudaGraphDestroy(ge.graph);
+  if (ge.done) cudaEventDestroy(ge.done);
   for (void* p : ge.dev_bufs) cudaFree(p);
   ge.exec = nullptr;
   ge.graph = nullptr;
+  ge.done = nullptr;
   ge.dev_bufs.clear();
 }
 
@@ -308,56 +325,81 @@ float time_graph(const GraphEntry& ge, cudaStream_t s) {
 
 // The propagation graph of a case range, recorded on first use.  Several
 // cases can go one per work item (more, shorter items; every item streams
-// its table for one case) or in blocks of 4 or kCaseBlock = 8 (each
-// streamed table chunk serves the block's cases).  Which is faster depends on the tree and the
-// number of cases: blocks pay off for cliques with many ports and many
-// cases, single cases for small trees, few cases or few ports.  So the
-// first use of a multi-case range times the schedules once each (after a
+// its table for one case), in blocks of 4 or kCaseBlock = 8 (each streamed
+// table chunk serves the block's cases), or, for FP32 trees of power-of-two
+// cliques, kCaseLanes = 32 cases on the lanes of every warp.  Which is
+// fastest depends on the tree and the number of cases, so the first use of a
+// multi-case range times each schedule the tree supports once (after a
 // warm-up launch of each; the launches compute the same propagation the
-// caller asked for) and keeps the fastest.  JT_CASE_BLOCK=1, 4 or 8 in the
-// environment fixes the choice instead.
+// caller asked for) and keeps the fastest.  JT_CASE_BLOCK=1, 4, 8 or 32 in
+// the environment fixes the choice instead (32 falls back to 8 where case
+// lanes do not apply).
 jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** out) {
   auto key = std::make_pair(first, n);
   auto it = t->graphs.find(key);
   if (it == t->graphs.end()) {
     if (t->graphs.size() >= 64) {
-      CU(cudaDeviceSynchronize(), "graph cache eviction");
+      // every cached graph's last launch has finished before it is destroyed
+      for (auto& kv : t->graphs)
+        if (kv.second.done) CU(cudaEventSynchronize(kv.second.done), "graph cache eviction");
       free_graphs(t);
     }
     int forced = 0;
-    if (const char* f = std::getenv("JT_CASE_BLOCK"); f && (*f == '1' || *f == '4' || *f == '8') && f[1] == 0)
-      forced = *f - '0';
+    if (const char* f = std::getenv("JT_CASE_BLOCK"); f && *f) {
+      const std::string v(f);
+      if (v == "1" || v == "4" || v == "8" || v == "32") forced = std::stoi(v);
+    }
     auto record = [&](int cb, GraphEntry* ge) {
       return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, t->cap_stream, ge)
                                   : record_schedule<float>(t, first, n, cb, t->cap_stream, ge);
     };
-    GraphEntry ge;
-    const int cb0 = n == 1 ? 1 : (forced ? forced : kCaseBlock);
-    jt_status st = record(cb0, &ge);
-    if (st != JT_OK) {
-      drop_graph(ge);
-      return st;
+    std::vector<int> cands;
+    if (n == 1) {
+      cands = {1};
+    } else if (forced == kCaseLanes) {
+      cands = {kCaseLanes, kCaseBlock};  // the first one the tree supports
+    } else if (forced) {
+      cands = {forced};
+    } else {
+      if (t->compute == JT_F32 && n >= 16) cands.push_back(kCaseLanes);
+      cands.push_back(kCaseBlock);
+      if (n > 4) cands.push_back(4);
+      cands.push_back(1);
     }
-    if (n > 1 && !forced) {
-      const std::string keep = g_err;   // a failed alternative leaves the chosen graph usable
-      time_graph(ge, s);
-      float best = time_graph(ge, s);
-      for (int cb : {4, 1}) {
-        if (cb >= n && cb != 1) continue;   // a block wider than the cases: no gain over one case
-        GraphEntry alt;
-        if (record(cb, &alt) == JT_OK) {
-          time_graph(alt, s);
-          const float ta = time_graph(alt, s);
-          if (ta >= 0.f && (best < 0.f || ta < best)) {
-            std::swap(ge, alt);
-            best = ta;
-          }
+    const bool timed = n > 1 && !forced;
+    GraphEntry best;
+    bool have = false;
+    float best_ms = -1.f;
+    jt_status first_err = JT_OK;
+    std::string first_msg;
+    for (int cb : cands) {
+      GraphEntry ge;
+      const jt_status st = record(cb, &ge);
+      if (st != JT_OK) {
+        drop_graph(ge);
+        if (first_err == JT_OK) {
+          first_err = st;
+          first_msg = g_err;
         }
-        drop_graph(alt);
+        continue;
       }
-      g_err = keep;
+      if (!timed) {
+        std::swap(best, ge);
+        have = true;
+        break;
+      }
+      time_graph(ge, s);
+      const float ms = time_graph(ge, s);
+      if (!have || (ms >= 0.f && (best_ms < 0.f || ms < best_ms))) {
+        std::swap(best, ge);
+        best_ms = ms;
+        have = true;
+      }
+      drop_graph(ge);
     }
-    it = t->graphs.emplace(key, std::move(ge)).first;
+    if (!have) return fail(first_err == JT_OK ? JT_ERR_CUDA : first_err, first_msg);
+    CU(cudaEventCreateWithFlags(&best.done, cudaEventDisableTiming), "event");
+    it = t->graphs.emplace(key, std::move(best)).first;
   }
   *out = &it->second;
   return JT_OK;
@@ -413,7 +455,10 @@ jt_status load_typed(jt_tree t, const jt_tree_desc* d, cudaStream_t s) {
   jt_status st;
   if ((st = alloc(t, (T**)&t->base, p.base_len, "clique tables")) != JT_OK) return st;
   CU(cudaMemcpyAsync(t->base, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s), "table upload");
-  if ((st = alloc(t, (T**)&t->d_msg, p.msg_stride * t->max_cases, "per-case messages")) != JT_OK) return st;
+  // (case-lane schedules keep whole slabs of kCaseLanes cases: the last slab of
+  // a range may reach past max_cases)
+  if ((st = alloc(t, (T**)&t->d_msg, p.msg_stride * (t->max_cases + kCaseLanes - 1), "per-case messages")) != JT_OK)
+    return st;
   if (t->flags & JT_MATERIALIZE_CLIQUES) {
     if ((st = alloc(t, (T**)&t->d_calib, p.base_len * t->max_cases, "calibrated tables")) != JT_OK) return st;
   }
@@ -635,6 +680,7 @@ cudaError_t run_permsg(jt_tree t, int cs, const std::vector<int4>& obs, const st
   f.marg_total = p.marg_total;
   f.marg_out = t->d_marg;
   f.logz_out = t->d_logz;
+  f.lanes = 1;
   chk(launch_finalize<T>(f, s));
   return err;
 }
@@ -862,6 +908,7 @@ jt_status jt_propagate(jt_tree t, int32_t first, int32_t n, void* stream) {
   GraphEntry* ge = nullptr;
   if ((st = get_graph(t, first, n, s, &ge)) != JT_OK) return st;
   CU(cudaGraphLaunch(ge->exec, s), "graph launch");
+  CU(cudaEventRecord(ge->done, s), "event");
   for (int i = first; i < first + n; ++i) t->ready[i] = 1;
   t->last_stream = s;
   return JT_OK;
@@ -1008,6 +1055,23 @@ jt_status jt_get_status(jt_tree t, int32_t first, int32_t n, int32_t* out) {
     else if (raw[i] & kStatusZero) out[i] = JT_ERR_ZERO_EVIDENCE;
     else out[i] = JT_OK;
   }
+  return JT_OK;
+}
+
+jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info* out) {
+  jt_status st = check_tree(t);
+  if (st != JT_OK) return st;
+  if ((st = check_range(t, first, n)) != JT_OK) return st;
+  if (!out || n < 1) return fail(JT_ERR_INVALID_ARG, "null output or empty range");
+  auto it = t->graphs.find(std::make_pair(first, n));
+  if (it == t->graphs.end()) return fail(JT_ERR_STATE, "case range not propagated yet");
+  const GraphEntry& ge = it->second;
+  *out = jt_schedule_info{};
+  out->case_block = ge.sched.cb;
+  out->n_items = (int32_t)ge.sched.items.size();
+  out->grid = ge.grid;
+  out->smem_bytes = ge.smem;
+  out->window_entries = ge.sched.win_max;
   return JT_OK;
 }
 

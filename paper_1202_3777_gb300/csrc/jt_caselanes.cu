@@ -1,0 +1,726 @@
+// Case-lane propagation kernel (FP32, power-of-two cliques).
+//
+// The same persistent schedule as k_propagate (Algorithm 4: collect,
+// Algorithm 2, then distribute, Algorithm 3, over work items that are blocks
+// of clique tables), with the evidence cases of an item laid across the lanes
+// of a warp: lane l of every consumer warp computes case l of the item's
+// block of kCaseLanes cases.  Per entry x of the streamed block and case l,
+//
+//   collect, clique c (Eq. 2):
+//       f_l(x) = phi_c(x) E_l(x) prod_g mu_g,l[key_g(x)]
+//       u_c,l[key_p(x)] += f_l(x)
+//   distribute, clique c (Eq. 3, then Eq. 2 towards every child):
+//       f_l(x) = phi_c(x) E_l(x) prod_g mu_g,l[key_g(x)] rho_c,l[key_p(x)]
+//       delta_g,l[key_g(x)] += f_l(x),   joint_c,l[key_priv(x)] += f_l(x)
+//
+// Every lane of a warp handles the same x at the same time, so the table
+// value phi_c(x) is one broadcast shared-memory load for the 32 cases, the
+// keys are common to them, and each lane gathers from and reduces into its
+// own column of case-minor windows (row = key, 32 cases of 4 bytes): loads
+// and reductions of a warp touch 32 consecutive words, conflict-free, and no
+// value crosses lanes.  Messages live in global memory in the same case-minor
+// order (a slab of 32 cases: [entry][case]), so a window moves with a single
+// bulk copy or bulk reduction.
+//
+// Per-case factors that are constant over a block (the child messages'
+// normalisation |S_g|/sigma_g, block-constant inputs, evidence on digits above
+// the block) are applied once per item to the reduced windows instead of per
+// entry.  Evidence E_l on a digit inside the block needs no per-entry work when
+// the digit's variable belongs to an input port of the stage: the message on
+// that port was computed under the same evidence and is already zero where
+// the state differs (a child's collect message, or the ratio of the own
+// separator, whose old table is then zero, with 0/0 := 0).  The remaining
+// in-block observed digits (private variables, and in the collect pass the
+// parent-separator variables no child shares) are masked per lane.
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "jt_device.cuh"
+
+namespace jt {
+namespace {
+
+constexpr int NT = 512;        // consumer threads
+constexpr int NW = NT / 32;    // consumer warps
+static_assert(NW * kClSlice == 2048, "a chunk of 2048 entries is the consumers' slices");
+static_assert(NW * kClTiles <= 64, "slot table");
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
+
+// Shared-memory carve-up of a case-lane CTA.  The common fields serve the
+// producer; per buffer: `obs` holds (V, M) per case, `bf` the block factor per
+// case, `win` the case-minor windows; `kiter` holds the per-item port tables.
+__device__ __forceinline__ Smem carve_cl(unsigned char* smem, const SmemLayoutCL& L, int ring_n, int win_max) {
+  Smem s{};
+  s.full = reinterpret_cast<uint64_t*>(smem + L.bar);
+  s.empty = s.full + ring_n;
+  s.ifull = s.empty + ring_n;
+  s.bfull = s.ifull + 2;
+  s.pfull = s.bfull + 2;
+  s.wfree = s.pfull + 2;
+  s.sfull = s.wfree + 2;
+  s.sempty = s.sfull + kSig;
+  s.info = reinterpret_cast<ItemInfo*>(smem + L.info);
+  s.sig = reinterpret_cast<int4*>(smem + L.sig);
+  s.blob0 = smem + L.blob;
+  s.blob_stride = (uint32_t)L.blob_bytes;
+  s.obs = reinterpret_cast<int4*>(smem + L.ev);
+  s.nobs = nullptr;
+  s.bf = reinterpret_cast<double*>(smem + L.bf);
+  s.pval = nullptr;
+  s.win = smem + L.win;
+  s.red = reinterpret_cast<double*>(smem + L.red);
+  s.misc = reinterpret_cast<int*>(smem + L.misc);
+  s.kiter = reinterpret_cast<int*>(smem + L.ports);
+  s.live = nullptr;
+  s.kt = nullptr;
+  s.ring = smem + L.ring;
+  s.obs_b = (uint32_t)(kCaseLanes * 16);
+  s.nobs_b = 0;
+  s.bf_b = (uint32_t)(kCaseLanes * 8);
+  s.pval_b = 0;
+  s.win_b = (uint32_t)(win_max * kClRow);
+  return s;
+}
+
+// ---- control warp 2: preparation of the next item (lane = case) ------------
+// Evidence (digits above the block into the case's block factor, uncovered
+// digits inside it into the case's mask), the output windows zeroed, the
+// dependency wait, the child-message windows by bulk copy (one per port: the
+// slab rows are already case-minor), the per-case factors, and the ratio
+// windows of the own separator, rho = delta (sigma_c / Delta_parent) / u with
+// 0/0 := 0 (Eq. 3 and its zero rule).
+__device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0) {
+  constexpr int U = 4;  // ratio rows per lane per round (their loads in flight together)
+  const int l = (int)(threadIdx.x & 31);
+  for (uint32_t slot = 0;; ++slot) {
+    const uint32_t b = slot & 1u, par = (slot >> 1) & 1u;
+    if (!__all_sync(kFull, mbar_wait(s0.ifull + b, par, a.err, s0.misc))) break;
+    ItemInfo& inf = s0.info[b];
+    const DevItem w = inf.w;
+    if (w.stage < 0) {
+      __syncwarp();
+      if (l == 0) mbar_arrive(s0.pfull + b);
+      break;
+    }
+    if (!__all_sync(kFull, mbar_wait(s0.bfull + b, par, a.err, s0.misc))) break;
+    const Smem s = with_buffer(s0, b);
+    const DevStage S = *s.stage;
+    const int cb0 = a.case0 + w.cbk * kCaseLanes;
+    const int ncb = min(kCaseLanes, a.case0 + a.n_cases - cb0);
+    const bool valid = l < ncb;
+    const int cs = cb0 + l;
+    const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
+    float* slab = a.msg + (int64_t)cb0 * a.msg_stride;
+    uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)inf.idx * kTraceSlots : nullptr;
+    if (tr != nullptr && l == 0) tr[11] = global_ns();
+    // evidence of this lane's case
+    double bf = valid ? 1.0 : 0.0;
+    uint32_t V = 0, M = 0;
+    if (valid) {
+      const int16_t* evr = a.ev + (int64_t)cs * a.n_vars;
+      for (int i = 0; i < S.k; ++i) {
+        const DevPos& P = s.pos[i];
+        const int st = evr[P.var];
+        if (st < 0) continue;
+        if (st >= P.card) {
+          atomicOr(&a.status[cs], kStatusBadState);
+          continue;
+        }
+        const int inside = max(0, min(P.cb, S.bits - P.sh));
+        const uint32_t lo_m = (1u << inside) - 1u;
+        const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
+        if (hi_d != ((uint32_t)st & ~lo_m)) {
+          bf = 0.0;
+        } else if (lo_m != 0u && !((S.covered >> i) & 1u)) {
+          M |= lo_m << P.sh;
+          V |= ((uint32_t)st & lo_m) << P.sh;
+        }
+      }
+    }
+    s.obs[l] = make_int4((int)V, (int)M, 0, 0);
+    // output windows start at zero (32 lanes x 16 bytes = four rows a store)
+    const uint32_t win32 = smem_u32(s.win);
+    {
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int pi = S.nin; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1) continue;
+        const uint32_t base = win32 + (uint32_t)P.win * kClRow, bytes = (uint32_t)P.K * kClRow;
+        for (uint32_t o = (uint32_t)l * 16u; o < bytes; o += 512u) sst_vec(base + o, z);
+      }
+    }
+    bool dok = true;
+    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, l, 32, kFull);
+    if (tr != nullptr && l == 0) tr[10] = global_ns();
+    if (dok) {
+      uint32_t bulk = 0;
+      for (int pi = 0; pi < S.nin; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K > 1 && P.kind == kPortMu) bulk += (uint32_t)P.K * kClRow;
+      }
+      if (l == 0) mbar_expect_tx_only(s.pfull + b, bulk);
+      __syncwarp();
+      if (bulk > 0) {
+        fence_proxy_async_all();  // the messages were written by other CTAs (bulk reductions)
+        int n = 0;
+        for (int pi = 0; pi < S.nin; ++pi) {
+          const DevPort& P = s.port[pi];
+          if (P.K <= 1 || P.kind != kPortMu) continue;
+          if (n++ % 32 != l) continue;
+          const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
+          bulk_g2s(s.win + (size_t)P.win * kClRow, slab + (int64_t)(P.tab + kb) * kCaseLanes,
+                   (uint32_t)P.K * kClRow, s.pfull + b);
+        }
+      }
+      // per-case factor: the child messages' scales and block-constant inputs
+      if (valid) {
+        const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
+        for (int pi = 0; pi < S.nin; ++pi) {
+          const DevPort& P = s.port[pi];
+          double v = 1.0;
+          if (P.kind == kPortMu) {
+            const double sg = __ldcg(sums + P.other);
+            v = sg > 0.0 ? (double)P.size / sg : 0.0;
+            if (P.K <= 1) {
+              const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
+              v *= (double)__ldcg(slab + (int64_t)(P.tab + key) * kCaseLanes + l);
+            }
+          } else if (P.K <= 1) {
+            const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
+            const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
+            const double u = (double)__ldcg(slab + (int64_t)(P.tab + key) * kCaseLanes + l);
+            const double d = (double)__ldcg(slab + (int64_t)(a.delta_off + P.tab + key) * kCaseLanes + l);
+            v = (dp > 0.0 && u > 0.0) ? d * (sgc / dp) / u : 0.0;
+          }
+          bf *= v;
+        }
+      }
+      // ratio windows of the own separator, row by row (lane = case)
+      for (int pi = 0; pi < S.nin; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1 || P.kind != kPortRho) continue;
+        const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
+        float sc = 0.f;
+        if (valid) {
+          const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
+          const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
+          sc = dp > 0.0 ? (float)(sgc / dp) : 0.f;
+        }
+        const float* ur = slab + (int64_t)(P.tab + kb) * kCaseLanes + l;
+        const float* dr = slab + (int64_t)(a.delta_off + P.tab + kb) * kCaseLanes + l;
+        const uint32_t dst = win32 + (uint32_t)P.win * kClRow + 4u * (uint32_t)l;
+        for (int i0 = 0; i0 < P.K; i0 += U) {
+          float u[U], d[U];
+#pragma unroll
+          for (int r = 0; r < U; ++r) {
+            const int ii = min(i0 + r, P.K - 1);
+            u[r] = __ldcg(ur + (int64_t)ii * kCaseLanes);
+            d[r] = __ldcg(dr + (int64_t)ii * kCaseLanes);
+          }
+#pragma unroll
+          for (int r = 0; r < U; ++r)
+            if (i0 + r < P.K) sst<float>(dst + (uint32_t)(i0 + r) * kClRow, u[r] > 0.f ? d[r] * sc / u[r] : 0.f);
+        }
+      }
+    }
+    s.bf[l] = bf;
+    if (l == 0) inf.ok = dok ? 1 : 0;
+    __syncwarp();
+    if (tr != nullptr && l == 0) tr[2] = global_ns();
+    if (l == 0) {
+      if (!dok) mbar_expect_tx_only(s.pfull + b, 0u);
+      mbar_arrive(s.pfull + b);  // completes once the bulk window bytes have landed
+    }
+    if (!dok) break;  // the consumers see ok = 0 and stop
+  }
+}
+
+// ---- control warp 1, lane 0: the signalling lane ---------------------------
+// For each finished item: add its output windows into the slab rows with one
+// bulk reduction per port, wait until they completed, make them visible
+// GPU-wide, count the block as done, and free the item's buffer.
+__device__ __forceinline__ void signaller_cl(const PropArgs<float>& a, const Smem& s0) {
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t sl = k % kSig;
+    if (!mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc)) break;
+    const int4 g = s0.sig[sl];   // stage, case block, buffer, item index
+    mbar_arrive(s0.sempty + sl);
+    if (g.x < 0) break;
+    fence_proxy_async();
+    const uint32_t b = (uint32_t)g.z;
+    const Smem s = with_buffer(s0, b);
+    const DevStage& S = *s.stage;
+    const DevItem& w = s0.info[b].w;
+    const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
+    float* slab = a.msg + (int64_t)(a.case0 + g.y * kCaseLanes) * a.msg_stride;
+    bool any = false;
+    for (int pi = S.nin; pi < S.np; ++pi) {
+      const DevPort& P = s.port[pi];
+      if (P.K <= 1) continue;
+      const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
+      bulk_reduce_add(slab + (int64_t)(P.tab + kb) * kCaseLanes, s.win + (size_t)P.win * kClRow,
+                      (uint32_t)P.K * kClRow);
+      any = true;
+    }
+    if (any) {
+      bulk_commit();
+      bulk_wait_all();
+      fence_proxy_async_all();
+    }
+    __threadfence();
+    atomicAdd(a.done + (int64_t)g.x * a.n_cb + g.y, 1);
+    if (a.trace != nullptr && g.w >= 0) a.trace[(int64_t)g.w * kTraceSlots + 9] = global_ns();
+    mbar_arrive(s0.wfree + b);
+  }
+}
+
+// ---- consumers -------------------------------------------------------------
+
+// The per-item key tables of the ports with windows (inputs first), computed
+// by all consumer threads: entry e of port li's table is one key.
+__device__ __forceinline__ void build_ports_cl(const Smem& s, const DevStage& S, int n_chunks, uint32_t win32,
+                                               int chunk, int& n_in, int& n_live) {
+  const int tid = threadIdx.x;
+  CLPort* cp = reinterpret_cast<CLPort*>(s.kiter);
+  constexpr int kFixed = 1 + 4 + 8 + NW * kClTiles;  // class, dvec, kvec, kslot
+  n_in = 0;
+  n_live = 0;
+  for (int pi = 0; pi < S.np; ++pi) {
+    const DevPort& P = s.port[pi];
+    if (P.K <= 1) continue;
+    const int li = n_live++;
+    if (pi < S.nin) ++n_in;
+    const DevField* f = s.fld + P.f0;
+    CLPort& C = cp[li];
+    for (int e = tid; e < kFixed + n_chunks; e += NT) {
+      if (e == 0) {
+        const bool edep = key_of<true>(1u, f, P.nf) != 0u || key_of<true>(2u, f, P.nf) != 0u;
+        const bool vdep = key_of<true>(4u, f, P.nf) != 0u || key_of<true>(8u, f, P.nf) != 0u ||
+                          key_of<true>(16u, f, P.nf) != 0u;
+        C.cls = (pi < S.nin ? kClInput : 0) | (edep ? kClEntry : (vdep ? kClVector : kClTile));
+      } else if (e < 5) {
+        C.dvec[e - 1] = (int32_t)(key_of<true>((uint32_t)(e - 1), f, P.nf) * (uint32_t)kClRow);
+      } else if (e < 13) {
+        C.kvec[e - 5] = (int32_t)(key_of<true>(4u * (uint32_t)(e - 5), f, P.nf) * (uint32_t)kClRow);
+      } else if (e < kFixed) {
+        const int sl = e - 13, ww = sl / kClTiles, t = sl - ww * kClTiles;
+        C.kslot[sl] = (int32_t)(key_of<true>((uint32_t)(ww * kClSlice + 32 * t), f, P.nf) * (uint32_t)kClRow);
+      } else {
+        const int ci = e - kFixed;
+        C.kchunk[ci] = (int32_t)(win32 + (uint32_t)P.win * kClRow +
+                                 key_of<true>((uint32_t)(ci * chunk), f, P.nf) * (uint32_t)kClRow);
+      }
+    }
+  }
+}
+
+// Stream one item: every warp takes its slice of each chunk in tiles of 32
+// entries; per tile a lane holds the 32 products of its case in registers
+// (as 16 pairs, multiplied and added two at a time).
+__device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& s, const DevItem& w, int ncb,
+                                          int cb0, int n_in, int n_live, float bfl, float& tot, RingPos& rp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t RS = (uint32_t)a.ring;
+  const int CH = a.chunk;
+  const uint32_t ring32 = smem_u32(s.ring);
+  const uint32_t cp32 = smem_u32(s.kiter);
+  const uint32_t lane4 = 4u * (uint32_t)lane;
+  const int nchunks = (w.n + CH - 1) / CH;
+  // this lane's evidence mask: tile-level bits (>= 5), per vector (2-4), per entry (0-1)
+  const int4 evm = s.obs[lane];
+  const uint32_t V = (uint32_t)evm.x, M = (uint32_t)evm.y;
+  const uint32_t VT = V & ~31u, MT = M & ~31u;
+  const bool ev_t = __any_sync(kFull, MT != 0u);
+  const bool ev_v = __any_sync(kFull, (M & 28u) != 0u);
+  const bool ev_e = __any_sync(kFull, (M & 3u) != 0u);
+  float mv[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) mv[v] = ((((uint32_t)(4 * v)) ^ V) & M & 28u) == 0u ? 1.f : 0.f;
+  const float2 mA01 = make_float2(((0u ^ V) & M & 3u) == 0u ? 1.f : 0.f, ((1u ^ V) & M & 3u) == 0u ? 1.f : 0.f);
+  const float2 mA23 = make_float2(((2u ^ V) & M & 3u) == 0u ? 1.f : 0.f, ((3u ^ V) & M & 3u) == 0u ? 1.f : 0.f);
+  float* calib = (a.calib != nullptr && lane < ncb) ? a.calib + (int64_t)(cb0 + lane) * a.calib_stride + w.off : nullptr;
+  bool ok = true;
+  for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
+    const uint32_t st = rp.st;
+    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc))) {
+      ok = false;
+      break;
+    }
+    const int nch = min(CH, w.n - ci * CH);
+    const uint32_t sb = ring32 + st * (uint32_t)CH * 4u;
+#pragma unroll 1
+    for (int t = 0; t < kClTiles; ++t) {
+      const int ot = warp * kClSlice + 32 * t;  // tile offset in the chunk
+      if (ot >= nch) break;                     // warp-uniform
+      const int slot = warp * kClTiles + t;
+      float2 f[16];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        float x[4];
+        sld_vec(sb + (uint32_t)(ot + 4 * v) * 4u, x);
+        f[2 * v] = make_float2(x[0], x[1]);
+        f[2 * v + 1] = make_float2(x[2], x[3]);
+      }
+      if (ev_t || ev_v || ev_e) {
+        const uint32_t oa = (uint32_t)(ci * CH + ot);
+        const float sc = ((oa ^ VT) & MT) == 0u ? 1.f : 0.f;
+        if (ev_e) {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const float2 m = dup(mv[v] * sc);
+            f[2 * v] = mul2(f[2 * v], mul2(mA01, m));
+            f[2 * v + 1] = mul2(f[2 * v + 1], mul2(mA23, m));
+          }
+        } else if (ev_v) {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const float2 m = dup(mv[v] * sc);
+            f[2 * v] = mul2(f[2 * v], m);
+            f[2 * v + 1] = mul2(f[2 * v + 1], m);
+          }
+        } else {
+          const float2 m = dup(sc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) f[i] = mul2(f[i], m);
+        }
+      }
+      // inputs: gather the lane's own case column and multiply
+#pragma unroll 1
+      for (int li = 0; li < n_in; ++li) {
+        const uint32_t pb = cp32 + (uint32_t)li * (uint32_t)sizeof(CLPort);
+        const int cls = sld_s32(pb + offsetof(CLPort, cls));
+        const uint32_t at = (uint32_t)sld_s32(pb + offsetof(CLPort, kchunk) + 4u * (uint32_t)ci) +
+                            (uint32_t)sld_s32(pb + offsetof(CLPort, kslot) + 4u * (uint32_t)slot) + lane4;
+        if (cls & kClEntry) {
+          const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
+          const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
+          const int4 dv = sld_v4s32(pb + offsetof(CLPort, dvec));
+          const int kv[8] = {kv0.x, kv0.y, kv0.z, kv0.w, kv1.x, kv1.y, kv1.z, kv1.w};
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const uint32_t av = at + (uint32_t)kv[v];
+            const float2 g01 = make_float2(sld<float>(av + (uint32_t)dv.x), sld<float>(av + (uint32_t)dv.y));
+            const float2 g23 = make_float2(sld<float>(av + (uint32_t)dv.z), sld<float>(av + (uint32_t)dv.w));
+            f[2 * v] = mul2(f[2 * v], g01);
+            f[2 * v + 1] = mul2(f[2 * v + 1], g23);
+          }
+        } else if (cls & kClVector) {
+          const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
+          const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
+          const int kv[8] = {kv0.x, kv0.y, kv0.z, kv0.w, kv1.x, kv1.y, kv1.z, kv1.w};
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const float2 g = dup(sld<float>(at + (uint32_t)kv[v]));
+            f[2 * v] = mul2(f[2 * v], g);
+            f[2 * v + 1] = mul2(f[2 * v + 1], g);
+          }
+        } else {
+          const float2 g = dup(sld<float>(at));
+#pragma unroll
+          for (int i = 0; i < 16; ++i) f[i] = mul2(f[i], g);
+        }
+      }
+      // per-vector and tile sums (the stage total and the coarser outputs)
+      float vs[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const float2 p = add2(f[2 * v], f[2 * v + 1]);
+        vs[v] = p.x + p.y;
+      }
+      const float ts = ((vs[0] + vs[1]) + (vs[2] + vs[3])) + ((vs[4] + vs[5]) + (vs[6] + vs[7]));
+      tot += ts;
+      // outputs: reduce into the lane's own case column
+#pragma unroll 1
+      for (int li = n_in; li < n_live; ++li) {
+        const uint32_t pb = cp32 + (uint32_t)li * (uint32_t)sizeof(CLPort);
+        const int cls = sld_s32(pb + offsetof(CLPort, cls));
+        const uint32_t at = (uint32_t)sld_s32(pb + offsetof(CLPort, kchunk) + 4u * (uint32_t)ci) +
+                            (uint32_t)sld_s32(pb + offsetof(CLPort, kslot) + 4u * (uint32_t)slot) + lane4;
+        if (cls & kClEntry) {
+          const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
+          const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
+          const int4 dv = sld_v4s32(pb + offsetof(CLPort, dvec));
+          const int kv[8] = {kv0.x, kv0.y, kv0.z, kv0.w, kv1.x, kv1.y, kv1.z, kv1.w};
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const uint32_t av = at + (uint32_t)kv[v];
+            sred_add(av + (uint32_t)dv.x, f[2 * v].x);
+            sred_add(av + (uint32_t)dv.y, f[2 * v].y);
+            sred_add(av + (uint32_t)dv.z, f[2 * v + 1].x);
+            sred_add(av + (uint32_t)dv.w, f[2 * v + 1].y);
+          }
+        } else if (cls & kClVector) {
+          const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
+          const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
+          const int kv[8] = {kv0.x, kv0.y, kv0.z, kv0.w, kv1.x, kv1.y, kv1.z, kv1.w};
+#pragma unroll
+          for (int v = 0; v < 8; ++v) sred_add(at + (uint32_t)kv[v], vs[v]);
+        } else {
+          sred_add(at, ts);
+        }
+      }
+      // calibrated table (JT_MATERIALIZE_CLIQUES): the product with the
+      // case's block factor, in the permuted layout of the base table
+      if (calib != nullptr) {
+        const float2 m = dup(bfl);
+        float* dst = calib + ci * CH + ot;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const float2 p0 = mul2(f[2 * v], m), p1 = mul2(f[2 * v + 1], m);
+          __stcs(reinterpret_cast<float4*>(dst + 4 * v), make_float4(p0.x, p0.y, p1.x, p1.y));
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(s.empty + st);
+  }
+  return __all_sync(kFull, ok);
+}
+
+// One work item (its buffer prepared by the control warp).  Every consumer
+// thread runs every barrier; the result is uniform over the consumers.
+__device__ __forceinline__ bool process_item_cl(const PropArgs<float>& a, const Smem& s, const DevItem& w, uint32_t b,
+                                                RingPos& rp, uint32_t& sigk) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const DevStage S = *s.stage;
+  const int cb0 = a.case0 + w.cbk * kCaseLanes;
+  const int ncb = min(kCaseLanes, a.case0 + a.n_cases - cb0);
+  const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
+  const uint32_t win32 = smem_u32(s.win);
+  const int idx_item = s.misc[2];
+  uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)idx_item * kTraceSlots : nullptr;
+  const int nchunks = (w.n + a.chunk - 1) / a.chunk;
+  int n_in = 0, n_live = 0;
+  build_ports_cl(s, S, nchunks, win32, a.chunk, n_in, n_live);
+  consumer_sync<NT>();
+  if (tr != nullptr && tid == 0) tr[3] = global_ns();
+  const double bfd = s.bf[lane];
+  const float bfl = (float)bfd;
+  float tot = 0.f;
+  const bool sok = stream_cl(a, s, w, ncb, cb0, n_in, n_live, bfl, tot, rp);
+  if (!consumer_all<NT>(sok)) {
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      s.misc[0] = 1;
+    }
+    return false;
+  }
+  if (tr != nullptr && tid == 0) tr[4] = global_ns();
+  s.red[lane * NW + warp] = (double)tot;
+  // the windows hold sums without the per-case block factor: apply it (a
+  // zero factor gives exact zeros whatever the lane gathered)
+  for (int pi = S.nin; pi < S.np; ++pi) {
+    const DevPort& P = s.port[pi];
+    if (P.K <= 1) continue;
+    const uint32_t base = win32 + (uint32_t)P.win * kClRow;
+    const int n = P.K * kCaseLanes;
+    for (int i = tid; i < n; i += NT) {
+      const float m = (float)s.bf[i & (kCaseLanes - 1)];
+      const uint32_t ad = base + 4u * (uint32_t)i;
+      sst<float>(ad, m != 0.f ? sld<float>(ad) * m : 0.f);
+    }
+  }
+  consumer_sync<NT>();
+  // per case: the block total into the stage total and the block-constant outputs
+  bool wrote_global = false;
+  if (tid < ncb) {
+    double t = 0.0;
+    for (int i = 0; i < NW; ++i) t += s.red[tid * NW + i];
+    t *= s.bf[tid];
+    if (t != 0.0) {
+      wrote_global = true;
+      const int cs = cb0 + tid;
+      float* slab = a.msg + (int64_t)cb0 * a.msg_stride;
+      for (int pi = S.nin; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K > 1) continue;
+        const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
+        atomicAdd(slab + (int64_t)(P.tab + key) * kCaseLanes + tid, (float)t);
+      }
+      atomicAdd(a.sums + (int64_t)cs * 2 * a.n_cliques + S.sum_slot, t);
+    }
+  }
+  // global additions visible GPU-wide before the item counts as done (the
+  // signalling lane's fence orders only what it wrote), and the window
+  // writes ordered before the bulk unit reads them
+  if (wrote_global) __threadfence();
+  fence_proxy_async();
+  consumer_sync<NT>();
+  if (tid == 0) {
+    if (tr != nullptr) tr[5] = global_ns();
+    if (!hand_over(s, sigk, make_int4(w.stage, w.cbk, (int)b, idx_item), a.err)) {
+      atomicExch(a.err, 1);
+      s.misc[0] = 1;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void consumer_cl(const PropArgs<float>& a, const Smem& s0) {
+  RingPos rp;
+  uint32_t sigk = 0;
+  for (uint32_t slot = 0;; ++slot) {
+    const uint32_t b = slot & 1u;
+    const bool ok = consumer_all<NT>(mbar_wait(s0.pfull + b, (slot >> 1) & 1u, a.err, s0.misc));
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        s0.misc[0] = 1;
+      }
+      break;
+    }
+    const ItemInfo& inf = s0.info[b];
+    const DevItem w = inf.w;
+    if (w.stage < 0) {
+      if (threadIdx.x == 0) hand_over(s0, sigk, make_int4(-1, 0, 0, -1), a.err);
+      break;
+    }
+    if (!inf.ok) {
+      if (threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        s0.misc[0] = 1;
+      }
+      break;
+    }
+    if (threadIdx.x == 0) {
+      s0.misc[2] = inf.idx;
+      if (a.trace != nullptr) {
+        uint32_t smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        a.trace[(int64_t)inf.idx * kTraceSlots] = smid;
+        a.trace[(int64_t)inf.idx * kTraceSlots + 1] = global_ns();
+      }
+    }
+    consumer_sync<NT>();
+    if (!process_item_cl(a, with_buffer(s0, b), w, b, rp, sigk)) break;
+  }
+}
+
+__global__ void __launch_bounds__(NT + kControlThreads, 1) k_propagate_cl(const PropArgs<float> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SmemLayoutCL L(a.ring, a.chunk, a.blob_max, a.win_max);
+  const Smem s = carve_cl(smem, L, a.ring, a.win_max);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.ring; ++i) {
+      mbar_init(s.full + i, 1);
+      mbar_init(s.empty + i, NW);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(s.ifull + i, 1);
+      mbar_init(s.bfull + i, 1);
+      mbar_init(s.pfull + i, 1);
+      mbar_init(s.wfree + i, 1);
+    }
+    for (int i = 0; i < kSig; ++i) {
+      mbar_init(s.sfull + i, 1);
+      mbar_init(s.sempty + i, 1);
+    }
+    s.misc[0] = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x >= NT) {
+    const int cw = (threadIdx.x - NT) >> 5, l = threadIdx.x & 31;
+    if (cw == 0) {
+      if (l == 0) producer<float>(a, s);
+    } else if (cw == 1) {
+      if (l == 0) signaller_cl(a, s);
+    } else {
+      prep_cl(a, s);
+    }
+    __syncwarp();
+  } else {
+    consumer_cl(a, s);
+  }
+  __syncthreads();
+}
+
+// Normalised marginals and log Z(e) of the cases of a slab: a warp per
+// variable, lane = case (coalesced reads of the case-minor rows).
+__global__ void __launch_bounds__(256) k_finalize_cl(const FinalArgs<float> a) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cb0 = a.case0 + (int)blockIdx.y * kCaseLanes;
+  const int ncb = min(kCaseLanes, a.case0 + a.n_cases - cb0);
+  const int cs = cb0 + lane;
+  const bool valid = lane < ncb;
+  const float* slab = a.msg + (int64_t)cb0 * a.msg_stride;
+  if (blockIdx.x == gridDim.x - 1) {
+    if (warp != 0 || !valid) return;
+    const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
+    double acc = 0.0;
+    bool zero = false;
+    for (int c = 1; c < a.n_cliques; ++c) {
+      const double sg = sums[c];
+      if (!(sg > 0.0)) zero = true;
+      else acc += log(sg) - log((double)a.sep_size[c]);
+    }
+    const double R = sums[a.n_cliques];
+    if (zero || !(R > 0.0)) {
+      atomicOr(&a.status[cs], kStatusZero);
+      a.logz_out[cs] = -INFINITY;
+    } else {
+      a.logz_out[cs] = acc + log(R);
+    }
+    return;
+  }
+  const int v = (int)blockIdx.x * 8 + warp;
+  if (v >= a.n_vars) return;
+  const VarSrc src = a.vs[v];
+  const float* tab = slab + (int64_t)src.off * kCaseLanes + lane;
+  double z = 0.0;
+  for (int j = 0; j < src.size; ++j) z += (double)tab[(int64_t)j * kCaseLanes];
+  const int per = src.size / src.card;
+  double* out = a.marg_out + (int64_t)cs * a.marg_total + src.moff;
+  for (int x = 0; x < src.card; ++x) {
+    double bsum = 0.0;
+    for (int qq = 0; qq < per; ++qq) {
+      const int hi = qq / src.st, lo = qq - hi * src.st;
+      bsum += (double)tab[((int64_t)(hi * src.card + x) * src.st + lo) * kCaseLanes];
+    }
+    if (valid) out[x] = z > 0.0 ? bsum / z : NAN;
+  }
+}
+
+// The dynamic shared-memory opt-in of the propagation kernel, once per device.
+std::mutex g_attr_mu;
+bool g_attr_done[64] = {};
+
+cudaError_t set_attrs_cl() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (!g_attr_done[dev]) {
+    e = cudaFuncSetAttribute(k_propagate_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_budget(dev, 1));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_propagate_cl, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    g_attr_done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  cudaError_t e = set_attrs_cl();
+  if (e != cudaSuccess) return e;
+  k_propagate_cl<<<grid, NT + kControlThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_cl(const FinalArgs<float>& a, cudaStream_t s) {
+  if (a.n_cases <= 0) return cudaSuccess;
+  dim3 grid((a.n_vars + 7) / 8 + 1, (a.n_cases + kCaseLanes - 1) / kCaseLanes);
+  k_finalize_cl<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace jt

@@ -120,6 +120,12 @@ struct DevStage {
   int32_t n_live, n_in_live;  // ports with windows, of which [0, n_in_live) are inputs
   int32_t n_iter;             // consumer iterations of one block
   int32_t live_off;
+  // positions (bit i = position i) whose variable is in some input port of
+  // the stage: evidence on such a variable inside a block already zeroes
+  // that input's window entries (the message it carries was computed with
+  // the evidence), so the case-lane schedule masks only the other positions
+  uint32_t covered;
+  int32_t pad2[3];
 };
 
 // A port with a window, as the fast path reads it.  An entry at block offset
@@ -217,6 +223,7 @@ struct FinalArgs {
   int32_t marg_total;
   double* marg_out;             // [max_cases][marg_total]
   double* logz_out;             // [max_cases]
+  int32_t lanes;                // cases interleaved in a message slab (1: one row per case)
 };
 
 // ---------------------------------------------------------------------------

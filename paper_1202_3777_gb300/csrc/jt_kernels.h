@@ -16,6 +16,13 @@ __host__ __device__ constexpr int ctas_per_sm_for(int cb) { return cb > 0 ? 1 : 
 // (processed together, so their latencies overlap), one vector for a block
 // of cases (eight cases already overlap; their windows need the room).
 __host__ __device__ constexpr int chunk_bytes_for(int cb) { return cb > 1 ? 8192 : 32768; }
+// Case-lane schedules: a work item carries kCaseLanes evidence cases, one per
+// lane of every consumer warp.  All lanes of a warp walk the same entries of
+// the streamed block, so the entry walk, the keys and the shared loads of the
+// table are common to the cases, and each lane reduces into its own case's
+// column of case-minor windows ([key][case]) and message slabs, with no
+// cross-lane reduction.
+constexpr int kCaseLanes = 32;
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
 constexpr int kControlThreads = 96;             // producer, signalling and preparation warps
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
@@ -70,6 +77,60 @@ struct SmemLayout {
   }
 };
 
+// Per-item key tables of one port of a case-lane item, in shared memory.  A
+// consumer warp w streams, from each chunk ci of the block, the slice
+// [w * kClSlice, (w + 1) * kClSlice) in tiles t of 32 entries, so an entry's
+// block offset is o = ci * chunk + w * kClSlice + 32 t + 4 v + j and (power-of-
+// two digits are bit fields) its key is the sum of the keys of those parts.
+// Every table holds byte offsets into the case-minor window (key * 128), the
+// chunk table also the window's start, so a lane's address is a sum of table
+// entries plus lane * 4.
+constexpr int kClSlice = 128;                   // entries of a warp's slice of one chunk
+constexpr int kClTiles = kClSlice / 32;         // tiles of 32 entries per slice
+constexpr int kClMaxChunks = 32;                // chunks of one block (blocks <= 2^16 entries)
+constexpr int kClRow = 32 * 4;                  // bytes of one window row (one key, every case)
+struct CLPort {
+  int32_t cls;                   // kClInput | kClTile, kClVector or kClEntry
+  int32_t pad[3];
+  int32_t dvec[4];               // key(j) * row, j < 4 (entries of a vector)
+  int32_t kvec[8];               // key(4 v) * row, v < 8 (vectors of a tile)
+  int32_t kslot[16 * kClTiles];  // key(w * kClSlice + 32 t) * row, slot w * kClTiles + t
+  int32_t kchunk[kClMaxChunks];  // window start + key(ci * chunk) * row (shared-space address)
+};
+constexpr int32_t kClInput = 1;
+constexpr int32_t kClTile = 0;      // key constant over a tile of 32 entries
+constexpr int32_t kClVector = 2;    // key constant over each vector of 4 entries
+constexpr int32_t kClEntry = 4;     // key changes within a vector
+static_assert(sizeof(CLPort) % 16 == 0, "case-lane port table");
+
+// Dynamic shared memory of a case-lane propagation CTA (host and device
+// carve it alike): barriers, item slots, descriptor blobs, then per buffer
+// the evidence masks (V, M per case), the block factor per case and the
+// case-minor windows, then the per-item port tables, the warps' partial
+// totals and the bulk-copy ring.
+struct SmemLayoutCL {
+  int32_t bar, info, sig, blob, blob_bytes, ev, bf, misc, ports, red, win, ring, bytes;
+
+  __host__ __device__ static int32_t a16(int32_t x) { return (x + 15) & ~15; }
+
+  __host__ __device__ SmemLayoutCL(int ring_n, int chunk, int blob_max, int win_max) {
+    int32_t o = 0;
+    bar = o;  o += (2 * ring_n + 8 + 2 * kSig) * 8;
+    info = a16(o);   o = info + 2 * 64;
+    sig = a16(o);    o = sig + kSig * 16;
+    blob_bytes = a16(blob_max);
+    blob = (o + 127) & ~127; o = blob + 2 * blob_bytes;
+    ev = a16(o);     o = ev + 2 * kCaseLanes * 16;             // per buffer, per case: V, M, -, -
+    bf = a16(o);     o = bf + 2 * kCaseLanes * 8;              // per buffer, per case: block factor
+    misc = a16(o);   o = misc + 16 * 4;
+    ports = a16(o);  o = ports + kMaxFastPorts * (int32_t)sizeof(CLPort);
+    red = a16(o);    o = red + kCaseLanes * 16 * 8;            // per case, per warp: partial totals
+    win = (o + 127) & ~127;  o = win + 2 * win_max * kClRow;
+    ring = (o + 127) & ~127; o = ring + ring_n * chunk * 4;
+    bytes = o;
+  }
+};
+
 // Enqueue one persistent propagation launch of `grid` CTAs (collect and
 // distribute of every clique for the case range of `a`).
 template <typename T>
@@ -78,6 +139,11 @@ cudaError_t launch_propagate(const PropArgs<T>& a, int cb, int grid, int smem, c
 // Enqueue the finalisation (log Z and normalised marginals) for a case range.
 template <typename T>
 cudaError_t launch_finalize(const FinalArgs<T>& a, cudaStream_t s);
+
+// Case-lane schedules (FP32): the persistent propagation over message slabs
+// of kCaseLanes interleaved cases, and its finalisation.
+cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, cudaStream_t s);
+cudaError_t launch_finalize_cl(const FinalArgs<float>& a, cudaStream_t s);
 
 // Normalised calibrated clique in the caller's listed order.
 struct CliqueOut {

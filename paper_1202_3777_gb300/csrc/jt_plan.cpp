@@ -431,9 +431,15 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
   // shared memory: what the windows may use once the ring and descriptors fit
   // (the blob bound: every descriptor at its maximum plus the key tables of
   // the most live ports and iterations a fast-path block can have)
+  const bool lanes = cb == kCaseLanes;   // case-lane schedule (FP32, power-of-two cliques only)
+  if (lanes && elem != 4) {
+    *err = "case-lane schedules are FP32 only";
+    return JT_ERR_UNSUPPORTED;
+  }
   const int blob_bound = desc_bytes(s->max_k, s->max_ports, s->max_fields) +
                          table_bytes(cb, std::min(s->max_ports, kMaxFastPorts));
-  const int fixed = SmemLayout(cb, s->ring, s->chunk, s->max_k, s->max_ports, blob_bound, 0, elem).bytes;
+  const int fixed = lanes ? SmemLayoutCL(s->ring, s->chunk, blob_bound, 0).bytes
+                          : SmemLayout(cb, s->ring, s->chunk, s->max_k, s->max_ports, blob_bound, 0, elem).bytes;
   const int64_t win_budget = (int64_t)(smem_bytes - fixed - 256) / (2ll * cb * elem);  // two buffers
   if (win_budget < (int64_t)s->max_ports * VEC) {
     *err = "the tree's descriptors do not fit in shared memory";
@@ -488,11 +494,18 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
           std::max<int64_t>(4096, level_n[pass][p.depth[c]] * s->n_cb / (2ll * ctas_per_sm_for(cb) * n_sm)));
       std::vector<int64_t> K;
       int64_t B = 1;
+      // a case-lane block holds at least one tile (32 entries) per warp slice
+      const int min_bits = lanes ? 5 : lv;
+      if (lanes && !(pow2 && S.n >= 32 && (int)sp.size() <= kMaxFastPorts)) {
+        *err = "case-lane schedules need power-of-two cliques of at least 32 entries and at most " +
+               std::to_string(kMaxFastPorts) + " ports";
+        return JT_ERR_UNSUPPORTED;
+      }
       if (pow2 && S.n >= VEC && (int)sp.size() <= kMaxFastPorts) {
         const int nbits = ilog2(S.n);
-        int bits = lv;
-        for (int b = nbits; b >= lv; --b) {
-          if ((1ll << b) > target && b > lv) continue;
+        int bits = min_bits;
+        for (int b = nbits; b >= min_bits; --b) {
+          if ((1ll << b) > target && b > min_bits) continue;
           if (windows(b, true, &K) <= win_budget) {
             bits = b;
             break;
@@ -572,6 +585,10 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         if (P.kind == kPortMu || P.kind == kPortRho) ++nin;
         s->ports.push_back(P);
       }
+      S.covered = 0;
+      for (int q = 0; q < nin; ++q)
+        for (int i = 0; i < k; ++i)
+          if (sp[q].in[i]) S.covered |= 1u << i;
       S.np = (int32_t)sp.size();
       S.nin = nin;
       S.nf = (int32_t)s->fields.size() - S.field0;
@@ -770,6 +787,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
 }
 
 int32_t prop_smem_bytes(const Schedule& s, int elem) {
+  if (s.cb == kCaseLanes) return SmemLayoutCL(s.ring, s.chunk, s.blob_max, s.win_max).bytes;
   return SmemLayout(s.cb, s.ring, s.chunk, s.max_k, s.max_ports, s.blob_max, s.win_max, elem).bytes;
 }
 

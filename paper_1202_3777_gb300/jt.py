@@ -68,6 +68,13 @@ class jt_tree_info(C.Structure):
     ]
 
 
+class jt_schedule_info(C.Structure):
+    _fields_ = [
+        ("case_block", C.c_int32), ("n_items", C.c_int32), ("grid", C.c_int32), ("smem_bytes", C.c_int32),
+        ("window_entries", C.c_int32), ("reserved", C.c_int32 * 3),
+    ]
+
+
 class jt_cpt_desc(C.Structure):
     _fields_ = [
         ("n_cpts", C.c_int32),
@@ -97,6 +104,7 @@ _sig = {
     "jt_init_from_cpts": (C.c_int, [_vp, C.POINTER(jt_cpt_desc), _vp, C.POINTER(C.c_float)]),
     "jt_get_potential": (C.c_int, [_vp, _i32, _vp]),
     "jt_get_info": (C.c_int, [_vp, C.POINTER(jt_tree_info)]),
+    "jt_get_schedule": (C.c_int, [_vp, _i32, _i32, C.POINTER(jt_schedule_info)]),
     "jt_free": (None, [_vp]),
     "jt_strerror": (C.c_char_p, [C.c_int]),
     "jt_last_error": (C.c_char_p, []),
@@ -320,6 +328,15 @@ def jt_get_potential(t: Tree, clique: int, size: int) -> np.ndarray:
     out = np.empty(size, dtype=np.float64)
     _check(_lib.jt_get_potential(t.handle, clique, _ptr(out)), "jt_get_potential")
     return out
+
+
+def jt_get_schedule(t: Tree, first_case: int, n_cases: int) -> dict:
+    """The schedule the case range's propagations use (after its first
+    jt_propagate): cases per work item, work items, grid, shared memory."""
+    info = jt_schedule_info()
+    _check(_lib.jt_get_schedule(t.handle, first_case, n_cases, C.byref(info)), "jt_get_schedule")
+    return {"case_block": info.case_block, "n_items": info.n_items, "grid": info.grid,
+            "smem_bytes": info.smem_bytes, "window_entries": info.window_entries}
 
 
 def jt_free(t: Tree):

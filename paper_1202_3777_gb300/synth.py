@@ -284,9 +284,12 @@ def binary_serving_tree(seed: int = 1005, n_cliques: int = 1024) -> Tree:
 
 
 def random_small_tree(seed: int, n_cliques: int = 5, max_states: float = 1 << 14,
-                      card_range=(2, 5), k_range=(2, 4), allow_empty_sep: bool = False) -> Tree:
+                      card_range=(2, 5), k_range=(2, 4), allow_empty_sep: bool = False,
+                      card_choices=None) -> Tree:
     """A random small tree (random cardinalities, separator sizes including
-    empty ones if allowed) whose joint has at most ``max_states`` states."""
+    empty ones if allowed) whose joint has at most ``max_states`` states.
+    ``card_choices`` (a sequence) draws each cardinality from it instead of
+    from ``card_range``."""
     for attempt in range(1000):
         rng = np.random.default_rng(seed * 7919 + attempt)
 
@@ -300,7 +303,8 @@ def random_small_tree(seed: int, n_cliques: int = 5, max_states: float = 1 << 14
         card, cl, par, fr = _build(rng, n_cliques,
                                    lambda: int(rng.integers(k_range[0], k_range[1] + 1)),
                                    shape,
-                                   lambda: int(rng.integers(card_range[0], card_range[1] + 1)),
+                                   (lambda: int(rng.integers(card_range[0], card_range[1] + 1)))
+                                   if card_choices is None else (lambda: int(rng.choice(card_choices))),
                                    _uniform_parent(rng))
         states = int(np.prod(card.astype(np.int64)))
         if states <= max_states:

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "jt_internal.h"
+#include "jt_kernels.h"
 
 using namespace jt;
 
@@ -74,6 +75,14 @@ std::string check(const Plan& p, const Schedule& s) {
       for (int i = 0; i < S.ndep; ++i)
         if (s.deps[S.dep0 + 2 * i] != want[i].first || s.deps[S.dep0 + 2 * i + 1] != want[i].second)
           return "dependency of stage " + std::to_string(pass * nc + c);
+    }
+  // case-lane schedules: every block holds whole tiles of 32 entries and at
+  // most kClMaxChunks chunks, on the power-of-two path
+  if (s.cb == kCaseLanes)
+    for (const DevStage& S : s.stages) {
+      if (S.n_blocks == 0) continue;
+      if (S.bits < 5 || S.B != (1 << S.bits)) return "case-lane block of stage " + std::to_string(&S - &s.stages[0]);
+      if ((S.B + s.chunk - 1) / s.chunk > kClMaxChunks) return "case-lane block longer than the chunk table";
     }
   // queue order: the blocks an item waits for are all claimed before it
   std::vector<int> done((size_t)nst * s.n_cb, 0);
@@ -132,7 +141,7 @@ int main(int argc, char** argv) {
     return 1;
   }
   const int smem = 232448 - 256;  // the opt-in shared memory of one CTA on this GPU, less the reserve
-  const int shapes[][2] = {{1, 1}, {4, 16}, {8, 16}, {8, 64}};
+  const int shapes[][2] = {{1, 1}, {4, 16}, {8, 16}, {8, 64}, {kCaseLanes, 64}, {kCaseLanes, 40}};
   int bad = 0;
   for (const auto& sh : shapes) {
     Schedule s;

@@ -24,11 +24,12 @@ def jt():
     return mod
 
 
-@pytest.fixture(params=["1", "4", "8"])
+@pytest.fixture(params=["1", "4", "8", "32"])
 def case_block(request, monkeypatch):
-    """Multi-case propagations pick one case per work item or blocks of 4 or
-    8 by timing them on first use; these tests pin each schedule in turn so
-    all stay covered."""
+    """Multi-case propagations pick one case per work item, blocks of 4 or 8,
+    or 32 cases on the lanes of a warp by timing them on first use; these
+    tests pin each schedule in turn so all stay covered (32 falls back to 8
+    on trees that case lanes do not apply to)."""
     monkeypatch.setenv("JT_CASE_BLOCK", request.param)
     return int(request.param)
 
