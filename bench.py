@@ -184,19 +184,50 @@ def msg_total(tree):
     return n
 
 
-def oracle_rate(tree, cases, budget_s=20.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the cases."""
+def oracle_rate(tree, cases, budget_s=20.0, gpu=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the cases; with
+    `gpu` = (log Z array, marginal rows) of the same cases from the GPU, also
+    the GPU's error against the oracle on that sample (rel_errors)."""
     from oracle import hugin
     w = tree.work_per_case()
     t0 = time.perf_counter()
     done = 0
+    refs = []
     for v, s in cases:
-        hugin.propagate_tree(tree, hugin.evidence_dict(v, s))
+        refs.append(hugin.propagate_tree(tree, hugin.evidence_dict(v, s)))
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return w * done / dt, done, dt
+    err = None
+    if gpu is not None:
+        err = rel_errors(tree, refs, gpu[0], gpu[1])
+    return w * done / dt, done, dt, err
+
+
+def rel_errors(tree, refs, lz_gpu, marg_rows, floor=1e-30):
+    """The parity metric on a sample: max relative error over normalised
+    marginal entries the oracle puts at or above `floor` (an entry the oracle
+    gives as exactly 0 must be 0; one below the floor counts its absolute
+    error in units of the floor), and the relative log Z error
+    |dlogZ| / max(1, |log Z|)."""
+    card = np.asarray(tree.card, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(card)])
+    worst, worst_lz = 0.0, 0.0
+    for i, ref in enumerate(refs):
+        row = np.asarray(marg_rows[i], dtype=np.float64)
+        for v in range(len(card)):
+            g = row[off[v]:off[v + 1]]
+            o = np.asarray(ref.marginals[v], dtype=np.float64)
+            big = o >= floor
+            if np.any(big):
+                worst = max(worst, float(np.max(np.abs(g[big] - o[big]) / o[big])))
+            small = ~big
+            if np.any(small):
+                worst = max(worst, float(np.max(np.abs(g[small] - o[small]))) / floor)
+        worst_lz = max(worst_lz, abs(float(lz_gpu[i]) - ref.log_z) / max(1.0, abs(ref.log_z)))
+    return {"cases": len(refs), "max_rel_err": worst, "logz_rel_err": worst_lz,
+            "tolerance": 1e-5, "oracle": "FP64 numpy oracle (oracle/hugin.py)"}
 
 
 def run_reference(args, rank, world):

@@ -57,6 +57,7 @@ struct GraphEntry {
   const uint4* blobs = nullptr;
   const DevItem* items = nullptr;
   int32_t grid = 0, smem = 0;
+  uint64_t wait_ns = 2000000000ull;  // limit of the kernel's bounded waits
   cudaEvent_t done = nullptr;   // recorded after every launch of the graph
 };
 
@@ -110,6 +111,9 @@ struct jt_tree_s {
   std::vector<uint8_t> ready;     // a propagation covered the case since its evidence changed
   cudaEvent_t upload_done = nullptr;
   cudaEvent_t readout_ready = nullptr;  // orders the allocation-free read-out after a propagation
+  cudaEvent_t readout_done = nullptr;   // recorded after an allocation-free read-out on its stream
+  bool readout_pending = false;         // a later call that rewrites the tables must wait for it
+  cudaEvent_t order_ev = nullptr;       // orders work on a new stream after the tree's last stream
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   std::map<std::pair<int, int>, GraphEntry> graphs;
@@ -152,6 +156,8 @@ void destroy(jt_tree t) {
   if (t->h_ev) cudaFreeHost(t->h_ev);
   if (t->upload_done) cudaEventDestroy(t->upload_done);
   if (t->readout_ready) cudaEventDestroy(t->readout_ready);
+  if (t->readout_done) cudaEventDestroy(t->readout_done);
+  if (t->order_ev) cudaEventDestroy(t->order_ev);
   if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
   delete t;
 }
@@ -190,6 +196,9 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
                       (size_t)n_cases * 2 * p.n_cliques * sizeof(double), s));
   chk(cudaMemsetAsync(t->d_status + case0, 0, (size_t)n_cases * sizeof(int32_t), s));
   chk(cudaMemsetAsync(t->d_done, 0, (1 + 2ull * p.n_cliques * sc.n_cb) * sizeof(int32_t), s));
+  // the error word reports this propagation (a timed-out one leaves nothing
+  // behind: every accumulator above starts again from zero)
+  chk(cudaMemsetAsync(t->d_err, 0, sizeof(int32_t), s));
   PropArgs<T> a{};
   a.base = (const T*)t->base;
   a.stages = ge.stages;
@@ -214,6 +223,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   a.queue = t->d_done;
   a.done = t->d_done + 1;
   a.err = t->d_err;
+  a.wait_ns = ge.wait_ns;
   a.calib = (T*)t->d_calib;
   a.calib_stride = p.base_len;
   a.trace = trace;
@@ -265,6 +275,18 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, cudaStream_
   const int smem_cap = smem_budget(t->device, ctas_per_sm_for(cb)) - 256;
   jt_status st = build_schedule(t->plan, (int)t->elem, cb, n_cases, t->n_sm, smem_cap, &ge->sched, &err);
   if (st != JT_OK) return fail(st, err);
+  // Failure-path hooks, read when a range's graph is recorded (host-side
+  // fault injection: nothing on the device faults or waits without limit).
+  // JT_WAIT_LIMIT_MS sets the limit of every bounded device wait (2000 by
+  // default); JT_FAULT_UNMET_DEPENDENCY=1 makes the first dependency of the
+  // schedule wait for one block more than its stage has, so the waiting item
+  // gives up at the limit and the propagation reports JT_ERR_TIMEOUT.
+  if (const char* w = std::getenv("JT_WAIT_LIMIT_MS"); w && *w) {
+    const long ms = std::strtol(w, nullptr, 10);
+    if (ms > 0 && ms <= 60000) ge->wait_ns = (uint64_t)ms * 1000000ull;
+  }
+  if (const char* f = std::getenv("JT_FAULT_UNMET_DEPENDENCY"); f && *f == '1' && ge->sched.deps.size() >= 2)
+    ge->sched.deps[1] += 1;
   const Schedule& sc = ge->sched;
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->stages, sc.stages, "schedule upload")) != JT_OK) return st;
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->ports, sc.ports, "schedule upload")) != JT_OK) return st;
@@ -425,6 +447,22 @@ jt_status wait_upload(jt_tree t) {
 
 jt_status sync_last(jt_tree t) {
   CU(cudaStreamSynchronize(t->last_stream), "synchronising the propagation stream");
+  return JT_OK;
+}
+
+// Order work about to be enqueued on `s` after the tree's earlier work: the
+// tree's last stream (work on two streams would otherwise run at the same
+// time over the same per-tree buffers), and an allocation-free read-out that
+// may still be reading a calibrated table on a stream of its own.
+jt_status order_on(jt_tree t, cudaStream_t s) {
+  if (s != t->last_stream) {
+    CU(cudaEventRecord(t->order_ev, t->last_stream), "stream ordering");
+    CU(cudaStreamWaitEvent(s, t->order_ev, 0), "stream ordering");
+  }
+  if (t->readout_pending) {
+    CU(cudaStreamWaitEvent(s, t->readout_done, 0), "read-out ordering");
+    t->readout_pending = false;
+  }
   return JT_OK;
 }
 
@@ -736,14 +774,16 @@ jt_status init_typed(jt_tree t, const std::vector<InitItem>& items, const std::v
   CU(tb.upload(&d_fac, fac, s), "initialisation upload");
   CU(tb.upload(&d_terms, terms, s), "initialisation upload");
   CU(tb.upload(&d_vals, vals, s), "initialisation upload");
+  // (events created here are destroyed on every path out)
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
   if (kernel_ms) {
-    CU(cudaEventCreate(&ev[0]), "event");
-    CU(cudaEventCreate(&ev[1]), "event");
-    CU(cudaEventRecord(ev[0], s), "event");
+    e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
   }
-  cudaError_t e = launch_init_cliques<T>((T*)t->base, d_items, (int32_t)items.size(), d_cl, d_fac, d_terms, d_vals,
-                                         t->n_sm, s);
+  if (e == cudaSuccess)
+    e = launch_init_cliques<T>((T*)t->base, d_items, (int32_t)items.size(), d_cl, d_fac, d_terms, d_vals, t->n_sm, s);
   if (e == cudaSuccess && kernel_ms) e = cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && kernel_ms) e = cudaEventElapsedTime(kernel_ms, ev[0], ev[1]);
@@ -838,6 +878,10 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   if ((e = cudaEventRecord(raw->upload_done, s)) != cudaSuccess) return bail(cuda_fail(e, "event"));
   if ((e = cudaEventCreateWithFlags(&raw->readout_ready, cudaEventDisableTiming)) != cudaSuccess)
     return bail(cuda_fail(e, "event"));
+  if ((e = cudaEventCreateWithFlags(&raw->readout_done, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(cuda_fail(e, "event"));
+  if ((e = cudaEventCreateWithFlags(&raw->order_ev, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(cuda_fail(e, "event"));
   if ((e = cudaStreamCreateWithFlags(&raw->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(e, "stream"));
   raw->last_stream = s;
@@ -877,6 +921,7 @@ jt_status jt_set_evidence_dense(jt_tree t, int32_t first, int32_t n, const int16
   const int nv = t->plan.n_vars;
   const size_t bytes = (size_t)n * nv * sizeof(int16_t);
   if (on_device) {
+    if ((st = order_on(t, (cudaStream_t)stream)) != JT_OK) return st;
     CU(cudaMemcpyAsync(t->d_ev + (int64_t)first * nv, states, bytes, cudaMemcpyDeviceToDevice,
                        (cudaStream_t)stream), "evidence copy");
     for (int i = 0; i < n; ++i) {
@@ -904,6 +949,7 @@ jt_status jt_propagate(jt_tree t, int32_t first, int32_t n, void* stream) {
   if ((st = check_range(t, first, n)) != JT_OK) return st;
   if (n == 0) return JT_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((st = order_on(t, s)) != JT_OK) return st;
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
   if ((st = get_graph(t, first, n, s, &ge)) != JT_OK) return st;
@@ -924,6 +970,7 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
   if (n == 0) return JT_OK;
   if (!launch_ms || max_launches < nl) return fail(JT_ERR_INVALID_ARG, "launch_ms needs 2 slots");
   cudaStream_t s = (cudaStream_t)stream;
+  if ((st = order_on(t, s)) != JT_OK) return st;
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
   if ((st = get_graph(t, first, n, s, &ge)) != JT_OK) return st;
@@ -1124,6 +1171,10 @@ jt_status jt_get_clique_noalloc(jt_tree t, int32_t case_id, int32_t clique, doub
                       ? launch_get_clique_noalloc<double>((const double*)t->d_calib + off, co, out_device, strm)
                       : launch_get_clique_noalloc<float>((const float*)t->d_calib + off, co, out_device, strm);
   if (e != cudaSuccess) return cuda_fail(e, "allocation-free clique read-out");
+  // a later propagation, per-message propagation or initialisation of this
+  // tree waits for the read-out before it rewrites the table
+  CU(cudaEventRecord(t->readout_done, strm), "read-out ordering");
+  t->readout_pending = true;
   return JT_OK;
 }
 
@@ -1225,8 +1276,13 @@ jt_status jt_init_from_cpts(jt_tree t, const jt_cpt_desc* cp, void* stream, floa
     for (int64_t e0 = 0; e0 < p.n_entries[c]; e0 += kInitChunk) items.push_back(InitItem{c, (int32_t)e0});
   }
   cudaStream_t s = (cudaStream_t)stream;
-  // the tables may still be read by earlier work on the tree's last stream
+  // the tables may still be read by earlier work on the tree's last stream,
+  // or by an allocation-free read-out on a stream of its own
   CU(cudaStreamSynchronize(t->last_stream), "synchronising the tree's last stream");
+  if (t->readout_pending) {
+    CU(cudaEventSynchronize(t->readout_done), "waiting for a read-out");
+    t->readout_pending = false;
+  }
   st = t->compute == JT_F64 ? init_typed<double>(t, items, cl, fac, terms, cvals, s, kernel_ms)
                             : init_typed<float>(t, items, cl, fac, terms, cvals, s, kernel_ms);
   if (st != JT_OK) return st;
@@ -1287,6 +1343,7 @@ jt_status jt_propagate_per_message(jt_tree t, int32_t case_id, int32_t layout, v
     return fail(JT_ERR_STATE, "the per-message propagation works in the calibrated tables: load with "
                               "JT_MATERIALIZE_CLIQUES");
   cudaStream_t s = (cudaStream_t)stream;
+  if ((st = order_on(t, s)) != JT_OK) return st;
   if ((st = upload_dirty(t, case_id, 1, s)) != JT_OK) return st;
   if (!t->permsg || t->permsg->layout != layout) {
     CU(cudaStreamSynchronize(s), "per-message setup");

@@ -98,7 +98,7 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
   const int l = (int)(threadIdx.x & 31);
   for (uint32_t slot = 0;; ++slot) {
     const uint32_t b = slot & 1u, par = (slot >> 1) & 1u;
-    if (!__all_sync(kFull, mbar_wait(s0.ifull + b, par, a.err, s0.misc))) break;
+    if (!__all_sync(kFull, mbar_wait(s0.ifull + b, par, a.err, s0.misc, a.wait_ns))) break;
     ItemInfo& inf = s0.info[b];
     const DevItem w = inf.w;
     if (w.stage < 0) {
@@ -106,7 +106,7 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
       if (l == 0) mbar_arrive(s0.pfull + b);
       break;
     }
-    if (!__all_sync(kFull, mbar_wait(s0.bfull + b, par, a.err, s0.misc))) break;
+    if (!__all_sync(kFull, mbar_wait(s0.bfull + b, par, a.err, s0.misc, a.wait_ns))) break;
     const Smem s = with_buffer(s0, b);
     const DevStage S = *s.stage;
     const int cb0 = a.case0 + w.cbk * kCaseLanes;
@@ -154,7 +154,7 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
       }
     }
     bool dok = true;
-    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, l, 32, kFull);
+    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, l, 32, kFull, a.wait_ns);
     if (tr != nullptr && l == 0) tr[10] = global_ns();
     if (dok) {
       uint32_t bulk = 0;
@@ -246,7 +246,7 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
 __device__ __forceinline__ void signaller_cl(const PropArgs<float>& a, const Smem& s0) {
   for (uint32_t k = 0;; ++k) {
     const uint32_t sl = k % kSig;
-    if (!mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc)) break;
+    if (!mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc, a.wait_ns)) break;
     const int4 g = s0.sig[sl];   // stage, case block, buffer, item index
     mbar_arrive(s0.sempty + sl);
     if (g.x < 0) break;
@@ -346,7 +346,7 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
   bool ok = true;
   for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
     const uint32_t st = rp.st;
-    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc))) {
+    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc, a.wait_ns))) {
       ok = false;
       break;
     }
@@ -565,7 +565,7 @@ __device__ __forceinline__ void consumer_cl(const PropArgs<float>& a, const Smem
   uint32_t sigk = 0;
   for (uint32_t slot = 0;; ++slot) {
     const uint32_t b = slot & 1u;
-    const bool ok = consumer_all<NT>(mbar_wait(s0.pfull + b, (slot >> 1) & 1u, a.err, s0.misc));
+    const bool ok = consumer_all<NT>(mbar_wait(s0.pfull + b, (slot >> 1) & 1u, a.err, s0.misc, a.wait_ns));
     if (!ok) {
       if (threadIdx.x == 0) {
         atomicExch(a.err, 1);
@@ -639,16 +639,23 @@ __global__ void __launch_bounds__(NT + kControlThreads, 1) k_propagate_cl(const 
   __syncthreads();
 }
 
-// Normalised marginals and log Z(e) of the cases of a slab: a warp per
-// variable, lane = case (coalesced reads of the case-minor rows).
+// Normalised marginals and log Z(e) of the cases of a slab (blockIdx.y),
+// lane = case (coalesced reads of the case-minor rows).  A CTA per variable
+// (blockIdx.x; the last one computes log Z): for each state x its eight
+// warps sum the source-table entries holding x (strided over the warps), the
+// partial sums meet in shared memory, and warp 0 writes the bin; the bins are
+// then normalised by their total.  Entries of a power-of-two table are split
+// into (hi, lo) around the variable's digit by shifts.
 __global__ void __launch_bounds__(256) k_finalize_cl(const FinalArgs<float> a) {
+  __shared__ double red[8][32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cb0 = a.case0 + (int)blockIdx.y * kCaseLanes;
   const int ncb = min(kCaseLanes, a.case0 + a.n_cases - cb0);
   const int cs = cb0 + lane;
   const bool valid = lane < ncb;
   const float* slab = a.msg + (int64_t)cb0 * a.msg_stride;
-  if (blockIdx.x == gridDim.x - 1) {
+  const int v = (int)blockIdx.x;
+  if (v == a.n_vars) {
     if (warp != 0 || !valid) return;
     const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
     double acc = 0.0;
@@ -667,22 +674,38 @@ __global__ void __launch_bounds__(256) k_finalize_cl(const FinalArgs<float> a) {
     }
     return;
   }
-  const int v = (int)blockIdx.x * 8 + warp;
-  if (v >= a.n_vars) return;
   const VarSrc src = a.vs[v];
   const float* tab = slab + (int64_t)src.off * kCaseLanes + lane;
-  double z = 0.0;
-  for (int j = 0; j < src.size; ++j) z += (double)tab[(int64_t)j * kCaseLanes];
   const int per = src.size / src.card;
+  const bool p2 = (src.st & (src.st - 1)) == 0;
+  const int sh = __ffs(src.st) - 1;
   double* out = a.marg_out + (int64_t)cs * a.marg_total + src.moff;
+  double z = 0.0;
   for (int x = 0; x < src.card; ++x) {
-    double bsum = 0.0;
-    for (int qq = 0; qq < per; ++qq) {
-      const int hi = qq / src.st, lo = qq - hi * src.st;
-      bsum += (double)tab[((int64_t)(hi * src.card + x) * src.st + lo) * kCaseLanes];
+    double s0 = 0.0, s1 = 0.0;
+    int q = warp;
+#pragma unroll 2
+    for (; q + 8 < per; q += 16) {
+      const int h0 = p2 ? q >> sh : q / src.st, h1 = p2 ? (q + 8) >> sh : (q + 8) / src.st;
+      s0 += (double)__ldcg(tab + ((int64_t)(h0 * src.card + x) * src.st + (q - h0 * src.st)) * kCaseLanes);
+      s1 += (double)__ldcg(tab + ((int64_t)(h1 * src.card + x) * src.st + (q + 8 - h1 * src.st)) * kCaseLanes);
     }
-    if (valid) out[x] = z > 0.0 ? bsum / z : NAN;
+    if (q < per) {
+      const int h0 = p2 ? q >> sh : q / src.st;
+      s0 += (double)__ldcg(tab + ((int64_t)(h0 * src.card + x) * src.st + (q - h0 * src.st)) * kCaseLanes);
+    }
+    red[warp][lane] = s0 + s1;
+    __syncthreads();
+    if (warp == 0) {
+      double b = 0.0;
+      for (int w = 0; w < 8; ++w) b += red[w][lane];
+      z += b;
+      if (valid) out[x] = b;
+    }
+    __syncthreads();
   }
+  if (warp == 0 && valid)
+    for (int x = 0; x < src.card; ++x) out[x] = z > 0.0 ? out[x] / z : NAN;
 }
 
 // The dynamic shared-memory opt-in of the propagation kernel, once per device.
@@ -718,7 +741,7 @@ cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, cu
 
 cudaError_t launch_finalize_cl(const FinalArgs<float>& a, cudaStream_t s) {
   if (a.n_cases <= 0) return cudaSuccess;
-  dim3 grid((a.n_vars + 7) / 8 + 1, (a.n_cases + kCaseLanes - 1) / kCaseLanes);
+  dim3 grid(a.n_vars + 1, (a.n_cases + kCaseLanes - 1) / kCaseLanes);
   k_finalize_cl<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

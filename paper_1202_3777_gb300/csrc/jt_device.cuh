@@ -180,13 +180,13 @@ __device__ __forceinline__ bool consumer_all(bool v) {
 // Wait for phase `parity` of `bar`.  False once the wait limit passed, or
 // (when given) once the error word or the CTA's abort flag is set.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int32_t* err,
-                                          const volatile int* abort) {
+                                          const volatile int* abort, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
     if ((++spins & 63u) == 0) {
-      if (global_ns() - t0 > kWaitLimitNs) return false;
+      if (global_ns() - t0 > limit_ns) return false;
       if (abort != nullptr && *abort) return false;
       if (err != nullptr && ld_relaxed(err) != 0) return false;
     }
@@ -377,7 +377,7 @@ __device__ __forceinline__ void producer(const PropArgs<T>& a, const Smem& s) {
   bool ok = true;
   for (uint32_t slot = 0;; ++slot) {
     const uint32_t b = slot & 1u;
-    if (slot >= 2 && !mbar_wait(s.wfree + b, ((slot >> 1) - 1) & 1u, a.err, abort)) {
+    if (slot >= 2 && !mbar_wait(s.wfree + b, ((slot >> 1) - 1) & 1u, a.err, abort, a.wait_ns)) {
       ok = false;
       break;
     }
@@ -402,7 +402,7 @@ __device__ __forceinline__ void producer(const PropArgs<T>& a, const Smem& s) {
     for (int64_t e = a0; e < a1; e += CH, ++q, rp.advance(S)) {
       const uint32_t st = rp.st;
       // the stage's previous round must have been released by every consumer warp
-      if (q >= S && !mbar_wait(s.empty + st, rp.ph ^ 1u, a.err, abort)) {
+      if (q >= S && !mbar_wait(s.empty + st, rp.ph ^ 1u, a.err, abort, a.wait_ns)) {
         ok = false;
         break;
       }
@@ -428,7 +428,7 @@ __device__ __forceinline__ void producer(const PropArgs<T>& a, const Smem& s) {
 // error was reported.
 __device__ __forceinline__ bool await_deps(const int32_t* deps, int ndep, const int32_t* done, int n_cb, int cbk,
                                            const int32_t* err, const volatile int* abort, int lane, int lanes,
-                                           unsigned mask) {
+                                           unsigned mask, uint64_t limit_ns = kWaitLimitNs) {
   bool ok = true;
   for (int d = lane; d < ndep; d += lanes) {
     const int32_t stg = deps[2 * d], need = deps[2 * d + 1];
@@ -436,7 +436,7 @@ __device__ __forceinline__ bool await_deps(const int32_t* deps, int ndep, const 
     if (ld_acquire(ctr) >= need) continue;
     const uint64_t t0 = global_ns();
     while (ld_acquire(ctr) < need) {
-      if (*abort || ld_relaxed(err) != 0 || global_ns() - t0 > kWaitLimitNs) {
+      if (*abort || ld_relaxed(err) != 0 || global_ns() - t0 > limit_ns) {
         ok = false;
         break;
       }

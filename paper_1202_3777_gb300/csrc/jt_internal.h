@@ -200,6 +200,7 @@ struct PropArgs {
   int32_t* done;                // [n_stages][n_cb] finished blocks
   int32_t* queue;               // next work item
   int32_t* err;                 // set when a bounded wait gives up
+  uint64_t wait_ns;             // limit of every bounded device-side wait (ns)
   T* calib;                     // [max_cases][calib_stride] calibrated tables, or null
   int64_t calib_stride;
   uint64_t* trace;              // [n_items][kTraceSlots] item timeline, or null

@@ -165,7 +165,7 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
   const int pl = (int)(threadIdx.x & 31);
   for (uint32_t slot = 0;; ++slot) {
     const uint32_t b = slot & 1u, par = (slot >> 1) & 1u;
-    bool ok = mbar_wait(s0.ifull + b, par, a.err, s0.misc);
+    bool ok = mbar_wait(s0.ifull + b, par, a.err, s0.misc, a.wait_ns);
     ok = __all_sync(kMask, ok);
     if (!ok) break;
     ItemInfo& inf = s0.info[b];
@@ -175,7 +175,7 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
       if (pl == 0) mbar_arrive(s0.pfull + b);
       break;
     }
-    ok = __all_sync(kMask, mbar_wait(s0.bfull + b, par, a.err, s0.misc));
+    ok = __all_sync(kMask, mbar_wait(s0.bfull + b, par, a.err, s0.misc, a.wait_ns));
     if (!ok) break;
     const Smem s = with_buffer(s0, b);
     const DevStage S = *s.stage;
@@ -252,7 +252,7 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
     }
     // dependencies
     bool dok = true;
-    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, pl, NL, kMask);
+    if (S.ndep > 0) dok = await_deps(a.deps + S.dep0, S.ndep, a.done, a.n_cb, w.cbk, a.err, s.misc, pl, NL, kMask, a.wait_ns);
     if (tr != nullptr && pl == 0) tr[10] = global_ns();
     // the child-message windows first (bulk copies; the consumers wait for their bytes)
     uint32_t bulk_bytes = 0;
@@ -392,7 +392,7 @@ template <typename T, int CB>
 __device__ __forceinline__ void signaller(const PropArgs<T>& a, const Smem& s0) {
   for (uint32_t k = 0;; ++k) {
     const uint32_t sl = k % kSig;
-    if (!mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc)) break;
+    if (!mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc, a.wait_ns)) break;
     const int4 g = s0.sig[sl];   // stage, case block, buffer, item index
     mbar_arrive(s0.sempty + sl);
     if (g.x < 0) break;
@@ -520,7 +520,7 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     const uint32_t st = rp.st;
     const uint64_t tw = (a.trace != nullptr && lane == 0) ? global_ns() : 0;
     // the warp leaves together (its lanes reduce with shuffles below)
-    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc))) {
+    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc, a.wait_ns))) {
       ok = false;
       break;
     }
@@ -765,7 +765,7 @@ __device__ __forceinline__ bool stream_generic(const PropArgs<T>& a, const Smem&
   for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
     const uint32_t st = rp.st;
     // the warp leaves together (its lanes reduce with shuffles below)
-    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc))) {
+    if (!__all_sync(kFull, mbar_wait(s.full + st, rp.ph, a.err, s.misc, a.wait_ns))) {
       ok = false;
       break;
     }
@@ -969,7 +969,7 @@ __device__ __forceinline__ void consumer(const PropArgs<T>& a, const Smem& s0) {
   uint32_t sigk = 0;  // items handed to the signalling lane (thread 0)
   for (uint32_t slot = 0;; ++slot) {
     const uint32_t b = slot & 1u;
-    const bool ok = consumer_all<NT>(mbar_wait(s0.pfull + b, (slot >> 1) & 1u, a.err, s0.misc));
+    const bool ok = consumer_all<NT>(mbar_wait(s0.pfull + b, (slot >> 1) & 1u, a.err, s0.misc, a.wait_ns));
     if (!ok) {
       if (threadIdx.x == 0) {
         atomicExch(a.err, 1);
