@@ -116,38 +116,48 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# DRAM traffic of the propagation kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, summarised in
-# profiles/k_propagate_large_clique.md), valid only while the kernel and
-# planner sources are the ones it was taken on.  One-case launch: bytes per
-# launch.  Case-block launch: bytes per case block (16 cases = 2 case blocks
-# captured; every case block streams the tables again, so traffic grows with
-# their number).
+# DRAM traffic of the propagation kernel from an ncu capture of the
+# large-clique workload (dram__bytes_read.sum + dram__bytes_write.sum, in
+# profiles/), valid only while the kernel and planner sources are the ones it
+# was taken on.  Per kind of schedule: a one-case launch; a block of 8 cases;
+# a slab of 32 cases on the lanes.  Every case block or slab streams the
+# tables again, so a launch's traffic grows with their number.
 TRAFFIC = {
-    "sources_sha256": "2b7ffdc46295254912ef5a082dcc0cce3cfa097de2460c4308983a50f7b4168e",
-    "plain": 470387584 + 1843136,       # mean of 4 launches
-    "per_case_block": (965038208 + 15660672) / 2,   # mean of 2 launches
+    "sources_sha256": None,
+    "plain": None,
+    "per_case_block": None,
+    "per_slab": None,
 }
-TRAFFIC_SOURCES = ["paper_1202_3777_gb300/csrc/jt_kernels.cu", "paper_1202_3777_gb300/csrc/jt_kernels.h",
+TRAFFIC_SOURCES = ["paper_1202_3777_gb300/csrc/jt_kernels.cu", "paper_1202_3777_gb300/csrc/jt_caselanes.cu",
+                   "paper_1202_3777_gb300/csrc/jt_device.cuh", "paper_1202_3777_gb300/csrc/jt_kernels.h",
                    "paper_1202_3777_gb300/csrc/jt_internal.h", "paper_1202_3777_gb300/csrc/jt_plan.cpp"]
 
 
-def measured_traffic(cases):
-    """ncu DRAM bytes per launch for `cases` cases, or None once the kernel
-    or planner sources differ from the profiled ones."""
+def sources_sha256():
     import hashlib
     h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(schedule, cases):
+    """ncu DRAM bytes per launch of the schedule over `cases` cases, or None
+    once the kernel or planner sources differ from the profiled ones."""
     try:
-        for f in TRAFFIC_SOURCES:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
+        if TRAFFIC["sources_sha256"] is None or sources_sha256() != TRAFFIC["sources_sha256"]:
+            return None
     except OSError:
         return None
-    if h.hexdigest() != TRAFFIC["sources_sha256"]:
-        return None
-    if cases == 1:
-        return int(TRAFFIC["plain"])
-    return int(TRAFFIC["per_case_block"] * ((cases + 7) // 8))
+    cb = schedule["case_block"]
+    if cb == 1:
+        per, units = TRAFFIC["plain"], cases
+    elif cb == 32:
+        per, units = TRAFFIC["per_slab"], (cases + 31) // 32
+    else:
+        per, units = TRAFFIC["per_case_block"], (cases + cb - 1) // cb
+    return None if per is None else int(per * units)
 
 
 def evidence_seed(rank: int) -> int:
@@ -387,9 +397,14 @@ def merging_sweep():
 def measure_serving(rank):
     """Continuous batching over the four resident trees (small, large-clique,
     high-cardinality, 1024-clique binary): a burst of queries gives the
-    sustained rate, then Poisson arrivals at a quarter and at half of it give
-    p50/p99 latency."""
-    from paper_1202_3777_gb300 import serve
+    sustained rate; Poisson arrivals at 0.5, 0.8 and 0.95 of it give p50/p99
+    latency.  Batches of different trees share the SMs and overlap on the
+    device (counted from the kernels' spans on the global timer).  Per tree,
+    the batched rate (a full batch of its slots) against the plain one (one
+    case per call), and a sample of served queries for the error against the
+    oracle."""
+    import torch
+    from paper_1202_3777_gb300 import jt, serve
     trees = {
         "small": synth.small_tree().as_dtype(np.float32),
         "large_clique": synth.large_clique_tree().as_dtype(np.float32),
@@ -411,29 +426,210 @@ def measure_serving(rank):
         return out
 
     burst = queries(512, 30000)
-    srv.completed = []
+    srv.completed, srv.spans = [], []
     done = srv.run_arrivals([(0.0, q) for q in burst])
     burst_s = max(q.done for q in done) - min(q.arrival for q in done)
     rate = len(done) / burst_s
-    # Poisson arrivals for 1.5 s at a quarter and at half of the burst rate;
-    # the headline p50/p99 are the quarter-load ones (each propagation fills
-    # every SM, so the trees' batches take turns on the GPU and small batches
-    # cost nearly as much as large ones: at half load the queues grow)
+    burst_overlap = serve.overlapping_pairs(srv.spans)
+    sample = [(q.tree, q.states.copy(), q.marginals.copy(), q.log_z) for q in sorted(done, key=lambda q: q.qid)[:12]]
     loads = []
-    for li, load in enumerate((0.25, 0.5)):
-        srv.completed = []
+    for li, load in enumerate((0.5, 0.8, 0.95)):
+        srv.completed, srv.spans = [], []
         qs = queries(int(load * rate * 1.5) + 1, 40000 + 10000 * li)
         t, arr = 0.0, []
         for q in qs:
             t += rng.exponential(1.0 / (load * rate))
             arr.append((t, q))
         done = srv.run_arrivals(arr)
-        loads.append({"load": load, "offered_queries_per_s": load * rate, **serve.latency_summary(done, work)})
+        loads.append({"load": load, "offered_queries_per_s": load * rate, **serve.latency_summary(done, work),
+                      "batches": len(srv.spans), "mean_batch": float(np.mean([sp[3] for sp in srv.spans])),
+                      "overlapping_batch_pairs": serve.overlapping_pairs(srv.spans)})
+    # per tree: a full batch of its slots against one case per call
+    per_tree = {}
+    for name, r in srv.trees.items():
+        n = r.slots
+        jt.jt_set_evidence_dense(r.handle, 0, synth.evidence_matrix(trees[name], n, (0.01, 0.20), 90000),
+                                 stream=r.stream)
+        ms = {}
+        for k in (n, 1):
+            for _ in range(3):
+                jt.jt_propagate(r.handle, 0, k, r.stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(r.stream)
+            reps = 10
+            for _ in range(reps):
+                jt.jt_propagate(r.handle, 0, k, r.stream)
+            e1.record(r.stream)
+            e1.synchronize()
+            ms[k] = e0.elapsed_time(e1) / reps
+        per_tree[name] = {"slots": n, "batched_clique_entries_per_s": work[name] * n / (ms[n] * 1e-3),
+                          "plain_clique_entries_per_s": work[name] / (ms[1] * 1e-3),
+                          "batched_over_plain": (work[name] * n / ms[n]) / (work[name] / ms[1]),
+                          "case_block": jt.jt_get_schedule(r.handle, 0, n)["case_block"]}
     srv.free()
     return {"trees": names, "budget_gb": 60, "max_batch": 64, "burst_queries_per_s": rate,
             "burst_clique_entries_per_s": sum(work[q.tree] for q in burst) / burst_s,
+            "burst_overlapping_batch_pairs": burst_overlap,
             "offered_queries_per_s": loads[0]["offered_queries_per_s"], "p50_ms": loads[0]["p50_ms"],
-            "p99_ms": loads[0]["p99_ms"], "loads": loads}
+            "p99_ms": loads[0]["p99_ms"], "loads": loads, "per_tree": per_tree, "_sample": (trees, sample)}
+
+
+def serving_errors(sample):
+    """Error against the oracle of a sample of served queries."""
+    from oracle import hugin
+    trees, rows = sample
+    worst, worst_lz = 0.0, 0.0
+    for name, states, marg, lz in rows:
+        t = trees[name]
+        ref = hugin.propagate_tree(t, hugin.evidence_dict(*synth.case_from_row(states)))
+        e = rel_errors(t, [ref], [lz], [marg])
+        worst, worst_lz = max(worst, e["max_rel_err"]), max(worst_lz, e["logz_rel_err"])
+    return {"cases": len(rows), "max_rel_err": worst, "logz_rel_err": worst_lz, "tolerance": 1e-5,
+            "oracle": "FP64 numpy oracle (oracle/hugin.py)"}
+
+
+def workload_rows(name, tree, n, seed):
+    """Dense evidence rows of n cases of a named workload (its own recipe:
+    a fraction of the variables, or a fixed number of observed variables)."""
+    w = synth.WORKLOADS[name]
+    if "n_obs" in w:
+        out = np.full((n, tree.n_vars), -1, np.int16)
+        for i in range(n):
+            v, st = synth.random_evidence(tree, w["n_obs"], seed + i)
+            out[i, v] = st
+        return out
+    return synth.evidence_matrix(tree, n, w["frac"], seed)
+
+
+def alg_bytes_of(tree, info, cases, w=4):
+    """Algorithmic bytes of a propagation launch over `cases` cases: per
+    case every clique table read once per pass (the root's collect total
+    comes from its distribute pass) plus the messages written and read in
+    each pass and the marginal sources; a batch counts each case's bytes (a
+    block of cases shares each table read)."""
+    streamed = 2 * tree.entries() - int(tree.table_sizes()[0])
+    return cases * (w * streamed + w * (4 * msg_total(tree) + info.marginal_len))
+
+
+def measure_workload(jt, torch, name, tree, B, steps, warmup, seed, world, clocks_index=None, e2e=False,
+                     plain=True, keep=4):
+    """One workload: B cases per jt_propagate (timed steps, CUDA events on the
+    launching stream, max over ranks), the plain one-case path, the device
+    time of the propagation and finalisation kernels (jt_profile_propagate),
+    the roofline of the propagation kernel, and the results of the first
+    `keep` cases for the error against the oracle."""
+    import torch.distributed as dist
+    W = tree.work_per_case()
+    ev = workload_rows(name, tree, B, seed)
+    h = jt.jt_load_synth(tree, compute=jt.JT_F32, max_cases=B)
+    jt.jt_set_evidence_dense(h, 0, ev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(first, n, k):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(k):
+            jt.jt_propagate(h, first, n, stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(s0.elapsed_time(s1) / k, world, "cuda")
+
+    out = {"workload": tree.name, "cases": B}
+    if plain:
+        for _ in range(warmup):
+            jt.jt_propagate(h, 0, 1, stream)
+        out["plain_ms"] = timed(0, 1, steps)
+    for _ in range(warmup):
+        jt.jt_propagate(h, 0, B, stream)
+    if clocks_index is not None:
+        with Clocks(clocks_index) as clk:
+            out["step_ms"] = timed(0, B, steps)
+        out["clocks"] = clk.summary()
+    else:
+        out["step_ms"] = timed(0, B, steps)
+    st = jt.jt_get_status(h, 0, B)
+    assert np.all(st == jt.JT_OK), st
+    out["schedule"] = jt.jt_get_schedule(h, 0, B)
+    prof_b = np.mean([jt.jt_profile_propagate(h, 0, B, stream) for _ in range(3)], axis=0)
+    out["kernel_ms"], out["finalize_ms"] = float(prof_b[0]), float(prof_b[1])
+    if plain:
+        prof_1 = np.mean([jt.jt_profile_propagate(h, 0, 1, stream) for _ in range(3)], axis=0)
+        out["plain_kernel_ms"], out["plain_finalize_ms"] = float(prof_1[0]), float(prof_1[1])
+    info = h.info
+    out["alg_bytes"] = int(alg_bytes_of(tree, info, B))
+    out["alg_bytes_plain"] = int(alg_bytes_of(tree, info, 1))
+    out["work_per_case"] = W
+    out["value"] = job_rate(W, B, world, out["step_ms"])
+    if plain:
+        out["plain_value"] = job_rate(W, 1, world, out["plain_ms"])
+    if e2e:
+        md = lzh = None
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            jt.jt_set_evidence_dense(h, 0, ev)
+            jt.jt_propagate(h, 0, B, stream)
+            md = jt.jt_get_marginals(h, 0, B, stream=stream)
+            lzh = jt.jt_get_log_evidence(h, 0, B, stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        out["e2e_ms"] = max_over_ranks(1e3 * (time.perf_counter() - t0) / steps, world, "cuda")
+        out["h2d_bytes"] = int(ev.nbytes)
+        out["d2h_bytes"] = int(md.nbytes + lzh.nbytes)
+    lz = jt.jt_get_log_evidence(h, 0, B)
+    m = jt.jt_get_marginals(h, 0, B)
+    out["_sample"] = (ev[:keep].copy(), lz[:keep].copy(), m[:keep].copy())
+    h.free()
+    return out
+
+
+def roofline_of(kernel, alg_bytes, kernel_ms, hbm, src, traffic=None):
+    ach = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+            "kernel": kernel, "kernel_ms": kernel_ms, "alg_bytes": int(alg_bytes),
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def prop_kernel_name(schedule):
+    return "k_propagate_cl" if schedule["case_block"] == 32 else f"k_propagate<float, {schedule['case_block']}>"
+
+
+def measure_latency(jt, torch, steps=50):
+    """Device time per propagation (propagation + finalisation kernels, one
+    case, CUDA events over back-to-back launches on one stream) of the small
+    trees: the 32-clique tree of ternary variables (FP64 potentials, also
+    run in FP32) and the 1024-clique binary tree (FP32)."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for key, tree, comp in (("small_f64", synth.small_tree(), jt.JT_F64),
+                            ("small_f32", synth.small_tree().as_dtype(np.float32), jt.JT_F32),
+                            ("binary_f32", synth.binary_serving_tree().as_dtype(np.float32), jt.JT_F32)):
+        h = jt.jt_load_synth(tree, compute=comp, max_cases=1)
+        jt.jt_set_evidence_dense(h, 0, synth.evidence_matrix(tree, 1, 0.10, 77))
+        for _ in range(5):
+            jt.jt_propagate(h, 0, 1, stream)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(steps):
+            jt.jt_propagate(h, 0, 1, stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        assert jt.jt_get_status(h, 0, 1)[0] == jt.JT_OK
+        out[key] = {"workload": tree.name, "us_per_propagation": 1e3 * s0.elapsed_time(s1) / steps,
+                    "cliques": tree.n_cliques, "depth": int(h.info.depth)}
+        h.free()
+    return out
 
 
 def main():
@@ -446,6 +642,8 @@ def main():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="only the headline workload (no high-cardinality, 4096-case or latency keys)")
     ap.add_argument("--sweep-separators", action="store_true",
                     help="print the separator-size sweep (Fig. 6 / Fig. 7 analogues) instead of the bench line")
     ap.add_argument("--sweep-merging", action="store_true",
@@ -476,138 +674,96 @@ def main():
         return 0
 
     B = args.batch
-    tree = synth.WORKLOADS[WORKLOAD]["build"]().as_dtype(np.float32)
-    W = tree.work_per_case()
-    ev = synth.evidence_matrix(tree, B, 0.05, evidence_seed(rank))
-    h = jt.jt_load_synth(tree, compute=jt.JT_F32, max_cases=B)
-    jt.jt_set_evidence_dense(h, 0, ev)
-    stream = torch.cuda.current_stream()
-    sync = torch.cuda.synchronize
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def timed(first, n, steps):
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        sync()
-        s0.record(stream)
-        for _ in range(steps):
-            jt.jt_propagate(h, first, n, stream)
-        s1.record(stream)
-        sync()
-        barrier()
-        return s0.elapsed_time(s1) / steps   # ms per step
-
-    def max_over(x):
-        return max_over_ranks(x, world, "cuda")
-
-    # plain: one case per jt_propagate call
-    for _ in range(args.warmup):
-        jt.jt_propagate(h, 0, 1, stream)
-    plain_ms = max_over(timed(0, 1, args.steps))
-
-    # batched (the timed step)
-    for _ in range(args.warmup):
-        jt.jt_propagate(h, 0, B, stream)
+    hbm, src = peaks()
     gi = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES") else local
-    with Clocks(gi) as clk:
-        step_ms = max_over(timed(0, B, args.steps))
-    clocks = clk.summary()
-
-    # correctness guard on the timed results
-    st = jt.jt_get_status(h, 0, B)
-    assert np.all(st == jt.JT_OK), st
-
-    # device time of the dominant kernel (the persistent propagation kernel),
-    # CUDA events on the launching stream, same schedule as the timed steps
-    prof_b = np.mean([jt.jt_profile_propagate(h, 0, B, stream) for _ in range(3)], axis=0)
-    prof_1 = np.mean([jt.jt_profile_propagate(h, 0, 1, stream) for _ in range(3)], axis=0)
-    hbm, src = peaks()
-    w = 4
-    entries = tree.entries()
-    info = h.info
-
-    root_entries = int(tree.table_sizes()[0])
-    streamed = 2 * entries - root_entries   # collect reads every non-root table, distribute every table
-
-    def alg_bytes(cases):
-        # per case: every clique table read once per pass (the root's collect
-        # total comes from its distribute pass), messages written and read in
-        # each pass; a batch of cases counts each case's bytes (the kernel
-        # shares each table read among a block of 8 cases)
-        return cases * (w * streamed + w * (4 * msg_total(tree) + info.marginal_len))
-
-    ach_b = alg_bytes(B) / (prof_b[0] * 1e-3) / 1e9
-    ach_1 = alg_bytes(1) / (prof_1[0] * 1e-3) / 1e9
-
-    # end to end through the public API with host buffers
-    md = np.empty((B, h.marginal_len))
-    lzh = np.empty(B)
-    sync()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        jt.jt_set_evidence_dense(h, 0, ev)
-        jt.jt_propagate(h, 0, B, stream)
-        md = jt.jt_get_marginals(h, 0, B, stream=stream)
-        lzh = jt.jt_get_log_evidence(h, 0, B, stream=stream)
-    sync()
-    barrier()
-    e2e_ms = max_over(1e3 * (time.perf_counter() - t0) / args.steps)
-
-    total_cases = B * world
-    value = job_rate(W, B, world, step_ms)
-    plain_value = job_rate(W, 1, world, plain_ms)
-    h.free()
+    tree = synth.WORKLOADS[WORKLOAD]["build"]().as_dtype(np.float32)
+    head = measure_workload(jt, torch, WORKLOAD, tree, B, args.steps, args.warmup, evidence_seed(rank), world,
+                            clocks_index=gi, e2e=True)
+    extra = {}
+    if not args.no_extra:
+        hc_tree = synth.WORKLOADS["high_card"]["build"]().as_dtype(np.float32)
+        extra["high_card"] = measure_workload(jt, torch, "high_card", hc_tree, B, args.steps, args.warmup,
+                                              evidence_seed(rank) + 500, world)
+        c4_tree = synth.WORKLOADS["batched"]["build"]().as_dtype(np.float32)
+        extra["batched_4096"] = measure_workload(jt, torch, "batched", c4_tree, synth.WORKLOADS["batched"]["n_cases"],
+                                                 min(args.steps, 3), args.warmup, 4000 + 100000 * rank, world,
+                                                 plain=True)
+    latency = None if args.no_extra else measure_latency(jt, torch)
     per_message = None
     if not args.no_ablation:
-        per_message = measure_per_message(tree, ev[0])
-        per_message["fused_kernel_ms"] = float(prof_1[0])
-        per_message["fused_with_finalisation_ms"] = float(prof_1[0] + prof_1[1])
+        per_message = measure_per_message(tree, workload_rows(WORKLOAD, tree, 1, evidence_seed(rank))[0])
+        per_message["fused_kernel_ms"] = head["plain_kernel_ms"]
+        per_message["fused_with_finalisation_ms"] = head["plain_kernel_ms"] + head["plain_finalize_ms"]
     cpt_init = measure_cpt_init(tree, hbm)
     serving = None
     if not args.no_serving:
         serving = measure_serving(rank)
     if rank != 0:
         return 0
+
+    # CPU leg: the oracle on a bounded sample of every workload's cases (its
+    # rate is the CPU baseline of the headline workload), and the GPU's error
+    # against it on the same cases
     cpu = None
+    errors = {}
     if not args.no_cpu_baseline:
-        cases = [synth.case_from_row(r) for r in ev[: min(B, 4)]]
-        rate, done, dt = oracle_rate(tree.as_dtype(np.float32), cases)
+        ev, lz, m = head["_sample"]
+        cases = [synth.case_from_row(r) for r in ev]
+        rate, done, dt, err = oracle_rate(tree, cases, 20.0, gpu=(lz, m))
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{done} of the {B} evidence cases of one step, FP64 numpy oracle ({dt:.1f} s)",
                "host_cores": host_cores()}
+        errors[WORKLOAD] = err
+        for key, res in extra.items():
+            t = hc_tree if key == "high_card" else c4_tree
+            ev, lz, m = res["_sample"]
+            _, _, _, errors[key] = oracle_rate(t, [synth.case_from_row(r) for r in ev], 10.0, gpu=(lz, m))
+        if serving is not None:
+            errors["serving"] = serving_errors(serving.pop("_sample"))
+    if serving is not None:
+        serving.pop("_sample", None)
+
+    def strip(d):
+        return {k: v for k, v in d.items() if not k.startswith("_")}
+
+    value = head["value"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": head["step_ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": tree.name, "cases_per_step": B, "cases_per_gpu": B,
-                   "observed_frac": 0.05, "entries_per_case": entries, "work_per_case": W,
+                   "observed_frac": 0.05, "entries_per_case": tree.entries(), "work_per_case": head["work_per_case"],
                    "l2": "inputs larger than L2 (268 MB of FP32 clique tables)",
                    "parallelism": f"replicas x{world}"},
-        "plain": {"value": plain_value, "unit": UNIT, "ms_per_case": plain_ms},
-        "batched_over_plain": value / plain_value,
-        "roofline": {"bound": "hbm", "achieved": ach_b, "peak": hbm, "unit": "GB/s",
-                     "frac": ach_b / hbm, "traffic": measured_traffic(B), "kernel": "k_propagate",
-                     "kernel_ms": float(prof_b[0]), "alg_bytes": int(alg_bytes(B)),
-                     "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"},
-        "roofline_plain": {"bound": "hbm", "achieved": ach_1, "peak": hbm, "unit": "GB/s", "frac": ach_1 / hbm,
-                           "traffic": measured_traffic(1), "kernel_ms": float(prof_1[0]),
-                           "alg_bytes": int(alg_bytes(1))},
-        "finalize_ms": {"batched": float(prof_b[1]), "plain": float(prof_1[1])},
-        "e2e": {"value": job_rate(W, B, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(ev.nbytes), "d2h_bytes_per_step": int(md.nbytes + lzh.nbytes)},
+        "schedule": head["schedule"],
+        "plain": {"value": head["plain_value"], "unit": UNIT, "ms_per_case": head["plain_ms"]},
+        "batched_over_plain": value / head["plain_value"],
+        "roofline": roofline_of(prop_kernel_name(head["schedule"]), head["alg_bytes"], head["kernel_ms"], hbm, src,
+                                measured_traffic(head["schedule"], B)),
+        "roofline_plain": roofline_of("k_propagate<float, 1>", head["alg_bytes_plain"], head["plain_kernel_ms"], hbm,
+                                      src, measured_traffic({"case_block": 1}, 1)),
+        "finalize_ms": {"batched": head["finalize_ms"], "plain": head["plain_finalize_ms"]},
+        "e2e": {"value": job_rate(head["work_per_case"], B, world, head["e2e_ms"]), "unit": UNIT,
+                "ms_per_step": head["e2e_ms"], "h2d_bytes_per_step": head["h2d_bytes"],
+                "d2h_bytes_per_step": head["d2h_bytes"]},
+        "oracle_error": errors or None,
         "serving": serving,
         "per_message": per_message,
         "cpt_init": cpt_init,
-        "gpu_launches": int(2 * args.steps),   # k_propagate + k_finalize per step
-        "clocks": clocks,
+        "gpu_launches": int(2 * args.steps),   # propagation + finalisation kernel per step
+        "clocks": head["clocks"],
         "cpu_baseline": cpu,
     }
+    for key, res in extra.items():
+        r = strip(res)
+        r["roofline"] = roofline_of(prop_kernel_name(res["schedule"]), res["alg_bytes"], res["kernel_ms"], hbm, src)
+        r["unit"] = UNIT
+        if "plain_value" in res:
+            r["batched_over_plain"] = res["value"] / res["plain_value"]
+        out[key] = r
+    if latency is not None:
+        out["latency"] = latency
     print(json.dumps(out, default=_json_default), flush=True)
     if world > 1:
         dist.destroy_process_group()

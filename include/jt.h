@@ -299,6 +299,26 @@ typedef struct {
 
 jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info* out);
 
+/* jt_propagate holding at most `max_ctas` SMs (0 or >= the SM count: all of
+ * them).  The persistent propagation kernel claims one SM per CTA, so a
+ * propagation of one tree normally holds the whole GPU; with a limit, the
+ * propagations of several trees (each on its own stream) run side by side on
+ * disjoint SMs, which is how a server overlaps batches of different trees.
+ * Not part of the paper's method (its propagation is one kernel launch per
+ * message, Sec. 3.4).  Results are the same as jt_propagate's (every
+ * schedule computes Eq. 1-3 over Algorithms 2-4); the graph of each
+ * (range, limit) is recorded on first use.  Errors as jt_propagate, plus
+ * JT_ERR_INVALID_ARG for a negative limit. */
+jt_status jt_propagate_ctas(jt_tree t, int32_t first, int32_t n, int32_t max_ctas, void* stream);
+
+/* Start and end, on the GPU's global nanosecond timer, of the tree's most
+ * recent propagation kernel (first CTA start, last CTA end): spans of
+ * different trees' kernels are comparable, so a caller can tell whether two
+ * propagations ran at the same time.  Synchronises with the tree's last
+ * stream.  JT_ERR_STATE before the first propagation; JT_ERR_INVALID_ARG for
+ * null outputs. */
+jt_status jt_get_kernel_span(jt_tree t, uint64_t* start_ns, uint64_t* end_ns);
+
 /* Release every resource of the tree (waits for its pending work). NULL is a no-op. */
 void jt_free(jt_tree t);
 

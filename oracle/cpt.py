@@ -12,7 +12,7 @@ contains its family {v} + pa(v).  The product of the clique tables is then
 the network's joint distribution prod_v P(v | pa(v)) (Sec. 2.1: the junction
 tree represents the joint).
 
-Readings where the paper is silent (each also listed in the design notes):
+Readings where the paper is silent:
 
 * a CPT is a table over its family, laid out like a clique table: the
   first-listed variable is the most significant digit;

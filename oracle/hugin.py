@@ -24,7 +24,7 @@ What it follows, step by step:
   by decoding each flat index into its state string (first-listed variable
   most significant) and matching the separator variables' states.
 
-Readings where the paper is silent (each also listed in the design notes):
+Readings where the paper is silent:
 
 * separator tables start at all ones;
 * evidence is entered by zeroing, in every clique holding an observed

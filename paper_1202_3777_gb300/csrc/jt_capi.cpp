@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <string>
 #include <type_traits>
@@ -116,7 +117,8 @@ struct jt_tree_s {
   cudaEvent_t order_ev = nullptr;       // orders work on a new stream after the tree's last stream
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
-  std::map<std::pair<int, int>, GraphEntry> graphs;
+  std::map<std::tuple<int, int, int>, GraphEntry> graphs;   // (first case, cases, CTA cap; 0 = every SM)
+  unsigned long long* d_span = nullptr;   // [2] global-timer span of the last propagation kernel
   std::unique_ptr<PerMsg> permsg;
 };
 
@@ -150,7 +152,8 @@ void destroy(jt_tree t) {
   if (t->permsg)
     for (void* q : t->permsg->bufs) cudaFree(q);
   void* ptrs[] = {t->base,   t->d_msg,  t->d_sums,  t->d_done,    t->d_err, t->d_status, t->d_marg,
-                  t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_sep_size};
+                  t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_sep_size,
+                  t->d_span};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->h_ev) cudaFreeHost(t->h_ev);
@@ -199,6 +202,9 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   // the error word reports this propagation (a timed-out one leaves nothing
   // behind: every accumulator above starts again from zero)
   chk(cudaMemsetAsync(t->d_err, 0, sizeof(int32_t), s));
+  // kernel span: start = min over CTAs (from all ones), end = max (from zero)
+  chk(cudaMemsetAsync(t->d_span, 0xFF, sizeof(unsigned long long), s));
+  chk(cudaMemsetAsync(t->d_span + 1, 0, sizeof(unsigned long long), s));
   PropArgs<T> a{};
   a.base = (const T*)t->base;
   a.stages = ge.stages;
@@ -227,6 +233,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   a.calib = (T*)t->d_calib;
   a.calib_stride = p.base_len;
   a.trace = trace;
+  a.span = t->d_span;
   a.ring = sc.ring;
   a.chunk = sc.chunk;
   a.max_k = sc.max_k;
@@ -270,10 +277,11 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
 // Plan the schedule of a case range, upload it, and record the propagation
 // into a CUDA graph.
 template <typename T>
-jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, cudaStream_t s, GraphEntry* ge) {
+jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cudaStream_t s, GraphEntry* ge) {
   std::string err;
   const int smem_cap = smem_budget(t->device, ctas_per_sm_for(cb)) - 256;
-  jt_status st = build_schedule(t->plan, (int)t->elem, cb, n_cases, t->n_sm, smem_cap, &ge->sched, &err);
+  const int sms = cap > 0 ? std::min(cap, t->n_sm) : t->n_sm;   // the SMs this propagation may hold
+  jt_status st = build_schedule(t->plan, (int)t->elem, cb, n_cases, sms, smem_cap, &ge->sched, &err);
   if (st != JT_OK) return fail(st, err);
   // Failure-path hooks, read when a range's graph is recorded (host-side
   // fault injection: nothing on the device faults or waits without limit).
@@ -296,7 +304,7 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, cudaStream_
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->blobs, sc.blobs, "schedule upload")) != JT_OK) return st;
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->items, sc.items, "schedule upload")) != JT_OK) return st;
   ge->smem = prop_smem_bytes(sc, (int)t->elem);
-  ge->grid = (int32_t)std::min<int64_t>((int64_t)sc.items.size(), (int64_t)t->n_sm * ctas_per_sm_for(cb));
+  ge->grid = (int32_t)std::min<int64_t>((int64_t)sc.items.size(), (int64_t)sms * ctas_per_sm_for(cb));
   if (const char* dbg = std::getenv("JT_DEBUG_PLAN"); dbg && *dbg == '1') {
     std::fprintf(stderr, "[jt plan] cases=%d cb=%d n_cb=%d items=%zu grid=%d smem=%d ring=%d win_max=%d\n", n_cases,
                  sc.cb, sc.n_cb, sc.items.size(), ge->grid, ge->smem, sc.ring, sc.win_max);
@@ -356,8 +364,8 @@ float time_graph(const GraphEntry& ge, cudaStream_t s) {
 // caller asked for) and keeps the fastest.  JT_CASE_BLOCK=1, 4, 8 or 32 in
 // the environment fixes the choice instead (32 falls back to 8 where case
 // lanes do not apply).
-jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** out) {
-  auto key = std::make_pair(first, n);
+jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphEntry** out) {
+  auto key = std::make_tuple(first, n, cap);
   auto it = t->graphs.find(key);
   if (it == t->graphs.end()) {
     if (t->graphs.size() >= 64) {
@@ -372,8 +380,8 @@ jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** ou
       if (v == "1" || v == "4" || v == "8" || v == "32") forced = std::stoi(v);
     }
     auto record = [&](int cb, GraphEntry* ge) {
-      return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, t->cap_stream, ge)
-                                  : record_schedule<float>(t, first, n, cb, t->cap_stream, ge);
+      return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, cap, t->cap_stream, ge)
+                                  : record_schedule<float>(t, first, n, cb, cap, t->cap_stream, ge);
     };
     std::vector<int> cands;
     if (n == 1) {
@@ -399,6 +407,8 @@ jt_status get_graph(jt_tree t, int first, int n, cudaStream_t s, GraphEntry** ou
       const jt_status st = record(cb, &ge);
       if (st != JT_OK) {
         drop_graph(ge);
+        if (const char* dbg = std::getenv("JT_DEBUG_PLAN"); dbg && *dbg == '1')
+          std::fprintf(stderr, "[jt plan] cases=%d width %d not used: %s\n", n, cb, g_err.c_str());
         if (first_err == JT_OK) {
           first_err = st;
           first_msg = g_err;
@@ -845,6 +855,9 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   if ((st = alloc(raw, &raw->d_sums, 2ll * nc * raw->max_cases, "stage totals")) != JT_OK) return bail(st);
   if ((st = alloc(raw, &raw->d_done, 1 + 2ll * nc * raw->max_cases, "block counters")) != JT_OK) return bail(st);
   if ((st = alloc(raw, &raw->d_err, 1, "error word")) != JT_OK) return bail(st);
+  if ((st = alloc(raw, &raw->d_span, 2, "kernel span")) != JT_OK) return bail(st);
+  if (cudaMemset(raw->d_span, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(fail(JT_ERR_CUDA, "memset"));
   if (cudaMemset(raw->d_err, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
   if ((st = alloc(raw, &raw->d_status, raw->max_cases, "status")) != JT_OK) return bail(st);
   if (cudaMemset(raw->d_status, 0, raw->max_cases * sizeof(int32_t)) != cudaSuccess)
@@ -952,11 +965,43 @@ jt_status jt_propagate(jt_tree t, int32_t first, int32_t n, void* stream) {
   if ((st = order_on(t, s)) != JT_OK) return st;
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
-  if ((st = get_graph(t, first, n, s, &ge)) != JT_OK) return st;
+  if ((st = get_graph(t, first, n, 0, s, &ge)) != JT_OK) return st;
   CU(cudaGraphLaunch(ge->exec, s), "graph launch");
   CU(cudaEventRecord(ge->done, s), "event");
   for (int i = first; i < first + n; ++i) t->ready[i] = 1;
   t->last_stream = s;
+  return JT_OK;
+}
+
+jt_status jt_propagate_ctas(jt_tree t, int32_t first, int32_t n, int32_t max_ctas, void* stream) {
+  jt_status st = check_tree(t);
+  if (st != JT_OK) return st;
+  if ((st = check_range(t, first, n)) != JT_OK) return st;
+  if (max_ctas < 0) return fail(JT_ERR_INVALID_ARG, "negative CTA limit");
+  if (n == 0) return JT_OK;
+  const int cap = (max_ctas == 0 || max_ctas >= t->n_sm) ? 0 : max_ctas;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = order_on(t, s)) != JT_OK) return st;
+  if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
+  GraphEntry* ge = nullptr;
+  if ((st = get_graph(t, first, n, cap, s, &ge)) != JT_OK) return st;
+  CU(cudaGraphLaunch(ge->exec, s), "graph launch");
+  CU(cudaEventRecord(ge->done, s), "event");
+  for (int i = first; i < first + n; ++i) t->ready[i] = 1;
+  t->last_stream = s;
+  return JT_OK;
+}
+
+jt_status jt_get_kernel_span(jt_tree t, uint64_t* start_ns, uint64_t* end_ns) {
+  jt_status st = check_tree(t);
+  if (st != JT_OK) return st;
+  if (!start_ns || !end_ns) return fail(JT_ERR_INVALID_ARG, "null output");
+  if ((st = sync_last(t)) != JT_OK) return st;
+  unsigned long long h[2] = {0, 0};
+  CU(cudaMemcpy(h, t->d_span, sizeof(h), cudaMemcpyDeviceToHost), "span read");
+  if (h[1] == 0 || h[0] > h[1]) return fail(JT_ERR_STATE, "no propagation kernel has run");
+  *start_ns = h[0];
+  *end_ns = h[1];
   return JT_OK;
 }
 
@@ -973,7 +1018,7 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
   if ((st = order_on(t, s)) != JT_OK) return st;
   if ((st = upload_dirty(t, first, n, s)) != JT_OK) return st;
   GraphEntry* ge = nullptr;
-  if ((st = get_graph(t, first, n, s, &ge)) != JT_OK) return st;
+  if ((st = get_graph(t, first, n, 0, s, &ge)) != JT_OK) return st;
   // JT_TRACE=<file>: also record every work item's SM and timeline
   // (global timer, ns) and write them to <file> as CSV
   const char* trace_path = std::getenv("JT_TRACE");
@@ -1110,7 +1155,7 @@ jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info*
   if (st != JT_OK) return st;
   if ((st = check_range(t, first, n)) != JT_OK) return st;
   if (!out || n < 1) return fail(JT_ERR_INVALID_ARG, "null output or empty range");
-  auto it = t->graphs.find(std::make_pair(first, n));
+  auto it = t->graphs.find(std::make_tuple(first, n, 0));
   if (it == t->graphs.end()) return fail(JT_ERR_STATE, "case range not propagated yet");
   const GraphEntry& ge = it->second;
   *out = jt_schedule_info{};

@@ -50,9 +50,40 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
 
+// Shared-memory load / reduction at a register address plus a compile-time
+// offset (one instruction, no address arithmetic).
+template <int OFF>
+__device__ __forceinline__ float sld_at(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sred_at(uint32_t a, float v) {
+  asm volatile("red.shared.add.f32 [%0+%1], %2;" ::"r"(a), "n"(OFF), "f"(v) : "memory");
+}
+// The 32 entries of a tile at consecutive window rows (keys key + e).
+template <int E>
+struct IdentRows {
+  __device__ __forceinline__ static void gather_mul(uint32_t at, float2 (&f)[16]) {
+    IdentRows<E - 2>::gather_mul(at, f);
+    f[(E - 2) / 2] = mul2(f[(E - 2) / 2], make_float2(sld_at<(E - 2) * kClRow>(at), sld_at<(E - 1) * kClRow>(at)));
+  }
+  __device__ __forceinline__ static void reduce(uint32_t at, const float2 (&f)[16]) {
+    IdentRows<E - 2>::reduce(at, f);
+    sred_at<(E - 2) * kClRow>(at, f[(E - 2) / 2].x);
+    sred_at<(E - 1) * kClRow>(at, f[(E - 2) / 2].y);
+  }
+};
+template <>
+struct IdentRows<0> {
+  __device__ __forceinline__ static void gather_mul(uint32_t, float2 (&)[16]) {}
+  __device__ __forceinline__ static void reduce(uint32_t, const float2 (&)[16]) {}
+};
+
 // Shared-memory carve-up of a case-lane CTA.  The common fields serve the
 // producer; per buffer: `obs` holds (V, M) per case, `bf` the block factor per
-// case, `win` the case-minor windows; `kiter` holds the per-item port tables.
+// case (then the block totals), `win` the case-minor windows.
 __device__ __forceinline__ Smem carve_cl(unsigned char* smem, const SmemLayoutCL& L, int ring_n, int win_max) {
   Smem s{};
   s.full = reinterpret_cast<uint64_t*>(smem + L.bar);
@@ -74,7 +105,7 @@ __device__ __forceinline__ Smem carve_cl(unsigned char* smem, const SmemLayoutCL
   s.win = smem + L.win;
   s.red = reinterpret_cast<double*>(smem + L.red);
   s.misc = reinterpret_cast<int*>(smem + L.misc);
-  s.kiter = reinterpret_cast<int*>(smem + L.ports);
+  s.kiter = nullptr;
   s.live = nullptr;
   s.kt = nullptr;
   s.ring = smem + L.ring;
@@ -94,7 +125,7 @@ __device__ __forceinline__ Smem carve_cl(unsigned char* smem, const SmemLayoutCL
 // windows of the own separator, rho = delta (sigma_c / Delta_parent) / u with
 // 0/0 := 0 (Eq. 3 and its zero rule).
 __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0) {
-  constexpr int U = 4;  // ratio rows per lane per round (their loads in flight together)
+  constexpr int U = 16;  // ratio rows per lane per round (their loads in flight together)
   const int l = (int)(threadIdx.x & 31);
   for (uint32_t slot = 0;; ++slot) {
     const uint32_t b = slot & 1u, par = (slot >> 1) & 1u;
@@ -239,84 +270,72 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
   }
 }
 
-// ---- control warp 1, lane 0: the signalling lane ---------------------------
-// For each finished item: add its output windows into the slab rows with one
-// bulk reduction per port, wait until they completed, make them visible
-// GPU-wide, count the block as done, and free the item's buffer.
+// ---- control warp 1: the signalling warp (lane = case) ---------------------
+// For each finished item: add each case's block total (left in the buffer's
+// block-factor slot) to its stage total and to the block-constant outputs
+// (lane l for case l), add the output windows into the slab rows with one
+// bulk reduction per port (lane 0), wait until they completed, make every
+// lane's writes visible GPU-wide, count the block as done, and free the
+// item's buffer.
 __device__ __forceinline__ void signaller_cl(const PropArgs<float>& a, const Smem& s0) {
+  const int l = (int)(threadIdx.x & 31);
   for (uint32_t k = 0;; ++k) {
     const uint32_t sl = k % kSig;
-    if (!mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc, a.wait_ns)) break;
+    if (!__all_sync(kFull, mbar_wait(s0.sfull + sl, (k / kSig) & 1u, a.err, s0.misc, a.wait_ns))) break;
     const int4 g = s0.sig[sl];   // stage, case block, buffer, item index
-    mbar_arrive(s0.sempty + sl);
+    __syncwarp();
+    if (l == 0) mbar_arrive(s0.sempty + sl);
     if (g.x < 0) break;
-    fence_proxy_async();
     const uint32_t b = (uint32_t)g.z;
     const Smem s = with_buffer(s0, b);
     const DevStage& S = *s.stage;
     const DevItem& w = s0.info[b].w;
     const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
-    float* slab = a.msg + (int64_t)(a.case0 + g.y * kCaseLanes) * a.msg_stride;
-    bool any = false;
-    for (int pi = S.nin; pi < S.np; ++pi) {
-      const DevPort& P = s.port[pi];
-      if (P.K <= 1) continue;
-      const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
-      bulk_reduce_add(slab + (int64_t)(P.tab + kb) * kCaseLanes, s.win + (size_t)P.win * kClRow,
-                      (uint32_t)P.K * kClRow);
-      any = true;
+    const int cb0 = a.case0 + g.y * kCaseLanes;
+    const int ncb = min(kCaseLanes, a.case0 + a.n_cases - cb0);
+    float* slab = a.msg + (int64_t)cb0 * a.msg_stride;
+    if (l < ncb) {
+      const double t = s.bf[l];
+      if (t != 0.0) {
+        for (int pi = S.nin; pi < S.np; ++pi) {
+          const DevPort& P = s.port[pi];
+          if (P.K > 1) continue;
+          const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
+          atomicAdd(slab + (int64_t)(P.tab + key) * kCaseLanes + l, (float)t);
+        }
+        atomicAdd(a.sums + (int64_t)(cb0 + l) * 2 * a.n_cliques + S.sum_slot, t);
+      }
     }
-    if (any) {
-      bulk_commit();
-      bulk_wait_all();
-      fence_proxy_async_all();
+    if (l == 0) {
+      // the consumers' window writes (generic proxy) before the bulk reads
+      fence_proxy_async();
+      bool any = false;
+      for (int pi = S.nin; pi < S.np; ++pi) {
+        const DevPort& P = s.port[pi];
+        if (P.K <= 1) continue;
+        const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
+        bulk_reduce_add(slab + (int64_t)(P.tab + kb) * kCaseLanes, s.win + (size_t)P.win * kClRow,
+                        (uint32_t)P.K * kClRow);
+        any = true;
+      }
+      if (any) {
+        bulk_commit();
+        bulk_wait_all();
+        fence_proxy_async_all();
+      }
     }
+    // every lane's additions visible GPU-wide before the block counts as done
     __threadfence();
-    atomicAdd(a.done + (int64_t)g.x * a.n_cb + g.y, 1);
-    if (a.trace != nullptr && g.w >= 0) a.trace[(int64_t)g.w * kTraceSlots + 9] = global_ns();
-    mbar_arrive(s0.wfree + b);
+    __syncwarp();
+    if (l == 0) {
+      atomicAdd(a.done + (int64_t)g.x * a.n_cb + g.y, 1);
+      if (a.trace != nullptr && g.w >= 0) a.trace[(int64_t)g.w * kTraceSlots + 9] = global_ns();
+      mbar_arrive(s0.wfree + b);
+    }
   }
 }
 
 // ---- consumers -------------------------------------------------------------
-
-// The per-item key tables of the ports with windows (inputs first), computed
-// by all consumer threads: entry e of port li's table is one key.
-__device__ __forceinline__ void build_ports_cl(const Smem& s, const DevStage& S, int n_chunks, uint32_t win32,
-                                               int chunk, int& n_in, int& n_live) {
-  const int tid = threadIdx.x;
-  CLPort* cp = reinterpret_cast<CLPort*>(s.kiter);
-  constexpr int kFixed = 1 + 4 + 8 + NW * kClTiles;  // class, dvec, kvec, kslot
-  n_in = 0;
-  n_live = 0;
-  for (int pi = 0; pi < S.np; ++pi) {
-    const DevPort& P = s.port[pi];
-    if (P.K <= 1) continue;
-    const int li = n_live++;
-    if (pi < S.nin) ++n_in;
-    const DevField* f = s.fld + P.f0;
-    CLPort& C = cp[li];
-    for (int e = tid; e < kFixed + n_chunks; e += NT) {
-      if (e == 0) {
-        const bool edep = key_of<true>(1u, f, P.nf) != 0u || key_of<true>(2u, f, P.nf) != 0u;
-        const bool vdep = key_of<true>(4u, f, P.nf) != 0u || key_of<true>(8u, f, P.nf) != 0u ||
-                          key_of<true>(16u, f, P.nf) != 0u;
-        C.cls = (pi < S.nin ? kClInput : 0) | (edep ? kClEntry : (vdep ? kClVector : kClTile));
-      } else if (e < 5) {
-        C.dvec[e - 1] = (int32_t)(key_of<true>((uint32_t)(e - 1), f, P.nf) * (uint32_t)kClRow);
-      } else if (e < 13) {
-        C.kvec[e - 5] = (int32_t)(key_of<true>(4u * (uint32_t)(e - 5), f, P.nf) * (uint32_t)kClRow);
-      } else if (e < kFixed) {
-        const int sl = e - 13, ww = sl / kClTiles, t = sl - ww * kClTiles;
-        C.kslot[sl] = (int32_t)(key_of<true>((uint32_t)(ww * kClSlice + 32 * t), f, P.nf) * (uint32_t)kClRow);
-      } else {
-        const int ci = e - kFixed;
-        C.kchunk[ci] = (int32_t)(win32 + (uint32_t)P.win * kClRow +
-                                 key_of<true>((uint32_t)(ci * chunk), f, P.nf) * (uint32_t)kClRow);
-      }
-    }
-  }
-}
 
 // Stream one item: every warp takes its slice of each chunk in tiles of 32
 // entries; per tile a lane holds the 32 products of its case in registers
@@ -327,8 +346,8 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
   const uint32_t RS = (uint32_t)a.ring;
   const int CH = a.chunk;
   const uint32_t ring32 = smem_u32(s.ring);
-  const uint32_t cp32 = smem_u32(s.kiter);
-  const uint32_t lane4 = 4u * (uint32_t)lane;
+  const uint32_t cp32 = smem_u32(s.stage) + (uint32_t)s.stage->live_off;   // the stage's port tables (blob)
+  const uint32_t lane4 = smem_u32(s.win) + 4u * (uint32_t)lane;           // the lane's column of the windows
   const int nchunks = (w.n + CH - 1) / CH;
   // this lane's evidence mask: tile-level bits (>= 5), per vector (2-4), per entry (0-1)
   const int4 evm = s.obs[lane];
@@ -337,9 +356,9 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
   const bool ev_t = __any_sync(kFull, MT != 0u);
   const bool ev_v = __any_sync(kFull, (M & 28u) != 0u);
   const bool ev_e = __any_sync(kFull, (M & 3u) != 0u);
-  float mv[8];
+  uint32_t mvb = 0;   // bit v: the lane's case admits vector v of a tile
 #pragma unroll
-  for (int v = 0; v < 8; ++v) mv[v] = ((((uint32_t)(4 * v)) ^ V) & M & 28u) == 0u ? 1.f : 0.f;
+  for (int v = 0; v < 8; ++v) mvb |= ((((uint32_t)(4 * v)) ^ V) & M & 28u) == 0u ? 1u << v : 0u;
   const float2 mA01 = make_float2(((0u ^ V) & M & 3u) == 0u ? 1.f : 0.f, ((1u ^ V) & M & 3u) == 0u ? 1.f : 0.f);
   const float2 mA23 = make_float2(((2u ^ V) & M & 3u) == 0u ? 1.f : 0.f, ((3u ^ V) & M & 3u) == 0u ? 1.f : 0.f);
   float* calib = (a.calib != nullptr && lane < ncb) ? a.calib + (int64_t)(cb0 + lane) * a.calib_stride + w.off : nullptr;
@@ -365,20 +384,22 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
         f[2 * v] = make_float2(x[0], x[1]);
         f[2 * v + 1] = make_float2(x[2], x[3]);
       }
-      if (ev_t || ev_v || ev_e) {
+      // the lane's evidence mask and block factor (every product carries the
+      // case's per-block factor, so the reduced windows need no rescaling)
+      {
         const uint32_t oa = (uint32_t)(ci * CH + ot);
-        const float sc = ((oa ^ VT) & MT) == 0u ? 1.f : 0.f;
+        const float sc = (!ev_t || ((oa ^ VT) & MT) == 0u) ? bfl : 0.f;
         if (ev_e) {
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
-            const float2 m = dup(mv[v] * sc);
+            const float2 m = dup((mvb >> v) & 1u ? sc : 0.f);
             f[2 * v] = mul2(f[2 * v], mul2(mA01, m));
             f[2 * v + 1] = mul2(f[2 * v + 1], mul2(mA23, m));
           }
         } else if (ev_v) {
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
-            const float2 m = dup(mv[v] * sc);
+            const float2 m = dup((mvb >> v) & 1u ? sc : 0.f);
             f[2 * v] = mul2(f[2 * v], m);
             f[2 * v + 1] = mul2(f[2 * v + 1], m);
           }
@@ -395,7 +416,9 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
         const int cls = sld_s32(pb + offsetof(CLPort, cls));
         const uint32_t at = (uint32_t)sld_s32(pb + offsetof(CLPort, kchunk) + 4u * (uint32_t)ci) +
                             (uint32_t)sld_s32(pb + offsetof(CLPort, kslot) + 4u * (uint32_t)slot) + lane4;
-        if (cls & kClEntry) {
+        if (cls & kClIdent) {
+          IdentRows<32>::gather_mul(at, f);
+        } else if (cls & kClEntry) {
           const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
           const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
           const int4 dv = sld_v4s32(pb + offsetof(CLPort, dvec));
@@ -440,7 +463,9 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
         const int cls = sld_s32(pb + offsetof(CLPort, cls));
         const uint32_t at = (uint32_t)sld_s32(pb + offsetof(CLPort, kchunk) + 4u * (uint32_t)ci) +
                             (uint32_t)sld_s32(pb + offsetof(CLPort, kslot) + 4u * (uint32_t)slot) + lane4;
-        if (cls & kClEntry) {
+        if (cls & kClIdent) {
+          IdentRows<32>::reduce(at, f);
+        } else if (cls & kClEntry) {
           const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
           const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
           const int4 dv = sld_v4s32(pb + offsetof(CLPort, dvec));
@@ -463,16 +488,14 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
           sred_add(at, ts);
         }
       }
-      // calibrated table (JT_MATERIALIZE_CLIQUES): the product with the
-      // case's block factor, in the permuted layout of the base table
+      // calibrated table (JT_MATERIALIZE_CLIQUES), in the permuted layout
+      // of the base table
       if (calib != nullptr) {
-        const float2 m = dup(bfl);
         float* dst = calib + ci * CH + ot;
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const float2 p0 = mul2(f[2 * v], m), p1 = mul2(f[2 * v + 1], m);
-          __stcs(reinterpret_cast<float4*>(dst + 4 * v), make_float4(p0.x, p0.y, p1.x, p1.y));
-        }
+        for (int v = 0; v < 8; ++v)
+          __stcs(reinterpret_cast<float4*>(dst + 4 * v),
+                 make_float4(f[2 * v].x, f[2 * v].y, f[2 * v + 1].x, f[2 * v + 1].y));
       }
     }
     __syncwarp();
@@ -486,22 +509,15 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
 __device__ __forceinline__ bool process_item_cl(const PropArgs<float>& a, const Smem& s, const DevItem& w, uint32_t b,
                                                 RingPos& rp, uint32_t& sigk) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const DevStage S = *s.stage;
+  const DevStage& S = *s.stage;
   const int cb0 = a.case0 + w.cbk * kCaseLanes;
   const int ncb = min(kCaseLanes, a.case0 + a.n_cases - cb0);
-  const uint32_t eb = (uint32_t)w.block * (uint32_t)S.B;
-  const uint32_t win32 = smem_u32(s.win);
   const int idx_item = s.misc[2];
   uint64_t* tr = a.trace != nullptr ? a.trace + (int64_t)idx_item * kTraceSlots : nullptr;
-  const int nchunks = (w.n + a.chunk - 1) / a.chunk;
-  int n_in = 0, n_live = 0;
-  build_ports_cl(s, S, nchunks, win32, a.chunk, n_in, n_live);
-  consumer_sync<NT>();
   if (tr != nullptr && tid == 0) tr[3] = global_ns();
-  const double bfd = s.bf[lane];
-  const float bfl = (float)bfd;
+  const float bfl = (float)s.bf[lane];
   float tot = 0.f;
-  const bool sok = stream_cl(a, s, w, ncb, cb0, n_in, n_live, bfl, tot, rp);
+  const bool sok = stream_cl(a, s, w, ncb, cb0, S.n_in_live, S.n_live, bfl, tot, rp);
   if (!consumer_all<NT>(sok)) {
     if (tid == 0) {
       atomicExch(a.err, 1);
@@ -511,43 +527,17 @@ __device__ __forceinline__ bool process_item_cl(const PropArgs<float>& a, const 
   }
   if (tr != nullptr && tid == 0) tr[4] = global_ns();
   s.red[lane * NW + warp] = (double)tot;
-  // the windows hold sums without the per-case block factor: apply it (a
-  // zero factor gives exact zeros whatever the lane gathered)
-  for (int pi = S.nin; pi < S.np; ++pi) {
-    const DevPort& P = s.port[pi];
-    if (P.K <= 1) continue;
-    const uint32_t base = win32 + (uint32_t)P.win * kClRow;
-    const int n = P.K * kCaseLanes;
-    for (int i = tid; i < n; i += NT) {
-      const float m = (float)s.bf[i & (kCaseLanes - 1)];
-      const uint32_t ad = base + 4u * (uint32_t)i;
-      sst<float>(ad, m != 0.f ? sld<float>(ad) * m : 0.f);
-    }
-  }
   consumer_sync<NT>();
-  // per case: the block total into the stage total and the block-constant outputs
-  bool wrote_global = false;
-  if (tid < ncb) {
+  // the block total of each case goes to the signalling lane through the
+  // buffer's block-factor slot (read by nothing else once the block has
+  // streamed); the lane adds it to the stage total and the block-constant
+  // outputs, so no consumer writes global memory here.  The window writes are
+  // ordered before the bulk unit reads them.
+  if (tid < kCaseLanes) {
     double t = 0.0;
     for (int i = 0; i < NW; ++i) t += s.red[tid * NW + i];
-    t *= s.bf[tid];
-    if (t != 0.0) {
-      wrote_global = true;
-      const int cs = cb0 + tid;
-      float* slab = a.msg + (int64_t)cb0 * a.msg_stride;
-      for (int pi = S.nin; pi < S.np; ++pi) {
-        const DevPort& P = s.port[pi];
-        if (P.K > 1) continue;
-        const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
-        atomicAdd(slab + (int64_t)(P.tab + key) * kCaseLanes + tid, (float)t);
-      }
-      atomicAdd(a.sums + (int64_t)cs * 2 * a.n_cliques + S.sum_slot, t);
-    }
+    s.bf[tid] = tid < ncb ? t : 0.0;
   }
-  // global additions visible GPU-wide before the item counts as done (the
-  // signalling lane's fence orders only what it wrote), and the window
-  // writes ordered before the bulk unit reads them
-  if (wrote_global) __threadfence();
   fence_proxy_async();
   consumer_sync<NT>();
   if (tid == 0) {
@@ -623,12 +613,13 @@ __global__ void __launch_bounds__(NT + kControlThreads, 1) k_propagate_cl(const 
     fence_mbar_init();
   }
   __syncthreads();
+  if (a.span != nullptr && threadIdx.x == 0) atomicMin(a.span, (unsigned long long)global_ns());
   if (threadIdx.x >= NT) {
     const int cw = (threadIdx.x - NT) >> 5, l = threadIdx.x & 31;
     if (cw == 0) {
       if (l == 0) producer<float>(a, s);
     } else if (cw == 1) {
-      if (l == 0) signaller_cl(a, s);
+      signaller_cl(a, s);
     } else {
       prep_cl(a, s);
     }
@@ -637,6 +628,7 @@ __global__ void __launch_bounds__(NT + kControlThreads, 1) k_propagate_cl(const 
     consumer_cl(a, s);
   }
   __syncthreads();
+  if (a.span != nullptr && threadIdx.x == 0) atomicMax(a.span + 1, (unsigned long long)global_ns());
 }
 
 // Normalised marginals and log Z(e) of the cases of a slab (blockIdx.y),

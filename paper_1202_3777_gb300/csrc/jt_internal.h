@@ -204,6 +204,7 @@ struct PropArgs {
   T* calib;                     // [max_cases][calib_stride] calibrated tables, or null
   int64_t calib_stride;
   uint64_t* trace;              // [n_items][kTraceSlots] item timeline, or null
+  unsigned long long* span;     // [2]: first CTA start, last CTA end (global timer, ns), or null
   // shared-memory plan
   int32_t ring;                 // bulk-copy stages
   int32_t chunk;                // entries per stage

@@ -1029,6 +1029,7 @@ __global__ void __launch_bounds__(consumers_for(CB) + kControlThreads, ctas_per_
     fence_mbar_init();
   }
   __syncthreads();
+  if (a.span != nullptr && threadIdx.x == 0) atomicMin(a.span, (unsigned long long)global_ns());
   if (threadIdx.x >= NT) {
     // control warps: each role has a warp of its own, so no role's waits
     // (a blocking bulk-group wait, a sleeping poll) hold up another
@@ -1045,6 +1046,7 @@ __global__ void __launch_bounds__(consumers_for(CB) + kControlThreads, ctas_per_
     consumer<T, CB>(a, s);
   }
   __syncthreads();
+  if (a.span != nullptr && threadIdx.x == 0) atomicMax(a.span + 1, (unsigned long long)global_ns());
 }
 
 // Normalised marginals (a warp per variable, binned from its source table)

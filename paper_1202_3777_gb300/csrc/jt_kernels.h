@@ -23,6 +23,7 @@ __host__ __device__ constexpr int chunk_bytes_for(int cb) { return cb > 1 ? 8192
 // column of case-minor windows ([key][case]) and message slabs, with no
 // cross-lane reduction.
 constexpr int kCaseLanes = 32;
+constexpr int kClPortBytes = 448;               // bytes of one port's key tables (CLPort, below)
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
 constexpr int kControlThreads = 96;             // producer, signalling and preparation warps
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
@@ -33,10 +34,11 @@ __host__ __device__ inline int32_t desc_bytes(int k, int np, int nf) {
          k * (int32_t)sizeof(DevPos);
 }
 // Bytes of a fast-path stage's live ports and key tables.
-// (one-case schedules carry them in the blob; case-block schedules compute
-// them per item into shared memory, which leaves their hot loop's registers
-// as they are)
+// (one-case and case-lane schedules carry them in the blob; case-block
+// schedules compute them per item into shared memory, which leaves their hot
+// loop's registers as they are)
 __host__ __device__ inline int32_t table_bytes(int cb, int n_live) {
+  if (cb == kCaseLanes) return n_live * kClPortBytes;
   return cb == 1 ? n_live * (32 + kMaxIter * 4 + consumers_for(cb) * 2) : 0;
 }
 
@@ -77,14 +79,15 @@ struct SmemLayout {
   }
 };
 
-// Per-item key tables of one port of a case-lane item, in shared memory.  A
-// consumer warp w streams, from each chunk ci of the block, the slice
+// Key tables of one port of a case-lane stage, built by the planner and
+// carried in the stage's descriptor blob (CLPort[n_live] at live_off).  A
+// consumer warp w streams, from each chunk ci of a block, the slice
 // [w * kClSlice, (w + 1) * kClSlice) in tiles t of 32 entries, so an entry's
 // block offset is o = ci * chunk + w * kClSlice + 32 t + 4 v + j and (power-of-
 // two digits are bit fields) its key is the sum of the keys of those parts.
-// Every table holds byte offsets into the case-minor window (key * 128), the
-// chunk table also the window's start, so a lane's address is a sum of table
-// entries plus lane * 4.
+// Every table holds byte offsets into the case-minor windows (key * 128), the
+// chunk table also the port's window start, so a lane's address is the item
+// buffer's window base plus a sum of table entries plus lane * 4.
 constexpr int kClSlice = 128;                   // entries of a warp's slice of one chunk
 constexpr int kClTiles = kClSlice / 32;         // tiles of 32 entries per slice
 constexpr int kClMaxChunks = 32;                // chunks of one block (blocks <= 2^16 entries)
@@ -95,21 +98,23 @@ struct CLPort {
   int32_t dvec[4];               // key(j) * row, j < 4 (entries of a vector)
   int32_t kvec[8];               // key(4 v) * row, v < 8 (vectors of a tile)
   int32_t kslot[16 * kClTiles];  // key(w * kClSlice + 32 t) * row, slot w * kClTiles + t
-  int32_t kchunk[kClMaxChunks];  // window start + key(ci * chunk) * row (shared-space address)
+  int32_t kchunk[kClMaxChunks];  // port window start + key(ci * chunk) * row (bytes from the buffer's windows)
 };
 constexpr int32_t kClInput = 1;
 constexpr int32_t kClTile = 0;      // key constant over a tile of 32 entries
 constexpr int32_t kClVector = 2;    // key constant over each vector of 4 entries
 constexpr int32_t kClEntry = 4;     // key changes within a vector
-static_assert(sizeof(CLPort) % 16 == 0, "case-lane port table");
+constexpr int32_t kClIdent = 8;     // with kClEntry: the tile's keys are key + e, e < 32 (consecutive rows)
+static_assert(sizeof(CLPort) == kClPortBytes && sizeof(CLPort) % 16 == 0, "case-lane port table");
 
 // Dynamic shared memory of a case-lane propagation CTA (host and device
-// carve it alike): barriers, item slots, descriptor blobs, then per buffer
-// the evidence masks (V, M per case), the block factor per case and the
-// case-minor windows, then the per-item port tables, the warps' partial
-// totals and the bulk-copy ring.
+// carve it alike): barriers, item slots, descriptor blobs (with the port
+// tables), then per buffer the evidence masks (V, M per case) and the block
+// factor per case (which carries the block totals to the signalling lane
+// once the block has streamed), the warps' partial totals, the case-minor
+// windows per buffer, and the bulk-copy ring.
 struct SmemLayoutCL {
-  int32_t bar, info, sig, blob, blob_bytes, ev, bf, misc, ports, red, win, ring, bytes;
+  int32_t bar, info, sig, blob, blob_bytes, ev, bf, misc, red, win, ring, bytes;
 
   __host__ __device__ static int32_t a16(int32_t x) { return (x + 15) & ~15; }
 
@@ -123,7 +128,6 @@ struct SmemLayoutCL {
     ev = a16(o);     o = ev + 2 * kCaseLanes * 16;             // per buffer, per case: V, M, -, -
     bf = a16(o);     o = bf + 2 * kCaseLanes * 8;              // per buffer, per case: block factor
     misc = a16(o);   o = misc + 16 * 4;
-    ports = a16(o);  o = ports + kMaxFastPorts * (int32_t)sizeof(CLPort);
     red = a16(o);    o = red + kCaseLanes * 16 * 8;            // per case, per warp: partial totals
     win = (o + 127) & ~127;  o = win + 2 * win_max * kClRow;
     ring = (o + 127) & ~127; o = ring + ring_n * chunk * 4;

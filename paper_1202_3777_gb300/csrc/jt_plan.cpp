@@ -680,6 +680,41 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       }
       S.live_off = desc_bytes(S.k, S.np, S.nf);
     }
+    // case-lane schedules: per port the class of its key over a tile of 32
+    // entries and the key tables of the parts of a block offset (CLPort)
+    std::vector<CLPort> clp;
+    if (S.bits >= 0 && cb == kCaseLanes) {
+      const int CH = s->chunk;
+      if ((S.B + CH - 1) / CH > kClMaxChunks) {
+        *err = "case-lane block longer than the chunk table";
+        return JT_ERR_UNSUPPORTED;
+      }
+      for (int li = 0; li < S.n_live; ++li) {
+        const DevPort& P = s->ports[S.port0 + live[li].port];
+        const DevField* f = &s->fields[S.field0 + P.f0];
+        auto key = [&](uint32_t x) {
+          uint32_t k = 0;
+          for (int q = 0; q < P.nf; ++q) k += ((x >> f[q].sh) & ((1u << f[q].lb) - 1u)) * (uint32_t)f[q].w;
+          return k;
+        };
+        CLPort C{};
+        const bool edep = key(1) != 0 || key(2) != 0;
+        const bool vdep = key(4) != 0 || key(8) != 0 || key(16) != 0;
+        bool ident = edep;
+        for (uint32_t x = 1; ident && x < 32u; x <<= 1) ident = key(x) == x;
+        C.cls = (live[li].port < S.nin ? kClInput : 0) | (edep ? kClEntry : (vdep ? kClVector : kClTile)) |
+                (ident ? kClIdent : 0);
+        for (int j = 0; j < 4; ++j) C.dvec[j] = (int32_t)(key((uint32_t)j) * kClRow);
+        for (int v = 0; v < 8; ++v) C.kvec[v] = (int32_t)(key(4u * (uint32_t)v) * kClRow);
+        for (int w = 0; w < 16; ++w)
+          for (int t = 0; t < kClTiles; ++t)
+            C.kslot[w * kClTiles + t] = (int32_t)(key((uint32_t)(w * kClSlice + 32 * t)) * kClRow);
+        for (int ci = 0; ci < kClMaxChunks; ++ci)
+          C.kchunk[ci] = (int32_t)((uint32_t)P.win * kClRow + key((uint32_t)(ci * CH)) * kClRow);
+        clp.push_back(C);
+      }
+      S.live_off = desc_bytes(S.k, S.np, S.nf);
+    }
     blob_at[st] = (int32_t)s->blobs.size();
     auto put = [&](const void* src, size_t bytes) {
       const unsigned char* q = static_cast<const unsigned char*>(src);
@@ -693,13 +728,14 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
     if (S.np) put(&s->ports[S.port0], S.np * sizeof(DevPort));
     if (S.nf) put(&s->fields[S.field0], S.nf * sizeof(DevField));
     put(&s->pos[S.pos0], S.k * sizeof(DevPos));
+    if (!clp.empty()) put(clp.data(), clp.size() * sizeof(CLPort));
     if (S.n_live && cb == 1) {
       put(live.data(), live.size() * sizeof(LivePort));
       put(kit.data(), kit.size() * sizeof(int32_t));     // padded to 16 bytes
       put(ktab.data(), ktab.size() * sizeof(uint16_t));
     }
     blob_len[st] = (int32_t)((s->blobs.size() - blob_at[st]) * sizeof(uint4));
-    if (S.n_live && cb == 1 && blob_len[st] != S.live_off + table_bytes(cb, S.n_live)) {
+    if (S.n_live && (cb == 1 || cb == kCaseLanes) && blob_len[st] != S.live_off + table_bytes(cb, S.n_live)) {
       *err = "stage blob layout mismatch";
       return JT_ERR_UNSUPPORTED;
     }

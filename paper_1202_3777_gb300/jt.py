@@ -105,6 +105,8 @@ _sig = {
     "jt_get_potential": (C.c_int, [_vp, _i32, _vp]),
     "jt_get_info": (C.c_int, [_vp, C.POINTER(jt_tree_info)]),
     "jt_get_schedule": (C.c_int, [_vp, _i32, _i32, C.POINTER(jt_schedule_info)]),
+    "jt_propagate_ctas": (C.c_int, [_vp, _i32, _i32, _i32, _vp]),
+    "jt_get_kernel_span": (C.c_int, [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "jt_free": (None, [_vp]),
     "jt_strerror": (C.c_char_p, [C.c_int]),
     "jt_last_error": (C.c_char_p, []),
@@ -337,6 +339,20 @@ def jt_get_schedule(t: Tree, first_case: int, n_cases: int) -> dict:
     _check(_lib.jt_get_schedule(t.handle, first_case, n_cases, C.byref(info)), "jt_get_schedule")
     return {"case_block": info.case_block, "n_items": info.n_items, "grid": info.grid,
             "smem_bytes": info.smem_bytes, "window_entries": info.window_entries}
+
+
+def jt_propagate_ctas(t: Tree, first_case: int, n_cases: int, max_ctas: int, stream=None):
+    """jt_propagate holding at most max_ctas SMs (0: all), so propagations of
+    several trees on their own streams can run side by side."""
+    _check(_lib.jt_propagate_ctas(t.handle, first_case, n_cases, max_ctas, _stream(stream)), "jt_propagate_ctas")
+
+
+def jt_get_kernel_span(t: Tree):
+    """(start_ns, end_ns) of the tree's last propagation kernel on the GPU's
+    global timer."""
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(_lib.jt_get_kernel_span(t.handle, C.byref(a), C.byref(b)), "jt_get_kernel_span")
+    return int(a.value), int(b.value)
 
 
 def jt_free(t: Tree):

@@ -15,8 +15,9 @@ int main(void) {
       (any_fn)jt_log_evidence,     (any_fn)jt_get_marginals,      (any_fn)jt_get_log_evidence,
       (any_fn)jt_get_status,       (any_fn)jt_get_clique,         (any_fn)jt_get_clique_noalloc,
       (any_fn)jt_propagate_per_message, (any_fn)jt_init_from_cpts, (any_fn)jt_get_potential,
-      (any_fn)jt_get_info,         (any_fn)jt_get_schedule,       (any_fn)jt_free,
-      (any_fn)jt_strerror,         (any_fn)jt_last_error,
+      (any_fn)jt_get_info,         (any_fn)jt_get_schedule,       (any_fn)jt_propagate_ctas,
+      (any_fn)jt_get_kernel_span,  (any_fn)jt_free,               (any_fn)jt_strerror,
+      (any_fn)jt_last_error,
   };
   size_t i;
   for (i = 0; i < sizeof(entry) / sizeof(entry[0]); ++i)

@@ -48,7 +48,11 @@ def test_results_alone_equal_results_in_the_mix(mods):
         arrivals.append((t, serve.Query(qid, name, ev)))
     done = srv.run_arrivals(arrivals)
     assert len(done) == 80 and all(q.status == jt.JT_OK for q in done)
-    # several queries shared a batch (continuous batching happened)
+    # several queries shared a batch (continuous batching happened) ...
+    assert max(q.batch for q in done) > 1, [q.batch for q in done]
+    # ... and batches of different trees ran on the GPU at the same time
+    # (their propagation kernels' spans on the global timer intersect)
+    assert serve.overlapping_pairs(srv.spans) >= 1, srv.spans
     srv.free()
     alone = {n: jt.jt_load_synth(tr, compute=jt.JT_F32, max_cases=1) for n, tr in trees.items()}
     for q in sorted(done, key=lambda q: q.qid):
@@ -76,3 +80,30 @@ def test_latency_summary(mods):
     s = serve.latency_summary(qs, {"a": 1000})
     assert abs(s["p50_ms"] - 50.5) < 1e-6 and abs(s["p99_ms"] - 99.01) < 1e-6
     assert abs(s["clique_entries_per_s"] - 1000 * 100 / 0.1) < 1e-3
+
+
+def test_capped_propagation_matches_full_grid(mods):
+    """jt_propagate_ctas on 1, 7 and 76 SMs gives the full-grid results (the
+    schedule's items are the same; fewer CTAs take them in the same queue
+    order), and each kernel's span on the global timer is reported."""
+    jt, serve = mods
+    t = synth.large_clique_tree(seed=5, n_cliques=10, n_vars_per=8, card=4, max_depth=4).as_dtype(np.float32)
+    h = jt.jt_load_synth(t, compute=jt.JT_F32, max_cases=16)
+    jt.jt_set_evidence_dense(h, 0, synth.evidence_matrix(t, 16, 0.1, 31))
+    jt.jt_propagate(h, 0, 16)
+    lz0, m0 = jt.jt_get_log_evidence(h, 0, 16), jt.jt_get_marginals(h, 0, 16)
+    s0, e0 = jt.jt_get_kernel_span(h)
+    assert e0 > s0
+    for cap in (1, 7, 76):
+        jt.jt_propagate_ctas(h, 0, 16, cap)
+        assert np.all(jt.jt_get_status(h, 0, 16) == jt.JT_OK)
+        lz, m = jt.jt_get_log_evidence(h, 0, 16), jt.jt_get_marginals(h, 0, 16)
+        assert np.all(np.abs(lz - lz0) <= 1e-5 * np.maximum(1.0, np.abs(lz0)))
+        for i in range(16):
+            assert marg_errors(split_marginals(m[i], t.card), split_marginals(m0[i], t.card), "f32") <= 1e-5
+        s, e = jt.jt_get_kernel_span(h)
+        assert e > s > e0
+    with pytest.raises(jt.JtError) as err:
+        jt.jt_propagate_ctas(h, 0, 16, -1)
+    assert err.value.status == jt.JT_ERR_INVALID_ARG
+    h.free()
