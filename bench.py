@@ -627,7 +627,7 @@ def measure_latency(jt, torch, steps=50):
         torch.cuda.synchronize()
         assert jt.jt_get_status(h, 0, 1)[0] == jt.JT_OK
         out[key] = {"workload": tree.name, "us_per_propagation": 1e3 * s0.elapsed_time(s1) / steps,
-                    "cliques": tree.n_cliques, "depth": int(h.info.depth)}
+                    "cliques": tree.n_cliques, "depth": int(h.info.depth), "schedule": jt.jt_get_schedule(h, 0, 1)}
         h.free()
     return out
 

@@ -289,12 +289,16 @@ jt_status jt_get_info(jt_tree t, jt_tree_info* out);
  * persistent launch over work items).  JT_ERR_STATE if the range has not been
  * propagated yet; JT_ERR_INVALID_ARG for a bad range or a null `out`. */
 typedef struct {
-  int32_t case_block;   /* evidence cases per work item: 1, 4, 8, or 32 (one case per lane) */
+  int32_t case_block;   /* evidence cases per work item: 1, 4, 8, or 32 (one case per lane); 0: the whole
+                           tree per CTA (a case is one CTA's work, from its shared memory) */
   int32_t n_items;      /* work items of one propagation */
   int32_t grid;         /* CTAs of the persistent launch */
   int32_t smem_bytes;   /* dynamic shared memory per CTA */
   int32_t window_entries; /* largest per-case window set of a work item */
   int32_t reserved[3];
+  float candidate_ms[5];  /* device time of one propagation of the range with 32, 8, 4 and 1 cases per
+                             work item and with the whole tree per CTA, as the first use timed them
+                             (-1: not timed or not applicable) */
 } jt_schedule_info;
 
 jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info* out);

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libjt.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["jt_kernels.cu", "jt_caselanes.cu", "jt_permsg.cu", "jt_init.cu", "jt_plan.cpp", "jt_capi.cpp"]
+SOURCES = ["jt_kernels.cu", "jt_caselanes.cu", "jt_small.cu", "jt_permsg.cu", "jt_init.cu", "jt_plan.cpp", "jt_capi.cpp"]
 
 
 def _nvcc() -> str:

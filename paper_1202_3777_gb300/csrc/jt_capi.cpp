@@ -60,6 +60,15 @@ struct GraphEntry {
   int32_t grid = 0, smem = 0;
   uint64_t wait_ns = 2000000000ull;  // limit of the kernel's bounded waits
   cudaEvent_t done = nullptr;   // recorded after every launch of the graph
+  float candidate_ms[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};   // first-use timing of widths 32, 8, 4, 1, whole tree
+  // whole-tree schedules: the level plan on the device
+  const uint4* small_blobs = nullptr;
+  const int32_t* lv_blob_off = nullptr;
+  const int32_t* stage_blob = nullptr;
+  const int2* segs = nullptr;
+  const int32_t* seg_lv = nullptr;
+  const int32_t* lv_stage = nullptr;
+  const int32_t* lv_stage_off = nullptr;
 };
 
 // State of the paper-literal per-message propagation (jt_propagate_per_message),
@@ -242,7 +251,33 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   a.win_max = sc.win_max;
   a.blob_max = sc.blob_max;
   if (ev) chk(cudaEventRecord(ev[0], s));
-  if constexpr (std::is_same<T, float>::value) {
+  if (sc.cb == kWholeTree) {
+    SmallArgs<T> w{};
+    w.base = (const T*)t->base;
+    w.blobs = ge.small_blobs;
+    w.lv_blob_off = ge.lv_blob_off;
+    w.lv_blob_max = sc.small.lv_blob_max;
+    w.stage_blob = ge.stage_blob;
+    w.segs = ge.segs;
+    w.seg_lv = ge.seg_lv;
+    w.lv_stage = ge.lv_stage;
+    w.lv_stage_off = ge.lv_stage_off;
+    w.levels = sc.small.levels;
+    w.ev = t->d_ev;
+    w.n_vars = p.n_vars;
+    w.msg = (T*)t->d_msg;
+    w.msg_stride = p.msg_stride;
+    w.msg_total = p.msg_total;
+    w.sums = t->d_sums;
+    w.n_cliques = p.n_cliques;
+    w.status = t->d_status;
+    w.case0 = case0;
+    w.n_cases = n_cases;
+    w.span = t->d_span;
+    w.base_in_smem = sc.small.base_in_smem ? 1 : 0;
+    w.base_len = p.base_len;
+    chk(launch_small<T>(w, ge.grid, ge.smem, s));
+  } else if constexpr (std::is_same<T, float>::value) {
     if (sc.cb == kCaseLanes) chk(launch_propagate_cl(a, ge.grid, ge.smem, s));
     else chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
   } else {
@@ -281,7 +316,9 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cu
   std::string err;
   const int smem_cap = smem_budget(t->device, ctas_per_sm_for(cb)) - 256;
   const int sms = cap > 0 ? std::min(cap, t->n_sm) : t->n_sm;   // the SMs this propagation may hold
-  jt_status st = build_schedule(t->plan, (int)t->elem, cb, n_cases, sms, smem_cap, &ge->sched, &err);
+  jt_status st = cb == kWholeTree
+                     ? build_small_schedule(t->plan, (int)t->elem, n_cases, sms, smem_cap, &ge->sched, &err)
+                     : build_schedule(t->plan, (int)t->elem, cb, n_cases, sms, smem_cap, &ge->sched, &err);
   if (st != JT_OK) return fail(st, err);
   // Failure-path hooks, read when a range's graph is recorded (host-side
   // fault injection: nothing on the device faults or waits without limit).
@@ -305,6 +342,21 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cu
   if ((st = upload_vec(t, &ge->dev_bufs, &ge->items, sc.items, "schedule upload")) != JT_OK) return st;
   ge->smem = prop_smem_bytes(sc, (int)t->elem);
   ge->grid = (int32_t)std::min<int64_t>((int64_t)sc.items.size(), (int64_t)sms * ctas_per_sm_for(cb));
+  if (cb == kWholeTree) {
+    const auto& sp = sc.small;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->small_blobs, sp.blobs, "schedule upload")) != JT_OK) return st;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->lv_blob_off, sp.lv_blob_off, "schedule upload")) != JT_OK) return st;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->stage_blob, sp.stage_blob, "schedule upload")) != JT_OK) return st;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->segs, sp.segs, "schedule upload")) != JT_OK) return st;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->seg_lv, sp.seg_lv, "schedule upload")) != JT_OK) return st;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->lv_stage, sp.lv_stage, "schedule upload")) != JT_OK) return st;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->lv_stage_off, sp.lv_stage_off, "schedule upload")) != JT_OK)
+      return st;
+    ge->smem = sp.smem;
+    // every case is one CTA's work; a few CTAs per SM share its shared memory
+    const int per_sm = std::max(1, std::min(4, smem_budget(t->device, 1) / std::max(1, sp.smem)));
+    ge->grid = (int32_t)std::min<int64_t>(n_cases, (int64_t)sms * per_sm);
+  }
   if (const char* dbg = std::getenv("JT_DEBUG_PLAN"); dbg && *dbg == '1') {
     std::fprintf(stderr, "[jt plan] cases=%d cb=%d n_cb=%d items=%zu grid=%d smem=%d ring=%d win_max=%d\n", n_cases,
                  sc.cb, sc.n_cb, sc.items.size(), ge->grid, ge->smem, sc.ring, sc.win_max);
@@ -374,29 +426,33 @@ jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphE
         if (kv.second.done) CU(cudaEventSynchronize(kv.second.done), "graph cache eviction");
       free_graphs(t);
     }
-    int forced = 0;
+    int forced = -1;
     if (const char* f = std::getenv("JT_CASE_BLOCK"); f && *f) {
       const std::string v(f);
-      if (v == "1" || v == "4" || v == "8" || v == "32") forced = std::stoi(v);
+      if (v == "0" || v == "1" || v == "4" || v == "8" || v == "32") forced = std::stoi(v);
     }
     auto record = [&](int cb, GraphEntry* ge) {
       return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, cap, t->cap_stream, ge)
                                   : record_schedule<float>(t, first, n, cb, cap, t->cap_stream, ge);
     };
     std::vector<int> cands;
-    if (n == 1) {
-      cands = {1};
+    if (forced == kWholeTree) {
+      cands = {kWholeTree, n == 1 ? 1 : kCaseBlock};  // the first one the tree supports
+    } else if (n == 1) {
+      cands = forced == 1 ? std::vector<int>{1} : std::vector<int>{kWholeTree, 1};
     } else if (forced == kCaseLanes) {
-      cands = {kCaseLanes, kCaseBlock};  // the first one the tree supports
-    } else if (forced) {
+      cands = {kCaseLanes, kCaseBlock};
+    } else if (forced > 0) {
       cands = {forced};
     } else {
+      cands.push_back(kWholeTree);
       if (t->compute == JT_F32 && n >= 16) cands.push_back(kCaseLanes);
       cands.push_back(kCaseBlock);
       if (n > 4) cands.push_back(4);
       cands.push_back(1);
     }
-    const bool timed = n > 1 && !forced;
+    const bool timed_choice = forced < 0;
+    float timed[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};
     GraphEntry best;
     bool have = false;
     float best_ms = -1.f;
@@ -415,13 +471,14 @@ jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphE
         }
         continue;
       }
-      if (!timed) {
+      if (!timed_choice) {
         std::swap(best, ge);
         have = true;
         break;
       }
       time_graph(ge, s);
       const float ms = time_graph(ge, s);
+      timed[cb == kCaseLanes ? 0 : cb == kCaseBlock ? 1 : cb == 4 ? 2 : cb == 1 ? 3 : 4] = ms;
       if (!have || (ms >= 0.f && (best_ms < 0.f || ms < best_ms))) {
         std::swap(best, ge);
         best_ms = ms;
@@ -431,6 +488,7 @@ jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphE
     }
     if (!have) return fail(first_err == JT_OK ? JT_ERR_CUDA : first_err, first_msg);
     CU(cudaEventCreateWithFlags(&best.done, cudaEventDisableTiming), "event");
+    std::copy(timed, timed + 5, best.candidate_ms);
     it = t->graphs.emplace(key, std::move(best)).first;
   }
   *out = &it->second;
@@ -1164,6 +1222,7 @@ jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info*
   out->grid = ge.grid;
   out->smem_bytes = ge.smem;
   out->window_entries = ge.sched.win_max;
+  std::copy(ge.candidate_ms, ge.candidate_ms + 5, out->candidate_ms);
   return JT_OK;
 }
 

@@ -290,12 +290,68 @@ struct Schedule {
   int32_t max_k = 1, max_ports = 1, max_fields = 1, win_max = 1;
   int32_t blob_max = 16;                    // bytes of the largest stage blob
   int64_t streamed_entries = 0;             // entries streamed per case block (all stages)
+  // whole-tree schedules (cb == kWholeTree): one CTA propagates one case at a
+  // time, level by level (see SmallPlan)
+  struct SmallPlan {
+    std::vector<uint4> blobs;               // each level's stage descriptors (DevStage, ports, fields,
+                                            // positions), level after level
+    std::vector<int32_t> lv_blob_off;       // [levels + 1] first 16-byte unit of each level's descriptors
+    int32_t lv_blob_max = 0;                // 16-byte units of the largest level
+    std::vector<int32_t> stage_blob;        // [2 n_cliques] a stage's descriptors within its level's
+                                            // (16-byte units), -1: empty
+    std::vector<int2> segs;                 // (stage, first entry) of every segment, level by level
+    std::vector<int32_t> seg_lv;            // [levels + 1] first segment of each level
+    std::vector<int32_t> lv_stage;          // the stages of each level
+    std::vector<int32_t> lv_stage_off;      // [levels + 1]
+    int32_t levels = 0;
+    int32_t smem = 0;                       // dynamic shared memory of one CTA
+    bool base_in_smem = false;              // the clique tables fit beside the rest: staged once per CTA
+  } small;
 };
+
+// Cases per work item of a whole-tree schedule (reported as 0): every case
+// of the range is one work item, propagated by one CTA from its shared memory.
+constexpr int kWholeTree = 0;
+constexpr int kSmallSeg = 256;              // entries of one segment (a warp's share of a clique)
 
 // Plan the schedule for `n_cases` cases in blocks of `cb` on a device with
 // `n_sm` SMs and `smem_bytes` of dynamic shared memory per CTA.
 jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm, int smem_bytes,
                          Schedule* s, std::string* err);
+
+// Plan a whole-tree schedule (one CTA per case): the one-case stage
+// descriptors plus the level-ordered segment list.  JT_ERR_UNSUPPORTED when
+// the tree's per-case state does not fit one CTA's shared memory or the tree
+// is too large for one CTA to propagate efficiently.
+jt_status build_small_schedule(const Plan& p, int elem, int n_cases, int n_sm, int smem_bytes, Schedule* s,
+                               std::string* err);
+
+// Arguments of the whole-tree propagation kernel.
+template <typename T>
+struct SmallArgs {
+  const T* base;                // permuted clique tables
+  const uint4* blobs;           // level-ordered stage descriptors
+  const int32_t* lv_blob_off;   // [levels + 1]
+  int32_t lv_blob_max;          // 16-byte units of the largest level (its shared-memory staging)
+  const int32_t* stage_blob;    // [2 n_cliques] within the level's descriptors
+  const int2* segs;
+  const int32_t* seg_lv;        // [levels + 1]
+  const int32_t* lv_stage;
+  const int32_t* lv_stage_off;  // [levels + 1]
+  int32_t levels;
+  const int16_t* ev;            // [max_cases][n_vars], -1 = unobserved
+  int32_t n_vars;
+  T* msg;                       // [max_cases][msg_stride]: u | delta | joint
+  int64_t msg_stride;
+  int32_t msg_total;            // entries of the collect (and of the distribute) messages
+  double* sums;                 // [max_cases][2 n_cliques]
+  int32_t n_cliques;
+  int32_t* status;
+  int32_t case0, n_cases;
+  unsigned long long* span;     // [2] kernel span (global timer), or null
+  int32_t base_in_smem;         // copy the clique tables into shared memory once per CTA
+  int64_t base_len;             // elements of the clique tables (a multiple of 32)
+};
 
 // Dynamic shared memory of the propagation kernel for a schedule.
 int32_t prop_smem_bytes(const Schedule& s, int elem);

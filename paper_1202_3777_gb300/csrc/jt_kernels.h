@@ -144,6 +144,13 @@ cudaError_t launch_propagate(const PropArgs<T>& a, int cb, int grid, int smem, c
 template <typename T>
 cudaError_t launch_finalize(const FinalArgs<T>& a, cudaStream_t s);
 
+// Whole-tree schedules: one CTA per case (at a time), the case's messages in
+// shared memory; the dynamic shared memory one CTA needs.
+int32_t small_smem_bytes(int64_t msg_stride, int32_t msg_total, int32_t n_cliques, int32_t n_vars, int elem,
+                         int32_t lv_blob_max);
+template <typename T>
+cudaError_t launch_small(const SmallArgs<T>& a, int grid, int smem, cudaStream_t s);
+
 // Case-lane schedules (FP32): the persistent propagation over message slabs
 // of kCaseLanes interleaved cases, and its finalisation.
 cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, cudaStream_t s);

@@ -822,6 +822,101 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
   return JT_OK;
 }
 
+int32_t small_smem_bytes(int64_t msg_stride, int32_t msg_total, int32_t n_cliques, int32_t n_vars, int elem,
+                         int32_t lv_blob_max) {
+  // messages and ratios (element type), then stage totals and scales (FP64),
+  // then the case's evidence row (int16), then one level's descriptors, as
+  // the whole-tree kernel carves it
+  const int64_t b = (((msg_stride + msg_total) * elem + 15) & ~int64_t(15)) + ((24ll * n_cliques + 15) & ~int64_t(15)) +
+                    ((2ll * n_vars + 15) & ~int64_t(15)) + 16ll * lv_blob_max;
+  return (int32_t)std::min<int64_t>(b + 16, INT32_MAX);
+}
+
+jt_status build_small_schedule(const Plan& p, int elem, int n_cases, int n_sm, int smem_bytes, Schedule* s,
+                               std::string* err) {
+  // one CTA streams every entry of the tree per case: worth it for trees of
+  // up to a few hundred thousand entries (beyond, the persistent schedules
+  // spread one case over many SMs)
+  constexpr int64_t kSmallMaxEntries = 1 << 17;
+  if (p.entries > kSmallMaxEntries) {
+    *err = "tree too large for one CTA per case";
+    return JT_ERR_UNSUPPORTED;
+  }
+  jt_status st = build_schedule(p, elem, 1, 1, n_sm, smem_bytes, s, err);
+  if (st != JT_OK) return st;
+  const int nc = p.n_cliques;
+  s->cb = kWholeTree;
+  s->n_cb = 1;
+  Schedule::SmallPlan& sp = s->small;
+  sp = Schedule::SmallPlan{};
+  sp.stage_blob.assign(2 * nc, -1);
+  // each stage's compact descriptors (no per-thread key tables), laid out
+  // level by level so that one copy brings a level's into shared memory
+  auto put = [&](const void* src, size_t bytes) {
+    const unsigned char* q = static_cast<const unsigned char*>(src);
+    for (size_t i = 0; i < bytes; i += sizeof(uint4)) {
+      uint4 u{};
+      std::memcpy(&u, q + i, std::min(sizeof(uint4), bytes - i));
+      sp.blobs.push_back(u);
+    }
+  };
+  // a level whose descriptors exceed the staging budget runs as several
+  // consecutive groups (its stages are independent of one another)
+  constexpr int32_t kStageUnits = 32768 / 16;
+  auto level = [&](const std::vector<int32_t>& stages) {
+    int32_t l0 = (int32_t)sp.blobs.size();
+    auto close = [&]() {
+      sp.lv_blob_max = std::max<int32_t>(sp.lv_blob_max, (int32_t)sp.blobs.size() - l0);
+      sp.lv_blob_off.push_back((int32_t)sp.blobs.size());
+      sp.seg_lv.push_back((int32_t)sp.segs.size());
+      sp.lv_stage_off.push_back((int32_t)sp.lv_stage.size());
+      ++sp.levels;
+      l0 = (int32_t)sp.blobs.size();
+    };
+    for (int stg : stages) {
+      const DevStage& S = s->stages[stg];
+      if (S.n_blocks == 0) continue;
+      const int32_t units = (desc_bytes(S.k, S.np, S.nf) + 15) / 16;
+      if ((int32_t)sp.blobs.size() - l0 + units > kStageUnits && (int32_t)sp.blobs.size() > l0) close();
+      sp.lv_stage.push_back(stg);
+      sp.stage_blob[stg] = (int32_t)sp.blobs.size() - l0;
+      DevStage C = S;
+      C.live_off = 0;
+      C.n_live = C.n_in_live = 0;
+      put(&C, sizeof(DevStage));
+      if (S.np) put(&s->ports[S.port0], S.np * sizeof(DevPort));
+      if (S.nf) put(&s->fields[S.field0], S.nf * sizeof(DevField));
+      put(&s->pos[S.pos0], S.k * sizeof(DevPos));
+      for (int e = 0; e < S.n; e += kSmallSeg) sp.segs.push_back(int2{stg, e});
+    }
+    close();
+  };
+  sp.lv_blob_off.push_back(0);
+  sp.seg_lv.push_back(0);
+  sp.lv_stage_off.push_back(0);
+  for (int d = p.max_depth; d >= 1; --d) level(p.levels[d]);          // collect: deepest level first
+  for (int d = 0; d <= p.max_depth; ++d) {                           // distribute: from the root
+    std::vector<int32_t> v;
+    for (int c : p.levels[d]) v.push_back(nc + c);
+    level(v);
+  }
+  const int32_t need = small_smem_bytes(p.msg_stride, p.msg_total, p.n_cliques, p.n_vars, elem, sp.lv_blob_max);
+  if (need > smem_bytes) {
+    *err = "a case's messages and a level's descriptors do not fit one CTA's shared memory";
+    return JT_ERR_UNSUPPORTED;
+  }
+  sp.smem = need;
+  // the clique tables too, when they fit: every level then reads them from
+  // shared memory
+  const int64_t with_base = (int64_t)need + p.base_len * elem;
+  if (with_base <= smem_bytes) {
+    sp.base_in_smem = true;
+    sp.smem = (int32_t)with_base;
+  }
+  (void)n_cases;
+  return JT_OK;
+}
+
 int32_t prop_smem_bytes(const Schedule& s, int elem) {
   if (s.cb == kCaseLanes) return SmemLayoutCL(s.ring, s.chunk, s.blob_max, s.win_max).bytes;
   return SmemLayout(s.cb, s.ring, s.chunk, s.max_k, s.max_ports, s.blob_max, s.win_max, elem).bytes;

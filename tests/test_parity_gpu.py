@@ -24,12 +24,13 @@ def jt():
     return mod
 
 
-@pytest.fixture(params=["1", "4", "8", "32"])
+@pytest.fixture(params=["0", "1", "4", "8", "32"])
 def case_block(request, monkeypatch):
-    """Multi-case propagations pick one case per work item, blocks of 4 or 8,
-    or 32 cases on the lanes of a warp by timing them on first use; these
-    tests pin each schedule in turn so all stay covered (32 falls back to 8
-    on trees that case lanes do not apply to)."""
+    """Propagations pick one case per work item, blocks of 4 or 8, 32 cases
+    on the lanes of a warp, or the whole tree per CTA by timing them on
+    first use; these tests pin each schedule in turn so all stay covered (32
+    falls back to 8 on trees that case lanes do not apply to, 0 to 8 -- or to
+    one case per item for a single case -- on trees too large for one CTA)."""
     monkeypatch.setenv("JT_CASE_BLOCK", request.param)
     return int(request.param)
 

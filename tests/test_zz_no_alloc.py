@@ -92,3 +92,51 @@ def test_noalloc_rejects_tables_above_limit(env):
     assert e.value.status == jt.JT_ERR_UNSUPPORTED
     assert "4194304" in jt.jt_last_error()
     h.free()
+
+
+def test_noalloc_on_a_side_stream_is_ordered_with_propagations(env):
+    """A read-out on a stream of its own, issued right after a propagation
+    and followed at once by the next propagation (new evidence) on the
+    propagation's stream, with no host synchronisation in between, reads the
+    table of the first propagation: the read-out waits for the propagation
+    that wrote the table, and the next propagation waits for the read-out
+    before it rewrites it."""
+    jt, torch = env
+    tree = synth.large_clique_tree(seed=5, n_cliques=6, n_vars_per=8, card=4, max_depth=3)
+    tp, h = _materialised(jt, tree, "f32", 1)
+    clique = 3
+    n = int(tp.table_sizes()[clique])
+    ref1 = jt.jt_get_clique(h, 0, clique, n)
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    jt.jt_propagate(h, 0, 1, main)                      # same evidence: rewrites the same table
+    jt.jt_get_clique_noalloc(h, 0, clique, out, stream=side)
+    jt.jt_set_evidence(h, 0, *synth.random_evidence(tp, 5, 999))
+    jt.jt_propagate(h, 0, 1, main)                      # new evidence: a different table
+    side.synchronize()
+    assert marg_errors([out.cpu().numpy()], [ref1], "f32") <= TOL["f32"]
+    ref2 = jt.jt_get_clique(h, 0, clique, n)
+    assert np.max(np.abs(ref2 - ref1)) > 1e-6              # the second propagation did change it
+    h.free()
+
+
+def test_noalloc_allocates_no_device_memory(env):
+    """After a first call (which looks up the scratch array's address),
+    further read-outs change neither the device's free memory
+    (cudaMemGetInfo) nor the memory torch has allocated."""
+    jt, torch = env
+    tp, h = _materialised(jt, synth.small_tree(), "f64", 1)
+    n = int(tp.table_sizes()[5])
+    out = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    jt.jt_get_clique_noalloc(h, 0, 5, out, stream=stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for c in (5, 7, 5, 11):
+        jt.jt_get_clique_noalloc(h, 0, c, out, stream=stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    h.free()
