@@ -113,6 +113,7 @@ struct jt_tree_s {
   int64_t scratch_len = 0;
   VarSrc* d_vs = nullptr;         // marginal sources, joint layout 0 (one-case schedules)
   VarSrc* d_vs_fine = nullptr;    // joint layout 1 (case-block schedules)
+  VarSrc* d_vs_var = nullptr;     // joint layout 2 (case-lane schedules: a joint per private variable)
   int32_t* d_sep_size = nullptr;
   int64_t device_bytes = 0;
   // host state
@@ -161,7 +162,7 @@ void destroy(jt_tree t) {
   if (t->permsg)
     for (void* q : t->permsg->bufs) cudaFree(q);
   void* ptrs[] = {t->base,   t->d_msg,  t->d_sums,  t->d_done,    t->d_err, t->d_status, t->d_marg,
-                  t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_sep_size,
+                  t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_vs_var, t->d_sep_size,
                   t->d_span};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -285,7 +286,8 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   }
   if (ev) chk(cudaEventRecord(ev[1], s));
   FinalArgs<T> f{};
-  f.vs = sc.cb > 1 ? t->d_vs_fine : t->d_vs;  // the joint layout the schedule's ports write
+  // the joint layout the schedule's ports write
+  f.vs = sc.cb == kCaseLanes ? t->d_vs_var : (sc.cb > 1 ? t->d_vs_fine : t->d_vs);
   f.n_vars = p.n_vars;
   f.n_cliques = p.n_cliques;
   f.case0 = case0;
@@ -927,6 +929,9 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   if (cudaMemset(raw->d_ev, 0xFF, nev * sizeof(int16_t)) != cudaSuccess) return bail(fail(JT_ERR_CUDA, "memset"));
   if ((st = alloc(raw, &raw->d_vs, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
   if (cudaMemcpy(raw->d_vs, p.vsrc[0].data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(JT_ERR_CUDA, "descriptor upload"));
+  if ((st = alloc(raw, &raw->d_vs_var, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
+  if (cudaMemcpy(raw->d_vs_var, p.vsrc[2].data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(JT_ERR_CUDA, "descriptor upload"));
   if ((st = alloc(raw, &raw->d_vs_fine, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
   if (cudaMemcpy(raw->d_vs_fine, p.vsrc[1].data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) !=

@@ -81,6 +81,47 @@ struct IdentRows<0> {
   __device__ __forceinline__ static void reduce(uint32_t, const float2 (&)[16]) {}
 };
 
+// Output reductions that first add up the values of a tile whose keys
+// coincide: VF holds the vector bits (tile-offset bits 2, 3, 4 as bits 0, 1,
+// 2) the port's key ignores, so vector v | u adds into vector v's rows for
+// every u inside VF, and only vectors outside VF reduce into the window --
+// 8 >> popcount(VF) of them instead of 8.  VF = 0 (no combining) is correct
+// for every port, so only the common patterns get their own instance: joint
+// ports over a variable on the lowest digit (VF = 7), and keys over a digit
+// on tile-offset bits 2-3 (VF = 4) or bit 4 (VF = 3).
+template <int VF>
+__device__ __forceinline__ void red_vectors(uint32_t at, uint32_t kv, const float (&vs)[8]) {
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    if (v & VF) continue;
+    float a = vs[v];
+#pragma unroll
+    for (int u = 1; u < 8; ++u)
+      if ((u & ~VF) == 0) a += vs[v | u];
+    sred_add(at + (uint32_t)sld_s32(kv + 4u * v), a);
+  }
+}
+template <int VF>
+__device__ __forceinline__ void red_entries(uint32_t at, uint32_t kv, const int4 dv, const float2 (&f)[16]) {
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    if (v & VF) continue;
+    float2 a = f[2 * v], b = f[2 * v + 1];
+#pragma unroll
+    for (int u = 1; u < 8; ++u)
+      if ((u & ~VF) == 0) {
+        a = add2(a, f[2 * (v | u)]);
+        b = add2(b, f[2 * (v | u) + 1]);
+      }
+    const uint32_t av = at + (uint32_t)sld_s32(kv + 4u * v);
+    sred_add(av + (uint32_t)dv.x, a.x);
+    sred_add(av + (uint32_t)dv.y, a.y);
+    sred_add(av + (uint32_t)dv.z, b.x);
+    sred_add(av + (uint32_t)dv.w, b.y);
+  }
+}
+
+
 // Shared-memory carve-up of a case-lane CTA.  The common fields serve the
 // producer; per buffer: `obs` holds (V, M) per case, `bf` the block factor per
 // case (then the block totals), `win` the case-minor windows.
@@ -465,25 +506,20 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
                             (uint32_t)sld_s32(pb + offsetof(CLPort, kslot) + 4u * (uint32_t)slot) + lane4;
         if (cls & kClIdent) {
           IdentRows<32>::reduce(at, f);
-        } else if (cls & kClEntry) {
-          const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
-          const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
-          const int4 dv = sld_v4s32(pb + offsetof(CLPort, dvec));
-          const int kv[8] = {kv0.x, kv0.y, kv0.z, kv0.w, kv1.x, kv1.y, kv1.z, kv1.w};
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const uint32_t av = at + (uint32_t)kv[v];
-            sred_add(av + (uint32_t)dv.x, f[2 * v].x);
-            sred_add(av + (uint32_t)dv.y, f[2 * v].y);
-            sred_add(av + (uint32_t)dv.z, f[2 * v + 1].x);
-            sred_add(av + (uint32_t)dv.w, f[2 * v + 1].y);
+        } else if (cls & (kClEntry | kClVector)) {
+          const uint32_t kv = pb + offsetof(CLPort, kvec);
+          const int vf = (~sld_s32(pb + offsetof(CLPort, dep)) >> 2) & 7;
+          if (cls & kClEntry) {
+            const int4 dv = sld_v4s32(pb + offsetof(CLPort, dvec));
+            if (vf == 7) red_entries<7>(at, kv, dv, f);
+            else if (vf == 4) red_entries<4>(at, kv, dv, f);
+            else red_entries<0>(at, kv, dv, f);
+          } else {
+            if (vf == 3) red_vectors<3>(at, kv, vs);
+            else if (vf == 4) red_vectors<4>(at, kv, vs);
+            else if (vf == 7) red_vectors<7>(at, kv, vs);
+            else red_vectors<0>(at, kv, vs);
           }
-        } else if (cls & kClVector) {
-          const int4 kv0 = sld_v4s32(pb + offsetof(CLPort, kvec));
-          const int4 kv1 = sld_v4s32(pb + offsetof(CLPort, kvec) + 16u);
-          const int kv[8] = {kv0.x, kv0.y, kv0.z, kv0.w, kv1.x, kv1.y, kv1.z, kv1.w};
-#pragma unroll
-          for (int v = 0; v < 8; ++v) sred_add(at + (uint32_t)kv[v], vs[v]);
         } else {
           sred_add(at, ts);
         }

@@ -246,21 +246,24 @@ struct Plan {
   std::vector<int32_t> sep_size, sep_off;   // root: a 1-entry slot
   int32_t msg_total = 0;                    // entries of all separator tables
   std::vector<int32_t> n_private;
-  // Private-variable joints, in two layouts, each a list of joints per clique
-  // over consecutive private positions.  Layout 0: one joint over all of a
-  // clique's private variables (one-case schedules accumulate it in
+  // Private-variable joints, in three layouts, each a list of joints per
+  // clique over consecutive private positions.  Layout 0: one joint over all
+  // of a clique's private variables (one-case schedules accumulate it in
   // registers).  Layout 1: joints of at most kFineJointEntries entries
   // (case-block schedules keep a window per case and joint in shared memory,
-  // so the windows must stay small for blocks to stay large).
+  // so the windows must stay small for blocks to stay large).  Layout 2: one
+  // joint per private variable -- its marginal is all the finalisation needs
+  // -- for case-lane schedules, whose reductions into a window cost per
+  // distinct key of a tile.
   struct JointGroup {
     int32_t off, size;                      // offset in the joint region, entries
     int32_t pos0, npos;                     // permuted positions [pos0, pos0 + npos)
   };
-  std::vector<std::vector<JointGroup>> joints[2];
+  std::vector<std::vector<JointGroup>> joints[3];
   int32_t joint_total = 0;                  // both layouts
   std::vector<int32_t> moff;                // per variable: offset of its marginal
   int32_t marg_total = 0;
-  std::vector<VarSrc> vsrc[2];              // per layout, per variable (offsets in a message row)
+  std::vector<VarSrc> vsrc[3];              // per layout, per variable (offsets in a message row)
   int64_t entries = 0, work_per_case = 0;
   int64_t msg_stride = 0;                   // u | delta | joint, padded
 };

@@ -94,7 +94,8 @@ constexpr int kClMaxChunks = 32;                // chunks of one block (blocks <
 constexpr int kClRow = 32 * 4;                  // bytes of one window row (one key, every case)
 struct CLPort {
   int32_t cls;                   // kClInput | kClTile, kClVector or kClEntry
-  int32_t pad[3];
+  int32_t dep;                   // bit b (b < 5): the key depends on bit b of a tile entry's offset
+  int32_t pad[2];
   int32_t dvec[4];               // key(j) * row, j < 4 (entries of a vector)
   int32_t kvec[8];               // key(4 v) * row, v < 8 (vectors of a tile)
   int32_t kslot[16 * kClTiles];  // key(w * kClSlice + 32 t) * row, slot w * kClTiles + t

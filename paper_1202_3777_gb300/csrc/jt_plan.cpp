@@ -196,7 +196,7 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
   // private joints, both layouts; a layout-1 joint grows from the least
   // significant private position up while it stays within kFineJointEntries
   int64_t jo = 0;
-  for (int L = 0; L < 2; ++L) {
+  for (int L = 0; L < 3; ++L) {
     p->joints[L].assign(nc, {});
     for (int c = 0; c < nc; ++c) {
       const int npv = p->n_private[c];
@@ -211,7 +211,7 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
       int64_t q = 1;
       for (int i = k - 1; i >= k - npv; --i) {
         const int64_t cq = p->card[pv[i]];
-        if (L == 1 && q > 1 && q * cq > kFineJointEntries) {
+        if ((L == 1 && q > 1 && q * cq > kFineJointEntries) || (L == 2 && q > 1)) {
           add(i + 1, hi, q);
           hi = i + 1;
           q = 1;
@@ -240,7 +240,7 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
       const int e = src_edge[v];
       if (e < 0 || p->sep_size[c] < p->sep_size[e]) src_edge[v] = c;
     }
-  for (int L = 0; L < 2; ++L) {
+  for (int L = 0; L < 3; ++L) {
     std::vector<VarSrc>& vs = p->vsrc[L];
     vs.assign(nv, VarSrc{});
     for (int v = 0; v < nv; ++v) {
@@ -411,7 +411,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       if (pass == 1) {
         for (int g : p.children[c])
           sp.push_back({kPortDelta, p.msg_total + p.sep_off[g], p.sep_size[g], g, -1, in_of(p.sep[g])});
-        for (const Plan::JointGroup& g : p.joints[cb > 1 ? 1 : 0][c]) {
+        for (const Plan::JointGroup& g : p.joints[cb == kCaseLanes ? 2 : (cb > 1 ? 1 : 0)][c]) {
           std::vector<char> in(k, 0);
           for (int i = g.pos0; i < g.pos0 + g.npos; ++i) in[i] = 1;
           sp.push_back({kPortJoint, 2 * p.msg_total + g.off, g.size, c, -1, in});
@@ -704,6 +704,9 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         for (uint32_t x = 1; ident && x < 32u; x <<= 1) ident = key(x) == x;
         C.cls = (live[li].port < S.nin ? kClInput : 0) | (edep ? kClEntry : (vdep ? kClVector : kClTile)) |
                 (ident ? kClIdent : 0);
+        C.dep = 0;
+        for (int b = 0; b < 5; ++b)
+          if (key(1u << b) != 0) C.dep |= 1 << b;
         for (int j = 0; j < 4; ++j) C.dvec[j] = (int32_t)(key((uint32_t)j) * kClRow);
         for (int v = 0; v < 8; ++v) C.kvec[v] = (int32_t)(key(4u * (uint32_t)v) * kClRow);
         for (int w = 0; w < 16; ++w)
