@@ -295,7 +295,10 @@ typedef struct {
   int32_t grid;         /* CTAs of the persistent launch */
   int32_t smem_bytes;   /* dynamic shared memory per CTA */
   int32_t window_entries; /* largest per-case window set of a work item */
-  int32_t reserved[3];
+  int32_t padded;       /* 1: the schedule runs over a copy of the tree with every cardinality raised to a
+                           power of two (the added states impossible: zero potential), which case lanes
+                           need; results are the original tree's */
+  int32_t reserved[2];
   float candidate_ms[5];  /* device time of one propagation of the range with 32, 8, 4 and 1 cases per
                              work item and with the whole tree per CTA, as the first use timed them
                              (-1: not timed or not applicable) */

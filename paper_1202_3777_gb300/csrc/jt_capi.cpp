@@ -61,6 +61,7 @@ struct GraphEntry {
   uint64_t wait_ns = 2000000000ull;  // limit of the kernel's bounded waits
   cudaEvent_t done = nullptr;   // recorded after every launch of the graph
   float candidate_ms[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};   // first-use timing of widths 32, 8, 4, 1, whole tree
+  bool padded = false;          // runs over the tree's power-of-two padded plan
   // whole-tree schedules: the level plan on the device
   const uint4* small_blobs = nullptr;
   const int32_t* lv_blob_off = nullptr;
@@ -130,6 +131,17 @@ struct jt_tree_s {
   std::map<std::tuple<int, int, int>, GraphEntry> graphs;   // (first case, cases, CTA cap; 0 = every SM)
   unsigned long long* d_span = nullptr;   // [2] global-timer span of the last propagation kernel
   std::unique_ptr<PerMsg> permsg;
+  // Power-of-two padded twin of the plan (FP32 trees with other
+  // cardinalities): its own resident tables, derived from `base` on the
+  // device, and its marginal sources and separator sizes; the case-lane
+  // schedules of such a tree run over it.
+  std::unique_ptr<Plan> pad;
+  float* pad_base = nullptr;
+  VarSrc* d_vs_pad = nullptr;
+  int32_t* d_sep_size_pad = nullptr;
+  int4* d_pad_digits = nullptr;
+  PadClique* d_pad_cliques = nullptr;
+  int64_t pad_max = 0;                  // largest padded table
 };
 
 namespace {
@@ -163,7 +175,7 @@ void destroy(jt_tree t) {
     for (void* q : t->permsg->bufs) cudaFree(q);
   void* ptrs[] = {t->base,   t->d_msg,  t->d_sums,  t->d_done,    t->d_err, t->d_status, t->d_marg,
                   t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_vs_var, t->d_sep_size,
-                  t->d_span};
+                  t->d_span, t->pad_base, t->d_vs_pad, t->d_sep_size_pad, t->d_pad_digits, t->d_pad_cliques};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->h_ev) cudaFreeHost(t->h_ev);
@@ -196,7 +208,7 @@ jt_status upload_vec(jt_tree t, std::vector<void*>* owner, const V** dst, const 
 template <typename T>
 cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry& ge, cudaStream_t s,
                              cudaEvent_t* ev, uint64_t* trace = nullptr) {
-  const Plan& p = t->plan;
+  const Plan& p = ge.padded ? *t->pad : t->plan;
   const Schedule& sc = ge.sched;
   cudaError_t err = cudaSuccess;
   auto chk = [&](cudaError_t e) {
@@ -216,7 +228,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   chk(cudaMemsetAsync(t->d_span, 0xFF, sizeof(unsigned long long), s));
   chk(cudaMemsetAsync(t->d_span + 1, 0, sizeof(unsigned long long), s));
   PropArgs<T> a{};
-  a.base = (const T*)t->base;
+  a.base = ge.padded ? (const T*)t->pad_base : (const T*)t->base;
   a.stages = ge.stages;
   a.ports = ge.ports;
   a.fields = ge.fields;
@@ -287,7 +299,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   if (ev) chk(cudaEventRecord(ev[1], s));
   FinalArgs<T> f{};
   // the joint layout the schedule's ports write
-  f.vs = sc.cb == kCaseLanes ? t->d_vs_var : (sc.cb > 1 ? t->d_vs_fine : t->d_vs);
+  f.vs = ge.padded ? t->d_vs_pad : sc.cb == kCaseLanes ? t->d_vs_var : (sc.cb > 1 ? t->d_vs_fine : t->d_vs);
   f.n_vars = p.n_vars;
   f.n_cliques = p.n_cliques;
   f.case0 = case0;
@@ -295,7 +307,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   f.msg = (const T*)t->d_msg;
   f.msg_stride = p.msg_stride;
   f.sums = t->d_sums;
-  f.sep_size = t->d_sep_size;
+  f.sep_size = ge.padded ? t->d_sep_size_pad : t->d_sep_size;
   f.status = t->d_status;
   f.marg_total = p.marg_total;
   f.marg_out = t->d_marg;
@@ -318,9 +330,12 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cu
   std::string err;
   const int smem_cap = smem_budget(t->device, ctas_per_sm_for(cb)) - 256;
   const int sms = cap > 0 ? std::min(cap, t->n_sm) : t->n_sm;   // the SMs this propagation may hold
+  // case lanes need power-of-two cliques: other trees run them padded
+  ge->padded = cb == kCaseLanes && t->pad != nullptr;
+  const Plan& plan = ge->padded ? *t->pad : t->plan;
   jt_status st = cb == kWholeTree
-                     ? build_small_schedule(t->plan, (int)t->elem, n_cases, sms, smem_cap, &ge->sched, &err)
-                     : build_schedule(t->plan, (int)t->elem, cb, n_cases, sms, smem_cap, &ge->sched, &err);
+                     ? build_small_schedule(plan, (int)t->elem, n_cases, sms, smem_cap, &ge->sched, &err)
+                     : build_schedule(plan, (int)t->elem, cb, n_cases, sms, smem_cap, &ge->sched, &err);
   if (st != JT_OK) return fail(st, err);
   // Failure-path hooks, read when a range's graph is recorded (host-side
   // fault injection: nothing on the device faults or waits without limit).
@@ -565,12 +580,48 @@ jt_status load_typed(jt_tree t, const jt_tree_desc* d, cudaStream_t s) {
   CU(cudaMemcpyAsync(t->base, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s), "table upload");
   // (case-lane schedules keep whole slabs of kCaseLanes cases: the last slab of
   // a range may reach past max_cases)
-  if ((st = alloc(t, (T**)&t->d_msg, p.msg_stride * (t->max_cases + kCaseLanes - 1), "per-case messages")) != JT_OK)
+  const int64_t msg_stride = std::max<int64_t>(p.msg_stride, t->pad ? t->pad->msg_stride : 0);
+  if ((st = alloc(t, (T**)&t->d_msg, msg_stride * (t->max_cases + kCaseLanes - 1), "per-case messages")) != JT_OK)
     return st;
   if (t->flags & JT_MATERIALIZE_CLIQUES) {
     if ((st = alloc(t, (T**)&t->d_calib, p.base_len * t->max_cases, "calibrated tables")) != JT_OK) return st;
   }
   CU(cudaStreamSynchronize(s), "table upload");
+  return JT_OK;
+}
+
+// A power-of-two padded twin pays where case lanes run (FP32, batches of
+// cases) on a tree with other cardinalities.  JT_PAD_CARDS=0 turns it off.
+bool want_pad(const Plan& p, const jt_tree_desc* d) {
+  if (d->compute != JT_F32 || (d->flags & JT_MATERIALIZE_CLIQUES) || d->max_cases < 16) return false;
+  if (const char* e = std::getenv("JT_PAD_CARDS"); e && *e == '0') return false;
+  return std::any_of(p.pow2.begin(), p.pow2.end(), [](uint8_t x) { return x == 0; });
+}
+
+// Device side of the padded twin: its tables (from the resident ones), the
+// map that derives them, its marginal sources and separator sizes.
+jt_status load_pad(jt_tree t, cudaStream_t s) {
+  const Plan& q = *t->pad;
+  jt_status st;
+  if ((st = alloc(t, &t->pad_base, q.base_len, "padded tables")) != JT_OK) return st;
+  CU(cudaMemsetAsync(t->pad_base, 0, (size_t)q.base_len * sizeof(float), s), "padded tables");
+  const PadMap m = build_pad_map(t->plan, q);
+  if ((st = alloc(t, &t->d_pad_digits, (int64_t)m.digits.size(), "padding map")) != JT_OK) return st;
+  if ((st = alloc(t, &t->d_pad_cliques, (int64_t)m.cliques.size(), "padding map")) != JT_OK) return st;
+  if ((st = alloc(t, &t->d_vs_pad, q.n_vars, "marginal sources")) != JT_OK) return st;
+  if ((st = alloc(t, &t->d_sep_size_pad, q.n_cliques, "separator sizes")) != JT_OK) return st;
+  CU(cudaMemcpy(t->d_pad_digits, m.digits.data(), m.digits.size() * sizeof(int4), cudaMemcpyHostToDevice),
+     "descriptor upload");
+  CU(cudaMemcpy(t->d_pad_cliques, m.cliques.data(), m.cliques.size() * sizeof(PadClique), cudaMemcpyHostToDevice),
+     "descriptor upload");
+  CU(cudaMemcpy(t->d_vs_pad, q.vsrc[2].data(), q.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice),
+     "descriptor upload");
+  CU(cudaMemcpy(t->d_sep_size_pad, q.sep_size.data(), q.n_cliques * sizeof(int32_t), cudaMemcpyHostToDevice),
+     "descriptor upload");
+  for (const PadClique& c : m.cliques) t->pad_max = std::max(t->pad_max, c.n_pad);
+  CU(launch_pad_tables((const float*)t->base, t->pad_base, t->d_pad_digits, t->d_pad_cliques, t->plan.n_cliques,
+                       t->pad_max, s),
+     "padding the tables");
   return JT_OK;
 }
 
@@ -855,6 +906,10 @@ jt_status init_typed(jt_tree t, const std::vector<InitItem>& items, const std::v
   if (e == cudaSuccess)
     e = launch_init_cliques<T>((T*)t->base, d_items, (int32_t)items.size(), d_cl, d_fac, d_terms, d_vals, t->n_sm, s);
   if (e == cudaSuccess && kernel_ms) e = cudaEventRecord(ev[1], s);
+  // the padded twin follows the new tables
+  if (e == cudaSuccess && t->pad)
+    e = launch_pad_tables((const float*)t->base, t->pad_base, t->d_pad_digits, t->d_pad_cliques, t->plan.n_cliques,
+                          t->pad_max, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && kernel_ms) e = cudaEventElapsedTime(kernel_ms, ev[0], ev[1]);
   for (cudaEvent_t x : ev)
@@ -896,6 +951,14 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   t->max_cases = d->max_cases;
   t->elem = d->compute == JT_F64 ? 8 : 4;
   Plan& p = t->plan;
+  if (want_pad(p, d)) {
+    // padding multiplies the table entries: kept within a few times the tree
+    auto q = std::make_unique<Plan>();
+    std::string perr;
+    if (build_padded_plan(p, q.get(), &perr) == JT_OK && q->base_len <= 5 * p.base_len &&
+        q->base_len < (1ll << 31))
+      t->pad = std::move(q);
+  }
   int dev = 0;
   CU(cudaGetDevice(&dev), "cudaGetDevice");
   t->device = dev;
@@ -911,6 +974,7 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   };
   if ((st = (raw->compute == JT_F64 ? load_typed<double>(raw, d, s) : load_typed<float>(raw, d, s))) != JT_OK)
     return bail(st);
+  if (raw->pad && (st = load_pad(raw, s)) != JT_OK) return bail(st);
   const int nc = p.n_cliques;
   if ((st = alloc(raw, &raw->d_sums, 2ll * nc * raw->max_cases, "stage totals")) != JT_OK) return bail(st);
   if ((st = alloc(raw, &raw->d_done, 1 + 2ll * nc * raw->max_cases, "block counters")) != JT_OK) return bail(st);
@@ -1227,6 +1291,7 @@ jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info*
   out->grid = ge.grid;
   out->smem_bytes = ge.smem;
   out->window_entries = ge.sched.win_max;
+  out->padded = ge.padded ? 1 : 0;
   std::copy(ge.candidate_ms, ge.candidate_ms + 5, out->candidate_ms);
   return JT_OK;
 }

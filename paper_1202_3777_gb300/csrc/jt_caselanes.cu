@@ -198,7 +198,7 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
         const DevPos& P = s.pos[i];
         const int st = evr[P.var];
         if (st < 0) continue;
-        if (st >= P.card) {
+        if (st >= P.card_ev) {
           atomicOr(&a.status[cs], kStatusBadState);
           continue;
         }
@@ -709,7 +709,8 @@ __global__ void __launch_bounds__(256) k_finalize_cl(const FinalArgs<float> a) {
   const int sh = __ffs(src.st) - 1;
   double* out = a.marg_out + (int64_t)cs * a.marg_total + src.moff;
   double z = 0.0;
-  for (int x = 0; x < src.card; ++x) {
+  // states from card_out up are padded ones (zero in every table)
+  for (int x = 0; x < src.card_out; ++x) {
     double s0 = 0.0, s1 = 0.0;
     int q = warp;
 #pragma unroll 2
@@ -733,7 +734,7 @@ __global__ void __launch_bounds__(256) k_finalize_cl(const FinalArgs<float> a) {
     __syncthreads();
   }
   if (warp == 0 && valid)
-    for (int x = 0; x < src.card; ++x) out[x] = z > 0.0 ? out[x] / z : NAN;
+    for (int x = 0; x < src.card_out; ++x) out[x] = z > 0.0 ? out[x] / z : NAN;
 }
 
 // The dynamic shared-memory opt-in of the propagation kernel, once per device.

@@ -117,7 +117,37 @@ __global__ void __launch_bounds__(256) k_table_unpermute(const T* table, CliqueO
   }
 }
 
+// One thread per padded entry, a clique per grid row; the digits of the
+// padded layout are bit fields, so the decode is shifts and masks.
+__global__ void __launch_bounds__(256) k_pad_tables(const float* __restrict__ base, float* __restrict__ pad,
+                                                    const int4* __restrict__ digits,
+                                                    const PadClique* __restrict__ cliques, int32_t n_cliques) {
+  for (int32_t c = blockIdx.y; c < n_cliques; c += gridDim.y) {
+    const PadClique q = cliques[c];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < q.n_pad;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      int64_t src = 0;
+      bool hole = false;
+      for (int i = 0; i < q.k; ++i) {
+        const int4 g = digits[q.d0 + i];
+        const int32_t d = (int32_t)((e >> g.x) & ((1ll << g.y) - 1));
+        hole |= d >= g.z;
+        src += (int64_t)d * g.w;
+      }
+      pad[q.off_pad + e] = hole ? 0.f : base[q.off + src];
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pad_tables(const float* base, float* pad, const int4* digits, const PadClique* cliques,
+                              int32_t n_cliques, int64_t max_pad, cudaStream_t s) {
+  if (n_cliques == 0 || max_pad == 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min<int64_t>(256, (max_pad + 255) / 256), (unsigned)std::min(n_cliques, 4096));
+  k_pad_tables<<<grid, 256, 0, s>>>(base, pad, digits, cliques, n_cliques);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_init_cliques(T* base, const InitItem* items, int32_t n_items, const InitClique* cliques,

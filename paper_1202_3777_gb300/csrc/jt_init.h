@@ -7,6 +7,7 @@
 
 #include <cstdint>
 
+#include "jt_internal.h"
 #include "jt_kernels.h"
 
 namespace jt {
@@ -59,5 +60,12 @@ cudaError_t launch_init_cliques(T* base, const InitItem* items, int32_t n_items,
 // A permuted table read back in its listed order, as double.
 template <typename T>
 cudaError_t launch_table_unpermute(const T* table, const CliqueOut& co, double* out_dev, cudaStream_t s);
+
+// The padded plan's tables from the resident ones (FP32): entry e of a
+// padded table, read as digits of the padded cardinalities, is the resident
+// entry with the same digits, or zero where a digit is an added state.  Run
+// after every change of the resident tables.
+cudaError_t launch_pad_tables(const float* base, float* pad, const int4* digits, const PadClique* cliques,
+                              int32_t n_cliques, int64_t max_pad, cudaStream_t s);
 
 }  // namespace jt

@@ -71,7 +71,8 @@ struct DevPos {       // one digit (position) of a clique's permuted layout
   uint32_t card_magic;
   int32_t sh;         // power-of-two cliques: log2(st)
   int32_t cb;         // power-of-two cliques: log2(card)
-  int32_t pad;
+  int32_t card_ev;    // evidence states must lie below this: the variable's
+                      // cardinality before any padding to a power of two
 };
 
 constexpr int32_t kVmodeStore = 4;
@@ -172,7 +173,9 @@ struct VarSrc {
   int32_t st;         // stride of the variable in the table
   int32_t card;
   int32_t moff;       // offset of the marginal in the output row
-  int32_t pad[3];
+  int32_t card_out;   // states written to the marginal row (the cardinality
+                      // before padding; padded states are zero)
+  int32_t pad[2];
 };
 
 // Arguments of the persistent propagation kernel.
@@ -234,6 +237,10 @@ struct FinalArgs {
 struct Plan {
   int32_t n_vars = 0, n_cliques = 0, max_depth = 0;
   std::vector<int32_t> card;
+  // A padded plan (build_padded_plan): every cardinality raised to a power of
+  // two, the added states impossible (their potential entries zero), and
+  // card_ev the cardinalities of the tree it pads; empty otherwise.
+  std::vector<int32_t> card_ev;
   std::vector<std::vector<int32_t>> vars;   // listed (user) order
   std::vector<std::vector<int32_t>> pvars;  // permuted (device) order
   std::vector<int32_t> parent, depth;
@@ -271,6 +278,31 @@ struct Plan {
 // Validation + layout.  Returns JT_OK or an error status with `err` filled.
 // Touches no CUDA API.
 jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err);
+
+// The tree of `p` with every cardinality raised to the next power of two.
+// The added states get zero potential in every clique that holds the
+// variable, so the padded tree has the same joint distribution on the
+// original states, the same normalising constant and the same marginals
+// (Eq. 1: every product with a zero entry vanishes).  The permuted variable
+// order of every clique is the one of `p` (it does not depend on
+// cardinalities); marginal offsets and evidence limits are those of `p`, so
+// a propagation over the padded plan writes the same output rows.
+// JT_ERR_UNSUPPORTED if the padded tables would exceed the layout's limits.
+jt_status build_padded_plan(const Plan& p, Plan* q, std::string* err);
+
+// Map from a plan's permuted tables to its padded plan's: per clique, per
+// permuted position, the padded shift and width and the original cardinality
+// and stride (int4 {sh, bits, card, stride}), and per clique where its digits
+// and both of its tables start.
+struct PadClique {
+  int64_t off, off_pad, n_pad;  // table offsets (original, padded), padded entries
+  int32_t d0, k;                // digits [d0, d0 + k)
+};
+struct PadMap {
+  std::vector<int4> digits;
+  std::vector<PadClique> cliques;
+};
+PadMap build_pad_map(const Plan& p, const Plan& q);
 
 // Copy the caller's tables (listed order, any dtype) into the permuted,
 // padded device layout (host buffer of base_len elements of T).

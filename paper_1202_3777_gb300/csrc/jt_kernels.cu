@@ -212,7 +212,7 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
         if (t >= nev || st < 0) continue;
         const int cl = t / S.k, i = t - cl * S.k;
         const DevPos& P = s.pos[i];
-        if (st >= P.card) {
+        if (st >= P.card_ev) {
           atomicOr(&a.status[cb0 + cl], kStatusBadState);
           continue;
         }

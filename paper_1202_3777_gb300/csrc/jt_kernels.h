@@ -27,6 +27,7 @@ constexpr int kClPortBytes = 448;               // bytes of one port's key table
 constexpr int kSig = 2;                         // finished items queued for the signalling lane
 constexpr int kControlThreads = 96;             // producer, signalling and preparation warps
 constexpr int kMaxFastPorts = 16;               // ports of a stage on the power-of-two fast path
+constexpr int kClMaxPorts = 32;                 // ports of a stage on the case-lane path (tables in the blob)
 
 // Bytes of a stage's descriptors (DevStage, ports, fields, positions).
 __host__ __device__ inline int32_t desc_bytes(int k, int np, int nf) {

@@ -246,6 +246,7 @@ jt_status build_plan(const jt_tree_desc* d, Plan* p, std::string* err) {
     for (int v = 0; v < nv; ++v) {
       VarSrc& q = vs[v];
       q.card = p->card[v];
+      q.card_out = p->card[v];
       q.moff = p->moff[v];
       const int e = src_edge[v];
       if (e >= 0) {
@@ -377,6 +378,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       q.card_magic = magic_for((uint32_t)q.card);
       q.sh = p.pow2[c] ? ilog2(stv[c][i]) : 0;
       q.cb = p.pow2[c] ? ilog2(q.card) : 0;
+      q.card_ev = p.card_ev.empty() ? q.card : p.card_ev[pv[i]];
       s->pos.push_back(q);
     }
   }
@@ -436,8 +438,9 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
     *err = "case-lane schedules are FP32 only";
     return JT_ERR_UNSUPPORTED;
   }
+  const int max_fast = lanes ? kClMaxPorts : kMaxFastPorts;
   const int blob_bound = desc_bytes(s->max_k, s->max_ports, s->max_fields) +
-                         table_bytes(cb, std::min(s->max_ports, kMaxFastPorts));
+                         table_bytes(cb, std::min(s->max_ports, max_fast));
   const int fixed = lanes ? SmemLayoutCL(s->ring, s->chunk, blob_bound, 0).bytes
                           : SmemLayout(cb, s->ring, s->chunk, s->max_k, s->max_ports, blob_bound, 0, elem).bytes;
   const int64_t win_budget = (int64_t)(smem_bytes - fixed - 256) / (2ll * cb * elem);  // two buffers
@@ -496,12 +499,12 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       int64_t B = 1;
       // a case-lane block holds at least one tile (32 entries) per warp slice
       const int min_bits = lanes ? 5 : lv;
-      if (lanes && !(pow2 && S.n >= 32 && (int)sp.size() <= kMaxFastPorts)) {
+      if (lanes && !(pow2 && S.n >= 32 && (int)sp.size() <= kClMaxPorts)) {
         *err = "case-lane schedules need power-of-two cliques of at least 32 entries and at most " +
-               std::to_string(kMaxFastPorts) + " ports";
+               std::to_string(kClMaxPorts) + " ports";
         return JT_ERR_UNSUPPORTED;
       }
-      if (pow2 && S.n >= VEC && (int)sp.size() <= kMaxFastPorts) {
+      if (pow2 && S.n >= VEC && (int)sp.size() <= max_fast) {
         const int nbits = ilog2(S.n);
         int bits = min_bits;
         for (int b = nbits; b >= min_bits; --b) {
@@ -923,6 +926,65 @@ jt_status build_small_schedule(const Plan& p, int elem, int n_cases, int n_sm, i
 int32_t prop_smem_bytes(const Schedule& s, int elem) {
   if (s.cb == kCaseLanes) return SmemLayoutCL(s.ring, s.chunk, s.blob_max, s.win_max).bytes;
   return SmemLayout(s.cb, s.ring, s.chunk, s.max_k, s.max_ports, s.blob_max, s.win_max, elem).bytes;
+}
+
+jt_status build_padded_plan(const Plan& p, Plan* q, std::string* err) {
+  const int nv = p.n_vars, nc = p.n_cliques;
+  std::vector<int32_t> card(nv);
+  for (int v = 0; v < nv; ++v) card[v] = (int32_t)(1ll << ilog2(p.card[v]));
+  std::vector<int64_t> off(1, 0);
+  std::vector<int32_t> vars;
+  for (int c = 0; c < nc; ++c) {
+    vars.insert(vars.end(), p.vars[c].begin(), p.vars[c].end());
+    off.push_back((int64_t)vars.size());
+  }
+  jt_tree_desc d{};
+  d.n_vars = nv;
+  d.card = card.data();
+  d.n_cliques = nc;
+  d.clique_off = off.data();
+  d.clique_vars = vars.data();
+  d.parent = p.parent.data();
+  d.potentials = nullptr;
+  d.potentials_dtype = JT_F32;
+  d.compute = JT_F32;
+  d.max_cases = 1;
+  d.flags = 0;
+  jt_status st = build_plan(&d, q, err);
+  if (st != JT_OK) return st;
+  for (int c = 0; c < nc; ++c)
+    if (q->pvars[c] != p.pvars[c]) FAIL(JT_ERR_UNSUPPORTED, "padded plan permutes a clique differently");
+  // outputs in the original layout: the padded plan writes p's marginal rows
+  q->card_ev = p.card;
+  q->moff = p.moff;
+  q->marg_total = p.marg_total;
+  for (int L = 0; L < 3; ++L)
+    for (int v = 0; v < nv; ++v) {
+      q->vsrc[L][v].moff = p.moff[v];
+      q->vsrc[L][v].card_out = p.card[v];
+    }
+  return JT_OK;
+}
+
+PadMap build_pad_map(const Plan& p, const Plan& q) {
+  PadMap m;
+  for (int c = 0; c < p.n_cliques; ++c) {
+    const auto& pv = p.pvars[c];
+    const int k = (int)pv.size();
+    const int32_t d0 = (int32_t)m.digits.size();
+    int64_t st = 1;
+    int32_t sh = 0;
+    std::vector<int4> dg(k);
+    for (int i = k - 1; i >= 0; --i) {
+      const int32_t b = ilog2(q.card[pv[i]]);
+      dg[i] = int4{sh, b, p.card[pv[i]], (int32_t)st};
+      sh += b;
+      st *= p.card[pv[i]];
+    }
+    m.digits.insert(m.digits.end(), dg.begin(), dg.end());
+    m.cliques.push_back(PadClique{p.base_off[c], q.base_off[c], q.n_entries[c], d0, k});
+  }
+  return m;
 }
 
 template <typename T>

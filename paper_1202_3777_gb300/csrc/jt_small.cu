@@ -75,7 +75,7 @@ __device__ __forceinline__ void run_segment(const SmallArgs<T>& a, const T* base
       const DevPos& P = pos[i];
       const int st = ev[P.var];
       if (st < 0) continue;
-      if (st >= P.card) {
+      if (st >= P.card_ev) {
         atomicOr(&a.status[cs], kStatusBadState);
         continue;
       }

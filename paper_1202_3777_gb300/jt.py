@@ -71,7 +71,8 @@ class jt_tree_info(C.Structure):
 class jt_schedule_info(C.Structure):
     _fields_ = [
         ("case_block", C.c_int32), ("n_items", C.c_int32), ("grid", C.c_int32), ("smem_bytes", C.c_int32),
-        ("window_entries", C.c_int32), ("reserved", C.c_int32 * 3), ("candidate_ms", C.c_float * 5),
+        ("window_entries", C.c_int32), ("padded", C.c_int32), ("reserved", C.c_int32 * 2),
+        ("candidate_ms", C.c_float * 5),
     ]
 
 
@@ -338,7 +339,7 @@ def jt_get_schedule(t: Tree, first_case: int, n_cases: int) -> dict:
     info = jt_schedule_info()
     _check(_lib.jt_get_schedule(t.handle, first_case, n_cases, C.byref(info)), "jt_get_schedule")
     return {"case_block": info.case_block, "n_items": info.n_items, "grid": info.grid,
-            "smem_bytes": info.smem_bytes, "window_entries": info.window_entries,
+            "smem_bytes": info.smem_bytes, "window_entries": info.window_entries, "padded": bool(info.padded),
             "candidate_ms": {w: float(info.candidate_ms[i]) for i, w in enumerate((32, 8, 4, 1, 0))
                              if info.candidate_ms[i] >= 0}}
 

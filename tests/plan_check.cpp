@@ -166,5 +166,84 @@ int main(int argc, char** argv) {
       ++bad;
     }
   }
+  // trees with other cardinalities: the power-of-two padded plan, its
+  // case-lane schedules, and the map that derives its tables
+  if (std::any_of(p.pow2.begin(), p.pow2.end(), [](uint8_t x) { return x == 0; })) {
+    Plan q;
+    err.clear();
+    if (build_padded_plan(p, &q, &err) != JT_OK) {
+      std::printf("pad FAIL plan %s\n", err.c_str());
+      return 1;
+    }
+    for (int cases : {64, 40}) {
+      Schedule s;
+      err.clear();
+      const jt_status st = build_schedule(q, 4, kCaseLanes, cases, 152, smem, &s, &err);
+      if (st == JT_ERR_UNSUPPORTED) {
+        std::printf("pad cb=%d cases=%d UNSUPPORTED %s\n", kCaseLanes, cases, err.c_str());
+        continue;
+      }
+      if (plant == "plant-order") std::reverse(s.items.begin(), s.items.end());
+      if (plant == "plant-repeat" && s.items.size() > 1) s.items.back() = s.items.front();
+      std::string why = st == JT_OK ? check(q, s) : "status " + std::to_string((int)st) + " " + err;
+      // evidence limits and output rows are the original tree's
+      for (const DevPos& P : s.pos)
+        if (why.empty() && P.card_ev != p.card[P.var]) why = "evidence limit of a padded digit";
+      if (why.empty()) {
+        std::printf("pad cb=%d cases=%d OK items=%zu\n", kCaseLanes, cases, s.items.size());
+      } else {
+        std::printf("pad cb=%d cases=%d FAIL %s\n", kCaseLanes, cases, why.c_str());
+        ++bad;
+      }
+    }
+    std::string why;
+    if (q.moff != p.moff || q.marg_total != p.marg_total) why = "marginal rows differ";
+    for (int v = 0; v < nv && why.empty(); ++v)
+      if (q.vsrc[2][v].card_out != p.card[v] || q.card[v] < p.card[v] || (q.card[v] & (q.card[v] - 1)))
+        why = "padded cardinality or output states of variable " + std::to_string(v);
+    // every padded entry, decoded by its own digits: the map must find the
+    // original entry with the same digits, or a hole where a digit is padded
+    PadMap m = build_pad_map(p, q);
+    if (plant == "plant-pad" && m.digits.size() > 1) std::swap(m.digits[0].w, m.digits[1].w);
+    int64_t holes = 0, kept = 0;
+    for (int c = 0; c < nc && why.empty(); ++c) {
+      const auto& pv = q.pvars[c];
+      const int k = (int)pv.size();
+      const PadClique& pc = m.cliques[c];
+      if (pc.k != k || pc.off != p.base_off[c] || pc.off_pad != q.base_off[c] || pc.n_pad != q.n_entries[c]) {
+        why = "clique record of clique " + std::to_string(c);
+        break;
+      }
+      for (int64_t e = 0; e < q.n_entries[c] && why.empty(); ++e) {
+        int64_t r = e, want = 0, st = 1;
+        bool hole = false;
+        for (int i = k - 1; i >= 0; --i) {
+          const int64_t dgt = r % q.card[pv[i]];
+          r /= q.card[pv[i]];
+          if (dgt >= p.card[pv[i]]) hole = true;
+          want += dgt * st;
+          st *= p.card[pv[i]];
+        }
+        int64_t got = 0;
+        bool ghole = false;
+        for (int i = 0; i < k; ++i) {
+          const int4 g = m.digits[pc.d0 + i];
+          const int64_t dgt = (e >> g.x) & ((1ll << g.y) - 1);
+          ghole |= dgt >= g.z;
+          got += dgt * g.w;
+        }
+        if (hole != ghole || (!hole && got != want))
+          why = "padded entry " + std::to_string(e) + " of clique " + std::to_string(c);
+        hole ? ++holes : ++kept;
+      }
+    }
+    if (why.empty() && kept != p.entries) why = "kept entries " + std::to_string(kept);
+    if (why.empty()) {
+      std::printf("padmap OK kept=%lld holes=%lld\n", (long long)kept, (long long)holes);
+    } else {
+      std::printf("padmap FAIL %s\n", why.c_str());
+      ++bad;
+    }
+  }
   return bad ? 1 : 0;
 }

@@ -4,8 +4,8 @@ separators of 2-5 variables, 10% of the variables observed per case, case
 seed = base seed + case id), FP32, in one persistent propagation launch
 (the schedule's width chosen by timing on first use), compared element by
 element with the FP64 oracle on a spread sample of cases: the first and last
-cases, the edges of case blocks, and cases spread over the range.  A second
-range of 4093 cases ends in a ragged case block."""
+cases, the edges of case blocks, and cases spread over the range.  Ranges of
+4093 cases end in a ragged case block and a ragged slab of case lanes."""
 import numpy as np
 import pytest
 
@@ -65,7 +65,9 @@ def test_4096_cases_one_launch(jt, loaded, monkeypatch):
     t, ev, h = loaded
     jt.jt_propagate(h, 0, N)
     sch = jt.jt_get_schedule(h, 0, N)
-    assert sch["case_block"] in (1, 4, 8) and sch["grid"] <= 152 * 2
+    # case lanes run over the tree's power-of-two padded copy (cardinality 3)
+    assert sch["case_block"] in (1, 4, 8, 32) and sch["grid"] <= 152 * 2
+    assert sch["padded"] == (sch["case_block"] == 32), sch
     _check(jt, t, ev, h, 0, N)
     # a second propagation of the range replays the recorded graph
     jt.jt_propagate(h, 0, N)
@@ -78,3 +80,14 @@ def test_ragged_last_case_block(jt, loaded, monkeypatch):
     jt.jt_propagate(h, 0, N - 3)
     assert jt.jt_get_schedule(h, 0, N - 3)["case_block"] == 8
     _check(jt, t, ev, h, 0, N - 3)
+
+
+def test_ragged_last_slab_padded_lanes(jt, loaded, monkeypatch):
+    """4091 cases (a range not recorded before: a range keeps the schedule of
+    its first propagation), so the last slab holds 27 cases."""
+    monkeypatch.setenv("JT_CASE_BLOCK", "32")
+    t, ev, h = loaded
+    jt.jt_propagate(h, 0, N - 5)
+    sch = jt.jt_get_schedule(h, 0, N - 5)
+    assert sch["case_block"] == 32 and sch["padded"], sch
+    _check(jt, t, ev, h, 0, N - 5)

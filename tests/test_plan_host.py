@@ -4,7 +4,14 @@ tree for one case, 4- and 8-case blocks, and checks what the persistent
 kernel relies on: every block of every stage is one work item per case
 block, the dependencies are those of Algorithms 2-4, and no item waits for
 a block queued after it.  Run on the workloads, on merged trees (high
-fan-out), on trees with empty separators and on the separator sweep."""
+fan-out), on trees with empty separators and on the separator sweep.
+
+Trees with cardinalities other than powers of two also get the padded plan
+(every cardinality raised to a power of two, the added states impossible):
+its case-lane schedules are checked the same way, its evidence limits and
+output rows must be the original tree's, and every padded table entry,
+decoded from its own digits, must map to the original entry with the same
+digits, or be a hole exactly where a digit is an added state."""
 import os
 import shutil
 import subprocess
@@ -55,18 +62,41 @@ TREES = {
 # trees whose cliques all have power-of-two cardinalities and >= 32 entries:
 # the case-lane schedule (32 cases per work item) must plan them
 CASE_LANE_TREES = {"large-clique", "high-card", "sep-sweep-4^1", "sep-sweep-4^7"}
+# trees with other cardinalities whose padded plan the case lanes must plan
+PADDED_TREES = {"small", "batched"}
+
+
+def _pow2(t):
+    return all(int(c) & (int(c) - 1) == 0 for c in t.card)
 
 
 @pytest.mark.parametrize("name", list(TREES))
 def test_schedules_of_the_workloads(checker, name):
     t = TREES[name]()
     rc, lines = _run(checker, t.card, t.cliques, t.parent)
-    assert rc == 0 and len(lines) == 6, lines
-    for ln in lines:
+    assert rc == 0, lines
+    base = [ln for ln in lines if ln.startswith("cb=")]
+    assert len(base) == 6, lines
+    for ln in base:
         if ln.startswith("cb=32 ") and name not in CASE_LANE_TREES:
             assert " OK " in ln or " UNSUPPORTED " in ln, ln
         else:
             assert " OK " in ln, ln
+    pad = [ln for ln in lines if ln.startswith("pad")]
+    if _pow2(t):
+        assert not pad, lines
+    else:
+        assert len(pad) == 3 and pad[-1].startswith("padmap OK"), lines
+        for ln in pad[:2]:
+            assert " OK " in ln or (name not in PADDED_TREES and " UNSUPPORTED " in ln), ln
+
+
+def test_planted_padding_mistake_is_caught(checker):
+    """Two digits' strides swapped in the padding map: some padded entry then
+    maps to an original entry with other digits."""
+    t = synth.small_tree()
+    rc, lines = _run(checker, t.card, t.cliques, t.parent, "plant-pad")
+    assert rc == 1 and any(ln.startswith("padmap FAIL") for ln in lines), lines
 
 
 @pytest.mark.parametrize("min_sep,cap", [(8, 1 << 8), (16, 1 << 10), (1 << 20, 1 << 12)])
@@ -83,6 +113,6 @@ def test_schedules_of_merged_trees(checker, min_sep, cap):
 def test_planted_schedule_mistakes_are_caught(checker, plant, what):
     t = synth.small_tree()
     rc, lines = _run(checker, t.card, t.cliques, t.parent, plant)
-    planned = [ln for ln in lines if " UNSUPPORTED " not in ln]   # (no case lanes on ternary cliques)
+    planned = [ln for ln in lines if " UNSUPPORTED " not in ln and not ln.startswith("padmap")]
     assert rc == 1 and len(planned) >= 4 and all(" FAIL " in ln and what in ln for ln in planned), lines
 
