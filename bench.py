@@ -600,7 +600,9 @@ def roofline_of(kernel, alg_bytes, kernel_ms, hbm, src, traffic=None):
 
 
 def prop_kernel_name(schedule):
-    return "k_propagate_cl" if schedule["case_block"] == 32 else f"k_propagate<float, {schedule['case_block']}>"
+    if schedule["case_block"] == 32:
+        return "k_propagate_cl<true>" if schedule.get("padded") else "k_propagate_cl<false>"
+    return f"k_propagate<float, {schedule['case_block']}>"
 
 
 def measure_latency(jt, torch, steps=50):

@@ -291,7 +291,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
     w.base_len = p.base_len;
     chk(launch_small<T>(w, ge.grid, ge.smem, s));
   } else if constexpr (std::is_same<T, float>::value) {
-    if (sc.cb == kCaseLanes) chk(launch_propagate_cl(a, ge.grid, ge.smem, s));
+    if (sc.cb == kCaseLanes) chk(launch_propagate_cl(a, ge.grid, ge.smem, ge.padded, s));
     else chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));
   } else {
     chk(launch_propagate<T>(a, sc.cb, ge.grid, ge.smem, s));

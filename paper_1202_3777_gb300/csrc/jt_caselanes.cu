@@ -378,9 +378,18 @@ __device__ __forceinline__ void signaller_cl(const PropArgs<float>& a, const Sme
 
 // ---- consumers -------------------------------------------------------------
 
+// A digit of a padded plan at one of its added states (packed as in
+// DevStage::holes): every table entry with it is zero.
+__device__ __forceinline__ bool added_state(uint32_t x, uint32_t h) {
+  return h != 0u && ((x >> (h & 31u)) & ((1u << ((h >> 5) & 31u)) - 1u)) >= (h >> 10);
+}
+
 // Stream one item: every warp takes its slice of each chunk in tiles of 32
 // entries; per tile a lane holds the 32 products of its case in registers
-// (as 16 pairs, multiplied and added two at a time).
+// (as 16 pairs, multiplied and added two at a time).  A tile of a padded
+// plan whose digits above the tile include an added state holds only zero
+// entries and is skipped: it would add nothing.
+template <bool HOLES>
 __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& s, const DevItem& w, int ncb,
                                           int cb0, int n_in, int n_live, float bfl, float& tot, RingPos& rp) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -403,6 +412,8 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
   const float2 mA01 = make_float2(((0u ^ V) & M & 3u) == 0u ? 1.f : 0.f, ((1u ^ V) & M & 3u) == 0u ? 1.f : 0.f);
   const float2 mA23 = make_float2(((2u ^ V) & M & 3u) == 0u ? 1.f : 0.f, ((3u ^ V) & M & 3u) == 0u ? 1.f : 0.f);
   float* calib = (a.calib != nullptr && lane < ncb) ? a.calib + (int64_t)(cb0 + lane) * a.calib_stride + w.off : nullptr;
+  const uint32_t h0 = s.stage->holes[0], h1 = s.stage->holes[1], h2 = s.stage->holes[2];
+  const uint32_t xb = (uint32_t)(w.off - s.stage->base_off);   // the block's first entry in its clique
   bool ok = true;
   for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
     const uint32_t st = rp.st;
@@ -416,6 +427,10 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
     for (int t = 0; t < kClTiles; ++t) {
       const int ot = warp * kClSlice + 32 * t;  // tile offset in the chunk
       if (ot >= nch) break;                     // warp-uniform
+      if (HOLES && h0 != 0u) {
+        const uint32_t x = xb + (uint32_t)(ci * CH + ot);
+        if (added_state(x, h0) || added_state(x, h1) || added_state(x, h2)) continue;
+      }
       const int slot = warp * kClTiles + t;
       float2 f[16];
 #pragma unroll
@@ -542,6 +557,7 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
 
 // One work item (its buffer prepared by the control warp).  Every consumer
 // thread runs every barrier; the result is uniform over the consumers.
+template <bool HOLES>
 __device__ __forceinline__ bool process_item_cl(const PropArgs<float>& a, const Smem& s, const DevItem& w, uint32_t b,
                                                 RingPos& rp, uint32_t& sigk) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -553,7 +569,7 @@ __device__ __forceinline__ bool process_item_cl(const PropArgs<float>& a, const 
   if (tr != nullptr && tid == 0) tr[3] = global_ns();
   const float bfl = (float)s.bf[lane];
   float tot = 0.f;
-  const bool sok = stream_cl(a, s, w, ncb, cb0, S.n_in_live, S.n_live, bfl, tot, rp);
+  const bool sok = stream_cl<HOLES>(a, s, w, ncb, cb0, S.n_in_live, S.n_live, bfl, tot, rp);
   if (!consumer_all<NT>(sok)) {
     if (tid == 0) {
       atomicExch(a.err, 1);
@@ -586,6 +602,7 @@ __device__ __forceinline__ bool process_item_cl(const PropArgs<float>& a, const 
   return true;
 }
 
+template <bool HOLES>
 __device__ __forceinline__ void consumer_cl(const PropArgs<float>& a, const Smem& s0) {
   RingPos rp;
   uint32_t sigk = 0;
@@ -622,10 +639,12 @@ __device__ __forceinline__ void consumer_cl(const PropArgs<float>& a, const Smem
       }
     }
     consumer_sync<NT>();
-    if (!process_item_cl(a, with_buffer(s0, b), w, b, rp, sigk)) break;
+    if (!process_item_cl<HOLES>(a, with_buffer(s0, b), w, b, rp, sigk)) break;
   }
 }
 
+// HOLES: the schedule is a padded plan's, whose all-zero tiles are skipped.
+template <bool HOLES>
 __global__ void __launch_bounds__(NT + kControlThreads, 1) k_propagate_cl(const PropArgs<float> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const SmemLayoutCL L(a.ring, a.chunk, a.blob_max, a.win_max);
@@ -661,7 +680,7 @@ __global__ void __launch_bounds__(NT + kControlThreads, 1) k_propagate_cl(const 
     }
     __syncwarp();
   } else {
-    consumer_cl(a, s);
+    consumer_cl<HOLES>(a, s);
   }
   __syncthreads();
   if (a.span != nullptr && threadIdx.x == 0) atomicMax(a.span + 1, (unsigned long long)global_ns());
@@ -748,11 +767,12 @@ cudaError_t set_attrs_cl() {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_attr_mu);
   if (!g_attr_done[dev]) {
-    e = cudaFuncSetAttribute(k_propagate_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_budget(dev, 1));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_propagate_cl, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
+    for (auto k : {k_propagate_cl<false>, k_propagate_cl<true>}) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_budget(dev, 1));
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+    }
     g_attr_done[dev] = true;
   }
   return cudaSuccess;
@@ -760,11 +780,12 @@ cudaError_t set_attrs_cl() {
 
 }  // namespace
 
-cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, cudaStream_t s) {
+cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, bool holes, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
   cudaError_t e = set_attrs_cl();
   if (e != cudaSuccess) return e;
-  k_propagate_cl<<<grid, NT + kControlThreads, smem, s>>>(a);
+  if (holes) k_propagate_cl<true><<<grid, NT + kControlThreads, smem, s>>>(a);
+  else k_propagate_cl<false><<<grid, NT + kControlThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

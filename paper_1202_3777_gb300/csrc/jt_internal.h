@@ -126,7 +126,11 @@ struct DevStage {
   // that input's window entries (the message it carries was computed with
   // the evidence), so the case-lane schedule masks only the other positions
   uint32_t covered;
-  int32_t pad2[3];
+  // padded plans: up to three digits lying above the 32-entry tile whose
+  // added states make a whole tile of zero entries (a tile with such a digit
+  // at an added state contributes nothing), packed as
+  // shift | bits << 5 | original cardinality << 10; 0 = none
+  uint32_t holes[3];
 };
 
 // A port with a window, as the fast path reads it.  An entry at block offset

@@ -155,7 +155,7 @@ cudaError_t launch_small(const SmallArgs<T>& a, int grid, int smem, cudaStream_t
 
 // Case-lane schedules (FP32): the persistent propagation over message slabs
 // of kCaseLanes interleaved cases, and its finalisation.
-cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, cudaStream_t s);
+cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, bool holes, cudaStream_t s);
 cudaError_t launch_finalize_cl(const FinalArgs<float>& a, cudaStream_t s);
 
 // Normalised calibrated clique in the caller's listed order.

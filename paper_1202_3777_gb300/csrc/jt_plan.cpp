@@ -592,6 +592,20 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
       for (int q = 0; q < nin; ++q)
         for (int i = 0; i < k; ++i)
           if (sp[q].in[i]) S.covered |= 1u << i;
+      // digits of a padded plan above the tile, those with the largest share
+      // of added states first
+      S.holes[0] = S.holes[1] = S.holes[2] = 0u;
+      if (!p.card_ev.empty() && pow2) {
+        std::vector<std::pair<double, uint32_t>> hd;
+        for (int i = 0; i < k; ++i) {
+          const int32_t ce = p.card_ev[p.pvars[c][i]];
+          const int sh = ilog2(stv[c][i]), nb = ilog2(cdv[c][i]);
+          if (ce < cdv[c][i] && sh >= 5)
+            hd.push_back({(double)ce / cdv[c][i], (uint32_t)sh | (uint32_t)nb << 5 | (uint32_t)ce << 10});
+        }
+        std::stable_sort(hd.begin(), hd.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+        for (size_t j = 0; j < hd.size() && j < 3; ++j) S.holes[j] = hd[j].second;
+      }
       S.np = (int32_t)sp.size();
       S.nin = nin;
       S.nf = (int32_t)s->fields.size() - S.field0;

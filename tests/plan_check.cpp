@@ -185,12 +185,41 @@ int main(int argc, char** argv) {
       }
       if (plant == "plant-order") std::reverse(s.items.begin(), s.items.end());
       if (plant == "plant-repeat" && s.items.size() > 1) s.items.back() = s.items.front();
+      if (plant == "plant-holes")   // one state too few: the last real state reads as added
+        for (DevStage& S : s.stages)
+          if (S.holes[0] != 0u) S.holes[0] -= 1u << 10;
       std::string why = st == JT_OK ? check(q, s) : "status " + std::to_string((int)st) + " " + err;
       // evidence limits and output rows are the original tree's
       for (const DevPos& P : s.pos)
         if (why.empty() && P.card_ev != p.card[P.var]) why = "evidence limit of a padded digit";
+      // a tile the stage marks as holes (a digit above it at an added state)
+      // must hold only entries with some digit at an added state
+      int64_t tiles = 0, skipped = 0;
+      for (const DevStage& S : s.stages) {
+        if (S.n_blocks == 0 || !why.empty()) continue;
+        const auto& pv = q.pvars[S.clique];
+        for (int64_t x0 = 0; x0 < S.n && why.empty(); x0 += 32) {
+          ++tiles;
+          bool flagged = false;
+          for (uint32_t h : S.holes)
+            if (h != 0u && ((x0 >> (h & 31u)) & ((1ll << ((h >> 5) & 31u)) - 1)) >= (int64_t)(h >> 10)) flagged = true;
+          if (!flagged) continue;
+          ++skipped;
+          for (int64_t e = x0; e < x0 + 32 && why.empty(); ++e) {
+            int64_t r = e;
+            bool hole = false;
+            for (int i = (int)pv.size() - 1; i >= 0; --i) {
+              if (r % q.card[pv[i]] >= p.card[pv[i]]) hole = true;
+              r /= q.card[pv[i]];
+            }
+            if (!hole) why = "tile at " + std::to_string(x0) + " of clique " + std::to_string(S.clique) +
+                             " marked as holes holds entry " + std::to_string(e);
+          }
+        }
+      }
       if (why.empty()) {
-        std::printf("pad cb=%d cases=%d OK items=%zu\n", kCaseLanes, cases, s.items.size());
+        std::printf("pad cb=%d cases=%d OK items=%zu hole-tiles=%.3f\n", kCaseLanes, cases, s.items.size(),
+                    tiles ? (double)skipped / tiles : 0.0);
       } else {
         std::printf("pad cb=%d cases=%d FAIL %s\n", kCaseLanes, cases, why.c_str());
         ++bad;

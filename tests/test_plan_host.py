@@ -9,7 +9,8 @@ fan-out), on trees with empty separators and on the separator sweep.
 Trees with cardinalities other than powers of two also get the padded plan
 (every cardinality raised to a power of two, the added states impossible):
 its case-lane schedules are checked the same way, its evidence limits and
-output rows must be the original tree's, and every padded table entry,
+output rows must be the original tree's, every tile a stage marks for
+skipping must hold only added-state entries, and every padded table entry,
 decoded from its own digits, must map to the original entry with the same
 digits, or be a hole exactly where a digit is an added state."""
 import os
@@ -89,6 +90,15 @@ def test_schedules_of_the_workloads(checker, name):
         assert len(pad) == 3 and pad[-1].startswith("padmap OK"), lines
         for ln in pad[:2]:
             assert " OK " in ln or (name not in PADDED_TREES and " UNSUPPORTED " in ln), ln
+
+
+def test_planted_hole_tile_mistake_is_caught(checker):
+    """A stage's first added-state digit given one state too few: tiles at
+    the digit's last real state are then marked as holes, and hold entries
+    that are not."""
+    t = synth.small_tree()
+    rc, lines = _run(checker, t.card, t.cliques, t.parent, "plant-holes")
+    assert rc == 1 and any(ln.startswith("pad cb=32") and "marked as holes" in ln for ln in lines), lines
 
 
 def test_planted_padding_mistake_is_caught(checker):
