@@ -214,13 +214,17 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   auto chk = [&](cudaError_t e) {
     if (err == cudaSuccess && e != cudaSuccess) err = e;
   };
+  // (the whole-tree kernel writes each case's row, totals and status itself)
+  const bool whole = sc.cb == kWholeTree;
   const int64_t msg_rows = sc.cb == kCaseLanes ? (int64_t)sc.n_cb * kCaseLanes : n_cases;
-  chk(cudaMemsetAsync((T*)t->d_msg + (int64_t)case0 * p.msg_stride, 0,
-                      (size_t)msg_rows * p.msg_stride * sizeof(T), s));
-  chk(cudaMemsetAsync(t->d_sums + (int64_t)case0 * 2 * p.n_cliques, 0,
-                      (size_t)n_cases * 2 * p.n_cliques * sizeof(double), s));
-  chk(cudaMemsetAsync(t->d_status + case0, 0, (size_t)n_cases * sizeof(int32_t), s));
-  chk(cudaMemsetAsync(t->d_done, 0, (1 + 2ull * p.n_cliques * sc.n_cb) * sizeof(int32_t), s));
+  if (!whole) {
+    chk(cudaMemsetAsync((T*)t->d_msg + (int64_t)case0 * p.msg_stride, 0,
+                        (size_t)msg_rows * p.msg_stride * sizeof(T), s));
+    chk(cudaMemsetAsync(t->d_sums + (int64_t)case0 * 2 * p.n_cliques, 0,
+                        (size_t)n_cases * 2 * p.n_cliques * sizeof(double), s));
+    chk(cudaMemsetAsync(t->d_status + case0, 0, (size_t)n_cases * sizeof(int32_t), s));
+    chk(cudaMemsetAsync(t->d_done, 0, (1 + 2ull * p.n_cliques * sc.n_cb) * sizeof(int32_t), s));
+  }
   // the error word reports this propagation (a timed-out one leaves nothing
   // behind: every accumulator above starts again from zero)
   chk(cudaMemsetAsync(t->d_err, 0, sizeof(int32_t), s));
@@ -289,6 +293,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
     w.span = t->d_span;
     w.base_in_smem = sc.small.base_in_smem ? 1 : 0;
     w.base_len = p.base_len;
+    w.desc_resident = sc.small.desc_resident ? 1 : 0;
     chk(launch_small<T>(w, ge.grid, ge.smem, s));
   } else if constexpr (std::is_same<T, float>::value) {
     if (sc.cb == kCaseLanes) chk(launch_propagate_cl(a, ge.grid, ge.smem, ge.padded, s));
@@ -370,9 +375,9 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cu
     if ((st = upload_vec(t, &ge->dev_bufs, &ge->lv_stage_off, sp.lv_stage_off, "schedule upload")) != JT_OK)
       return st;
     ge->smem = sp.smem;
-    // every case is one CTA's work; a few CTAs per SM share its shared memory
-    const int per_sm = std::max(1, std::min(4, smem_budget(t->device, 1) / std::max(1, sp.smem)));
-    ge->grid = (int32_t)std::min<int64_t>(n_cases, (int64_t)sms * per_sm);
+    // every case is one CTA's work; a CTA of 1024 threads at 64 registers
+    // fills an SM's register file, so one per SM is resident
+    ge->grid = (int32_t)std::min<int64_t>(n_cases, (int64_t)sms);
   }
   if (const char* dbg = std::getenv("JT_DEBUG_PLAN"); dbg && *dbg == '1') {
     std::fprintf(stderr, "[jt plan] cases=%d cb=%d n_cb=%d items=%zu grid=%d smem=%d ring=%d win_max=%d\n", n_cases,

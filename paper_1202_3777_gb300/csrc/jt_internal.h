@@ -345,13 +345,15 @@ struct Schedule {
     int32_t levels = 0;
     int32_t smem = 0;                       // dynamic shared memory of one CTA
     bool base_in_smem = false;              // the clique tables fit beside the rest: staged once per CTA
+    bool desc_resident = false;             // every level's descriptors fit (lv_blob_max is then all
+                                            // of them): staged once per CTA
   } small;
 };
 
 // Cases per work item of a whole-tree schedule (reported as 0): every case
 // of the range is one work item, propagated by one CTA from its shared memory.
 constexpr int kWholeTree = 0;
-constexpr int kSmallSeg = 256;              // entries of one segment (a warp's share of a clique)
+constexpr int kSmallSeg = 32;               // entries of one segment (a warp's share of a clique)
 
 // Plan the schedule for `n_cases` cases in blocks of `cb` on a device with
 // `n_sm` SMs and `smem_bytes` of dynamic shared memory per CTA.
@@ -390,6 +392,7 @@ struct SmallArgs {
   unsigned long long* span;     // [2] kernel span (global timer), or null
   int32_t base_in_smem;         // copy the clique tables into shared memory once per CTA
   int64_t base_len;             // elements of the clique tables (a multiple of 32)
+  int32_t desc_resident;        // every level's descriptors staged once per CTA
 };
 
 // Dynamic shared memory of the propagation kernel for a schedule.

@@ -933,6 +933,17 @@ jt_status build_small_schedule(const Plan& p, int elem, int n_cases, int n_sm, i
     sp.base_in_smem = true;
     sp.smem = (int32_t)with_base;
   }
+  // and every level's descriptors at once, when they also fit: staged once
+  // per CTA instead of once per level and case
+  const int32_t all_units = (int32_t)sp.blobs.size();
+  const int64_t with_all = (int64_t)small_smem_bytes(p.msg_stride, p.msg_total, p.n_cliques, p.n_vars, elem,
+                                                     all_units) +
+                           (sp.base_in_smem ? p.base_len * elem : 0);
+  if (with_all <= smem_bytes) {
+    sp.desc_resident = true;
+    sp.lv_blob_max = all_units;
+    sp.smem = (int32_t)with_all;
+  }
   (void)n_cases;
   return JT_OK;
 }

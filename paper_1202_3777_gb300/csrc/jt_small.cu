@@ -19,7 +19,15 @@
 // with the same quantities as the persistent kernel (Eq. 1-3 with the
 // messages scaled to mean one, mu_g = u_g |S_g| / sigma_g, and the ratio
 // rho_c = delta_c (sigma_c / Delta_parent) / u_c with 0/0 := 0), so the
-// finalisation reads the case's message row and stage totals unchanged.
+// finalisation kernel reads the case's message row and stage totals
+// unchanged.  (Finalising in this kernel was measured slower: its FP64 sums
+// and divisions then run on one SM, whose FP64 rate on this part is small.)
+//
+// Latency matters here (a single case of a small tree is a chain of
+// 2 x depth levels on one SM): every level's descriptors stay in shared
+// memory when they fit, segments are 32 entries so that a level's work
+// spreads over every warp, and evidence is tested only on the positions the
+// case observes.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -30,7 +38,7 @@
 namespace jt {
 namespace {
 
-constexpr int kSmallThreads = 512;
+constexpr int kSmallThreads = 1024;
 
 // Add v at tab[key] for every lane of the warp, where runs of consecutive
 // lanes share a key (a key over digits above the lanes' entries): an
@@ -64,6 +72,17 @@ __device__ __forceinline__ void run_segment(const SmallArgs<T>& a, const T* base
   const DevField* fld = reinterpret_cast<const DevField*>(port + S.np);
   const DevPos* pos = reinterpret_cast<const DevPos*>(fld + S.nf);
   const int e1 = min(S.n, e0 + kSmallSeg);
+  // the case's observed positions of the stage (bit i = position i), found
+  // once per segment; a state beyond the cardinality marks the case and
+  // masks nothing
+  uint32_t obs = 0u;
+  for (int i = lane; i < S.k; i += 32) {
+    const int st = ev[pos[i].var];
+    if (st < 0) continue;
+    if (st >= pos[i].card_ev) atomicOr(&a.status[cs], kStatusBadState);
+    else obs |= 1u << i;
+  }
+  obs = __reduce_or_sync(kFull, obs);
   // (the segment's total in the element type -- at most kSmallSeg terms per
   // lane group -- then once per warp into the stage total in FP64)
   T acc = T(0);
@@ -71,16 +90,10 @@ __device__ __forceinline__ void run_segment(const SmallArgs<T>& a, const T* base
     const int e = eb + lane;
     const bool valid = e < e1;
     T f = valid ? base[S.base_off + e] : T(0);
-    for (int i = 0; i < S.k; ++i) {
-      const DevPos& P = pos[i];
-      const int st = ev[P.var];
-      if (st < 0) continue;
-      if (st >= P.card_ev) {
-        atomicOr(&a.status[cs], kStatusBadState);
-        continue;
-      }
+    for (uint32_t m = obs; m != 0u; m &= m - 1u) {
+      const DevPos& P = pos[__ffs(m) - 1];
       const uint32_t d = POW2 ? ((uint32_t)e >> P.sh) & ((1u << P.cb) - 1u) : digit_of((uint32_t)e, P);
-      if (d != (uint32_t)st) f = T(0);
+      if (d != (uint32_t)ev[P.var]) f = T(0);
     }
     if (f != T(0)) {
       for (int pi = 0; pi < S.nin; ++pi) {
@@ -102,7 +115,7 @@ __device__ __forceinline__ void run_segment(const SmallArgs<T>& a, const T* base
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSmallThreads) k_small(const SmallArgs<T> a) {
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small(const SmallArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nc = a.n_cliques;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSmallThreads / 32;
@@ -126,21 +139,29 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const SmallArgs<T> a) {
     base = sb;
     __syncthreads();
   }
+  if (a.desc_resident) {
+    for (int i = tid; i < a.lv_blob_off[a.levels]; i += kSmallThreads) lvd[i] = __ldg(a.blobs + i);
+    __syncthreads();
+  }
   if (a.span != nullptr && tid == 0) atomicMin(a.span, (unsigned long long)global_ns());
   for (int cs = a.case0 + (int)blockIdx.x; cs < a.case0 + a.n_cases; cs += (int)gridDim.x) {
+    if (tid == 0) a.status[cs] = 0;
     for (int64_t i = tid; i < a.msg_stride; i += kSmallThreads) msg[i] = T(0);
     for (int i = tid; i < 2 * nc; i += kSmallThreads) sums[i] = 0.0;
     for (int i = tid; i < nc; i += kSmallThreads) scale[i] = T(0);
     for (int i = tid; i < a.n_vars; i += kSmallThreads) ev[i] = a.ev[(int64_t)cs * a.n_vars + i];
     __syncthreads();
     for (int lv = 0; lv < a.levels; ++lv) {
-      for (int i = a.lv_blob_off[lv] + tid; i < a.lv_blob_off[lv + 1]; i += kSmallThreads)
-        lvd[i - a.lv_blob_off[lv]] = __ldg(a.blobs + i);
-      __syncthreads();
+      const uint4* lvl = a.desc_resident ? lvd + a.lv_blob_off[lv] : lvd;   // this level's descriptors
+      if (!a.desc_resident) {
+        for (int i = a.lv_blob_off[lv] + tid; i < a.lv_blob_off[lv + 1]; i += kSmallThreads)
+          lvd[i - a.lv_blob_off[lv]] = __ldg(a.blobs + i);
+        __syncthreads();
+      }
       // the ratios of the own separators of the level's distribute stages (a
       // warp per stage)
       for (int j = a.lv_stage_off[lv] + warp; j < a.lv_stage_off[lv + 1]; j += nw) {
-        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvd + a.stage_blob[a.lv_stage[j]]);
+        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + a.stage_blob[a.lv_stage[j]]);
         const DevStage& S = *reinterpret_cast<const DevStage*>(blob);
         const DevPort* port = reinterpret_cast<const DevPort*>(blob + sizeof(DevStage));
         for (int pi = 0; pi < S.nin; ++pi) {
@@ -157,7 +178,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const SmallArgs<T> a) {
       __syncthreads();
       for (int sg = a.seg_lv[lv] + warp; sg < a.seg_lv[lv + 1]; sg += nw) {
         const int2 g = a.segs[sg];
-        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvd + a.stage_blob[g.x]);
+        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + a.stage_blob[g.x]);
         if (reinterpret_cast<const DevStage*>(blob)->bits >= 0)
           run_segment<T, true>(a, base, blob, g.y, msg, rho, scale, ev, sums, cs, lane);
         else
@@ -168,7 +189,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const SmallArgs<T> a) {
       for (int j = a.lv_stage_off[lv] + tid; j < a.lv_stage_off[lv + 1]; j += kSmallThreads) {
         const int st = a.lv_stage[j];
         if (st >= nc) continue;
-        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvd + a.stage_blob[st]);
+        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + a.stage_blob[st]);
         const DevStage& S = *reinterpret_cast<const DevStage*>(blob);
         const DevPort* port = reinterpret_cast<const DevPort*>(blob + sizeof(DevStage));
         int size = 1;
