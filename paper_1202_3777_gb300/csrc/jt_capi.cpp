@@ -64,12 +64,7 @@ struct GraphEntry {
   bool padded = false;          // runs over the tree's power-of-two padded plan
   // whole-tree schedules: the level plan on the device
   const uint4* small_blobs = nullptr;
-  const int32_t* lv_blob_off = nullptr;
-  const int32_t* stage_blob = nullptr;
-  const int2* segs = nullptr;
-  const int32_t* seg_lv = nullptr;
-  const int32_t* lv_stage = nullptr;
-  const int32_t* lv_stage_off = nullptr;
+  const int32_t* small_idx = nullptr;   // packed level indices (SmallPlan::idx)
 };
 
 // State of the paper-literal per-message propagation (jt_propagate_per_message),
@@ -272,13 +267,16 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
     SmallArgs<T> w{};
     w.base = (const T*)t->base;
     w.blobs = ge.small_blobs;
-    w.lv_blob_off = ge.lv_blob_off;
     w.lv_blob_max = sc.small.lv_blob_max;
-    w.stage_blob = ge.stage_blob;
-    w.segs = ge.segs;
-    w.seg_lv = ge.seg_lv;
-    w.lv_stage = ge.lv_stage;
-    w.lv_stage_off = ge.lv_stage_off;
+    w.idx = ge.small_idx;
+    w.idx_len = (int32_t)sc.small.idx.size();
+    w.o_seg_lv = sc.small.o_seg_lv;
+    w.o_lv_stage_off = sc.small.o_lv_stage_off;
+    w.o_stage_blob = sc.small.o_stage_blob;
+    w.o_lv_stage = sc.small.o_lv_stage;
+    w.o_sep_size = sc.small.o_sep_size;
+    w.o_segs = sc.small.o_segs;
+    w.idx_in_smem = sc.small.idx_in_smem ? 1 : 0;
     w.levels = sc.small.levels;
     w.ev = t->d_ev;
     w.n_vars = p.n_vars;
@@ -294,6 +292,7 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
     w.base_in_smem = sc.small.base_in_smem ? 1 : 0;
     w.base_len = p.base_len;
     w.desc_resident = sc.small.desc_resident ? 1 : 0;
+    w.trace = trace;
     chk(launch_small<T>(w, ge.grid, ge.smem, s));
   } else if constexpr (std::is_same<T, float>::value) {
     if (sc.cb == kCaseLanes) chk(launch_propagate_cl(a, ge.grid, ge.smem, ge.padded, s));
@@ -367,13 +366,7 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cu
   if (cb == kWholeTree) {
     const auto& sp = sc.small;
     if ((st = upload_vec(t, &ge->dev_bufs, &ge->small_blobs, sp.blobs, "schedule upload")) != JT_OK) return st;
-    if ((st = upload_vec(t, &ge->dev_bufs, &ge->lv_blob_off, sp.lv_blob_off, "schedule upload")) != JT_OK) return st;
-    if ((st = upload_vec(t, &ge->dev_bufs, &ge->stage_blob, sp.stage_blob, "schedule upload")) != JT_OK) return st;
-    if ((st = upload_vec(t, &ge->dev_bufs, &ge->segs, sp.segs, "schedule upload")) != JT_OK) return st;
-    if ((st = upload_vec(t, &ge->dev_bufs, &ge->seg_lv, sp.seg_lv, "schedule upload")) != JT_OK) return st;
-    if ((st = upload_vec(t, &ge->dev_bufs, &ge->lv_stage, sp.lv_stage, "schedule upload")) != JT_OK) return st;
-    if ((st = upload_vec(t, &ge->dev_bufs, &ge->lv_stage_off, sp.lv_stage_off, "schedule upload")) != JT_OK)
-      return st;
+    if ((st = upload_vec(t, &ge->dev_bufs, &ge->small_idx, sp.idx, "schedule upload")) != JT_OK) return st;
     ge->smem = sp.smem;
     // every case is one CTA's work; a CTA of 1024 threads at 64 registers
     // fills an SM's register file, so one per SM is resident
@@ -1171,7 +1164,19 @@ jt_status jt_profile_propagate(jt_tree t, int32_t first, int32_t n, void* stream
     std::vector<uint64_t> h(n_items * kTraceSlots);
     if (err == cudaSuccess) err = cudaMemcpy(h.data(), trace, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
     cudaFree(trace);
-    if (FILE* f = err == cudaSuccess ? std::fopen(trace_path, "w") : nullptr) {
+    FILE* f = err == cudaSuccess ? std::fopen(trace_path, "w") : nullptr;
+    if (f != nullptr && ge->sched.cb == kWholeTree) {
+      // phase ends per level of the first case (ns from the kernel start)
+      std::fprintf(f, "level,start_ns,ratios_ns,segments_ns,scales_ns\n");
+      std::fprintf(f, "-1,0,0,%lld,%lld\n", (long long)(h[1] - h[0]), (long long)(h[1] - h[0]));
+      for (int lv = 0; lv < ge->sched.small.levels; ++lv)
+        std::fprintf(f, "%d,%lld,%lld,%lld,%lld\n", lv, (long long)(h[2 + 4 * lv] - h[0]),
+                     (long long)(h[3 + 4 * lv] - h[0]), (long long)(h[4 + 4 * lv] - h[0]),
+                     (long long)(h[5 + 4 * lv] - h[0]));
+      std::fclose(f);
+      f = nullptr;
+    }
+    if (f != nullptr) {
       uint64_t t0 = ~0ull;
       for (size_t i = 0; i < n_items; ++i)
         if (h[i * kTraceSlots + 1]) t0 = std::min(t0, h[i * kTraceSlots + 1]);

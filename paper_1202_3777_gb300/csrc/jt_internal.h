@@ -347,6 +347,13 @@ struct Schedule {
     bool base_in_smem = false;              // the clique tables fit beside the rest: staged once per CTA
     bool desc_resident = false;             // every level's descriptors fit (lv_blob_max is then all
                                             // of them): staged once per CTA
+    // every index array above and the separator sizes, packed (int32) for
+    // one copy into shared memory: lv_blob_off | seg_lv | lv_stage_off |
+    // stage_blob | lv_stage | sep_size | segs (as pairs), each part starting
+    // on an even element; offsets of the parts
+    std::vector<int32_t> idx;
+    int32_t o_seg_lv = 0, o_lv_stage_off = 0, o_stage_blob = 0, o_lv_stage = 0, o_sep_size = 0, o_segs = 0;
+    bool idx_in_smem = false;               // the packed indices fit too: staged once per CTA
   } small;
 };
 
@@ -372,13 +379,14 @@ template <typename T>
 struct SmallArgs {
   const T* base;                // permuted clique tables
   const uint4* blobs;           // level-ordered stage descriptors
-  const int32_t* lv_blob_off;   // [levels + 1]
   int32_t lv_blob_max;          // 16-byte units of the largest level (its shared-memory staging)
-  const int32_t* stage_blob;    // [2 n_cliques] within the level's descriptors
-  const int2* segs;
-  const int32_t* seg_lv;        // [levels + 1]
-  const int32_t* lv_stage;
-  const int32_t* lv_stage_off;  // [levels + 1]
+  // packed indices (Schedule::SmallPlan::idx): lv_blob_off [levels + 1],
+  // seg_lv [levels + 1], lv_stage_off [levels + 1], stage_blob [2 n_cliques]
+  // (within the level's descriptors), lv_stage, sep_size [n_cliques], segs
+  const int32_t* idx;
+  int32_t idx_len;              // elements (a multiple of 4)
+  int32_t o_seg_lv, o_lv_stage_off, o_stage_blob, o_lv_stage, o_sep_size, o_segs;
+  int32_t idx_in_smem;
   int32_t levels;
   const int16_t* ev;            // [max_cases][n_vars], -1 = unobserved
   int32_t n_vars;
@@ -393,6 +401,7 @@ struct SmallArgs {
   int32_t base_in_smem;         // copy the clique tables into shared memory once per CTA
   int64_t base_len;             // elements of the clique tables (a multiple of 32)
   int32_t desc_resident;        // every level's descriptors staged once per CTA
+  uint64_t* trace;              // [2 + 4 levels] phase times of CTA 0's first case, or null
 };
 
 // Dynamic shared memory of the propagation kernel for a schedule.

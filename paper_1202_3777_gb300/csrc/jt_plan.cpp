@@ -926,24 +926,48 @@ jt_status build_small_schedule(const Plan& p, int elem, int n_cases, int n_sm, i
     return JT_ERR_UNSUPPORTED;
   }
   sp.smem = need;
-  // the clique tables too, when they fit: every level then reads them from
-  // shared memory
-  const int64_t with_base = (int64_t)need + p.base_len * elem;
-  if (with_base <= smem_bytes) {
-    sp.base_in_smem = true;
-    sp.smem = (int32_t)with_base;
+  // the packed index arrays
+  auto put_idx = [&](const std::vector<int32_t>& v) {
+    const int32_t o = (int32_t)sp.idx.size();
+    sp.idx.insert(sp.idx.end(), v.begin(), v.end());
+    if (sp.idx.size() & 1) sp.idx.push_back(0);
+    return o;
+  };
+  sp.idx.clear();
+  put_idx(sp.lv_blob_off);
+  sp.o_seg_lv = put_idx(sp.seg_lv);
+  sp.o_lv_stage_off = put_idx(sp.lv_stage_off);
+  sp.o_stage_blob = put_idx(sp.stage_blob);
+  sp.o_lv_stage = put_idx(sp.lv_stage);
+  sp.o_sep_size = put_idx(p.sep_size);
+  sp.o_segs = (int32_t)sp.idx.size();
+  for (const int2& g : sp.segs) {
+    sp.idx.push_back(g.x);
+    sp.idx.push_back(g.y);
   }
-  // and every level's descriptors at once, when they also fit: staged once
-  // per CTA instead of once per level and case
+  while (sp.idx.size() % 4) sp.idx.push_back(0);
+  // what else fits in shared memory, in order of use per entry: the clique
+  // tables (read by every entry), the packed indices (per segment), every
+  // level's descriptors at once (staged once per CTA instead of once per
+  // level and case)
+  int64_t used = need;
+  if (used + p.base_len * elem <= smem_bytes) {
+    sp.base_in_smem = true;
+    used += p.base_len * elem;
+  }
+  const int64_t idx_bytes = (int64_t)sp.idx.size() * 4;
+  if (used + idx_bytes <= smem_bytes) {
+    sp.idx_in_smem = true;
+    used += idx_bytes;
+  }
   const int32_t all_units = (int32_t)sp.blobs.size();
-  const int64_t with_all = (int64_t)small_smem_bytes(p.msg_stride, p.msg_total, p.n_cliques, p.n_vars, elem,
-                                                     all_units) +
-                           (sp.base_in_smem ? p.base_len * elem : 0);
-  if (with_all <= smem_bytes) {
+  const int64_t extra_desc = 16ll * (all_units - sp.lv_blob_max);
+  if (used + extra_desc <= smem_bytes) {
     sp.desc_resident = true;
     sp.lv_blob_max = all_units;
-    sp.smem = (int32_t)with_all;
+    used += extra_desc;
   }
+  sp.smem = (int32_t)used;
   (void)n_cases;
   return JT_OK;
 }

@@ -117,6 +117,7 @@ __device__ __forceinline__ void run_segment(const SmallArgs<T>& a, const T* base
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const SmallArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (a.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0) a.trace[0] = global_ns();
   const int nc = a.n_cliques;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSmallThreads / 32;
   T* msg = reinterpret_cast<T*>(smem);                                   // [msg_stride]
@@ -127,23 +128,44 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const SmallArgs<T> a
   // descriptors are read as 16-byte units)
   int16_t* ev = reinterpret_cast<int16_t*>(reinterpret_cast<unsigned char*>(sums) + ((3 * nc * 8 + 15) & ~15));
   uint4* lvd = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(ev) + ((2 * a.n_vars + 15) & ~15));
-  // (the level's stage descriptors, copied in before the level runs; then,
-  // when they fit, the tree's clique tables, copied in once per CTA)
+  // then, when they fit: the clique tables and the packed indices, staged
+  // once per CTA (and every level's descriptors, lv_blob_max then covering
+  // all of them)
+  unsigned char* after = reinterpret_cast<unsigned char*>(lvd + a.lv_blob_max);
   const T* base = a.base;
   if (a.base_in_smem) {
-    T* sb = reinterpret_cast<T*>(lvd + a.lv_blob_max);
+    T* sb = reinterpret_cast<T*>(after);
     const uint4* src = reinterpret_cast<const uint4*>(a.base);
     uint4* dst = reinterpret_cast<uint4*>(sb);
     const int64_t n16 = a.base_len * (int64_t)sizeof(T) / 16;
     for (int64_t i = tid; i < n16; i += kSmallThreads) dst[i] = __ldg(src + i);
     base = sb;
-    __syncthreads();
+    after += a.base_len * sizeof(T);
+  }
+  const int32_t* ix = a.idx;
+  if (a.idx_in_smem) {
+    const uint4* src = reinterpret_cast<const uint4*>(a.idx);
+    uint4* dst = reinterpret_cast<uint4*>(after);
+    for (int i = tid; i < a.idx_len / 4; i += kSmallThreads) dst[i] = __ldg(src + i);
+    ix = reinterpret_cast<const int32_t*>(after);
   }
   if (a.desc_resident) {
-    for (int i = tid; i < a.lv_blob_off[a.levels]; i += kSmallThreads) lvd[i] = __ldg(a.blobs + i);
-    __syncthreads();
+    for (int i = tid; i < a.lv_blob_max; i += kSmallThreads) lvd[i] = __ldg(a.blobs + i);
   }
+  __syncthreads();
+  const int32_t* lv_blob_off = ix;
+  const int32_t* seg_lv = ix + a.o_seg_lv;
+  const int32_t* lv_stage_off = ix + a.o_lv_stage_off;
+  const int32_t* stage_blob = ix + a.o_stage_blob;
+  const int32_t* lv_stage = ix + a.o_lv_stage;
+  const int32_t* sep_size = ix + a.o_sep_size;
+  const int2* segs = reinterpret_cast<const int2*>(ix + a.o_segs);
   if (a.span != nullptr && tid == 0) atomicMin(a.span, (unsigned long long)global_ns());
+  // JT_TRACE: CTA 0's first case, [0] kernel start, [1] prologue done, then
+  // per level its start and the ends of its first phase (scales and ratios),
+  // its segments, and (unused, equal) a third stamp
+  uint64_t* tr = (a.trace != nullptr && blockIdx.x == 0) ? a.trace : nullptr;
+  if (tr != nullptr && tid == 0) tr[1] = global_ns();
   for (int cs = a.case0 + (int)blockIdx.x; cs < a.case0 + a.n_cases; cs += (int)gridDim.x) {
     if (tid == 0) a.status[cs] = 0;
     for (int64_t i = tid; i < a.msg_stride; i += kSmallThreads) msg[i] = T(0);
@@ -152,16 +174,28 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const SmallArgs<T> a
     for (int i = tid; i < a.n_vars; i += kSmallThreads) ev[i] = a.ev[(int64_t)cs * a.n_vars + i];
     __syncthreads();
     for (int lv = 0; lv < a.levels; ++lv) {
-      const uint4* lvl = a.desc_resident ? lvd + a.lv_blob_off[lv] : lvd;   // this level's descriptors
+      if (tr != nullptr && tid == 0) tr[2 + 4 * lv] = global_ns();
+      const uint4* lvl = a.desc_resident ? lvd + lv_blob_off[lv] : lvd;   // this level's descriptors
       if (!a.desc_resident) {
-        for (int i = a.lv_blob_off[lv] + tid; i < a.lv_blob_off[lv + 1]; i += kSmallThreads)
-          lvd[i - a.lv_blob_off[lv]] = __ldg(a.blobs + i);
+        for (int i = lv_blob_off[lv] + tid; i < lv_blob_off[lv + 1]; i += kSmallThreads)
+          lvd[i - lv_blob_off[lv]] = __ldg(a.blobs + i);
         __syncthreads();
       }
-      // the ratios of the own separators of the level's distribute stages (a
-      // warp per stage)
-      for (int j = a.lv_stage_off[lv] + warp; j < a.lv_stage_off[lv + 1]; j += nw) {
-        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + a.stage_blob[a.lv_stage[j]]);
+      // first phase, one barrier: the scales |S_c| / sigma_c of the previous
+      // level's collect messages (the totals are complete; this level's
+      // parents read them), and the ratios of the own separators of this
+      // level's distribute stages (a warp per stage)
+      if (lv > 0)
+        for (int j = lv_stage_off[lv - 1] + tid; j < lv_stage_off[lv]; j += kSmallThreads) {
+          const int st = lv_stage[j];
+          if (st >= nc) continue;
+          const double sg = sums[st];
+          scale[st] = sg > 0.0 ? (T)((double)sep_size[st] / sg) : T(0);
+        }
+      for (int j = lv_stage_off[lv] + warp; j < lv_stage_off[lv + 1]; j += nw) {
+        const int st = lv_stage[j];
+        if (st < nc) continue;
+        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + stage_blob[st]);
         const DevStage& S = *reinterpret_cast<const DevStage*>(blob);
         const DevPort* port = reinterpret_cast<const DevPort*>(blob + sizeof(DevStage));
         for (int pi = 0; pi < S.nin; ++pi) {
@@ -176,30 +210,19 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(const SmallArgs<T> a
         }
       }
       __syncthreads();
-      for (int sg = a.seg_lv[lv] + warp; sg < a.seg_lv[lv + 1]; sg += nw) {
-        const int2 g = a.segs[sg];
-        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + a.stage_blob[g.x]);
+      if (tr != nullptr && tid == 0) tr[3 + 4 * lv] = global_ns();
+      for (int sg = seg_lv[lv] + warp; sg < seg_lv[lv + 1]; sg += nw) {
+        const int2 g = segs[sg];
+        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + stage_blob[g.x]);
         if (reinterpret_cast<const DevStage*>(blob)->bits >= 0)
           run_segment<T, true>(a, base, blob, g.y, msg, rho, scale, ev, sums, cs, lane);
         else
           run_segment<T, false>(a, base, blob, g.y, msg, rho, scale, ev, sums, cs, lane);
       }
       __syncthreads();
-      // scales of the level's collect messages (for the parents' level)
-      for (int j = a.lv_stage_off[lv] + tid; j < a.lv_stage_off[lv + 1]; j += kSmallThreads) {
-        const int st = a.lv_stage[j];
-        if (st >= nc) continue;
-        const unsigned char* blob = reinterpret_cast<const unsigned char*>(lvl + a.stage_blob[st]);
-        const DevStage& S = *reinterpret_cast<const DevStage*>(blob);
-        const DevPort* port = reinterpret_cast<const DevPort*>(blob + sizeof(DevStage));
-        int size = 1;
-        for (int pi = S.nin; pi < S.np; ++pi)
-          if (port[pi].kind == kPortU) size = port[pi].size;
-        const double sg = sums[st];
-        scale[st] = sg > 0.0 ? (T)((double)size / sg) : T(0);
-      }
-      __syncthreads();
+      if (tr != nullptr && tid == 0) tr[4 + 4 * lv] = tr[5 + 4 * lv] = global_ns();
     }
+    tr = nullptr;
     T* row = a.msg + (int64_t)cs * a.msg_stride;
     for (int64_t i = tid; i < a.msg_stride; i += kSmallThreads) row[i] = msg[i];
     for (int i = tid; i < 2 * nc; i += kSmallThreads) a.sums[(int64_t)cs * 2 * nc + i] = sums[i];

@@ -166,6 +166,54 @@ int main(int argc, char** argv) {
       ++bad;
     }
   }
+  // the whole-tree plan: the packed indices unpack to the plan's arrays, and
+  // a collect stage's scale (written in the first phase of the level after
+  // its own) is ready before its parent's collect level runs
+  {
+    Schedule s;
+    err.clear();
+    const jt_status st = build_small_schedule(p, 4, 64, 152, smem, &s, &err);
+    if (st == JT_ERR_UNSUPPORTED) {
+      std::printf("small UNSUPPORTED %s\n", err.c_str());
+    } else if (st != JT_OK) {
+      std::printf("small FAIL status %d %s\n", (int)st, err.c_str());
+      ++bad;
+    } else {
+      const auto& sp = s.small;
+      std::string why;
+      auto same = [&](int32_t o, const std::vector<int32_t>& v, const char* what) {
+        for (size_t i = 0; i < v.size() && why.empty(); ++i)
+          if (sp.idx[o + i] != v[i]) why = std::string("packed ") + what + " differs";
+      };
+      same(0, sp.lv_blob_off, "lv_blob_off");
+      same(sp.o_seg_lv, sp.seg_lv, "seg_lv");
+      same(sp.o_lv_stage_off, sp.lv_stage_off, "lv_stage_off");
+      same(sp.o_stage_blob, sp.stage_blob, "stage_blob");
+      same(sp.o_lv_stage, sp.lv_stage, "lv_stage");
+      same(sp.o_sep_size, p.sep_size, "sep_size");
+      for (size_t i = 0; i < sp.segs.size() && why.empty(); ++i)
+        if (sp.idx[sp.o_segs + 2 * i] != sp.segs[i].x || sp.idx[sp.o_segs + 2 * i + 1] != sp.segs[i].y)
+          why = "packed segs differ";
+      if (why.empty() && (sp.idx.size() % 4 || sp.o_segs % 2)) why = "packed layout misaligned";
+      std::vector<int> level_of(2 * nc, -1);
+      for (int lv = 0; lv < sp.levels; ++lv)
+        for (int j = sp.lv_stage_off[lv]; j < sp.lv_stage_off[lv + 1]; ++j) level_of[sp.lv_stage[j]] = lv;
+      for (int c = 1; c < nc && why.empty(); ++c) {
+        const int par = p.parent[c];
+        const int lc = level_of[c], lp = par == 0 ? level_of[nc] : level_of[par];
+        if (lc < 0 || lp < 0 || lp <= lc)
+          why = "collect of clique " + std::to_string(c) + " is not before its parent's stage";
+      }
+      if (why.empty() && sp.smem > smem) why = "shared memory over budget";
+      if (why.empty()) {
+        std::printf("small OK levels=%d segs=%zu smem=%d idx_in_smem=%d desc_resident=%d\n", sp.levels,
+                    sp.segs.size(), sp.smem, (int)sp.idx_in_smem, (int)sp.desc_resident);
+      } else {
+        std::printf("small FAIL %s\n", why.c_str());
+        ++bad;
+      }
+    }
+  }
   // trees with other cardinalities: the power-of-two padded plan, its
   // case-lane schedules, and the map that derives its tables
   if (std::any_of(p.pow2.begin(), p.pow2.end(), [](uint8_t x) { return x == 0; })) {

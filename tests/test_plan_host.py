@@ -4,7 +4,9 @@ tree for one case, 4- and 8-case blocks, and checks what the persistent
 kernel relies on: every block of every stage is one work item per case
 block, the dependencies are those of Algorithms 2-4, and no item waits for
 a block queued after it.  Run on the workloads, on merged trees (high
-fan-out), on trees with empty separators and on the separator sweep.
+fan-out), on trees with empty separators and on the separator sweep.  The
+whole-tree plan (one CTA per case) must pack its level indices so that they
+unpack to its arrays, and order every collect stage before its parent's.
 
 Trees with cardinalities other than powers of two also get the padded plan
 (every cardinality raised to a power of two, the added states impossible):
@@ -65,6 +67,8 @@ TREES = {
 CASE_LANE_TREES = {"large-clique", "high-card", "sep-sweep-4^1", "sep-sweep-4^7"}
 # trees with other cardinalities whose padded plan the case lanes must plan
 PADDED_TREES = {"small", "batched"}
+# trees the whole-tree schedule (one CTA per case) must plan
+WHOLE_TREE_TREES = {"small", "binary-serving", "empty-separators"}
 
 
 def _pow2(t):
@@ -83,6 +87,9 @@ def test_schedules_of_the_workloads(checker, name):
             assert " OK " in ln or " UNSUPPORTED " in ln, ln
         else:
             assert " OK " in ln, ln
+    small = [ln for ln in lines if ln.startswith("small ")]
+    assert len(small) == 1 and (" OK " in small[0] or (name not in WHOLE_TREE_TREES and " UNSUPPORTED " in small[0])), \
+        lines
     pad = [ln for ln in lines if ln.startswith("pad")]
     if _pow2(t):
         assert not pad, lines
@@ -116,13 +123,13 @@ def test_schedules_of_merged_trees(checker, min_sep, cap):
     rc, lines = _run(checker, t.card, m.cliques, m.parent)
     assert rc == 0, lines
     for ln in lines:
-        assert " OK " in ln or (ln.startswith("cb=32 ") and " UNSUPPORTED " in ln), ln
+        assert " OK " in ln or ((ln.startswith("cb=32 ") or ln.startswith("small ")) and " UNSUPPORTED " in ln), ln
 
 
 @pytest.mark.parametrize("plant,what", [("plant-order", "queued after"), ("plant-repeat", "block")])
 def test_planted_schedule_mistakes_are_caught(checker, plant, what):
     t = synth.small_tree()
     rc, lines = _run(checker, t.card, t.cliques, t.parent, plant)
-    planned = [ln for ln in lines if " UNSUPPORTED " not in ln and not ln.startswith("padmap")]
+    planned = [ln for ln in lines if " UNSUPPORTED " not in ln and not ln.startswith(("padmap", "small "))]
     assert rc == 1 and len(planned) >= 4 and all(" FAIL " in ln and what in ln for ln in planned), lines
 
