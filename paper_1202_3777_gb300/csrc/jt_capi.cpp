@@ -762,6 +762,7 @@ jt_status build_permsg(jt_tree t, int layout) {
       if (stride_of(c, v) > 0 && (best < 0 || p.n_entries[c] < p.n_entries[best])) best = c;
     VarSrc& r = vs[(size_t)v];
     r.card = p.card[v];
+    r.card_out = p.card[v];
     r.moff = p.moff[v];
     r.off = (int32_t)p.base_off[best];
     r.size = (int32_t)p.n_entries[best];

@@ -704,20 +704,34 @@ __global__ void __launch_bounds__(256) k_finalize_cl(const FinalArgs<float> a) {
   const int v = (int)blockIdx.x;
   if (v == a.n_vars) {
     if (warp != 0 || !valid) return;
+    // log Z = sum_c (log sigma_c - log |S_c|) + log Delta_root, as the log of
+    // a product (mantissas multiplied, binary exponents summed, both read off
+    // the bits): two logarithms per case instead of two per clique
     const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
-    double acc = 0.0;
+    double pn = 1.0, pd = 1.0;
+    long long en = 0, ed = 0;
     bool zero = false;
+    int terms = 0;
     for (int c = 1; c < a.n_cliques; ++c) {
       const double sg = sums[c];
-      if (!(sg > 0.0)) zero = true;
-      else acc += log(sg) - log((double)a.sep_size[c]);
+      if (!(sg > 0.0)) {
+        zero = true;
+        continue;
+      }
+      pn *= split_exp(sg, en);
+      pd *= split_exp((double)a.sep_size[c], ed);
+      if (++terms == 256) {   // (a product of 256 mantissas stays above 2^-256)
+        pn = split_exp(pn, en);
+        pd = split_exp(pd, ed);
+        terms = 0;
+      }
     }
     const double R = sums[a.n_cliques];
     if (zero || !(R > 0.0)) {
       atomicOr(&a.status[cs], kStatusZero);
       a.logz_out[cs] = -INFINITY;
     } else {
-      a.logz_out[cs] = acc + log(R);
+      a.logz_out[cs] = log(pn) - log(pd) + (double)(en - ed) * 0.69314718055994530942 + log(R);
     }
     return;
   }

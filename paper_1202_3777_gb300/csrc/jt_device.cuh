@@ -226,6 +226,22 @@ __device__ __forceinline__ uint32_t digit_of(uint32_t x, const DevPos& p) {
   return t - udiv(t, (uint32_t)p.card, p.card_magic) * (uint32_t)p.card;
 }
 
+// x = m 2^e with m in [0.5, 1), for finite x > 0, adding e to `ex`: the
+// exponent field is read and replaced with integer operations (no FP64
+// arithmetic); subnormal x goes through frexp.
+__device__ __forceinline__ double split_exp(double x, long long& ex) {
+  const long long b = __double_as_longlong(x);
+  const int f = (int)((b >> 52) & 0x7FF);
+  if (f == 0) {
+    int k;
+    const double m = frexp(x, &k);
+    ex += k;
+    return m;
+  }
+  ex += f - 1022;
+  return __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FE0000000000000ll);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

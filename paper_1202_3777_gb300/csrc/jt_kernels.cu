@@ -1051,6 +1051,23 @@ __global__ void __launch_bounds__(consumers_for(CB) + kControlThreads, ctas_per_
 
 // Normalised marginals (a warp per variable, binned from its source table)
 // and log Z(e) (the last CTA along x), per case (y).
+// Warp-wide product of (pn, pd) mantissa pairs (each in [0.5, 1)) with
+// their binary exponents: every lane ends with the warp's result, the
+// numerator's exponent summed into en and the denominator's into ed.
+__device__ __forceinline__ void mul_reduce(double& pn, double& pd, long long& en, long long& ed) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double qn = __shfl_xor_sync(kFull, pn, o), qd = __shfl_xor_sync(kFull, pd, o);
+    const long long qen = __shfl_xor_sync(kFull, en, o), qed = __shfl_xor_sync(kFull, ed, o);
+    en += qen;
+    ed += qed;
+    pn = split_exp(pn * qn, en);
+    pd = split_exp(pd * qd, ed);
+  }
+}
+
+constexpr int kFinStates = 8;   // variables of at most this many states: one pass over the table
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
   const int cs = a.case0 + (int)blockIdx.y;
@@ -1058,23 +1075,58 @@ __global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
   const T* row = a.msg + (int64_t)cs * a.msg_stride;
   const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
   if (blockIdx.x == gridDim.x - 1) {
-    if (warp != 0) return;
-    double acc = 0.0;
+    // log Z = sum_c (log sigma_c - log |S_c|) + log Delta_root, as the log of
+    // a product: mantissas multiplied, binary exponents summed (both read
+    // off the bits), over the CTA's threads, then two logarithms in all
+    // (FP64 throughput per SM is small on this part: one log per clique
+    // costs more than the rest of the finalisation)
+    __shared__ double pn_s[8], pd_s[8];
+    __shared__ long long en_s[8], ed_s[8];
+    __shared__ int zero_s[8];
+    double pn = 1.0, pd = 1.0;
+    long long en = 0, ed = 0;
     bool zero = false;
-    for (int c = 1 + lane; c < a.n_cliques; c += 32) {
+    int terms = 0;
+    for (int c = 1 + tid; c < a.n_cliques; c += 256) {
       const double sg = sums[c];
-      if (!(sg > 0.0)) zero = true;
-      else acc += log(sg) - log((double)a.sep_size[c]);
+      if (!(sg > 0.0)) {
+        zero = true;
+        continue;
+      }
+      pn *= split_exp(sg, en);
+      pd *= split_exp((double)a.sep_size[c], ed);
+      if (++terms == 256) {   // (a product of 256 mantissas stays above 2^-256)
+        pn = split_exp(pn, en);
+        pd = split_exp(pd, ed);
+        terms = 0;
+      }
     }
-    acc = warp_sum(acc);
+    pn = split_exp(pn, en);
+    pd = split_exp(pd, ed);
+    mul_reduce(pn, pd, en, ed);
     zero = __any_sync(kFull, zero);
     if (lane == 0) {
+      pn_s[warp] = pn;
+      pd_s[warp] = pd;
+      en_s[warp] = en;
+      ed_s[warp] = ed;
+      zero_s[warp] = zero;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < 8; ++w) {
+        en += en_s[w];
+        ed += ed_s[w];
+        pn = split_exp(pn * pn_s[w], en);
+        pd = split_exp(pd * pd_s[w], ed);
+        zero = zero || zero_s[w];
+      }
       const double R = sums[a.n_cliques];  // the root's distribute total
       if (zero || !(R > 0.0)) {
         atomicOr(&a.status[cs], kStatusZero);
         a.logz_out[cs] = -INFINITY;
       } else {
-        a.logz_out[cs] = acc + log(R);
+        a.logz_out[cs] = log(pn) - log(pd) + (double)(en - ed) * 0.69314718055994530942 + log(R);
       }
     }
     return;
@@ -1084,11 +1136,39 @@ __global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
   const VarSrc src = a.vs[v];
   double* out = a.marg_out + (int64_t)cs * a.marg_total + src.moff;
   const T* tab = row + src.off;
+  if (src.card <= kFinStates) {
+    // one pass over the table: every state's partial sum at once (the
+    // loads of all states in flight together), then one reduction each
+    double b[kFinStates];
+#pragma unroll
+    for (int x = 0; x < kFinStates; ++x) b[x] = 0.0;
+    for (int j = lane; j < src.size; j += 32) {
+      const int x = (j / src.st) % src.card;
+      const double val = (double)tab[j];
+#pragma unroll
+      for (int y = 0; y < kFinStates; ++y)
+        if (y == x) b[y] += val;
+    }
+    double z = 0.0;
+#pragma unroll
+    for (int x = 0; x < kFinStates; ++x) {
+      if (x < src.card) b[x] = warp_sum(b[x]);
+      z += b[x];
+    }
+    if (lane < src.card_out) {
+      double bx = b[0];
+#pragma unroll
+      for (int y = 1; y < kFinStates; ++y)
+        if (y == lane) bx = b[y];
+      out[lane] = z > 0.0 ? bx / z : NAN;
+    }
+    return;
+  }
   double z = 0.0;
   for (int j = lane; j < src.size; j += 32) z += (double)tab[j];
   z = warp_sum(z);
   const int per = src.size / src.card;  // entries holding one state
-  for (int x = 0; x < src.card; ++x) {
+  for (int x = 0; x < src.card_out; ++x) {
     double b = 0.0;
     for (int qq = lane; qq < per; qq += 32) {
       const int hi = qq / src.st, lo = qq - hi * src.st;
