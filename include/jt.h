@@ -298,7 +298,10 @@ typedef struct {
   int32_t padded;       /* 1: the schedule runs over a copy of the tree with every cardinality raised to a
                            power of two (the added states impossible: zero potential), which case lanes
                            need; results are the original tree's */
-  int32_t reserved[2];
+  int8_t block_shift[4];  /* the block-size target of each clique-size class (tables of < 2^14, < 2^18 and
+                             more entries; the 4th is unused) scaled by 2^shift, as the first timed range
+                             of this width found fastest (0: the planner's own target) */
+  int32_t reserved;
   float candidate_ms[5];  /* device time of one propagation of the range with 32, 8, 4 and 1 cases per
                              work item and with the whole tree per CTA, as the first use timed them
                              (-1: not timed or not applicable) */

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -124,6 +125,9 @@ struct jt_tree_s {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   std::map<std::tuple<int, int, int>, GraphEntry> graphs;   // (first case, cases, CTA cap; 0 = every SM)
+  // block-target shifts per clique-size class found by the first timed range
+  // of each (width, padded) schedule, reused by later ranges
+  std::map<std::pair<int, bool>, std::array<int8_t, kBlockClasses>> tuned;
   unsigned long long* d_span = nullptr;   // [2] global-timer span of the last propagation kernel
   std::unique_ptr<PerMsg> permsg;
   // Power-of-two padded twin of the plan (FP32 trees with other
@@ -330,7 +334,8 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
 // Plan the schedule of a case range, upload it, and record the propagation
 // into a CUDA graph.
 template <typename T>
-jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cudaStream_t s, GraphEntry* ge) {
+jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cudaStream_t s, GraphEntry* ge,
+                          const int8_t* block_shift = nullptr) {
   std::string err;
   const int smem_cap = smem_budget(t->device, ctas_per_sm_for(cb)) - 256;
   const int sms = cap > 0 ? std::min(cap, t->n_sm) : t->n_sm;   // the SMs this propagation may hold
@@ -339,7 +344,7 @@ jt_status record_schedule(jt_tree t, int case0, int n_cases, int cb, int cap, cu
   const Plan& plan = ge->padded ? *t->pad : t->plan;
   jt_status st = cb == kWholeTree
                      ? build_small_schedule(plan, (int)t->elem, n_cases, sms, smem_cap, &ge->sched, &err)
-                     : build_schedule(plan, (int)t->elem, cb, n_cases, sms, smem_cap, &ge->sched, &err);
+                     : build_schedule(plan, (int)t->elem, cb, n_cases, sms, smem_cap, &ge->sched, &err, block_shift);
   if (st != JT_OK) return fail(st, err);
   // Failure-path hooks, read when a range's graph is recorded (host-side
   // fault injection: nothing on the device faults or waits without limit).
@@ -446,9 +451,9 @@ jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphE
       const std::string v(f);
       if (v == "0" || v == "1" || v == "4" || v == "8" || v == "32") forced = std::stoi(v);
     }
-    auto record = [&](int cb, GraphEntry* ge) {
-      return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, cap, t->cap_stream, ge)
-                                  : record_schedule<float>(t, first, n, cb, cap, t->cap_stream, ge);
+    auto record = [&](int cb, GraphEntry* ge, const int8_t* shift = nullptr) {
+      return t->compute == JT_F64 ? record_schedule<double>(t, first, n, cb, cap, t->cap_stream, ge, shift)
+                                  : record_schedule<float>(t, first, n, cb, cap, t->cap_stream, ge, shift);
     };
     std::vector<int> cands;
     if (forced == kWholeTree) {
@@ -502,6 +507,60 @@ jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphE
       drop_graph(ge);
     }
     if (!have) return fail(first_err == JT_OK ? JT_ERR_CUDA : first_err, first_msg);
+    // Block sizes per clique-size class for the chosen width: from an
+    // earlier range of this tree and width, or searched here one class at a
+    // time (the block target halved, then doubled, and a direction that
+    // helps once more; a change is kept when it is at least 2% faster).
+    // JT_BLOCK_TUNE=0 keeps the planner's targets.
+    const char* bt = std::getenv("JT_BLOCK_TUNE");
+    if (best.sched.cb != kWholeTree && !(bt && *bt == '0')) {
+      const auto tkey = std::make_pair(best.sched.cb, best.padded);
+      auto tit = t->tuned.find(tkey);
+      if (tit != t->tuned.end()) {
+        bool zero = true;
+        for (int8_t x : tit->second) zero = zero && x == 0;
+        GraphEntry ge;
+        if (!zero && record(best.sched.cb, &ge, tit->second.data()) == JT_OK) {
+          drop_graph(best);
+          std::swap(best, ge);
+        }
+        drop_graph(ge);
+      } else if (timed_choice) {
+        bool present[kBlockClasses] = {};
+        for (const DevStage& S : best.sched.stages)
+          if (S.n_blocks > 0) present[block_class(S.n)] = true;
+        std::array<int8_t, kBlockClasses> cur{};
+        float cur_ms = best_ms;
+        auto attempt = [&](int q, int8_t v) {
+          std::array<int8_t, kBlockClasses> trial = cur;
+          trial[q] = v;
+          GraphEntry ge;
+          bool kept = false;
+          if (record(best.sched.cb, &ge, trial.data()) == JT_OK) {
+            time_graph(ge, s);
+            const float ms = time_graph(ge, s);
+            if (ms >= 0.f && ms < 0.98f * cur_ms) {
+              std::swap(best, ge);
+              cur = trial;
+              cur_ms = ms;
+              kept = true;
+            }
+          }
+          drop_graph(ge);
+          return kept;
+        };
+        for (int q = 0; q < kBlockClasses; ++q) {
+          if (!present[q]) continue;
+          // halved, then doubled; a direction that helps is tried once more
+          for (int8_t d : {(int8_t)-1, (int8_t)1})
+            if (attempt(q, d)) {
+              attempt(q, (int8_t)(2 * d));
+              break;
+            }
+        }
+        t->tuned[tkey] = cur;
+      }
+    }
     CU(cudaEventCreateWithFlags(&best.done, cudaEventDisableTiming), "event");
     std::copy(timed, timed + 5, best.candidate_ms);
     it = t->graphs.emplace(key, std::move(best)).first;
@@ -1303,6 +1362,7 @@ jt_status jt_get_schedule(jt_tree t, int32_t first, int32_t n, jt_schedule_info*
   out->smem_bytes = ge.smem;
   out->window_entries = ge.sched.win_max;
   out->padded = ge.padded ? 1 : 0;
+  for (int q = 0; q < kBlockClasses; ++q) out->block_shift[q] = ge.sched.block_shift[q];
   std::copy(ge.candidate_ms, ge.candidate_ms + 5, out->candidate_ms);
   return JT_OK;
 }

@@ -313,10 +313,16 @@ PadMap build_pad_map(const Plan& p, const Plan& q);
 template <typename T>
 void permute_tables(const Plan& p, const void* pot, jt_dtype pot_dtype, T* out);
 
+// Clique-size classes of the block-size tuning: tables of fewer than 2^14
+// entries, fewer than 2^18, and larger.
+constexpr int kBlockClasses = 3;
+inline int block_class(int64_t entries) { return entries < (1 << 14) ? 0 : entries < (1 << 18) ? 1 : 2; }
+
 // Schedule of one propagation shape (case-block size): stages, ports,
 // fields, dependencies and the ordered work items.
 struct Schedule {
   int32_t cb = 1, n_cb = 1;
+  int8_t block_shift[kBlockClasses] = {0, 0, 0};  // the block-target shifts it was planned with
   std::vector<DevStage> stages;             // [2 * n_cliques]; the root's collect stage is empty
   std::vector<DevPort> ports;
   std::vector<DevField> fields;
@@ -363,9 +369,13 @@ constexpr int kWholeTree = 0;
 constexpr int kSmallSeg = 32;               // entries of one segment (a warp's share of a clique)
 
 // Plan the schedule for `n_cases` cases in blocks of `cb` on a device with
-// `n_sm` SMs and `smem_bytes` of dynamic shared memory per CTA.
+// `n_sm` SMs and `smem_bytes` of dynamic shared memory per CTA.  A stage's
+// block size is the largest power of two (or digit product) within a target
+// that spreads its level over the SMs and within the shared-memory budget of
+// its windows; `block_shift` (per clique-size class, or null) scales that
+// target by 2^shift before the hard limits apply.
 jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm, int smem_bytes,
-                         Schedule* s, std::string* err);
+                         Schedule* s, std::string* err, const int8_t* block_shift = nullptr);
 
 // Plan a whole-tree schedule (one CTA per case): the one-case stage
 // descriptors plus the level-ordered segment list.  JT_ERR_UNSUPPORTED when

@@ -337,7 +337,8 @@ int64_t eval_key(const std::vector<DevField>& f, int64_t x) {
 }  // namespace
 
 jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm, int smem_bytes, Schedule* s,
-                         std::string* err) {
+                         std::string* err, const int8_t* block_shift) {
+  for (int q = 0; q < kBlockClasses; ++q) s->block_shift[q] = block_shift ? block_shift[q] : 0;
   const int VEC = 16 / elem;
   const int lv = VEC == 4 ? 2 : 1;
   const int nc = p.n_cliques;
@@ -492,9 +493,11 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         }
         return tot;
       };
-      const int64_t target = std::min<int64_t>(
-          std::min<int64_t>(1 << 16, (int64_t)kMaxIter * consumers_for(cb) * VEC),
-          std::max<int64_t>(4096, level_n[pass][p.depth[c]] * s->n_cb / (2ll * ctas_per_sm_for(cb) * n_sm)));
+      int64_t spread = std::max<int64_t>(4096, level_n[pass][p.depth[c]] * s->n_cb / (2ll * ctas_per_sm_for(cb) * n_sm));
+      const int shift = s->block_shift[block_class(S.n)];
+      spread = shift >= 0 ? spread << shift : std::max<int64_t>(32, spread >> -shift);
+      const int64_t target =
+          std::min<int64_t>(std::min<int64_t>(1 << 16, (int64_t)kMaxIter * consumers_for(cb) * VEC), spread);
       std::vector<int64_t> K;
       int64_t B = 1;
       // a case-lane block holds at least one tile (32 entries) per warp slice

@@ -71,7 +71,8 @@ class jt_tree_info(C.Structure):
 class jt_schedule_info(C.Structure):
     _fields_ = [
         ("case_block", C.c_int32), ("n_items", C.c_int32), ("grid", C.c_int32), ("smem_bytes", C.c_int32),
-        ("window_entries", C.c_int32), ("padded", C.c_int32), ("reserved", C.c_int32 * 2),
+        ("window_entries", C.c_int32), ("padded", C.c_int32), ("block_shift", C.c_int8 * 4),
+        ("reserved", C.c_int32),
         ("candidate_ms", C.c_float * 5),
     ]
 
@@ -340,6 +341,7 @@ def jt_get_schedule(t: Tree, first_case: int, n_cases: int) -> dict:
     _check(_lib.jt_get_schedule(t.handle, first_case, n_cases, C.byref(info)), "jt_get_schedule")
     return {"case_block": info.case_block, "n_items": info.n_items, "grid": info.grid,
             "smem_bytes": info.smem_bytes, "window_entries": info.window_entries, "padded": bool(info.padded),
+            "block_shift": [int(x) for x in info.block_shift[:3]],
             "candidate_ms": {w: float(info.candidate_ms[i]) for i, w in enumerate((32, 8, 4, 1, 0))
                              if info.candidate_ms[i] >= 0}}
 

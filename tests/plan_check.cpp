@@ -1,3 +1,4 @@
+#include <array>
 // Host-side check of the propagation planner (no GPU): builds the plan and
 // the schedules of a tree read from stdin and checks the invariants the
 // persistent kernel relies on.
@@ -164,6 +165,26 @@ int main(int argc, char** argv) {
     } else {
       std::printf("cb=%d cases=%d FAIL %s\n", sh[0], sh[1], why.c_str());
       ++bad;
+    }
+  }
+  // block targets scaled per clique-size class (the autotuner's search
+  // space): the same invariants hold, and a shift moves the block sizes
+  for (int d : {-1, 1}) {
+    const int8_t sh[kBlockClasses] = {(int8_t)d, (int8_t)d, (int8_t)d};
+    for (const auto& shp : {std::array<int, 2>{1, 1}, std::array<int, 2>{8, 64}}) {
+      Schedule s;
+      err.clear();
+      const jt_status st = build_schedule(p, 4, shp[0], shp[1], 152, smem, &s, &err, sh);
+      if (st == JT_ERR_UNSUPPORTED) continue;
+      std::string why = st == JT_OK ? check(p, s) : "status " + std::to_string((int)st) + " " + err;
+      for (int q = 0; q < kBlockClasses && why.empty(); ++q)
+        if (s.block_shift[q] != d) why = "shift not recorded";
+      if (why.empty()) {
+        std::printf("tune shift=%d cb=%d cases=%d OK items=%zu\n", d, shp[0], shp[1], s.items.size());
+      } else {
+        std::printf("tune shift=%d cb=%d cases=%d FAIL %s\n", d, shp[0], shp[1], why.c_str());
+        ++bad;
+      }
     }
   }
   // the whole-tree plan: the packed indices unpack to the plan's arrays, and

@@ -7,6 +7,8 @@ a block queued after it.  Run on the workloads, on merged trees (high
 fan-out), on trees with empty separators and on the separator sweep.  The
 whole-tree plan (one CTA per case) must pack its level indices so that they
 unpack to its arrays, and order every collect stage before its parent's.
+Schedules planned with the block targets halved or doubled (the block-size
+autotuner's search space) must satisfy the same invariants.
 
 Trees with cardinalities other than powers of two also get the padded plan
 (every cardinality raised to a power of two, the added states impossible):
@@ -87,6 +89,8 @@ def test_schedules_of_the_workloads(checker, name):
             assert " OK " in ln or " UNSUPPORTED " in ln, ln
         else:
             assert " OK " in ln, ln
+    tune = [ln for ln in lines if ln.startswith("tune ")]
+    assert tune and all(" OK " in ln for ln in tune), lines
     small = [ln for ln in lines if ln.startswith("small ")]
     assert len(small) == 1 and (" OK " in small[0] or (name not in WHOLE_TREE_TREES and " UNSUPPORTED " in small[0])), \
         lines
@@ -130,6 +134,6 @@ def test_schedules_of_merged_trees(checker, min_sep, cap):
 def test_planted_schedule_mistakes_are_caught(checker, plant, what):
     t = synth.small_tree()
     rc, lines = _run(checker, t.card, t.cliques, t.parent, plant)
-    planned = [ln for ln in lines if " UNSUPPORTED " not in ln and not ln.startswith(("padmap", "small "))]
+    planned = [ln for ln in lines if " UNSUPPORTED " not in ln and not ln.startswith(("padmap", "small ", "tune "))]
     assert rc == 1 and len(planned) >= 4 and all(" FAIL " in ln and what in ln for ln in planned), lines
 
