@@ -413,6 +413,19 @@ void drop_graph(GraphEntry& ge) {
 
 // Device time of one launch of a recorded propagation on `s` (ms), or a
 // negative value on error.
+float time_graph(const GraphEntry& ge, cudaStream_t s);
+
+// The fastest of `reps` launches (after the caller's warm-up): block-size
+// candidates differ by a few percent, below one launch's spread.
+float time_graph_min(const GraphEntry& ge, cudaStream_t s, int reps) {
+  float best = -1.f;
+  for (int r = 0; r < reps; ++r) {
+    const float ms = time_graph(ge, s);
+    if (ms >= 0.f && (best < 0.f || ms < best)) best = ms;
+  }
+  return best;
+}
+
 float time_graph(const GraphEntry& ge, cudaStream_t s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float ms = -1.f;
@@ -530,7 +543,8 @@ jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphE
         for (const DevStage& S : best.sched.stages)
           if (S.n_blocks > 0) present[block_class(S.n)] = true;
         std::array<int8_t, kBlockClasses> cur{};
-        float cur_ms = best_ms;
+        const float cur_ms0 = time_graph_min(best, s, 3);
+        float cur_ms = cur_ms0 >= 0.f ? cur_ms0 : best_ms;
         auto attempt = [&](int q, int8_t v) {
           std::array<int8_t, kBlockClasses> trial = cur;
           trial[q] = v;
@@ -538,7 +552,7 @@ jt_status get_graph(jt_tree t, int first, int n, int cap, cudaStream_t s, GraphE
           bool kept = false;
           if (record(best.sched.cb, &ge, trial.data()) == JT_OK) {
             time_graph(ge, s);
-            const float ms = time_graph(ge, s);
+            const float ms = time_graph_min(ge, s, 3);
             if (ms >= 0.f && ms < 0.98f * cur_ms) {
               std::swap(best, ge);
               cur = trial;

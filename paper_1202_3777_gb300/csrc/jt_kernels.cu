@@ -1067,6 +1067,7 @@ __device__ __forceinline__ void mul_reduce(double& pn, double& pd, long long& en
 }
 
 constexpr int kFinStates = 8;   // variables of at most this many states: one pass over the table
+constexpr int kFinUnroll = 8;   // table loads per lane in flight
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
@@ -1136,18 +1137,29 @@ __global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
   const VarSrc src = a.vs[v];
   double* out = a.marg_out + (int64_t)cs * a.marg_total + src.moff;
   const T* tab = row + src.off;
-  if (src.card <= kFinStates) {
-    // one pass over the table: every state's partial sum at once (the
-    // loads of all states in flight together), then one reduction each
+  if (src.card <= kFinStates && src.size <= 2 * 32 * kFinUnroll) {
+    // small tables, one pass: every state's partial sum at once (the loads
+    // of all states in flight together), then one reduction each.  (Per
+    // element it adds into every state's sum under a predicate: FP64 work
+    // that only small tables can afford on this part.)
     double b[kFinStates];
 #pragma unroll
     for (int x = 0; x < kFinStates; ++x) b[x] = 0.0;
-    for (int j = lane; j < src.size; j += 32) {
-      const int x = (j / src.st) % src.card;
-      const double val = (double)tab[j];
+    // (eight loads per lane in flight: the tables come from L2)
+    for (int j0 = lane; j0 < src.size; j0 += 32 * kFinUnroll) {
+      T val[kFinUnroll];
 #pragma unroll
-      for (int y = 0; y < kFinStates; ++y)
-        if (y == x) b[y] += val;
+      for (int u = 0; u < kFinUnroll; ++u) {
+        const int j = j0 + 32 * u;
+        val[u] = j < src.size ? tab[j] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kFinUnroll; ++u) {
+        const int x = ((j0 + 32 * u) / src.st) % src.card;
+#pragma unroll
+        for (int y = 0; y < kFinStates; ++y)
+          if (y == x) b[y] += (double)val[u];
+      }
     }
     double z = 0.0;
 #pragma unroll
@@ -1164,15 +1176,45 @@ __global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
     }
     return;
   }
-  double z = 0.0;
-  for (int j = lane; j < src.size; j += 32) z += (double)tab[j];
-  z = warp_sum(z);
+  // larger tables: a pass per state (one FP64 addition per entry), eight
+  // loads per lane in flight; z is the sum of the states' sums, and lane x
+  // keeps the sum of state x until z is known
   const int per = src.size / src.card;  // entries holding one state
+  double z = 0.0, mine = 0.0;
+  for (int x = 0; x < src.card; ++x) {
+    double b = 0.0;
+    for (int q0 = lane; q0 < per; q0 += 32 * kFinUnroll) {
+      T val[kFinUnroll];
+#pragma unroll
+      for (int u = 0; u < kFinUnroll; ++u) {
+        const int qq = q0 + 32 * u;
+        const int hi = qq / src.st, lo = qq - hi * src.st;
+        val[u] = qq < per ? tab[(int64_t)(hi * src.card + x) * src.st + lo] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kFinUnroll; ++u) b += (double)val[u];
+    }
+    b = warp_sum(b);
+    z += b;
+    if (x == lane) mine = b;
+  }
+  if (src.card <= 32) {
+    if (lane < src.card_out) out[lane] = z > 0.0 ? mine / z : NAN;
+    return;
+  }
+  // more than 32 states: each state's sum again, now that z is known
   for (int x = 0; x < src.card_out; ++x) {
     double b = 0.0;
-    for (int qq = lane; qq < per; qq += 32) {
-      const int hi = qq / src.st, lo = qq - hi * src.st;
-      b += (double)tab[(int64_t)(hi * src.card + x) * src.st + lo];
+    for (int q0 = lane; q0 < per; q0 += 32 * kFinUnroll) {
+      T val[kFinUnroll];
+#pragma unroll
+      for (int u = 0; u < kFinUnroll; ++u) {
+        const int qq = q0 + 32 * u;
+        const int hi = qq / src.st, lo = qq - hi * src.st;
+        val[u] = qq < per ? tab[(int64_t)(hi * src.card + x) * src.st + lo] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kFinUnroll; ++u) b += (double)val[u];
     }
     b = warp_sum(b);
     if (lane == 0) out[x] = z > 0.0 ? b / z : NAN;
