@@ -121,6 +121,25 @@ __device__ __forceinline__ void red_entries(uint32_t at, uint32_t kv, const int4
   }
 }
 
+// The four distinct sums of a tile for an output whose key depends only on
+// entry bits 0-1 (a joint over the lowest digit; the slot is encoded in the
+// class): each entry position summed over the tile's eight vectors.
+__device__ __forceinline__ void tile_sums(const float2 (&f)[16], float (&o)[4]) {
+  float2 a = f[0], b = f[1];
+#pragma unroll
+  for (int v = 1; v < 8; ++v) {
+    a = add2(a, f[2 * v]);
+    b = add2(b, f[2 * v + 1]);
+  }
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = b.x;
+  o[3] = b.y;
+}
+__device__ __forceinline__ void acc4(float (&r)[4], const float (&o)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r[i] += o[i];
+}
 
 // Shared-memory carve-up of a case-lane CTA.  The common fields serve the
 // producer; per buffer: `obs` holds (V, M) per case, `bf` the block factor per
@@ -414,6 +433,12 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
   float* calib = (a.calib != nullptr && lane < ncb) ? a.calib + (int64_t)(cb0 + lane) * a.calib_stride + w.off : nullptr;
   const uint32_t h0 = s.stage->holes[0], h1 = s.stage->holes[1], h2 = s.stage->holes[2];
   const uint32_t xb = (uint32_t)(w.off - s.stage->base_off);   // the block's first entry in its clique
+  // register-accumulated outputs (tile-only keys), reduced after the block
+  float racc[kClRegSlots][4];
+#pragma unroll
+  for (int r = 0; r < kClRegSlots; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) racc[r][i] = 0.f;
   bool ok = true;
   for (int ci = 0; ci < nchunks; ++ci, rp.advance(RS)) {
     const uint32_t st = rp.st;
@@ -517,6 +542,14 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
       for (int li = n_in; li < n_live; ++li) {
         const uint32_t pb = cp32 + (uint32_t)li * (uint32_t)sizeof(CLPort);
         const int cls = sld_s32(pb + offsetof(CLPort, cls));
+        // (the variant that skips tiles has no registers to spare: there a
+        // marked output reduces per tile like the others)
+        if (const int rs = HOLES ? 0 : (cls >> kClRegShift) & 3) {
+          float o[4];
+          tile_sums(f, o);
+          acc4(racc[0], o);
+          continue;
+        }
         const uint32_t at = (uint32_t)sld_s32(pb + offsetof(CLPort, kchunk) + 4u * (uint32_t)ci) +
                             (uint32_t)sld_s32(pb + offsetof(CLPort, kslot) + 4u * (uint32_t)slot) + lane4;
         if (cls & kClIdent) {
@@ -551,6 +584,29 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(s.empty + st);
+  }
+  // the register-accumulated outputs, once per item (their rows are the same
+  // for every tile: chunk 0, slot 0)
+  if (!HOLES && ok) {
+#pragma unroll 1
+    for (int li = n_in; li < n_live; ++li) {
+      const uint32_t pb = cp32 + (uint32_t)li * (uint32_t)sizeof(CLPort);
+      const int cls = sld_s32(pb + offsetof(CLPort, cls));
+      const int rs = (cls >> kClRegShift) & 3;
+      if (rs == 0) continue;
+      float o[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) o[i] = racc[0][i];
+      const uint32_t at = (uint32_t)sld_s32(pb + offsetof(CLPort, kchunk)) +
+                          (uint32_t)sld_s32(pb + offsetof(CLPort, kslot)) + lane4;
+      const uint32_t kv = pb + offsetof(CLPort, kvec);
+      const int4 dv = sld_v4s32(pb + offsetof(CLPort, dvec));
+      const uint32_t av = at + (uint32_t)sld_s32(kv);
+      sred_add(av + (uint32_t)dv.x, o[0]);
+      sred_add(av + (uint32_t)dv.y, o[1]);
+      sred_add(av + (uint32_t)dv.z, o[2]);
+      sred_add(av + (uint32_t)dv.w, o[3]);
+    }
   }
   return __all_sync(kFull, ok);
 }

@@ -107,6 +107,13 @@ constexpr int32_t kClTile = 0;      // key constant over a tile of 32 entries
 constexpr int32_t kClVector = 2;    // key constant over each vector of 4 entries
 constexpr int32_t kClEntry = 4;     // key changes within a vector
 constexpr int32_t kClIdent = 8;     // with kClEntry: the tile's keys are key + e, e < 32 (consecutive rows)
+// bits 4-5: register slot + 1 of an output whose key depends only on entry
+// bits 0-1 (the same four rows for every tile of a block): its four sums
+// accumulate in registers over the block and reduce once per item.  One
+// slot: more accumulators were measured slower (they push the hot loop into
+// spills).
+constexpr int32_t kClRegShift = 4;
+constexpr int kClRegSlots = 1;
 static_assert(sizeof(CLPort) == kClPortBytes && sizeof(CLPort) % 16 == 0, "case-lane port table");
 
 // Dynamic shared memory of a case-lane propagation CTA (host and device

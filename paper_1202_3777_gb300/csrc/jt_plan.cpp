@@ -709,6 +709,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         *err = "case-lane block longer than the chunk table";
         return JT_ERR_UNSUPPORTED;
       }
+      int n_reg = 0;
       for (int li = 0; li < S.n_live; ++li) {
         const DevPort& P = s->ports[S.port0 + live[li].port];
         const DevField* f = &s->fields[S.field0 + P.f0];
@@ -727,6 +728,14 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         C.dep = 0;
         for (int b = 0; b < 5; ++b)
           if (key(1u << b) != 0) C.dep |= 1 << b;
+        // an output whose key depends only on entry bits 0-1 (a joint over
+        // the lowest digit): four sums per tile, the same rows in every tile
+        bool tile_only = true;
+        for (int b = 5; b < S.bits; ++b) tile_only = tile_only && key(1u << b) == 0;
+        const int vf = (~C.dep >> 2) & 7;
+        const bool regable = live[li].port >= S.nin && tile_only && !ident &&
+                             edep && vf == 7;
+        if (regable && n_reg < kClRegSlots) C.cls |= (++n_reg) << kClRegShift;
         for (int j = 0; j < 4; ++j) C.dvec[j] = (int32_t)(key((uint32_t)j) * kClRow);
         for (int v = 0; v < 8; ++v) C.kvec[v] = (int32_t)(key(4u * (uint32_t)v) * kClRow);
         for (int w = 0; w < 16; ++w)

@@ -97,6 +97,26 @@ std::string check(const Plan& p, const Schedule& s) {
     }
     ++done[(size_t)it.stage * s.n_cb + it.cbk];
   }
+  // case lanes: an output marked for register accumulation must have the
+  // same four rows in every tile of its block (a key over entry bits 0-1
+  // only), and be no input
+  if (s.cb == kCaseLanes)
+    for (const DevItem& it : s.items) {
+      const DevStage& S = s.stages[it.stage];
+      const unsigned char* blob = reinterpret_cast<const unsigned char*>(s.blobs.data()) + (size_t)it.blob * 16;
+      const CLPort* cp = reinterpret_cast<const CLPort*>(blob + S.live_off);
+      int marked = 0;
+      for (int li = 0; li < S.n_live; ++li) {
+        const CLPort& C = cp[li];
+        if (((C.cls >> kClRegShift) & 3) == 0) continue;
+        ++marked;
+        bool same = (C.cls & kClInput) == 0 && (C.dep & ~3) == 0 && (C.cls & kClEntry) != 0;
+        for (int q = 1; q < 64; ++q) same = same && C.kslot[q] == C.kslot[0];
+        for (int q = 1; q < kClMaxChunks; ++q) same = same && C.kchunk[q] == C.kchunk[0];
+        if (!same) return "stage of clique " + std::to_string(S.clique) + " accumulates an output whose rows vary";
+      }
+      if (marked > kClRegSlots) return "more register-accumulated outputs than slots";
+    }
   return "";
 }
 
