@@ -306,6 +306,61 @@ def measure_cpt_init(tree, hbm):
             "alg_bytes": alg, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm}
 
 
+def kernel_tour():
+    """One small invocation of every kernel family, for profiling each on its
+    own: case lanes (large-clique tree, one slab of 32 cases), padded case
+    lanes with their table padding (256-clique tree, 64 cases), one case per
+    item (large-clique tree), 4-case blocks (high-cardinality tree, 16
+    cases), the whole tree per CTA (32-clique tree, FP32 and FP64), the
+    paper's per-message propagation (32-clique tree), CPT initialisation and
+    the calibrated-table read-out (large-clique tree).  Schedules are fixed
+    (no width timing, no block tuning), every result is checked for its
+    status, and the device time of each propagation's two kernels is
+    printed (CUDA events; the kernels are the ones a capture of this run
+    sees)."""
+    from paper_1202_3777_gb300 import jt
+    os.environ["JT_BLOCK_TUNE"] = "0"
+    out = {}
+
+    def run(name, tree, n, cb, compute=jt.JT_F32, flags=0, seed=50):
+        os.environ["JT_CASE_BLOCK"] = str(cb)
+        h = jt.jt_load_synth(tree, compute=compute, max_cases=n, flags=flags)
+        jt.jt_set_evidence_dense(h, 0, synth.evidence_matrix(tree, n, 0.05, seed))
+        jt.jt_propagate(h, 0, n)
+        ms = [float(x) for x in jt.jt_profile_propagate(h, 0, n)]
+        assert np.all(jt.jt_get_status(h, 0, n) == jt.JT_OK), name
+        sch = jt.jt_get_schedule(h, 0, n)
+        out[name] = {"cases": n, "case_block": sch["case_block"], "padded": sch["padded"],
+                     "propagation_ms": ms[0], "finalisation_ms": ms[1]}
+        return h
+
+    large = synth.large_clique_tree().as_dtype(np.float32)
+    run("case_lanes", large, 32, 32).free()
+    run("padded_lanes", synth.batched_tree().as_dtype(np.float32), 64, 32).free()
+    run("one_case", large, 1, 1).free()
+    run("case_blocks", synth.high_card_tree().as_dtype(np.float32), 16, 4).free()
+    small = synth.small_tree()
+    run("whole_tree_f32", small.as_dtype(np.float32), 1, 0).free()
+    run("whole_tree_f64", small, 1, 0, compute=jt.JT_F64).free()
+    h = run("per_message_tree", small.as_dtype(np.float32), 1, 1, flags=jt.JT_MATERIALIZE_CLIQUES)
+    out["per_message"] = {"naive_ms": jt.jt_propagate_per_message(h, 0, 0),
+                          "interleaved_ms": jt.jt_propagate_per_message(h, 0, 1)}
+    h.free()
+    fams, vals = synth.bn_for_tree(large, 7, max_parents=3)
+    h = jt.jt_load_tree(large.card, large.cliques, large.parent, None, compute=jt.JT_F32, max_cases=1,
+                        flags=jt.JT_MATERIALIZE_CLIQUES)
+    out["cpt_init_ms"] = jt.jt_init_from_cpts(h, fams, vals)
+    os.environ["JT_CASE_BLOCK"] = "1"
+    jt.jt_propagate(h, 0, 1)
+    sizes = large.table_sizes()
+    tab = jt.jt_get_clique(h, 0, 3, int(sizes[3]))
+    assert np.isfinite(tab).all() and abs(float(tab.sum()) - 1.0) < 1e-6
+    h.free()
+    for k in ("JT_CASE_BLOCK", "JT_BLOCK_TUNE"):
+        os.environ.pop(k, None)
+    return out
+
+
 def separator_sweep():
     """Analogues of Fig. 6 and Fig. 7 on trees that differ only in separator
     size (32 cliques of 4^8 entries, separators of 4^1 .. 4^7 entries), one
@@ -650,6 +705,8 @@ def main():
                     help="print the separator-size sweep (Fig. 6 / Fig. 7 analogues) instead of the bench line")
     ap.add_argument("--sweep-merging", action="store_true",
                     help="print original against merged-tree propagation times instead of the bench line")
+    ap.add_argument("--kernel-tour", action="store_true",
+                    help="run one small case of every kernel family (for profiling) instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -669,9 +726,10 @@ def main():
     build.build()
     from paper_1202_3777_gb300 import jt
 
-    if args.sweep_separators or args.sweep_merging:
+    if args.sweep_separators or args.sweep_merging or args.kernel_tour:
         if rank == 0:
-            out = separator_sweep() if args.sweep_separators else merging_sweep()
+            out = separator_sweep() if args.sweep_separators else merging_sweep() if args.sweep_merging \
+                else kernel_tour()
             print(json.dumps(out, default=_json_default), flush=True)
         return 0
 
