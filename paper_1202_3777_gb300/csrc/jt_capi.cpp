@@ -111,6 +111,8 @@ struct jt_tree_s {
   VarSrc* d_vs = nullptr;         // marginal sources, joint layout 0 (one-case schedules)
   VarSrc* d_vs_fine = nullptr;    // joint layout 1 (case-block schedules)
   VarSrc* d_vs_var = nullptr;     // joint layout 2 (case-lane schedules: a joint per private variable)
+  int32_t* d_order_var = nullptr;  // case-lane finalisation order of layout 2 (small sources first)
+  int32_t n_small_var = 0;
   int32_t* d_sep_size = nullptr;
   int64_t device_bytes = 0;
   // host state
@@ -137,6 +139,8 @@ struct jt_tree_s {
   std::unique_ptr<Plan> pad;
   float* pad_base = nullptr;
   VarSrc* d_vs_pad = nullptr;
+  int32_t* d_order_pad = nullptr;
+  int32_t n_small_pad = 0;
   int32_t* d_sep_size_pad = nullptr;
   int4* d_pad_digits = nullptr;
   PadClique* d_pad_cliques = nullptr;
@@ -174,7 +178,8 @@ void destroy(jt_tree t) {
     for (void* q : t->permsg->bufs) cudaFree(q);
   void* ptrs[] = {t->base,   t->d_msg,  t->d_sums,  t->d_done,    t->d_err, t->d_status, t->d_marg,
                   t->d_logz, t->d_ev,   t->d_calib, t->d_scratch, t->d_vs,  t->d_vs_fine, t->d_vs_var, t->d_sep_size,
-                  t->d_span, t->pad_base, t->d_vs_pad, t->d_sep_size_pad, t->d_pad_digits, t->d_pad_cliques};
+                  t->d_span, t->pad_base, t->d_vs_pad, t->d_sep_size_pad, t->d_pad_digits, t->d_pad_cliques,
+                  t->d_order_var, t->d_order_pad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->h_ev) cudaFreeHost(t->h_ev);
@@ -321,6 +326,8 @@ cudaError_t enqueue_schedule(jt_tree t, int case0, int n_cases, const GraphEntry
   f.marg_out = t->d_marg;
   f.logz_out = t->d_logz;
   f.lanes = sc.cb == kCaseLanes ? kCaseLanes : 1;
+  f.var_order = ge.padded ? t->d_order_pad : t->d_order_var;
+  f.n_small = ge.padded ? t->n_small_pad : t->n_small_var;
   if constexpr (std::is_same<T, float>::value) {
     if (sc.cb == kCaseLanes) chk(launch_finalize_cl(f, s));
     else chk(launch_finalize<T>(f, s));
@@ -687,6 +694,12 @@ jt_status load_pad(jt_tree t, cudaStream_t s) {
      "descriptor upload");
   CU(cudaMemcpy(t->d_vs_pad, q.vsrc[2].data(), q.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice),
      "descriptor upload");
+  {
+    const std::vector<int32_t> order = fin_order(q.vsrc[2], &t->n_small_pad);
+    if ((st = alloc(t, &t->d_order_pad, q.n_vars, "finalisation order")) != JT_OK) return st;
+    CU(cudaMemcpy(t->d_order_pad, order.data(), q.n_vars * sizeof(int32_t), cudaMemcpyHostToDevice),
+       "descriptor upload");
+  }
   CU(cudaMemcpy(t->d_sep_size_pad, q.sep_size.data(), q.n_cliques * sizeof(int32_t), cudaMemcpyHostToDevice),
      "descriptor upload");
   for (const PadClique& c : m.cliques) t->pad_max = std::max(t->pad_max, c.n_pad);
@@ -1069,6 +1082,13 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
   if ((st = alloc(raw, &raw->d_vs_var, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
   if (cudaMemcpy(raw->d_vs_var, p.vsrc[2].data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(JT_ERR_CUDA, "descriptor upload"));
+  {
+    const std::vector<int32_t> order = fin_order(p.vsrc[2], &raw->n_small_var);
+    if ((st = alloc(raw, &raw->d_order_var, p.n_vars, "finalisation order")) != JT_OK) return bail(st);
+    if (cudaMemcpy(raw->d_order_var, order.data(), p.n_vars * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return bail(fail(JT_ERR_CUDA, "descriptor upload"));
+  }
   if ((st = alloc(raw, &raw->d_vs_fine, p.n_vars, "marginal sources")) != JT_OK) return bail(st);
   if (cudaMemcpy(raw->d_vs_fine, p.vsrc[1].data(), p.n_vars * sizeof(VarSrc), cudaMemcpyHostToDevice) !=
       cudaSuccess)

@@ -757,7 +757,36 @@ __global__ void __launch_bounds__(256) k_finalize_cl(const FinalArgs<float> a) {
   const int cs = cb0 + lane;
   const bool valid = lane < ncb;
   const float* slab = a.msg + (int64_t)cb0 * a.msg_stride;
-  const int v = (int)blockIdx.x;
+  // blocks: groups of 8 small-source variables (a warp each), then one block
+  // per other variable, then log Z
+  const int g_small = (a.n_small + 7) / 8;
+  const int bx = (int)blockIdx.x;
+  if (bx < g_small) {
+    const int i = bx * 8 + warp;
+    if (i >= a.n_small || !valid) return;
+    const VarSrc src = a.vs[a.var_order[i]];
+    const float* tab = slab + (int64_t)src.off * kCaseLanes + lane;
+    const int per = src.size / src.card;
+    const bool p2 = (src.st & (src.st - 1)) == 0;
+    const int sh = __ffs(src.st) - 1;
+    double* out = a.marg_out + (int64_t)cs * a.marg_total + src.moff;
+    // lane = case: each state's entries summed by the lane itself (rows of 32
+    // cases, so a warp's loads are 128 consecutive bytes), no barrier
+    double z = 0.0;
+    for (int x = 0; x < src.card; ++x) {
+      double b = 0.0;
+#pragma unroll 8
+      for (int q = 0; q < per; ++q) {
+        const int h = p2 ? q >> sh : q / src.st;
+        b += (double)__ldcg(tab + ((int64_t)(h * src.card + x) * src.st + (q - h * src.st)) * kCaseLanes);
+      }
+      z += b;
+      if (x < src.card_out) out[x] = b;
+    }
+    for (int x = 0; x < src.card_out; ++x) out[x] = z > 0.0 ? out[x] / z : NAN;
+    return;
+  }
+  const int v = bx - g_small < a.n_vars - a.n_small ? a.var_order[a.n_small + (bx - g_small)] : a.n_vars;
   if (v == a.n_vars) {
     if (warp != 0 || !valid) return;
     // log Z = sum_c (log sigma_c - log |S_c|) + log Delta_root, as the log of
@@ -861,7 +890,7 @@ cudaError_t launch_propagate_cl(const PropArgs<float>& a, int grid, int smem, bo
 
 cudaError_t launch_finalize_cl(const FinalArgs<float>& a, cudaStream_t s) {
   if (a.n_cases <= 0) return cudaSuccess;
-  dim3 grid(a.n_vars + 1, (a.n_cases + kCaseLanes - 1) / kCaseLanes);
+  dim3 grid((a.n_small + 7) / 8 + (a.n_vars - a.n_small) + 1, (a.n_cases + kCaseLanes - 1) / kCaseLanes);
   k_finalize_cl<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
