@@ -106,8 +106,9 @@ struct jt_tree_s {
   double* d_logz = nullptr;       // [max_cases]
   int16_t* d_ev = nullptr;        // [max_cases][n_vars]
   void* d_calib = nullptr;        // [max_cases][base_len] (JT_MATERIALIZE_CLIQUES)
-  double* d_scratch = nullptr;    // read-out scratch (sum + clique table)
+  double* d_scratch = nullptr;    // read-out scratch (partial sums + clique table)
   int64_t scratch_len = 0;
+  int64_t scratch_parts = 0;      // leading partial-sum slots of the scratch
   VarSrc* d_vs = nullptr;         // marginal sources, joint layout 0 (one-case schedules)
   VarSrc* d_vs_fine = nullptr;    // joint layout 1 (case-block schedules)
   VarSrc* d_vs_var = nullptr;     // joint layout 2 (case-lane schedules: a joint per private variable)
@@ -1098,7 +1099,9 @@ jt_status jt_load_tree(const jt_tree_desc* d, void* stream, jt_tree* out) {
     return bail(fail(JT_ERR_CUDA, "descriptor upload"));
   int64_t maxn = 0;
   for (int64_t n : p.n_entries) maxn = std::max(maxn, n);
-  raw->scratch_len = maxn + 2;
+  // [partial sums of the normalisation, 16-byte aligned] [clique table]
+  raw->scratch_parts = ((maxn + kNoAllocPerBlock - 1) / kNoAllocPerBlock + 1) / 2 * 2;
+  raw->scratch_len = raw->scratch_parts + maxn + 2;
   if ((st = alloc(raw, &raw->d_scratch, raw->scratch_len, "read-out scratch")) != JT_OK) return bail(st);
   cudaError_t e = cudaMallocHost((void**)&raw->h_ev, (size_t)nev * sizeof(int16_t));
   if (e != cudaSuccess) return bail(cuda_fail(e, "pinned evidence mirror"));
@@ -1413,12 +1416,13 @@ jt_status jt_get_clique(jt_tree t, int32_t case_id, int32_t clique, double* out)
   cudaStream_t strm = t->last_stream;
   const int64_t off = (int64_t)case_id * p.base_len + p.base_off[clique];
   cudaError_t e = t->compute == JT_F64
-                      ? launch_get_clique<double>((const double*)t->d_calib + off, co, t->d_scratch + 1,
-                                                  t->d_scratch, strm)
-                      : launch_get_clique<float>((const float*)t->d_calib + off, co, t->d_scratch + 1,
-                                                 t->d_scratch, strm);
+                      ? launch_get_clique<double>((const double*)t->d_calib + off, co,
+                                                  t->d_scratch + t->scratch_parts, t->d_scratch, strm)
+                      : launch_get_clique<float>((const float*)t->d_calib + off, co,
+                                                 t->d_scratch + t->scratch_parts, t->d_scratch, strm);
   if (e != cudaSuccess) return cuda_fail(e, "clique read-out");
-  CU(cudaMemcpyAsync(out, t->d_scratch + 1, (size_t)co.n * sizeof(double), cudaMemcpyDeviceToHost, strm),
+  CU(cudaMemcpyAsync(out, t->d_scratch + t->scratch_parts, (size_t)co.n * sizeof(double), cudaMemcpyDeviceToHost,
+                     strm),
      "clique read");
   CU(cudaStreamSynchronize(strm), "clique read");
   int32_t code = 0;

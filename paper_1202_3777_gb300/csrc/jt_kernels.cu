@@ -1221,39 +1221,12 @@ __global__ void __launch_bounds__(256) k_finalize(const FinalArgs<T> a) {
   }
 }
 
-template <typename T>
-__global__ void k_clique_sum(const T* p, int n, double* out) {
-  __shared__ double red[8];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) s += (double)p[i];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 8; ++i) t += red[i];
-    *out = t;
-  }
-}
-
-template <typename T>
-__global__ void k_clique_gather(const T* p, CliqueOut co, const double* sum, double* out) {
-  const double z = *sum;
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < co.n; u += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = u, src = 0;
-    for (int i = co.k - 1; i >= 0; --i) {
-      const int64_t d = rem % co.lcard[i];
-      rem /= co.lcard[i];
-      src += d * co.pst[i];
-    }
-    out[u] = z > 0.0 ? (double)p[src] / z : NAN;
-  }
-}
-
-// ---- clique read-out without allocation ------------------------------------
-// Scratch of the allocation-free read-out: one partial sum per CTA of the
-// first pass.  Every call shares it (calls that overlap on the GPU race); it
-// lives as long as the library is loaded on a device.
+// ---- calibrated-clique read-out ---------------------------------------------
+// Both read-outs normalise with partial sums (one per CTA of a first pass)
+// that every CTA of the gather adds up.  Scratch of the allocation-free
+// read-out: the partials in a file-scope array.  Every call shares it
+// (calls that overlap on the GPU race); it lives as long as the library is
+// loaded on a device.
 __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 
 // Pass 1: CTA b sums entries [b * E, (b + 1) * E) of the table into partials[b]
@@ -1361,9 +1334,13 @@ cudaError_t launch_finalize(const FinalArgs<T>& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_get_clique(const T* calib_clique, const CliqueOut& co, double* out_dev, double* sum_dev,
                               cudaStream_t s) {
-  k_clique_sum<T><<<1, 256, 0, s>>>(calib_clique, co.n, sum_dev);
+  // the normalising sum as partial sums of kNoAllocPerBlock entries each
+  // (sum_dev holds one per block), which every gather block adds up
+  const int nb = (int)((co.n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+  if (nb == 0) return cudaSuccess;
+  k_clique_partials<T><<<nb, 256, 0, s>>>(calib_clique, (int64_t)co.n, sum_dev);
   const int blocks = (int)std::min<int64_t>(1024, (co.n + 255) / 256);
-  k_clique_gather<T><<<blocks, 256, 0, s>>>(calib_clique, co, sum_dev, out_dev);
+  k_clique_gather_partials<T><<<blocks, 256, 0, s>>>(calib_clique, co, sum_dev, nb, out_dev);
   return cudaGetLastError();
 }
 

@@ -171,6 +171,8 @@ struct CliqueOut {
   int32_t lcard[32];             // listed cardinalities
   int32_t pst[32];               // permuted stride of each listed position
 };
+// Calibrated-clique read-out: out_dev = the table in listed order, normalised
+// to sum one; sum_dev holds ceil(n / kNoAllocPerBlock) partial sums.
 template <typename T>
 cudaError_t launch_get_clique(const T* calib_clique, const CliqueOut& co, double* out_dev,
                               double* sum_dev, cudaStream_t s);
