@@ -119,14 +119,14 @@ class Clocks:
 # DRAM traffic of the propagation kernel from an ncu capture of the
 # large-clique workload (dram__bytes_read.sum + dram__bytes_write.sum, in
 # profiles/), valid only while the kernel and planner sources are the ones it
-# was taken on.  Per kind of schedule: a one-case launch; a block of 8 cases;
-# a slab of 32 cases on the lanes.  Every case block or slab streams the
-# tables again, so a launch's traffic grows with their number.
+# was taken on.  Per kind of schedule: a one-case launch; a block of 4 or 8
+# cases; a slab of 32 cases on the lanes.  Every case block or slab streams
+# the tables again, so a launch's traffic grows with their number.
 TRAFFIC = {
-    "sources_sha256": None,
-    "plain": None,
-    "per_case_block": None,
-    "per_slab": None,
+    "sources_sha256": "0de83afafdfbcb9aeb9b1ca7f320894238001dc6490c449abf1132f4de01573c",
+    "plain": 471.4e6,
+    "per_case_block": {4: 496.3e6, 8: 524.3e6},
+    "per_slab": 565.6e6,
 }
 TRAFFIC_SOURCES = ["paper_1202_3777_gb300/csrc/jt_kernels.cu", "paper_1202_3777_gb300/csrc/jt_caselanes.cu",
                    "paper_1202_3777_gb300/csrc/jt_device.cuh", "paper_1202_3777_gb300/csrc/jt_kernels.h",
@@ -156,7 +156,7 @@ def measured_traffic(schedule, cases):
     elif cb == 32:
         per, units = TRAFFIC["per_slab"], (cases + 31) // 32
     else:
-        per, units = TRAFFIC["per_case_block"], (cases + cb - 1) // cb
+        per, units = (TRAFFIC["per_case_block"] or {}).get(cb), (cases + cb - 1) // cb
     return None if per is None else int(per * units)
 
 
