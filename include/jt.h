@@ -86,8 +86,13 @@ typedef struct {
  * Validate the tree (Sec. 2.1 structure; running intersection), plan the
  * device layout, and upload the potentials.  Each clique table is stored
  * with its variables re-ordered so that its parent-separator variables are
- * the most significant digits, in `compute` precision.  `stream` orders the
- * uploads; the call returns after they complete.  All inputs are copied.
+ * the most significant digits, in `compute` precision.  An FP32 tree whose
+ * cardinalities are not all powers of two, with max_cases >= 16 and without
+ * JT_MATERIALIZE_CLIQUES, also gets a device copy with every cardinality
+ * raised to the next power of two (the added states have zero potential, so
+ * every result is the tree's own); it costs at most 5x the tables' memory,
+ * counted in jt_get_info's device_bytes.  `stream` orders the uploads; the
+ * call returns after they complete.  All inputs are copied.
  * On failure *out is set to NULL and nothing is leaked.
  */
 jt_status jt_load_tree(const jt_tree_desc* desc, void* stream, jt_tree* out);
@@ -119,11 +124,22 @@ jt_status jt_set_evidence_dense(jt_tree t, int32_t first_case, int32_t n_cases,
  * Eq. 1-3, all cases in one CUDA-graph launch.  Asynchronous: only enqueues
  * work on `stream`.  Per-message rescaling keeps FP32 in range; log Z(e) is
  * accumulated in FP64.
- * The first call for a given (first_case, n_cases) with n_cases > 1 records
- * the schedules (one case per work item, or blocks of 4 or 8 cases sharing
- * each table read), runs each twice on `stream` and keeps the fastest: that
- * call synchronises `stream`.  The environment variable JT_CASE_BLOCK=1, 4
- * or 8 fixes the choice instead.
+ * The first call for a given (first_case, n_cases) records the schedules
+ * the tree supports, runs each on `stream` and keeps the fastest; that call
+ * synchronises `stream`.  The schedules: the whole tree per CTA (trees of
+ * up to 2^17 entries), 32 cases on the lanes of a warp (FP32, 16 cases or
+ * more; over a copy of the tree with power-of-two cardinalities when its
+ * own are not), blocks of 8 or 4 cases sharing each table read, and one
+ * case per work item (a single case times only the first and the last).
+ * Then, for the width kept, it scales the planner's block size per
+ * clique-size class (tables of < 2^14, < 2^18 and more entries) by 2^shift
+ * where a shift is at least 2% faster; later ranges of the same tree and
+ * width reuse the shifts.  jt_get_schedule reports the outcome.
+ * Environment variables, read when a range is first propagated:
+ * JT_CASE_BLOCK=0, 1, 4, 8 or 32 fixes the width (0 and 32 fall back where
+ * they do not apply); JT_BLOCK_TUNE=0 keeps the planner's block sizes;
+ * JT_WAIT_LIMIT_MS sets the limit of the kernels' bounded waits (2000 ms).
+ * JT_PAD_CARDS=0, read by jt_load_tree, builds no power-of-two copy.
  */
 jt_status jt_propagate(jt_tree t, int32_t first_case, int32_t n_cases, void* stream);
 
