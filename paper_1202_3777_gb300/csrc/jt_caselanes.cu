@@ -450,13 +450,15 @@ __device__ __forceinline__ bool stream_cl(const PropArgs<float>& a, const Smem& 
     const uint32_t sb = ring32 + st * (uint32_t)CH * 4u;
 #pragma unroll 1
     for (int t = 0; t < kClTiles; ++t) {
-      const int ot = warp * kClSlice + 32 * t;  // tile offset in the chunk
+      // tile positions interleave over the warps: a short block still keeps
+      // every warp busy
+      const int slot = warp + NW * t;
+      const int ot = 32 * slot;                 // tile offset in the chunk
       if (ot >= nch) break;                     // warp-uniform
       if (HOLES && h0 != 0u) {
         const uint32_t x = xb + (uint32_t)(ci * CH + ot);
         if (added_state(x, h0) || added_state(x, h1) || added_state(x, h2)) continue;
       }
-      const int slot = warp * kClTiles + t;
       float2 f[16];
 #pragma unroll
       for (int v = 0; v < 8; ++v) {

@@ -82,14 +82,15 @@ struct SmemLayout {
 
 // Key tables of one port of a case-lane stage, built by the planner and
 // carried in the stage's descriptor blob (CLPort[n_live] at live_off).  A
-// consumer warp w streams, from each chunk ci of a block, the slice
-// [w * kClSlice, (w + 1) * kClSlice) in tiles t of 32 entries, so an entry's
-// block offset is o = ci * chunk + w * kClSlice + 32 t + 4 v + j and (power-of-
-// two digits are bit fields) its key is the sum of the keys of those parts.
+// chunk ci of a block is 64 tiles of 32 entries; consumer warp w streams the
+// tiles at positions p = w + 16 t (t < kClTiles), interleaved so that a block
+// shorter than a chunk still spreads over the warps.  An entry's block offset
+// is o = ci * chunk + 32 p + 4 v + j and (power-of-two digits are bit fields)
+// its key is the sum of the keys of those parts.
 // Every table holds byte offsets into the case-minor windows (key * 128), the
 // chunk table also the port's window start, so a lane's address is the item
 // buffer's window base plus a sum of table entries plus lane * 4.
-constexpr int kClSlice = 128;                   // entries of a warp's slice of one chunk
+constexpr int kClSlice = 128;                   // entries a warp streams from one chunk
 constexpr int kClTiles = kClSlice / 32;         // tiles of 32 entries per slice
 constexpr int kClMaxChunks = 32;                // chunks of one block (blocks <= 2^16 entries)
 constexpr int kClRow = 32 * 4;                  // bytes of one window row (one key, every case)
@@ -99,7 +100,7 @@ struct CLPort {
   int32_t pad[2];
   int32_t dvec[4];               // key(j) * row, j < 4 (entries of a vector)
   int32_t kvec[8];               // key(4 v) * row, v < 8 (vectors of a tile)
-  int32_t kslot[16 * kClTiles];  // key(w * kClSlice + 32 t) * row, slot w * kClTiles + t
+  int32_t kslot[16 * kClTiles];  // key(32 p) * row for tile position p of a chunk
   int32_t kchunk[kClMaxChunks];  // port window start + key(ci * chunk) * row (bytes from the buffer's windows)
 };
 constexpr int32_t kClInput = 1;

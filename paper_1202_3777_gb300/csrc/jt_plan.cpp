@@ -738,9 +738,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         if (regable && n_reg < kClRegSlots) C.cls |= (++n_reg) << kClRegShift;
         for (int j = 0; j < 4; ++j) C.dvec[j] = (int32_t)(key((uint32_t)j) * kClRow);
         for (int v = 0; v < 8; ++v) C.kvec[v] = (int32_t)(key(4u * (uint32_t)v) * kClRow);
-        for (int w = 0; w < 16; ++w)
-          for (int t = 0; t < kClTiles; ++t)
-            C.kslot[w * kClTiles + t] = (int32_t)(key((uint32_t)(w * kClSlice + 32 * t)) * kClRow);
+        for (int q = 0; q < 16 * kClTiles; ++q) C.kslot[q] = (int32_t)(key((uint32_t)(32 * q)) * kClRow);
         for (int ci = 0; ci < kClMaxChunks; ++ci)
           C.kchunk[ci] = (int32_t)((uint32_t)P.win * kClRow + key((uint32_t)(ci * CH)) * kClRow);
         clp.push_back(C);
