@@ -233,22 +233,21 @@ struct FinalArgs {
   double* marg_out;             // [max_cases][marg_total]
   double* logz_out;             // [max_cases]
   int32_t lanes;                // cases interleaved in a message slab (1: one row per case)
-  // case lanes: the variables, those whose source holds at most
-  // kFinWarpEntries entries per state first (a warp each), then the others
-  // (a CTA each)
+  // case lanes: the variables, those whose source table holds at most
+  // kFinWarpEntries entries first (a warp each), then the others (a CTA each)
   const int32_t* var_order;
   int32_t n_small;
 };
-constexpr int32_t kFinWarpEntries = 64;
+constexpr int32_t kFinWarpEntries = 256;
 
 // The finalisation order of a marginal-source layout (small sources first).
 inline std::vector<int32_t> fin_order(const std::vector<VarSrc>& vs, int32_t* n_small) {
   std::vector<int32_t> order;
   for (int v = 0; v < (int)vs.size(); ++v)
-    if (vs[v].size / vs[v].card <= kFinWarpEntries) order.push_back(v);
+    if (vs[v].size <= kFinWarpEntries) order.push_back(v);
   *n_small = (int32_t)order.size();
   for (int v = 0; v < (int)vs.size(); ++v)
-    if (vs[v].size / vs[v].card > kFinWarpEntries) order.push_back(v);
+    if (vs[v].size > kFinWarpEntries) order.push_back(v);
   return order;
 }
 
