@@ -93,7 +93,8 @@ struct DevPort {
                       // has one entry per block entry (no two entries share a key)
   int32_t dvec[4];    // fast path: key offsets of the entries of a vector
   int32_t iter_dep;   // fast path: bit 0: the key depends on the iteration bits (entry bits above
-                      // the thread's vector index); bit 1: on the chunk bits (above one chunk)
+                      // the thread's vector index); bit 1: on the chunk bits (above one chunk);
+                      // bit 2: on the iteration bits inside one chunk
 };
 
 // One clique in one pass.
@@ -138,7 +139,9 @@ struct DevStage {
 // kt[port][tid] + kiter[port][m] + dvec[j] (kt includes the window start).
 struct LivePort {
   int32_t mode;       // bits 0-1 vmode, bit 2 key depends on the iteration, bits 3-7 lane_free,
-                      // bit 8 key depends on the chunk, bit 9 the window is the block itself
+                      // bit 8 key depends on the chunk, bit 9 the window is the block itself,
+                      // bit 10 key depends on the iteration inside a chunk (without it, a
+                      // thread's vectors of one chunk share their keys)
   int32_t port;
   int32_t win;        // start of the port's window (in every case's window row)
   int32_t pad;
@@ -149,6 +152,7 @@ static_assert(sizeof(LivePort) == 32 && offsetof(LivePort, win) == 8 && offsetof
 constexpr int32_t kModeIter = 4;
 constexpr int32_t kModeChunk = 256;
 constexpr int32_t kModeStore = 512;
+constexpr int32_t kModeInChunk = 1024;
 
 // Byte offsets of the key tables inside a stage blob.
 __host__ __device__ inline int32_t kiter_off(const DevStage& S) { return S.live_off + S.n_live * 32; }

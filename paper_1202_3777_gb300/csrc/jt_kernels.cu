@@ -504,11 +504,14 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
 #pragma unroll
   for (int cl = 0; cl < CB; ++cl) racc[cl] = T(0);
   uint32_t rkt = 0, rlf = 0, rcur = 0;
+  bool rin = true, jiter = true;
   if (ra >= 0) {
     rkt = (uint32_t)ktld(ra);
     rlf = (uint32_t)(lp[ra].mode >> 3) & 31u;
     rcur = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter));
+    rin = (lp[ra].mode & kModeInChunk) != 0;
   }
+  if (ja >= 0) jiter = (lp[ja].mode & kModeIter) != 0;
   T jacc[VPT][VEC];
 #pragma unroll
   for (int it = 0; it < VPT; ++it)
@@ -553,13 +556,21 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       mi[it] = ci * VPT + it;
       o0[it] = cbase + (uint32_t)vi * VEC;
 #pragma unroll
-      for (int cl = 0; cl < CB; ++cl) {
+      for (int cl = 0; cl < CB; ++cl)
 #pragma unroll
         for (int j = 0; j < VEC; ++j) f[it][cl][j] = xs[it][j] * bfv[cl];
-        if (any_obs && bfv[cl] != T(0)) {
-          const int no = sld_s32(nobs32 + 4u * (uint32_t)cl);
-          for (int e = 0; e < no; ++e) {
-            const int4 ob = sld_v4s32(obs32 + 16u * (uint32_t)(cl * a.max_k + e));
+    }
+    // evidence inside the block: each observation read once for all of the
+    // thread's vectors
+    if (any_obs) {
+#pragma unroll
+      for (int cl = 0; cl < CB; ++cl) {
+        if (bfv[cl] == T(0)) continue;
+        const int no = sld_s32(nobs32 + 4u * (uint32_t)cl);
+        for (int e = 0; e < no; ++e) {
+          const int4 ob = sld_v4s32(obs32 + 16u * (uint32_t)(cl * a.max_k + e));
+#pragma unroll
+          for (int it = 0; it < VPT; ++it) {
             const uint32_t d = (o0[it] >> ob.x) & (uint32_t)ob.y;
 #pragma unroll
             for (int j = 0; j < VEC; ++j)
@@ -575,6 +586,33 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       // (a lane past the block's end reads its port window's first entries,
       // which are always filled: its own key may lie outside the window)
       const uint32_t kwin = (uint32_t)sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 8u);
+      if (VPT > 1 && CB == 1 && !(md & kModeInChunk)) {
+        // the thread's vectors of this chunk share the key: one gather for
+        // all (a vector past the block's end multiplies zeros)
+        if (bfv[0] == T(0)) continue;
+        uint32_t k = kti;
+        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + mi[0]));
+        const uint32_t k0 = win32 + (act[0] ? k : kwin) * (uint32_t)sizeof(T);
+        const int vm = md & 3;
+        T g[VEC];
+        if (vm == 1) {
+          sld_vec(k0, g);
+        } else if (vm == 0) {
+          const T g0 = sld<T>(k0);
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) g[j] = g0;
+        } else {
+          const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
+          const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) g[j] = sld<T>(k0 + (uint32_t)dva[j] * (uint32_t)sizeof(T));
+        }
+#pragma unroll
+        for (int it = 0; it < VPT; ++it)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) f[it][0][j] *= g[j];
+        continue;
+      }
       uint32_t ka[VPT];
 #pragma unroll
       for (int it = 0; it < VPT; ++it) {
@@ -633,7 +671,19 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       }
     // the register-accumulated output: flush when its key changes (the
     // iterations in order)
-    if (ra >= 0) {
+    if (VPT > 1 && CB == 1 && ra >= 0 && !rin) {
+      // a key shared by the thread's vectors of the chunk: one check
+      const uint32_t kc = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter + mi[0]));
+      if (kc != rcur) {
+        const uint32_t ra_a = win32 + (rkt + rcur) * (uint32_t)sizeof(T);
+        CaseScatter<T, CB>::run(rlf != 0u ? __shfl_sync(kFull, ra_a, lane & ~(int)rlf) : ra_a, wstride, racc, 0u,
+                                rlf, lane);
+        racc[0] = T(0);
+        rcur = kc;
+      }
+#pragma unroll
+      for (int it = 0; it < VPT; ++it) racc[0] += sum[it][0];
+    } else if (ra >= 0) {
 #pragma unroll
       for (int it = 0; it < VPT; ++it) {
         const uint32_t kc = (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ra * kMaxIter + mi[it]));
@@ -649,7 +699,13 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
         for (int cl = 0; cl < CB; ++cl) racc[cl] += sum[it][cl];
       }
     }
-    if (ja >= 0) {
+    if (VPT > 1 && ja >= 0 && !jiter) {
+      // a key that ignores the iteration: one accumulator for all vectors
+#pragma unroll
+      for (int it = 0; it < VPT; ++it)
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) jacc[0][j] += f[it][0][j];
+    } else if (ja >= 0) {
 #pragma unroll
       for (int it = 0; it < VPT; ++it)
 #pragma unroll
@@ -660,6 +716,33 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
       if (i == ra || i == ja) continue;
       const int32_t md = sld_s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort));
       const uint32_t kti = (uint32_t)ktld(i);
+      const uint32_t lf = (uint32_t)(md >> 3) & 31u;
+      if (VPT > 1 && CB == 1 && !(md & (kModeInChunk | kModeStore))) {
+        // the thread's vectors of this chunk share the key: add them first,
+        // then one reduction over the lanes
+        uint32_t k = kti;
+        if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + mi[0]));
+        const uint32_t k0 = win32 + k * (uint32_t)sizeof(T);
+        if ((md & 3) == 0) {
+          T v = T(0);
+#pragma unroll
+          for (int it = 0; it < VPT; ++it) v += sum[it][0];
+          v = lane_reduce(v, lf);
+          if (act[0] && (lane & lf) == 0u && v != T(0)) sred_add(k0, v);
+        } else if (bfv[0] != T(0)) {
+          const int4 dv = sld_v4s32(lp32 + (uint32_t)i * (uint32_t)sizeof(LivePort) + 16u);
+          T fs[VEC];
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) {
+            fs[j] = f[0][0][j];
+#pragma unroll
+            for (int it = 1; it < VPT; ++it) fs[j] += f[it][0][j];
+          }
+          const uint32_t kg = lf != 0u ? __shfl_sync(kFull, k0, lane & ~(int)lf) : k0;
+          scatter_vec(kg, fs, lf, lane, act[0], dv);
+        }
+        continue;
+      }
       uint32_t ka[VPT];
 #pragma unroll
       for (int it = 0; it < VPT; ++it) {
@@ -667,7 +750,6 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
         if (md & kModeIter) k += (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(i * kMaxIter + mi[it]));
         ka[it] = win32 + k * (uint32_t)sizeof(T);
       }
-      const uint32_t lf = (uint32_t)(md >> 3) & 31u;
       if ((md & 3) == 0) {
         if (CB == 1) {
           T v[VPT];
@@ -732,9 +814,10 @@ __device__ __forceinline__ bool stream_fast(const PropArgs<T>& a, const Smem& s,
     const int4 dv = make_int4(lp[ja].dvec[0], lp[ja].dvec[1], lp[ja].dvec[2], lp[ja].dvec[3]);
     const int dva[4] = {dv.x, dv.y, dv.z, dv.w};
     const bool lead = (lane & lf) == 0u;
+    const int nit = jiter ? VPT : 1;  // (one accumulator when the key ignores the iteration)
 #pragma unroll
     for (int it = 0; it < VPT; ++it) {
-      if (it >= (w.n + NT * VEC - 1) / (NT * VEC)) break;  // iteration never reached
+      if (it >= nit || it >= (w.n + NT * VEC - 1) / (NT * VEC)) break;  // iteration never reached
       const uint32_t k = kt + (uint32_t)sld_s32(ki32 + 4u * (uint32_t)(ja * kMaxIter + it));
 #pragma unroll
       for (int j = 0; j < VEC; ++j) {
@@ -853,7 +936,8 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
         if (tid == li) {
           LivePort L;
           L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
-                   ((P.vmode & kVmodeStore) ? kModeStore : 0) | (int32_t)((P.lane_free & 31u) << 3);
+                   ((P.iter_dep & 4) ? kModeInChunk : 0) | ((P.vmode & kVmodeStore) ? kModeStore : 0) |
+                   (int32_t)((P.lane_free & 31u) << 3);
           L.port = pi;
           L.win = P.win;
           L.pad = 0;
@@ -907,8 +991,14 @@ __device__ __forceinline__ bool process_item(const PropArgs<T>& a, const Smem& s
   // its totals here.
   bool wrote_global = false;
   if (tid < ncb) {
-    double t = 0.0;
-    for (int i = 0; i < NT / 32; ++i) t += s.red[tid * (NT / 32) + i];
+    // four independent chains (FP64 latency is long on this part)
+    static_assert((NT / 32) % 4 == 0, "consumer warps in fours");
+    double t4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < NT / 32; i += 4)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t4[q] += s.red[tid * (NT / 32) + i + q];
+    const double t = (t4[0] + t4[1]) + (t4[2] + t4[3]);
     if constexpr (CB == 1) {
       s.bf[tid] = t;
     } else {

@@ -586,6 +586,7 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
             const int lo = ilog2(stv[c][i]), hi = lo + ilog2(cdv[c][i]);
             if (hi > ib && lo < S.bits) P.iter_dep |= 1;
             if (hi > cbit && lo < S.bits) P.iter_dep |= 2;
+            if (hi > ib && lo < std::min(cbit, S.bits)) P.iter_dep |= 4;
           }
         }
         if (P.kind == kPortMu || P.kind == kPortRho) ++nin;
@@ -660,7 +661,8 @@ jt_status build_schedule(const Plan& p, int elem, int cb, int n_cases, int n_sm,
         if (P.K <= 1) continue;
         LivePort L{};
         L.mode = (P.vmode & 3) | ((P.iter_dep & 1) ? kModeIter : 0) | ((P.iter_dep & 2) ? kModeChunk : 0) |
-                 ((P.vmode & kVmodeStore) ? kModeStore : 0) | (int32_t)((P.lane_free & 31u) << 3);
+                 ((P.iter_dep & 4) ? kModeInChunk : 0) | ((P.vmode & kVmodeStore) ? kModeStore : 0) |
+                 (int32_t)((P.lane_free & 31u) << 3);
         L.port = pi;
         L.win = P.win;
         for (int j = 0; j < 4; ++j) L.dvec[j] = P.dvec[j];
