@@ -469,11 +469,6 @@ __device__ __forceinline__ bool bulk_window(const DevStage& S, const DevPort& P)
   return S.bits >= 0 && ((uint32_t)P.K * (uint32_t)sizeof(T)) % 16u == 0u;
 }
 
-// ---- control warp, lanes 2..31: preparation of the next item ---------------
-// For the item in buffer b: wait for its blob and dependencies, enter the
-// evidence (block-level digits into the block factor, in-block digits into
-
-
 // Consumer thread 0: hand a finished item to the signalling lane (stage < 0
 // ends it).  False if the lane did not free the slot in time.
 __device__ __forceinline__ bool hand_over(const Smem& s, uint32_t& k, int4 g, const int32_t* err) {

@@ -153,6 +153,9 @@ struct CaseScatter<T, 1> {
   }
 };
 
+// ---- control warp 2: preparation of the next item ---------------------------
+// For the item in buffer b: wait for its blob and dependencies, enter the
+// evidence (block-level digits into the block factor, in-block digits into
 // per-case lists), fold block-constant inputs and child-message scales into
 // the block factor, and fill the windows (child messages by bulk copy, own
 // separator ratios computed, outputs zeroed).  The item is ready for the
@@ -383,7 +386,7 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
   }
 }
 
-// ---- control warp, lane 1: the signalling lane ----------------------------
+// ---- control warp 1, lane 0: the signalling lane ---------------------------
 // For each finished item: add the output windows into the message arrays
 // with bulk reductions (the consumers already added the rest), wait until
 // they completed, make them visible GPU-wide, count the block as done, and
