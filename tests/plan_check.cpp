@@ -16,6 +16,9 @@
 //
 // Input (whitespace-separated integers): n_vars, card[n_vars], n_cliques,
 // then per clique k followed by its k variables, then parent[n_cliques].
+// With "plant-inchunk" every one-case port is claimed to keep its key over a
+// chunk's iterations (the check must then fail on trees whose blocks span
+// several iterations).
 // With argument "plant-order" the queue is reversed, with "plant-repeat" one
 // item is queued twice, before the checks (each must then fail).
 // Output: one line per (case-block width, case count):
@@ -96,6 +99,33 @@ std::string check(const Plan& p, const Schedule& s) {
         return "item " + std::to_string(i) + " waits for blocks queued after it";
     }
     ++done[(size_t)it.stage * s.n_cb + it.cbk];
+  }
+  // one case: a port not marked as depending on the iteration bits inside a
+  // chunk has one key for all of a thread's vectors of the chunk (the kernel
+  // gathers and reduces them once), and one not marked as depending on the
+  // iteration has one key for the whole block (FP32 plans: four entries per
+  // vector)
+  if (s.cb == 1) {
+    const int ipc = std::max<int>(1, (int)(s.chunk / (consumers_for(1) * 4)));
+    std::vector<char> seen_st(s.stages.size(), 0);
+    for (const DevItem& it : s.items) {
+      if (seen_st[it.stage]) continue;
+      seen_st[it.stage] = 1;
+      const DevStage& S = s.stages[it.stage];
+      if (S.bits < 0 || S.n_live == 0) continue;
+      const unsigned char* blob = reinterpret_cast<const unsigned char*>(s.blobs.data()) + (size_t)it.blob * 16;
+      const LivePort* lp = reinterpret_cast<const LivePort*>(blob + S.live_off);
+      const int32_t* ki = reinterpret_cast<const int32_t*>(blob + kiter_off(S));
+      for (int li = 0; li < S.n_live; ++li) {
+        const int32_t* k = ki + (size_t)li * kMaxIter;
+        for (int m = 0; m < S.n_iter; ++m) {
+          if (!(lp[li].mode & kModeInChunk) && k[m] != k[m / ipc * ipc])
+            return "stage of clique " + std::to_string(S.clique) + " shares a key that varies inside a chunk";
+          if (!(lp[li].mode & kModeIter) && k[m] != k[0])
+            return "stage of clique " + std::to_string(S.clique) + " has an iteration-free key that varies";
+        }
+      }
+    }
   }
   // case lanes: an output marked for register accumulation must have the
   // same four rows in every tile of its block (a key over entry bits 0-1
@@ -179,6 +209,14 @@ int main(int argc, char** argv) {
     }
     if (plant == "plant-order") std::reverse(s.items.begin(), s.items.end());
     if (plant == "plant-repeat" && s.items.size() > 1) s.items.back() = s.items.front();
+    if (plant == "plant-inchunk" && s.cb == 1)  // every port claimed to share its key inside a chunk
+      for (const DevItem& it : s.items) {
+        const DevStage& S = s.stages[it.stage];
+        if (S.bits < 0) continue;
+        LivePort* lp = reinterpret_cast<LivePort*>(reinterpret_cast<unsigned char*>(s.blobs.data()) +
+                                                   (size_t)it.blob * 16 + S.live_off);
+        for (int li = 0; li < S.n_live; ++li) lp[li].mode &= ~kModeInChunk;
+      }
     const std::string why = check(p, s);
     if (why.empty()) {
       std::printf("cb=%d cases=%d OK items=%zu stages=%zu\n", sh[0], sh[1], s.items.size(), s.stages.size());

@@ -120,6 +120,17 @@ def test_planted_padding_mistake_is_caught(checker):
     assert rc == 1 and any(ln.startswith("padmap FAIL") for ln in lines), lines
 
 
+def test_planted_chunk_key_mistake_is_caught(checker):
+    """Every one-case port of the large-clique tree claimed to keep its key
+    over the iterations of a chunk: the consumers would then gather and
+    reduce a thread's four vectors under one key, and the check must see a
+    port whose key changes inside a chunk."""
+    t = synth.large_clique_tree()
+    rc, lines = _run(checker, t.card, t.cliques, t.parent, "plant-inchunk")
+    one = [ln for ln in lines if ln.startswith("cb=1 ")]
+    assert rc == 1 and one and all("varies inside a chunk" in ln for ln in one), lines
+
+
 @pytest.mark.parametrize("min_sep,cap", [(8, 1 << 8), (16, 1 << 10), (1 << 20, 1 << 12)])
 def test_schedules_of_merged_trees(checker, min_sep, cap):
     t = synth.binary_serving_tree()
