@@ -213,22 +213,32 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
     uint32_t V = 0, M = 0;
     if (valid) {
       const int16_t* evr = a.ev + (int64_t)cs * a.n_vars;
-      for (int i = 0; i < S.k; ++i) {
-        const DevPos& P = s.pos[i];
-        const int st = evr[P.var];
-        if (st < 0) continue;
-        if (st >= P.card_ev) {
-          atomicOr(&a.status[cs], kStatusBadState);
-          continue;
-        }
-        const int inside = max(0, min(P.cb, S.bits - P.sh));
-        const uint32_t lo_m = (1u << inside) - 1u;
-        const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
-        if (hi_d != ((uint32_t)st & ~lo_m)) {
-          bf = 0.0;
-        } else if (lo_m != 0u && !((S.covered >> i) & 1u)) {
-          M |= lo_m << P.sh;
-          V |= ((uint32_t)st & lo_m) << P.sh;
+      // the case's states of kEB positions are loaded before any is used
+      // (independent loads in flight together)
+      constexpr int kEB = 8;
+      for (int i0 = 0; i0 < S.k; i0 += kEB) {
+        int sts[kEB];
+#pragma unroll
+        for (int j = 0; j < kEB; ++j) sts[j] = i0 + j < S.k ? (int)evr[s.pos[i0 + j].var] : -1;
+#pragma unroll
+        for (int j = 0; j < kEB; ++j) {
+          const int i = i0 + j;
+          const int st = sts[j];
+          if (i >= S.k || st < 0) continue;
+          const DevPos& P = s.pos[i];
+          if (st >= P.card_ev) {
+            atomicOr(&a.status[cs], kStatusBadState);
+            continue;
+          }
+          const int inside = max(0, min(P.cb, S.bits - P.sh));
+          const uint32_t lo_m = (1u << inside) - 1u;
+          const uint32_t hi_d = (eb >> P.sh) & ((1u << P.cb) - 1u);
+          if (hi_d != ((uint32_t)st & ~lo_m)) {
+            bf = 0.0;
+          } else if (lo_m != 0u && !((S.covered >> i) & 1u)) {
+            M |= lo_m << P.sh;
+            V |= ((uint32_t)st & lo_m) << P.sh;
+          }
         }
       }
     }
@@ -267,28 +277,57 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
                    (uint32_t)P.K * kClRow, s.pfull + b);
         }
       }
-      // per-case factor: the child messages' scales and block-constant inputs
+      // per-case factor: the child messages' scales and block-constant inputs.
+      // The loads of kPB ports are issued together (one round trip to L2 per
+      // group instead of one per port; nothing uses a loaded value before
+      // the group's last load is issued), and the factors are formed in
+      // FP32: the consumers apply the block factor in FP32, and FP64
+      // divisions are slow on this part.
       if (valid) {
+        constexpr int kPB = 8;
         const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
-        for (int pi = 0; pi < S.nin; ++pi) {
-          const DevPort& P = s.port[pi];
-          double v = 1.0;
-          if (P.kind == kPortMu) {
-            const double sg = __ldcg(sums + P.other);
-            v = sg > 0.0 ? (double)P.size / sg : 0.0;
-            if (P.K <= 1) {
+        float bff = 1.f;
+        for (int p0 = 0; p0 < S.nin; p0 += kPB) {
+          double t0[kPB], t1[kPB];  // stage totals
+          float e0[kPB], e1[kPB];   // slab entries
+#pragma unroll
+          for (int j = 0; j < kPB; ++j) {
+            t0[j] = t1[j] = 0.0;
+            e0[j] = e1[j] = 0.f;
+            const int pi = p0 + j;
+            if (pi >= S.nin) continue;
+            const DevPort& P = s.port[pi];
+            if (P.kind == kPortMu) {
+              t0[j] = __ldcg(sums + P.other);
+              if (P.K <= 1) {
+                const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
+                e0[j] = __ldcg(slab + (int64_t)(P.tab + key) * kCaseLanes + l);
+              }
+            } else if (P.K <= 1) {
               const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
-              v *= (double)__ldcg(slab + (int64_t)(P.tab + key) * kCaseLanes + l);
+              t0[j] = __ldcg(sums + P.other);
+              t1[j] = __ldcg(sums + a.n_cliques + P.other2);
+              e0[j] = __ldcg(slab + (int64_t)(P.tab + key) * kCaseLanes + l);
+              e1[j] = __ldcg(slab + (int64_t)(a.delta_off + P.tab + key) * kCaseLanes + l);
             }
-          } else if (P.K <= 1) {
-            const uint32_t key = key_of<true>(eb, s.fld + P.f0, P.nf);
-            const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
-            const double u = (double)__ldcg(slab + (int64_t)(P.tab + key) * kCaseLanes + l);
-            const double d = (double)__ldcg(slab + (int64_t)(a.delta_off + P.tab + key) * kCaseLanes + l);
-            v = (dp > 0.0 && u > 0.0) ? d * (sgc / dp) / u : 0.0;
           }
-          bf *= v;
+#pragma unroll
+          for (int j = 0; j < kPB; ++j) {
+            const int pi = p0 + j;
+            if (pi >= S.nin) continue;
+            const DevPort& P = s.port[pi];
+            const float s0 = (float)t0[j], s1 = (float)t1[j];
+            float v = 1.f;
+            if (P.kind == kPortMu) {
+              v = s0 > 0.f ? (float)P.size / s0 : 0.f;
+              if (P.K <= 1) v *= e0[j];
+            } else if (P.K <= 1) {
+              v = (s1 > 0.f && e0[j] > 0.f) ? e1[j] * (s0 / s1) / e0[j] : 0.f;
+            }
+            bff *= v;
+          }
         }
+        bf *= (double)bff;
       }
       // ratio windows of the own separator, row by row (lane = case)
       for (int pi = 0; pi < S.nin; ++pi) {
@@ -298,8 +337,8 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
         float sc = 0.f;
         if (valid) {
           const double* sums = a.sums + (int64_t)cs * 2 * a.n_cliques;
-          const double sgc = __ldcg(sums + P.other), dp = __ldcg(sums + a.n_cliques + P.other2);
-          sc = dp > 0.0 ? (float)(sgc / dp) : 0.f;
+          const float sgc = (float)__ldcg(sums + P.other), dp = (float)__ldcg(sums + a.n_cliques + P.other2);
+          sc = dp > 0.f ? sgc / dp : 0.f;
         }
         const float* ur = slab + (int64_t)(P.tab + kb) * kCaseLanes + l;
         const float* dr = slab + (int64_t)(a.delta_off + P.tab + kb) * kCaseLanes + l;
