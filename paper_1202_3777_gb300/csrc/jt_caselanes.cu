@@ -267,11 +267,17 @@ __device__ __forceinline__ void prep_cl(const PropArgs<float>& a, const Smem& s0
       __syncwarp();
       if (bulk > 0) {
         fence_proxy_async_all();  // the messages were written by other CTAs (bulk reductions)
-        int n = 0;
+        // lane l copies the l-th such window: the lanes find theirs first,
+        // then compute the window keys and issue the copies together (a
+        // case-lane stage has at most as many ports as a warp has lanes)
+        int mine = -1, n = 0;
         for (int pi = 0; pi < S.nin; ++pi) {
           const DevPort& P = s.port[pi];
           if (P.K <= 1 || P.kind != kPortMu) continue;
-          if (n++ % 32 != l) continue;
+          if (n++ == l) mine = pi;
+        }
+        if (mine >= 0) {
+          const DevPort& P = s.port[mine];
           const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
           bulk_g2s(s.win + (size_t)P.win * kClRow, slab + (int64_t)(P.tab + kb) * kCaseLanes,
                    (uint32_t)P.K * kClRow, s.pfull + b);

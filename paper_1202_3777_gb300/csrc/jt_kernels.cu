@@ -268,17 +268,41 @@ __device__ __forceinline__ void prep_lanes(const PropArgs<T>& a, const Smem& s0)
       __syncwarp(kMask);
       if (bulk_bytes > 0) {
         fence_proxy_async_all();  // the messages were written by other CTAs (generic and bulk-reduce writes)
+        // copy n (port, case) goes to lane n % NL: the lanes find their ports
+        // first, then compute the window keys and issue the copies together
+        // (up to kBT rounds; any further copies one lane at a time)
+        constexpr int kBT = 4;
+        int mp[kBT], mc[kBT];
+#pragma unroll
+        for (int r = 0; r < kBT; ++r) mp[r] = -1, mc[r] = 0;
         int n = 0;
         for (int pi = 0; pi < S.nin; ++pi) {
           const DevPort& P = s.port[pi];
           if (P.K <= 1 || P.kind != kPortMu || !bulk_window<T>(S, P)) continue;
-          const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
           for (int cl = 0; cl < ncb; ++cl, ++n) {
             if (n % NL != pl) continue;
+            const int r = n / NL;
+            if (r < kBT) {
+#pragma unroll
+              for (int q = 0; q < kBT; ++q)
+                if (q == r) mp[q] = pi, mc[q] = cl;
+              continue;
+            }
+            const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
             const T* src = a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb;
             bulk_g2s(s.win + (size_t)(cl * a.win_max + P.win) * sizeof(T), src, (uint32_t)P.K * (uint32_t)sizeof(T),
                      s.pfull + b);
           }
+        }
+#pragma unroll
+        for (int r = 0; r < kBT; ++r) {
+          if (mp[r] < 0) continue;
+          const DevPort& P = s.port[mp[r]];
+          const int cl = mc[r];
+          const uint32_t kb = key_of<true>(eb, s.fld + P.f0, P.nf);
+          const T* src = a.msg + (int64_t)(cb0 + cl) * a.msg_stride + P.tab + kb;
+          bulk_g2s(s.win + (size_t)(cl * a.win_max + P.win) * sizeof(T), src, (uint32_t)P.K * (uint32_t)sizeof(T),
+                   s.pfull + b);
         }
       }
     }
