@@ -123,10 +123,10 @@ class Clocks:
 # cases; a slab of 32 cases on the lanes.  Every case block or slab streams
 # the tables again, so a launch's traffic grows with their number.
 TRAFFIC = {
-    "sources_sha256": "ce3b608a810b7d1715d8a00ec1f0267abff16c1d477fb5b6922a4b1d3b750f16",
-    "plain": 471.7e6,
-    "per_case_block": {4: 496.4e6, 8: 524.3e6},
-    "per_slab": 565.1e6,
+    "sources_sha256": "af87dea2809168b62fe89e9711b586c8290ed1b775998ccf465cf617f7312821",
+    "plain": 471.5e6,
+    "per_case_block": {4: 496.4e6, 8: 524.4e6},
+    "per_slab": 565.2e6,
 }
 TRAFFIC_SOURCES = ["paper_1202_3777_gb300/csrc/jt_kernels.cu", "paper_1202_3777_gb300/csrc/jt_caselanes.cu",
                    "paper_1202_3777_gb300/csrc/jt_device.cuh", "paper_1202_3777_gb300/csrc/jt_kernels.h",
